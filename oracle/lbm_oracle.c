@@ -1,0 +1,723 @@
+/*
+ * Plain FP64 CPU oracle of the consistent double-distribution lattice Boltzmann
+ * model with body force and heat source (arxiv 2609.28679).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * reference that the CUDA path is checked against.  Only the test suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it; the
+ * product library never links, loads or calls it, and it shares no code,
+ * header, table or constant with the CUDA sources.
+ *
+ * One time step follows the paper's flowchart (Sec. II.E, Fig. "Structure of
+ * the algorithm") in order, with every intermediate field held in a full-size
+ * array so that each phase can be read against its equation:
+ *
+ *   A  rho = sum_i f_i,  J = sum_i c_i f_i,  G = sum_i g_i        (Eq. def_h)
+ *   B  F = rho*a + F_K,  F_K = kappa rho grad(lap rho);  Q(x)    (Eqs. force_decomposition, korteweg_force)
+ *   C  u = (J + F/2)/rho;  rho E = G + (u.F + Q)/2;  T(rho,e);  P   (Eqs. def_u, def_E, TdependsongenericEOS)
+ *      theta = P/rho (Eq. theta), c_s^2, gamma, alpha (Eqs. corr_bulk, corr_heat_source)
+ *   D  u*, theta*, Phi, T*, q^c                                   (Eqs. sh_vel_1, sh_temp_1, correction, sh_T_1, qc_1)
+ *   E  f^eq, f*, g^eq, g*  (Eqs. LBMeq, LBMstar, LBMeqG, LBMgstar); beta (Eq. beta);
+ *      collide and stream (Eqs. LBM_f, LBM_g) with lambda = dt = 1.
+ *
+ * Lattice units: dt = dx = c = 1, varsigma^2 = 1/3 (Eq. cs).  D = 3 uses the
+ * paper's D3Q27 set (Eq. D3Q27c); D = 2 uses its tensor-product restriction
+ * D2Q9 (the paper names no 2-D set).
+ *
+ * Readings of points the paper leaves open (each also listed in the design doc):
+ *  - beta = 1/(2 tau + 1) with a constant tau per distribution (Eq. beta); the
+ *    shear viscosity mu = tau P then follows the local pressure.  eta and k
+ *    enter only through the ratios eta/mu and k/mu.
+ *  - alpha*theta is evaluated as ((D+2)/D - eta/mu) theta - c_s^2, which equals
+ *    alpha*theta of Eq. corr_bulk with theta = P/rho but has no removable
+ *    singularity where P = 0 (spinodal region of van der Waals / Peng-Robinson).
+ *  - The upwind-biased first derivative in Eq. correction is the second-order
+ *    one-sided difference chosen by the sign of the local u_alpha (u >= 0:
+ *    backward).  With phi_central = 1 the 2-point central difference is used
+ *    instead: the one-sided switch injects grid-scale noise where u changes
+ *    sign, which makes fluids with theta < 1/3 near rest (the liquid-vapour
+ *    cases) diverge.  Laplacian and gradients are the standard (2D+1)-point
+ *    and 2-point central differences (Sec. II.E).
+ *  - Half-way bounce-back walls at the z faces (Sec. III.A, Poiseuille) act on
+ *    both f and g.  For the macroscopic stencils, cells beyond a wall mirror
+ *    the interior: scalars (rho, lap rho, T, h) even, velocity odd, so X_z is
+ *    odd.
+ *  - Peng-Robinson: the paper names the model only.  The textbook form with the
+ *    Soave alpha(T) and a constant ideal-part c_v is used; e(rho,T) follows by
+ *    integrating Eq. de_rho at constant T from rho = 0.  T(rho,e) is found by
+ *    Newton's method in T from the previous step's T, stopping at
+ *    |dT| <= 1e-14 T, at most 50 iterations (hits of the cap are counted).
+ *  - c_v in Eq. sh_T_1 is the local (de/dT)_rho.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_IDEAL 0
+#define ORC_VDW 1
+#define ORC_PR 2
+
+typedef struct {
+    int dim;            /* 2 or 3 */
+    int nx, ny, nz;     /* nz = 1 when dim = 2 */
+    int zwalls;         /* 0: periodic in z; 1: half-way bounce-back walls at both z faces */
+    int eos;            /* ORC_IDEAL, ORC_VDW, ORC_PR */
+    double R, cv;       /* gas constant; constant (ideal-part) specific heat */
+    double a, b;        /* vdW / PR attraction and co-volume */
+    double Tc, omega;   /* PR critical temperature and acentric factor */
+    double kappa;       /* Korteweg capillarity coefficient */
+    double eta_over_mu; /* bulk / shear viscosity ratio */
+    double k_over_mu;   /* conductivity / shear viscosity ratio */
+    double tau_f, tau_g;
+    double accel[3];    /* body acceleration: F_B = rho * accel */
+    double q;           /* volumetric heat source Q */
+    int zlo, zhi;       /* Q acts where zlo <= z < zhi; zhi <= 0 means everywhere */
+    int phi_central;    /* 0: upwind-biased derivative in Phi; 1: central difference */
+} orc_params;
+
+typedef struct {
+    orc_params p;
+    int Q;
+    long N;
+    int c[27][3];
+    int opp[27];
+    double *f, *g, *fn, *gn;         /* populations [Q][N] and the streaming targets */
+    double *rho, *J, *G;             /* phase A */
+    double *lap, *F, *Qs;            /* phase B */
+    double *u, *T, *P, *theta, *h, *cvl, *gam, *athe, *E, *e; /* phase C */
+    double *X;                       /* phase D helper: X_alpha = rho u_alpha^3 + 3 rho u_alpha (theta - 1/3) */
+    long newton_cap_hits;
+    long theta_nonpos;
+} orc_state;
+
+/* ------------------------------------------------------------------------- */
+/* Lattice (Eq. D3Q27c; D2Q9 is its restriction to two axes).                */
+/* Direction i has base-3 digits (d_x, d_y, d_z); digit 0,1,2 -> c = 0,+1,-1. */
+/* ------------------------------------------------------------------------- */
+static int digit_to_c(int d) { return d == 0 ? 0 : (d == 1 ? 1 : -1); }
+
+int orc_lattice(int dim, int *c_out /* [27*3] */, int *opp_out /* [27] */)
+{
+    int Q = (dim == 2) ? 9 : 27;
+    for (int i = 0; i < Q; ++i) {
+        int d0 = i % 3, d1 = (i / 3) % 3, d2 = (i / 9) % 3;
+        c_out[3 * i + 0] = digit_to_c(d0);
+        c_out[3 * i + 1] = digit_to_c(d1);
+        c_out[3 * i + 2] = dim == 3 ? digit_to_c(d2) : 0;
+    }
+    for (int i = 0; i < Q; ++i)
+        for (int j = 0; j < Q; ++j)
+            if (c_out[3 * j] == -c_out[3 * i] && c_out[3 * j + 1] == -c_out[3 * i + 1] &&
+                c_out[3 * j + 2] == -c_out[3 * i + 2])
+                opp_out[i] = j;
+    return Q;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Product-form factor, Eq. phi:                                              */
+/*   Psi(c; xi, zeta) = 1 - c^2 + ( (3c^2 - 2) zeta + c xi ) / 2             */
+/* ------------------------------------------------------------------------- */
+double orc_psi(int c, double xi, double zeta)
+{
+    double c2 = (double)(c * c);
+    return 1.0 - c2 + 0.5 * ((3.0 * c2 - 2.0) * zeta + (double)c * xi);
+}
+
+/* f_i = rho prod_alpha Psi(c_i alpha; xi_alpha, zeta_alpha).
+ * Eq. LBMeq with xi = u, zeta = theta + u^2; Eq. LBMstar with xi = u*,
+ * zeta = theta* + u*^2 + Phi.  The caller supplies xi and zeta per axis. */
+void orc_fprod(int dim, double rho, const double *xi, const double *zeta, double *out)
+{
+    int c[81], opp[27];
+    int Q = orc_lattice(dim, c, opp);
+    for (int i = 0; i < Q; ++i) {
+        double v = rho;
+        for (int a = 0; a < dim; ++a) v *= orc_psi(c[3 * i + a], xi[a], zeta[a]);
+        out[i] = v;
+    }
+}
+
+/* g^eq_i (Eq. LBMeqG): the product of Psi(c_alpha; O_alpha, O_alpha^2) applied to
+ * the generating function E = e + |u|^2/2 (Eq. Egen), with
+ * O_alpha = theta d/du_alpha + u_alpha (Eq. Oa).  The operators of different
+ * axes commute and e does not depend on u, so the product splits:
+ *   O 1 = u,  O^2 1 = theta + u^2                      -> Psi(c; u, theta + u^2) =: P0
+ *   O (u^2/2) = theta u + u^3/2,
+ *   O^2 (u^2/2) = theta^2 + (5/2) theta u^2 + u^4/2    -> H := Psi applied to u^2/2
+ *   g_i = rho [ e prod_a P0_a + sum_b H_b prod_{a != b} P0_a ].
+ * The test suite checks this expansion against direct symbolic application of
+ * the operators. */
+void orc_geq(int dim, double rho, const double *u, double e, double theta, double *out)
+{
+    int c[81], opp[27];
+    int Q = orc_lattice(dim, c, opp);
+    for (int i = 0; i < Q; ++i) {
+        double P0[3], H[3];
+        for (int a = 0; a < dim; ++a) {
+            int ca = c[3 * i + a];
+            double ua = u[a];
+            P0[a] = orc_psi(ca, ua, theta + ua * ua);
+            double o1 = theta * ua + 0.5 * ua * ua * ua;
+            double o2 = theta * theta + 2.5 * theta * ua * ua + 0.5 * ua * ua * ua * ua;
+            double c2 = (double)(ca * ca);
+            H[a] = (1.0 - c2) * 0.5 * ua * ua + 0.5 * ((3.0 * c2 - 2.0) * o2 + (double)ca * o1);
+        }
+        double prod = 1.0;
+        for (int a = 0; a < dim; ++a) prod *= P0[a];
+        double sum = e * prod;
+        for (int b = 0; b < dim; ++b) {
+            double t = H[b];
+            for (int a = 0; a < dim; ++a)
+                if (a != b) t *= P0[a];
+            sum += t;
+        }
+        out[i] = rho * sum;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Equations of state                                                         */
+/*   ideal (Eq. idealEOS):  P = rho R T,                      e = cv T       */
+/*   vdW   (Eq. vdw_eos):   P = rho R T/(1 - b rho) - a rho^2, e = cv T - a rho */
+/*   PR    (textbook, Soave alpha):                                          */
+/*     P = rho R T/(1 - b rho) - a al(T) rho^2 / (1 + 2 b rho - b^2 rho^2),   */
+/*     al(T) = (1 + k (1 - s))^2,  s = sqrt(T/Tc),                           */
+/*     k = 0.37464 + 1.54226 omega - 0.26992 omega^2,                        */
+/*     e = cv T - a (1 + k)(1 + k - k s) Lam(rho), where Lam(rho) is the      */
+/*     integral of 1/(1 + 2 b r - b^2 r^2) from 0 to rho, which makes         */
+/*     de = cv dT - [T dP/dT - P] drho/rho^2 (Eq. de_rho) hold exactly.       */
+/* ------------------------------------------------------------------------- */
+static double pr_k(const orc_params *p)
+{
+    return 0.37464 + 1.54226 * p->omega - 0.26992 * p->omega * p->omega;
+}
+
+static double pr_lambda(const orc_params *p, double rho)
+{
+    double s2 = sqrt(2.0);
+    double br = p->b * rho;
+    return log((1.0 + (1.0 + s2) * br) / (1.0 + (1.0 - s2) * br)) / (2.0 * s2 * p->b);
+}
+
+double orc_eos_P(const orc_params *p, double rho, double T)
+{
+    switch (p->eos) {
+    case ORC_IDEAL:
+        return rho * p->R * T;
+    case ORC_VDW:
+        return rho * p->R * T / (1.0 - p->b * rho) - p->a * rho * rho;
+    default: {
+        double k = pr_k(p);
+        double s = sqrt(T / p->Tc);
+        double al = (1.0 + k * (1.0 - s)) * (1.0 + k * (1.0 - s));
+        double br = p->b * rho;
+        return rho * p->R * T / (1.0 - br) - p->a * al * rho * rho / (1.0 + 2.0 * br - br * br);
+    }
+    }
+}
+
+double orc_eos_e(const orc_params *p, double rho, double T)
+{
+    switch (p->eos) {
+    case ORC_IDEAL:
+        return p->cv * T;
+    case ORC_VDW:
+        return p->cv * T - p->a * rho;
+    default: {
+        double k = pr_k(p);
+        double s = sqrt(T / p->Tc);
+        return p->cv * T - p->a * (1.0 + k) * (1.0 + k - k * s) * pr_lambda(p, rho);
+    }
+    }
+}
+
+/* (dP/dT) at constant rho */
+double orc_eos_dPdT(const orc_params *p, double rho, double T)
+{
+    switch (p->eos) {
+    case ORC_IDEAL:
+        return rho * p->R;
+    case ORC_VDW:
+        return rho * p->R / (1.0 - p->b * rho);
+    default: {
+        double k = pr_k(p);
+        double s = sqrt(T / p->Tc);
+        /* d al/dT = 2 (1 + k(1-s)) (-k) / (2 s Tc) */
+        double dal = -(1.0 + k * (1.0 - s)) * k / (s * p->Tc);
+        double br = p->b * rho;
+        return rho * p->R / (1.0 - br) - p->a * dal * rho * rho / (1.0 + 2.0 * br - br * br);
+    }
+    }
+}
+
+/* (dP/drho) at constant T */
+double orc_eos_dPdrho(const orc_params *p, double rho, double T)
+{
+    switch (p->eos) {
+    case ORC_IDEAL:
+        return p->R * T;
+    case ORC_VDW: {
+        double d = 1.0 - p->b * rho;
+        return p->R * T / (d * d) - 2.0 * p->a * rho;
+    }
+    default: {
+        double k = pr_k(p);
+        double s = sqrt(T / p->Tc);
+        double al = (1.0 + k * (1.0 - s)) * (1.0 + k * (1.0 - s));
+        double b = p->b;
+        double d1 = 1.0 - b * rho;
+        double den = 1.0 + 2.0 * b * rho - b * b * rho * rho;
+        /* d/drho [rho^2/den] = (2 rho den - rho^2 (2b - 2 b^2 rho)) / den^2 */
+        double dq = (2.0 * rho * den - rho * rho * (2.0 * b - 2.0 * b * b * rho)) / (den * den);
+        return p->R * T / (d1 * d1) - p->a * al * dq;
+    }
+    }
+}
+
+/* c_v = (de/dT) at constant rho */
+double orc_eos_cv(const orc_params *p, double rho, double T)
+{
+    if (p->eos != ORC_PR) return p->cv;
+    double k = pr_k(p);
+    double s = sqrt(T / p->Tc);
+    /* d/dT [ -a (1+k)(1+k-k s) Lam ] = a (1+k) k Lam ds/dT,  ds/dT = 1/(2 s Tc) */
+    return p->cv + p->a * (1.0 + k) * k * pr_lambda(p, rho) / (2.0 * s * p->Tc);
+}
+
+/* T from (rho, e).  Ideal and vdW: the explicit inversions of Eqs. idealgasT
+ * and lbm_temp.  PR: Newton's method on e(rho,T) - e = 0 in T, started from
+ * T_guess.  *iters receives the iteration count (cap 50). */
+double orc_eos_T(const orc_params *p, double rho, double e, double T_guess, int *iters)
+{
+    if (iters) *iters = 0;
+    switch (p->eos) {
+    case ORC_IDEAL:
+        return e / p->cv;
+    case ORC_VDW:
+        return (e + p->a * rho) / p->cv;
+    default: {
+        double T = T_guess > 0.0 ? T_guess : e / p->cv;
+        int it;
+        for (it = 1; it <= 50; ++it) {
+            double r = orc_eos_e(p, rho, T) - e;
+            double dT = -r / orc_eos_cv(p, rho, T);
+            T += dT;
+            if (fabs(dT) <= 1e-14 * fabs(T)) break;
+        }
+        if (iters) *iters = it;
+        return T;
+    }
+    }
+}
+
+/* vdW constants from critical data (Sec. III.B): a = 27 R^2 Tc^2/(64 Pc), b = R Tc/(8 Pc) */
+void orc_vdw_from_critical(double R, double Tc, double Pc, double *a, double *b)
+{
+    *a = 27.0 * R * R * Tc * Tc / (64.0 * Pc);
+    *b = R * Tc / (8.0 * Pc);
+}
+
+/* PR constants from critical data (textbook): a = 0.45724 R^2 Tc^2/Pc, b = 0.07780 R Tc/Pc */
+void orc_pr_from_critical(double R, double Tc, double Pc, double *a, double *b)
+{
+    *a = 0.45724 * R * R * Tc * Tc / Pc;
+    *b = 0.07780 * R * Tc / Pc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* State                                                                      */
+/* ------------------------------------------------------------------------- */
+static double *zalloc(long n) { return (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double)); }
+
+orc_state *orc_create(const orc_params *p)
+{
+    if (!p || (p->dim != 2 && p->dim != 3) || p->nx < 1 || p->ny < 1 || p->nz < 1) return NULL;
+    if (p->dim == 2 && (p->nz != 1 || p->zwalls)) return NULL;
+    orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
+    s->p = *p;
+    int cflat[81];
+    s->Q = orc_lattice(p->dim, cflat, s->opp);
+    for (int i = 0; i < s->Q; ++i)
+        for (int a = 0; a < 3; ++a) s->c[i][a] = cflat[3 * i + a];
+    s->N = (long)p->nx * p->ny * p->nz;
+    long N = s->N, Q = s->Q;
+    s->f = zalloc(Q * N); s->g = zalloc(Q * N);
+    s->fn = zalloc(Q * N); s->gn = zalloc(Q * N);
+    s->rho = zalloc(N); s->J = zalloc(3 * N); s->G = zalloc(N);
+    s->lap = zalloc(N); s->F = zalloc(3 * N); s->Qs = zalloc(N);
+    s->u = zalloc(3 * N); s->T = zalloc(N); s->P = zalloc(N); s->theta = zalloc(N);
+    s->h = zalloc(N); s->cvl = zalloc(N); s->gam = zalloc(N); s->athe = zalloc(N);
+    s->E = zalloc(N); s->e = zalloc(N); s->X = zalloc(3 * N);
+    return s;
+}
+
+void orc_destroy(orc_state *s)
+{
+    if (!s) return;
+    double *arr[] = {s->f, s->g, s->fn, s->gn, s->rho, s->J, s->G, s->lap, s->F, s->Qs, s->u, s->T,
+                     s->P, s->theta, s->h, s->cvl, s->gam, s->athe, s->E, s->e, s->X};
+    for (size_t k = 0; k < sizeof(arr) / sizeof(arr[0]); ++k) free(arr[k]);
+    free(s);
+}
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static inline long cidx(const orc_state *s, int x, int y, int z)
+{
+    return (long)x + (long)s->p.nx * ((long)y + (long)s->p.ny * (long)z);
+}
+
+static inline int wrap(int v, int n) { v %= n; return v < 0 ? v + n : v; }
+
+/* Index of the cell whose value stands at (x,y,z) for a macroscopic stencil:
+ * periodic in x, y (and z without walls); mirrored about a wall at z = -1/2
+ * or z = nz - 1/2.  *sign is -1 where the mirror flips a velocity. */
+static long stencil_idx(const orc_state *s, int x, int y, int z, int *mirrored)
+{
+    x = wrap(x, s->p.nx);
+    y = wrap(y, s->p.ny);
+    *mirrored = 0;
+    if (s->p.zwalls) {
+        int nz = s->p.nz;
+        while (z < 0 || z >= nz) {
+            if (z < 0) z = -1 - z;
+            else z = 2 * nz - 1 - z;
+            *mirrored ^= 1;
+        }
+    } else {
+        z = wrap(z, s->p.nz);
+    }
+    return cidx(s, x, y, z);
+}
+
+/* scalar field value at the neighbour (x+dx, y+dy, z+dz) (even mirror) */
+static inline double nb_scalar(const orc_state *s, const double *fld, int x, int y, int z, int dx, int dy, int dz)
+{
+    int m;
+    return fld[stencil_idx(s, x + dx, y + dy, z + dz, &m)];
+}
+
+/* component a of a vector field [3][N] at the neighbour; odd mirror */
+static inline double nb_vector(const orc_state *s, const double *fld, int a, int x, int y, int z, int dx, int dy, int dz)
+{
+    int m;
+    long k = stencil_idx(s, x + dx, y + dy, z + dz, &m);
+    double v = fld[(long)a * s->N + k];
+    return m ? -v : v;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Initial state: f = f^eq(rho0, u0, theta0), g = g^eq (flowchart, first box) */
+/* ------------------------------------------------------------------------- */
+int orc_init(orc_state *s, const double *rho, const double *u /* [dim][N] */, const double *T)
+{
+    int D = s->p.dim, Q = s->Q;
+    long N = s->N;
+    for (long k = 0; k < N; ++k) {
+        double r = rho[k], uu[3] = {0, 0, 0}, xi[3], zeta[3], tmp[27];
+        for (int a = 0; a < D; ++a) uu[a] = u[(long)a * N + k];
+        double P = orc_eos_P(&s->p, r, T[k]);
+        double th = P / r;
+        for (int a = 0; a < D; ++a) { xi[a] = uu[a]; zeta[a] = th + uu[a] * uu[a]; }
+        orc_fprod(D, r, xi, zeta, tmp);
+        for (int i = 0; i < Q; ++i) s->f[(long)i * N + k] = tmp[i];
+        orc_geq(D, r, uu, orc_eos_e(&s->p, r, T[k]), th, tmp);
+        for (int i = 0; i < Q; ++i) s->g[(long)i * N + k] = tmp[i];
+        s->T[k] = T[k];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Phases A-C: macroscopic fields of the current populations                 */
+/* ------------------------------------------------------------------------- */
+static void macro_fields(orc_state *s)
+{
+    const orc_params *p = &s->p;
+    int D = p->dim, Q = s->Q;
+    long N = s->N;
+    int nx = p->nx, ny = p->ny, nz = p->nz;
+
+    /* A: Eq. def_h and the raw first moments */
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < N; ++k) {
+        double r = 0, j[3] = {0, 0, 0}, G = 0;
+        for (int i = 0; i < Q; ++i) {
+            double fi = s->f[(long)i * N + k];
+            r += fi;
+            for (int a = 0; a < D; ++a) j[a] += s->c[i][a] * fi;
+            G += s->g[(long)i * N + k];
+        }
+        s->rho[k] = r;
+        for (int a = 0; a < 3; ++a) s->J[(long)a * N + k] = j[a];
+        s->G[k] = G;
+    }
+
+    /* B1: Laplacian of rho, (2D+1)-point stencil */
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long k = cidx(s, x, y, z);
+                double L = 0;
+                for (int a = 0; a < D; ++a) {
+                    int e[3] = {0, 0, 0};
+                    e[a] = 1;
+                    L += nb_scalar(s, s->rho, x, y, z, e[0], e[1], e[2]) - 2.0 * s->rho[k] +
+                         nb_scalar(s, s->rho, x, y, z, -e[0], -e[1], -e[2]);
+                }
+                s->lap[k] = L;
+            }
+
+    /* B2: F = F_B + F_K with F_K = kappa rho grad(lap rho) (Eq. korteweg_force); Q(x) */
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long k = cidx(s, x, y, z);
+                double r = s->rho[k];
+                for (int a = 0; a < 3; ++a) {
+                    double Fa = 0.0;
+                    if (a < D) {
+                        int e[3] = {0, 0, 0};
+                        e[a] = 1;
+                        double gL = 0.5 * (nb_scalar(s, s->lap, x, y, z, e[0], e[1], e[2]) -
+                                           nb_scalar(s, s->lap, x, y, z, -e[0], -e[1], -e[2]));
+                        Fa = r * p->accel[a] + p->kappa * r * gL;
+                    }
+                    s->F[(long)a * N + k] = Fa;
+                }
+                int in_mask = (p->zhi <= 0) || (z >= p->zlo && z < p->zhi);
+                s->Qs[k] = in_mask ? p->q : 0.0;
+            }
+
+    /* C: Eqs. def_u, def_E, T(rho,e), P, and the closure scalars */
+    long caps = 0, nonpos = 0;
+#pragma omp parallel for schedule(static) reduction(+ : caps, nonpos)
+    for (long k = 0; k < N; ++k) {
+        double r = s->rho[k];
+        double uu[3] = {0, 0, 0}, uF = 0, u2 = 0;
+        for (int a = 0; a < D; ++a) {
+            uu[a] = (s->J[(long)a * N + k] + 0.5 * s->F[(long)a * N + k]) / r;
+            uF += uu[a] * s->F[(long)a * N + k];
+            u2 += uu[a] * uu[a];
+        }
+        for (int a = 0; a < 3; ++a) s->u[(long)a * N + k] = uu[a];
+        double rhoE = s->G[k] + 0.5 * (uF + s->Qs[k]);
+        double E = rhoE / r;
+        double e = E - 0.5 * u2;
+        int it;
+        double T = orc_eos_T(p, r, e, s->T[k], &it);
+        if (p->eos == ORC_PR && it >= 50) caps++;
+        double P = orc_eos_P(p, r, T);
+        double th = P / r;
+        if (!(th > 0.0)) nonpos++;
+        double cv = orc_eos_cv(p, r, T);
+        double PT = orc_eos_dPdT(p, r, T);
+        double Pr = orc_eos_dPdrho(p, r, T);
+        double cs2 = Pr + T * PT * PT / (r * r * cv);
+        s->E[k] = E;
+        s->e[k] = e;
+        s->T[k] = T;
+        s->P[k] = P;
+        s->theta[k] = th;
+        s->h[k] = e + P / r;
+        s->cvl[k] = cv;
+        s->gam[k] = 1.0 + PT / (r * cv);
+        s->athe[k] = ((double)(D + 2) / D - p->eta_over_mu) * th - cs2;
+        for (int a = 0; a < 3; ++a)
+            s->X[(long)a * N + k] = (a < D) ? r * uu[a] * uu[a] * uu[a] + 3.0 * r * uu[a] * (th - 1.0 / 3.0) : 0.0;
+    }
+    s->newton_cap_hits += caps;
+    s->theta_nonpos += nonpos;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One time step                                                              */
+/* ------------------------------------------------------------------------- */
+static void one_step(orc_state *s)
+{
+    const orc_params *p = &s->p;
+    int D = p->dim, Q = s->Q;
+    long N = s->N;
+    int nx = p->nx, ny = p->ny, nz = p->nz;
+    double beta_f = 1.0 / (2.0 * p->tau_f + 1.0);
+    double beta_g = 1.0 / (2.0 * p->tau_g + 1.0);
+
+    macro_fields(s);
+
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long k = cidx(s, x, y, z);
+                double r = s->rho[k], T = s->T[k], P = s->P[k], th = s->theta[k];
+                double cv = s->cvl[k], Qk = s->Qs[k];
+                double uu[3], Fv[3];
+                for (int a = 0; a < 3; ++a) { uu[a] = s->u[(long)a * N + k]; Fv[a] = s->F[(long)a * N + k]; }
+
+                /* D: gradients (central) and the Galilean correction (upwind-biased) */
+                double divu = 0, gh[3] = {0, 0, 0}, gT[3] = {0, 0, 0}, Phi[3] = {0, 0, 0};
+                for (int a = 0; a < D; ++a) {
+                    int e[3] = {0, 0, 0};
+                    e[a] = 1;
+                    divu += 0.5 * (nb_vector(s, s->u, a, x, y, z, e[0], e[1], e[2]) -
+                                   nb_vector(s, s->u, a, x, y, z, -e[0], -e[1], -e[2]));
+                    gh[a] = 0.5 * (nb_scalar(s, s->h, x, y, z, e[0], e[1], e[2]) -
+                                   nb_scalar(s, s->h, x, y, z, -e[0], -e[1], -e[2]));
+                    gT[a] = 0.5 * (nb_scalar(s, s->T, x, y, z, e[0], e[1], e[2]) -
+                                   nb_scalar(s, s->T, x, y, z, -e[0], -e[1], -e[2]));
+                    double X0 = s->X[(long)a * N + k], dX;
+                    if (p->phi_central) {
+                        dX = 0.5 * (nb_vector(s, s->X, a, x, y, z, e[0], e[1], e[2]) -
+                                    nb_vector(s, s->X, a, x, y, z, -e[0], -e[1], -e[2]));
+                    } else if (uu[a] >= 0.0) {
+                        double Xm1 = nb_vector(s, s->X, a, x, y, z, -e[0], -e[1], -e[2]);
+                        double Xm2 = nb_vector(s, s->X, a, x, y, z, -2 * e[0], -2 * e[1], -2 * e[2]);
+                        dX = 0.5 * (3.0 * X0 - 4.0 * Xm1 + Xm2);
+                    } else {
+                        double Xp1 = nb_vector(s, s->X, a, x, y, z, e[0], e[1], e[2]);
+                        double Xp2 = nb_vector(s, s->X, a, x, y, z, 2 * e[0], 2 * e[1], 2 * e[2]);
+                        dX = -0.5 * (3.0 * X0 - 4.0 * Xp1 + Xp2);
+                    }
+                    Phi[a] = -dX / r; /* Eq. correction */
+                }
+
+                /* shifted states, Eqs. sh_vel_1, sh_temp_1, sh_T_1, qc_1 */
+                double us[3] = {0, 0, 0}, FF = 0, qc[3] = {0, 0, 0};
+                for (int a = 0; a < D; ++a) {
+                    us[a] = uu[a] + Fv[a] / r;
+                    FF += Fv[a] * Fv[a];
+                    qc[a] = P * (gh[a] - p->k_over_mu * gT[a]);
+                }
+                double ths = th + s->athe[k] * divu + (s->gam[k] - 1.0) * Qk / r;
+                double Ts = T + Qk / (r * cv) - FF / (2.0 * r * r * cv);
+                double es = orc_eos_e(p, r, Ts);
+
+                /* E: equilibria in product form */
+                double xi[3], zeta[3], feq[27], fst[27], geq[27], gst[27];
+                for (int a = 0; a < D; ++a) { xi[a] = uu[a]; zeta[a] = th + uu[a] * uu[a]; }
+                orc_fprod(D, r, xi, zeta, feq);                          /* Eq. LBMeq */
+                for (int a = 0; a < D; ++a) { xi[a] = us[a]; zeta[a] = ths + us[a] * us[a] + Phi[a]; }
+                orc_fprod(D, r, xi, zeta, fst);                          /* Eq. LBMstar */
+                orc_geq(D, r, uu, s->e[k], th, geq);                      /* Eq. LBMeqG */
+                orc_geq(D, r, us, es, ths, gst);                          /* Eq. LBMgstar, first term */
+                for (int i = 0; i < Q; ++i) {
+                    int c2 = 0;
+                    double cq = 0;
+                    for (int a = 0; a < D; ++a) { c2 += s->c[i][a] * s->c[i][a]; cq += s->c[i][a] * qc[a]; }
+                    if (c2 == 1) gst[i] += 0.5 * cq;                      /* Eq. LBMgstar, correction */
+                }
+
+                /* collide (Eqs. LBM_f, LBM_g with lambda = dt) and stream (push) */
+                for (int i = 0; i < Q; ++i) {
+                    double fi = s->f[(long)i * N + k], gi = s->g[(long)i * N + k];
+                    double fo = fi + 2.0 * beta_f * (feq[i] - fi) + (1.0 - beta_f) * (fst[i] - feq[i]);
+                    double go = gi + 2.0 * beta_g * (geq[i] - gi) + (1.0 - beta_g) * (gst[i] - geq[i]);
+                    int zt = z + s->c[i][2];
+                    if (p->zwalls && (zt < 0 || zt >= nz)) {
+                        /* half-way bounce-back: returns to this cell reversed */
+                        s->fn[(long)s->opp[i] * N + k] = fo;
+                        s->gn[(long)s->opp[i] * N + k] = go;
+                    } else {
+                        long kt = cidx(s, wrap(x + s->c[i][0], nx), wrap(y + s->c[i][1], ny), wrap(zt, nz));
+                        s->fn[(long)i * N + kt] = fo;
+                        s->gn[(long)i * N + kt] = go;
+                    }
+                }
+            }
+
+    double *t;
+    t = s->f; s->f = s->fn; s->fn = t;
+    t = s->g; s->g = s->gn; s->gn = t;
+}
+
+int orc_step(orc_state *s, int n)
+{
+    for (int it = 0; it < n; ++it) one_step(s);
+    return 0;
+}
+
+/* Macroscopic fields of the current state: rho, u (Eq. def_u), T. */
+int orc_moments(orc_state *s, double *rho, double *u /* [dim][N] */, double *T)
+{
+    macro_fields(s);
+    long N = s->N;
+    for (long k = 0; k < N; ++k) {
+        if (rho) rho[k] = s->rho[k];
+        if (T) T[k] = s->T[k];
+        if (u)
+            for (int a = 0; a < s->p.dim; ++a) u[(long)a * N + k] = s->u[(long)a * N + k];
+    }
+    return 0;
+}
+
+/* Totals of the current state:
+ *   out = [ sum rho, sum rho u (dim), sum rho E, sum F (dim), sum (u.F + Q) ]
+ * with rho u and rho E from Eqs. def_u and def_E. */
+int orc_invariants(orc_state *s, double *out)
+{
+    macro_fields(s);
+    int D = s->p.dim;
+    long N = s->N;
+    double m = 0, M[3] = {0, 0, 0}, En = 0, Fs[3] = {0, 0, 0}, S = 0;
+    for (long k = 0; k < N; ++k) {
+        double r = s->rho[k], uF = 0;
+        m += r;
+        for (int a = 0; a < D; ++a) {
+            M[a] += r * s->u[(long)a * N + k];
+            Fs[a] += s->F[(long)a * N + k];
+            uF += s->u[(long)a * N + k] * s->F[(long)a * N + k];
+        }
+        En += r * s->E[k];
+        S += uF + s->Qs[k];
+    }
+    int o = 0;
+    out[o++] = m;
+    for (int a = 0; a < D; ++a) out[o++] = M[a];
+    out[o++] = En;
+    for (int a = 0; a < D; ++a) out[o++] = Fs[a];
+    out[o++] = S;
+    return o;
+}
+
+/* Copies of the populations [Q][N]. */
+int orc_populations(const orc_state *s, double *f, double *g)
+{
+    size_t n = (size_t)s->Q * (size_t)s->N * sizeof(double);
+    if (f) memcpy(f, s->f, n);
+    if (g) memcpy(g, s->g, n);
+    return 0;
+}
+
+/* Overwrite the populations (used by tests that start from a given state). */
+int orc_set_populations(orc_state *s, const double *f, const double *g, const double *T_guess)
+{
+    size_t n = (size_t)s->Q * (size_t)s->N * sizeof(double);
+    memcpy(s->f, f, n);
+    memcpy(s->g, g, n);
+    if (T_guess) memcpy(s->T, T_guess, (size_t)s->N * sizeof(double));
+    return 0;
+}
+
+long orc_newton_cap_hits(const orc_state *s) { return s->newton_cap_hits; }
+long orc_theta_nonpositive(const orc_state *s) { return s->theta_nonpos; }

@@ -1,0 +1,257 @@
+"""ctypes wrapper of the FP64 CPU oracle (``lbm_oracle.c``).
+
+Test infrastructure only: the test suite, the smoke check and the CPU-baseline
+leg of the benchmark use it to produce the values the CUDA path must match.
+The product library never imports it.
+
+Field layout matches the library's host-side convention: scalars are ``[N]``
+and vectors ``[dim][N]`` float64 arrays, cell index ``x + nx*(y + ny*z)``.
+Populations are ``[Q][N]``; direction ``i`` has base-3 digits
+``(d_x, d_y, d_z)`` with digit 0, 1, 2 meaning c = 0, +1, -1.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+IDEAL, VDW, PR = 0, 1, 2
+_EOS_NAMES = {"ideal": IDEAL, "vdw": VDW, "pr": PR}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-std=c11", "-Wall", "-o", _LIB, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+    return _LIB
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("zwalls", ctypes.c_int), ("eos", ctypes.c_int),
+        ("R", ctypes.c_double), ("cv", ctypes.c_double),
+        ("a", ctypes.c_double), ("b", ctypes.c_double),
+        ("Tc", ctypes.c_double), ("omega", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("eta_over_mu", ctypes.c_double), ("k_over_mu", ctypes.c_double),
+        ("tau_f", ctypes.c_double), ("tau_g", ctypes.c_double),
+        ("accel", ctypes.c_double * 3),
+        ("q", ctypes.c_double), ("zlo", ctypes.c_int), ("zhi", ctypes.c_int),
+        ("phi_central", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        d, i, vp, dp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        pp = ctypes.POINTER(OrcParams)
+        sig = {
+            "orc_lattice": (i, [i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+            "orc_psi": (d, [i, d, d]),
+            "orc_fprod": (None, [i, d, dp, dp, dp]),
+            "orc_geq": (None, [i, d, dp, d, d, dp]),
+            "orc_eos_P": (d, [pp, d, d]),
+            "orc_eos_e": (d, [pp, d, d]),
+            "orc_eos_dPdT": (d, [pp, d, d]),
+            "orc_eos_dPdrho": (d, [pp, d, d]),
+            "orc_eos_cv": (d, [pp, d, d]),
+            "orc_eos_T": (d, [pp, d, d, d, ctypes.POINTER(ctypes.c_int)]),
+            "orc_vdw_from_critical": (None, [d, d, d, dp, dp]),
+            "orc_pr_from_critical": (None, [d, d, d, dp, dp]),
+            "orc_create": (vp, [pp]),
+            "orc_destroy": (None, [vp]),
+            "orc_set_threads": (None, [i]),
+            "orc_get_threads": (i, []),
+            "orc_init": (i, [vp, dp, dp, dp]),
+            "orc_step": (i, [vp, i]),
+            "orc_moments": (i, [vp, dp, dp, dp]),
+            "orc_invariants": (i, [vp, dp]),
+            "orc_populations": (i, [vp, dp, dp]),
+            "orc_set_populations": (i, [vp, dp, dp, dp]),
+            "orc_newton_cap_hits": (ctypes.c_long, [vp]),
+            "orc_theta_nonpositive": (ctypes.c_long, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(_lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_params(dim=2, nx=8, ny=8, nz=1, zwalls=0, eos="ideal", R=1.0, cv=2.5, a=0.0, b=0.0,
+                Tc=1.0, omega=0.0, Pc=None, kappa=0.0, eta_over_mu=0.0, k_over_mu=0.0,
+                tau_f=0.8, tau_g=0.8, accel=(0.0, 0.0, 0.0), q=0.0, zlo=0, zhi=0,
+                phi_central=0) -> OrcParams:
+    """Build the oracle's parameter struct.  For Peng-Robinson with ``Pc`` given
+    and ``a == 0``, a and b follow from (Tc, Pc) by the oracle's own helper."""
+    kind = _EOS_NAMES[eos] if isinstance(eos, str) else int(eos)
+    if kind == PR and a == 0.0 and Pc is not None:
+        a, b = pr_from_critical(R, Tc, Pc)
+    p = OrcParams()
+    p.dim, p.nx, p.ny, p.nz, p.zwalls, p.eos = dim, nx, ny, nz, zwalls, kind
+    p.R, p.cv, p.a, p.b, p.Tc, p.omega = R, cv, a, b, Tc, omega
+    p.kappa, p.eta_over_mu, p.k_over_mu = kappa, eta_over_mu, k_over_mu
+    p.tau_f, p.tau_g = tau_f, tau_g
+    for k in range(3):
+        p.accel[k] = accel[k] if k < len(accel) else 0.0
+    p.q, p.zlo, p.zhi = q, zlo, zhi
+    p.phi_central = int(phi_central)
+    return p
+
+
+def lattice(dim: int):
+    c = (ctypes.c_int * 81)()
+    opp = (ctypes.c_int * 27)()
+    Q = lib().orc_lattice(dim, c, opp)
+    cv = np.array(c[: 3 * Q], dtype=np.int64).reshape(Q, 3)[:, :dim]
+    return cv, np.array(opp[:Q], dtype=np.int64)
+
+
+def psi(c: int, xi: float, zeta: float) -> float:
+    return lib().orc_psi(c, xi, zeta)
+
+
+def fprod(dim: int, rho: float, xi, zeta) -> np.ndarray:
+    Q = 3 ** dim
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    zeta = np.ascontiguousarray(zeta, dtype=np.float64)
+    out = np.zeros(Q)
+    lib().orc_fprod(dim, rho, _dp(xi), _dp(zeta), _dp(out))
+    return out
+
+
+def feq(dim: int, rho: float, u, theta: float) -> np.ndarray:
+    u = np.asarray(u, dtype=np.float64)
+    return fprod(dim, rho, u, theta + u * u)
+
+
+def geq(dim: int, rho: float, u, e: float, theta: float) -> np.ndarray:
+    Q = 3 ** dim
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(Q)
+    lib().orc_geq(dim, rho, _dp(u), e, theta, _dp(out))
+    return out
+
+
+class EoS:
+    """Equation-of-state functions of the oracle for one parameter set."""
+
+    def __init__(self, params: OrcParams):
+        self.p = params
+
+    def P(self, rho, T):
+        return lib().orc_eos_P(ctypes.byref(self.p), rho, T)
+
+    def e(self, rho, T):
+        return lib().orc_eos_e(ctypes.byref(self.p), rho, T)
+
+    def dPdT(self, rho, T):
+        return lib().orc_eos_dPdT(ctypes.byref(self.p), rho, T)
+
+    def dPdrho(self, rho, T):
+        return lib().orc_eos_dPdrho(ctypes.byref(self.p), rho, T)
+
+    def cv(self, rho, T):
+        return lib().orc_eos_cv(ctypes.byref(self.p), rho, T)
+
+    def T(self, rho, e, T_guess=0.0):
+        it = ctypes.c_int(0)
+        T = lib().orc_eos_T(ctypes.byref(self.p), rho, e, T_guess, ctypes.byref(it))
+        return T, it.value
+
+
+def vdw_from_critical(R, Tc, Pc):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().orc_vdw_from_critical(R, Tc, Pc, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def pr_from_critical(R, Tc, Pc):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().orc_pr_from_critical(R, Tc, Pc, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+class Oracle:
+    """One simulation on the CPU oracle."""
+
+    def __init__(self, params: OrcParams):
+        self.p = params
+        self.dim = params.dim
+        self.N = params.nx * params.ny * params.nz
+        self.Q = 3 ** params.dim
+        self._h = lib().orc_create(ctypes.byref(params))
+        if not self._h:
+            raise ValueError("oracle: invalid parameters")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_destroy(h)
+            self._h = None
+
+    def init(self, rho, u, T):
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(self.N)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(self.dim, self.N)
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape(self.N)
+        lib().orc_init(self._h, _dp(rho), _dp(u), _dp(T))
+
+    def step(self, n: int = 1):
+        lib().orc_step(self._h, int(n))
+
+    def moments(self):
+        rho = np.zeros(self.N)
+        u = np.zeros((self.dim, self.N))
+        T = np.zeros(self.N)
+        lib().orc_moments(self._h, _dp(rho), _dp(u), _dp(T))
+        return rho, u, T
+
+    def invariants(self) -> np.ndarray:
+        out = np.zeros(2 * self.dim + 3)
+        lib().orc_invariants(self._h, _dp(out))
+        return out
+
+    def populations(self):
+        f = np.zeros((self.Q, self.N))
+        g = np.zeros((self.Q, self.N))
+        lib().orc_populations(self._h, _dp(f), _dp(g))
+        return f, g
+
+    def set_populations(self, f, g, T_guess=None):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        tg = None if T_guess is None else _dp(np.ascontiguousarray(T_guess, dtype=np.float64))
+        lib().orc_set_populations(self._h, _dp(f), _dp(g), tg)
+
+    @property
+    def newton_cap_hits(self) -> int:
+        return int(lib().orc_newton_cap_hits(self._h))
+
+    @property
+    def theta_nonpositive(self) -> int:
+        return int(lib().orc_theta_nonpositive(self._h))
