@@ -1,0 +1,309 @@
+"""Benchmark of the fused DDF lattice Boltzmann step on B300.
+
+Workload (one "step" = one time step of the whole hot path): the 2-D van der
+Waals liquid-vapour quench on a 512 x 512 D2Q9 lattice with float32
+populations, Korteweg capillarity, gravity and the explicit temperature
+inversion (the paper-shaped configuration the MLUPS metric is quoted on).
+Inputs are synthetic and seeded (paper_2609_28679_b300.workloads).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (no data-path collective); value = cells x steps of
+all ranks / max over ranks of the timed region.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (million lattice-cell updates per second, f and g populations)"
+UNIT = "MLUPS"
+FALLBACK_HBM_GBS = 6400.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (6.4 TB/s, no MEASURED_PEAKS.json)"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("lbm_device.cuh", "lbm_fused.cuh"):
+        with open(os.path.join(ROOT, "paper_2609_28679_b300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = _kernel_source_hash()
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split()
+            if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload \
+                    and parts[2] == src:
+                return float(parts[3])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_mlups(case, steps_budget_s: float, threads: int | None = None):
+    """Time the FP64 CPU oracle on the workload (bounded number of full steps)."""
+    from oracle import oracle as orc
+
+    if threads:
+        orc.set_threads(threads)
+    o = orc.Oracle(orc.params_from_case(case))
+    o.init(*case.fields())
+    t0 = time.perf_counter()
+    o.step(1)  # warm-up step (also sizes the sample)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(200, int(steps_budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    return case.ncell * n / dt / 1e6, n, dt, orc.get_threads()
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_2609_28679_b300 import workloads as wl
+
+    case = wl.vdw_spinodal(512, storage="f64")
+    budget = min(120.0, 2.0 * max(args.steps, 1))
+    value, n, dt, cores = _oracle_mlups(case, budget)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / n * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "vdw_spinodal_512: 2-D van der Waals quench, 512x512 D2Q9, Korteweg + gravity",
+                   "cells": case.ncell},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} full time steps of the 512x512 workload (FP64 C oracle, OpenMP)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2609_28679_b300 import lbm
+    from paper_2609_28679_b300 import workloads as wl
+
+    rank, world, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    case = wl.vdw_spinodal(512, storage="f32")
+    sim = lbm.Simulation(case)
+    sim.init()
+    variant, tx, ty, tz = sim.kernel()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    # device-timed region: one event pair per step, L2 flushed between steps (outside the pairs)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    diag = sim.diagnostics()
+
+    # end to end through the C ABI with host buffers: upload the state, one step, read the fields back
+    rho, u, T = case.fields()
+    rho_h = torch.from_numpy(rho).pin_memory().numpy()
+    u_h = torch.from_numpy(np.ascontiguousarray(u.ravel())).pin_memory().numpy()
+    T_h = torch.from_numpy(T).pin_memory().numpy()
+    out_r = torch.empty(case.ncell, dtype=torch.float64).pin_memory().numpy()
+    out_u = torch.empty(2 * case.ncell, dtype=torch.float64).pin_memory().numpy()
+    out_T = torch.empty(case.ncell, dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(3, min(args.steps, 50))
+    for it in range(2):
+        lbm.lbm_init(sim.h, rho_h, u_h, T_h, 0)
+        lbm.lbm_step(sim.h, 1)
+        lbm.lbm_moments(sim.h, out_r, out_u, out_T, 0)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for it in range(e2e_steps):
+        lbm.lbm_init(sim.h, rho_h, u_h, T_h, 0)
+        lbm.lbm_step(sim.h, 1)
+        lbm.lbm_moments(sim.h, out_r, out_u, out_T, 0)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    sim.close()
+
+    Q = 9
+    alg_bytes = 4 * Q * 4 * case.ncell  # read + write f and g once, float32
+    avg_ms = total_ms / args.steps
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    peak, peak_src = _peaks()
+    kname = "k_fused" if variant == lbm.LBM_KERNEL_FUSED else "k_collide"
+    value = world * case.ncell * args.steps / (total_ms * 1e-3) / 1e6
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cb_case = wl.vdw_spinodal(512, storage="f64")
+            cv, n, dt, cores = _oracle_mlups(cb_case, 15.0)
+            cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{n} full time steps of the same 512x512 workload ({dt:.1f} s, FP64 C oracle, OpenMP)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; paper-shaped vdW quench)",
+            "config": {"workload": "vdw_spinodal_512: 2-D van der Waals quench, 512x512 D2Q9, f32 populations, "
+                                   "Korteweg capillarity + gravity", "cells": case.ncell, "storage": "f32",
+                       "kernel": kname, "tile": [tx, ty, tz],
+                       "l2": "flushed between timed steps (256 MiB write outside the event pairs)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": _ncu_traffic(kname, "vdw_spinodal_512_f32"),
+                         "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": avg_ms},
+            "e2e": {"value": case.ncell * e2e_steps / e2e_s / 1e6, "unit": UNIT,
+                    "h2d_bytes_per_step": int(rho_h.nbytes + u_h.nbytes + T_h.nbytes),
+                    "d2h_bytes_per_step": int(out_r.nbytes + out_u.nbytes + out_T.nbytes),
+                    "what": "lbm_init from pinned host fields + lbm_step(1) + lbm_moments to pinned host, per step"},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "diagnostics": {"nonfinite": int(diag[0]), "theta_le_0": int(diag[1]), "newton_cap": int(diag[2])},
+            "wall_s_timed_region": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

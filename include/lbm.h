@@ -1,0 +1,185 @@
+/*
+ * lbm.h -- C ABI of the B300 (sm_103a) double-distribution lattice Boltzmann
+ * library: consistent body force and heat source for compressible flows of
+ * generic fluids (arxiv 2609.28679).
+ *
+ * One call of lbm_step advances every population of a simulation by one time
+ * step of the paper's scheme (Sec. II.E, Fig. "Structure of the algorithm"):
+ *   moments with the half-force/half-source shifts (Eqs. def_h, def_u, def_E),
+ *   force F = rho*a + Korteweg kappa rho grad lap rho (Eqs. force_decomposition,
+ *   korteweg_force) and heat source Q, temperature from the equation of state
+ *   (Eq. TdependsongenericEOS), closure scalars theta = P/rho, alpha, gamma
+ *   (Eqs. theta, corr_bulk, corr_heat_source), shifted states u*, theta*, T*,
+ *   q^c and the Galilean correction Phi (Eqs. sh_vel_1, sh_temp_1, sh_T_1,
+ *   qc_1, correction), product-form equilibria f^eq, f*, g^eq, g* (Eqs. LBMeq,
+ *   LBMstar, LBMeqG, LBMgstar), collision with beta = 1/(2 tau + 1)
+ *   (Eqs. beta, LBM_f, LBM_g, lambda = dt) and streaming.
+ *
+ * Units: lattice units, dt = dx = c = 1, varsigma^2 = 1/3 (Eq. cs).
+ * Lattices: dim = 3 is the paper's D3Q27 (Eq. D3Q27c); dim = 2 its product
+ * restriction D2Q9.  Population i has base-3 digits (d_x, d_y, d_z) with digit
+ * 0, 1, 2 meaning c = 0, +1, -1.
+ *
+ * Conventions shared by every call:
+ *  - Host-visible fields are float64, cell index k = x + nx*(y + ny*z);
+ *    scalars are [N], vectors [dim][N] (component-major).  For a batch handle
+ *    the fields of simulation s follow those of simulation s-1 (rho and T by
+ *    N_s, u by dim*N_s).
+ *  - Pointers are host pointers when on_device == 0, device pointers of the
+ *    library's device otherwise.  The caller owns every buffer it passes; the
+ *    library owns the populations and its work arrays, which callers never see
+ *    except through lbm_populations.
+ *  - Device memory comes from PyTorch's CUDA caching allocator (libc10_cuda);
+ *    it must be initialised (torch.cuda.init(), which the Python binding does)
+ *    before lbm_create.  Work is enqueued on the handle's stream (default: the
+ *    current PyTorch stream of the device at lbm_create; see lbm_set_stream).
+ *  - Every function returns LBM_OK (0) or a negative LBM_E_* code and keeps a
+ *    message retrievable with lbm_last_error.  Calls that copy to host memory
+ *    synchronise the handle's stream; lbm_step only enqueues.
+ *  - A handle is not safe to use from several threads at once.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_E_INVALID (-1)     /* bad argument or struct field            */
+#define LBM_E_NOMEM (-2)       /* device allocation failed                */
+#define LBM_E_CUDA (-3)        /* a CUDA runtime call or launch failed    */
+#define LBM_E_UNSUPPORTED (-4) /* valid but not built (e.g. form/lattice) */
+#define LBM_E_STATE (-5)       /* call out of order (e.g. step before init) */
+
+/* population storage */
+#define LBM_F64 0  /* float64 populations, float64 arithmetic                   */
+#define LBM_F32 1  /* float32 populations, float32 arithmetic                   */
+#define LBM_BF16 2 /* bfloat16 of f_i - f_i^ref, float32 arithmetic            */
+#define LBM_F16 3  /* float16 of f_i - f_i^ref, float32 arithmetic             */
+
+/* equations of state */
+#define LBM_IDEAL 0 /* P = rho R T (Eq. idealEOS)                                 */
+#define LBM_VDW 1   /* P = rho R T/(1 - b rho) - a rho^2 (Eq. vdw_eos)             */
+#define LBM_PR 2    /* Peng-Robinson, Soave alpha(T), constant ideal-part c_v    */
+
+/* temperature inversion T(rho, e) for Peng-Robinson */
+#define LBM_T_NEWTON 0 /* Newton's method, warm-started from the previous T         */
+#define LBM_T_MLP 1    /* learned T(rho, e) (lbm_mlp_load) with Newton fallback      */
+
+/* derivative in the Galilean correction Phi (Eq. correction) */
+#define LBM_PHI_UPWIND 0  /* 2nd-order one-sided, chosen by the sign of u_alpha */
+#define LBM_PHI_CENTRAL 1 /* 2-point central                                     */
+
+/* kernel variants (lbm_set_kernel) */
+#define LBM_KERNEL_AUTO 0  /* the library's choice (autotuned when a cache entry exists) */
+#define LBM_KERNEL_SPLIT 1 /* moments, macroscopic, collide-stream: three passes         */
+#define LBM_KERNEL_FUSED 2 /* one pass per step, shared-memory halo tiles                */
+
+typedef struct lbm_ctx *lbm_handle;
+
+typedef struct {
+    int dim;        /* 2 -> D2Q9, 3 -> D3Q27                                   */
+    int nx, ny, nz; /* cells; nz = 1 when dim = 2                             */
+    int zwalls;     /* 0: periodic in z; 1: half-way bounce-back at both z faces (dim 3) */
+    int storage;    /* LBM_F64 | LBM_F32 | LBM_BF16 | LBM_F16                  */
+    int phi_scheme; /* LBM_PHI_UPWIND | LBM_PHI_CENTRAL                        */
+} lbm_lattice;
+
+typedef struct {
+    int kind;           /* LBM_IDEAL | LBM_VDW | LBM_PR                          */
+    double R, cv;       /* gas constant; constant (ideal-part) specific heat    */
+    double a, b;        /* attraction, co-volume (vdW, PR); PR: if a == 0 they
+                           follow from (Tc, Pc): a = 0.45724 R^2 Tc^2/Pc,
+                           b = 0.07780 R Tc/Pc                                  */
+    double Tc, Pc;      /* PR critical temperature and pressure                 */
+    double omega;       /* PR acentric factor                                    */
+    double kappa;       /* Korteweg capillarity coefficient (0: no F_K)         */
+    double eta_over_mu; /* bulk / shear viscosity (Eq. corr_bulk)                */
+    double k_over_mu;   /* thermal conductivity / shear viscosity (Eq. qc_1)    */
+    int t_solver;       /* LBM_T_NEWTON | LBM_T_MLP                              */
+} lbm_eos;
+
+typedef struct {
+    double accel[3]; /* body acceleration a: F_B = rho a (Eq. force_decomposition) */
+} lbm_force;
+
+typedef struct {
+    double q;         /* volumetric heat source Q                                 */
+    int zmask_lo;     /* Q acts on cells with zmask_lo <= z < zmask_hi ...        */
+    int zmask_hi;     /* ... and everywhere when zmask_hi <= 0                    */
+} lbm_heat;
+
+/* Create one simulation.  tau_f, tau_g are the paper's relaxation time tau of
+ * f and g (beta = 1/(2 tau + 1), Eq. beta; tau > 0).  force and heat may be
+ * NULL (no body force / no heat source).  Allocates 2 x 2 x Q x N populations
+ * of the storage type plus work arrays.  Errors: LBM_E_INVALID (dim not 2/3,
+ * sizes < 1, nz != 1 in 2-D, walls in 2-D, kind/storage/scheme out of range,
+ * tau <= 0, b*rho limits are not checked), LBM_E_NOMEM, LBM_E_CUDA. */
+int lbm_create(const lbm_lattice *lattice, const lbm_eos *eos, double tau_f, double tau_g,
+               const lbm_force *force, const lbm_heat *heat, lbm_handle *out);
+
+/* Create nsim independent simulations stepped together (one launch per step
+ * for all of them).  Arrays of nsim entries; every lattice must share dim and
+ * storage; force/heat may be NULL (none for all) or arrays of nsim. */
+int lbm_create_batch(int nsim, const lbm_lattice *lattices, const lbm_eos *eos, const double *tau_f,
+                     const double *tau_g, const lbm_force *force, const lbm_heat *heat, lbm_handle *out);
+
+void lbm_destroy(lbm_handle h);
+
+/* Use `stream` (a cudaStream_t) for all later work of h; NULL selects the
+ * legacy default stream. */
+int lbm_set_stream(lbm_handle h, void *stream);
+
+/* Initial state (flowchart, first box): f = f^eq(rho, u, theta), g = g^eq with
+ * theta = P(rho,T)/rho and e = e(rho,T).  rho > 0 and T > 0 everywhere.  For
+ * 16-bit storage the per-direction offsets f^ref, g^ref are the rest
+ * equilibria at the mean rho and mean T of the first simulation of the call. */
+int lbm_init(lbm_handle h, const double *rho, const double *u, const double *T, int on_device);
+
+/* Advance every simulation of h by n >= 0 time steps (enqueue only). */
+int lbm_step(lbm_handle h, int n);
+
+/* Macroscopic fields of the current state: rho (Eq. def_h), the physical
+ * velocity u = (sum c f + F/2)/rho (Eq. def_u) and T from the EoS.  Any of the
+ * three pointers may be NULL. */
+int lbm_moments(lbm_handle h, double *rho, double *u, double *T, int on_device);
+
+/* The current populations as float64 [Q][N] (f) and [Q][N] (g), decoded from
+ * the storage type (offset added back).  For tests and diagnostics. */
+int lbm_populations(lbm_handle h, double *f, double *g, int on_device);
+
+/* Totals of the current state, per simulation, 2*dim + 3 doubles each:
+ *   [ sum rho, sum rho u (dim), sum rho E, sum F (dim), sum (u.F + Q) ]
+ * with rho u, rho E the half-force moments (Eqs. def_u, def_E).  Reduced in
+ * float64 (warp shuffles, then a fixed-order pass over the block partials).
+ * Host pointer; synchronises. */
+int lbm_invariants(lbm_handle h, double *out);
+
+/* Diagnostic counters accumulated since lbm_init, summed over simulations:
+ *   out[0] cells with a non-finite rho, u or T seen by a step
+ *   out[1] cells with theta = P/rho <= 0 seen by a step
+ *   out[2] Newton solves that hit the iteration cap
+ *   out[3] cells whose learned temperature failed the residual test (Newton fallback)
+ * Host pointer; synchronises. */
+int lbm_diagnostics(lbm_handle h, long long out[4]);
+
+/* Kernel selection: variant LBM_KERNEL_AUTO / SPLIT / FUSED; tx, ty, tz the
+ * tile of the fused variant (0: default).  Errors: LBM_E_INVALID for a tile
+ * the variant cannot run. */
+int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz);
+
+/* The variant and tile that lbm_step uses now. */
+int lbm_get_kernel(lbm_handle h, int *variant, int *tx, int *ty, int *tz);
+
+/* Message of the last failing call on h (or of the last failing lbm_create*
+ * when h is NULL).  Valid until the next call on h. */
+const char *lbm_last_error(lbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -255,3 +255,15 @@ class Oracle:
     @property
     def theta_nonpositive(self) -> int:
         return int(lib().orc_theta_nonpositive(self._h))
+
+
+def params_from_case(case) -> OrcParams:
+    """Oracle parameters of a workload case (paper_2609_28679_b300.workloads.Case)."""
+    a, b = case.a, case.b
+    if case.eos == "pr" and a == 0.0:
+        a, b = pr_from_critical(case.R, case.Tc, case.Pc)
+    return make_params(dim=case.dim, nx=case.nx, ny=case.ny, nz=case.nz, zwalls=case.zwalls,
+                       eos=case.eos, R=case.R, cv=case.cv, a=a, b=b, Tc=case.Tc, omega=case.omega,
+                       kappa=case.kappa, eta_over_mu=case.eta_over_mu, k_over_mu=case.k_over_mu,
+                       tau_f=case.tau_f, tau_g=case.tau_g, accel=case.accel, q=case.q,
+                       zlo=case.zlo, zhi=case.zhi, phi_central=case.phi_central)

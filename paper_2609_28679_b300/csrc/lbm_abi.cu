@@ -1,0 +1,649 @@
+// Host side of the C ABI declared in include/lbm.h: argument checking,
+// device buffers (through PyTorch's caching allocator), simulation tables and
+// kernel launches on the handle's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_fused.cuh"
+#include "lbm_split.cuh"
+
+extern "C" void* lbm_glue_alloc(size_t nbytes, void* stream);
+extern "C" void lbm_glue_free(void* ptr);
+extern "C" void* lbm_glue_current_stream(int device);
+
+using namespace lbm;
+
+struct lbm_ctx;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Ops {
+    int (*init)(lbm_ctx*, const double*, const double*, const double*);
+    int (*step)(lbm_ctx*, int);
+    int (*macro)(lbm_ctx*);
+    int (*export_moments)(lbm_ctx*, double*, double*, double*);
+    int (*export_pops)(lbm_ctx*, double*, double*);
+    int (*invariants)(lbm_ctx*, double*);
+    int (*fused_ok)(lbm_ctx*, int, int, int);
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    int nsim = 0, dim = 0, Q = 0, storage = 0;
+    size_t rbytes = 0, sbytes = 0;
+    std::vector<SimDev> sims;
+    SimDev* d_sims = nullptr;
+    std::vector<BlockEntry> table;
+    BlockEntry* d_table = nullptr;
+    std::vector<int> sim_block_start;
+    int* d_sim_block_start = nullptr;
+    std::vector<TileEntry> tiles;
+    TileEntry* d_tiles = nullptr;
+    long long Ntot = 0, pop_elems = 0;
+    void* pop[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* W = nullptr;            // split-path work arrays [W_NF][Ntot]
+    void* M = nullptr;            // fused-path moments 2 x [M_NF][Ntot]
+    unsigned long long* d_diag = nullptr;
+    double* d_partials = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool initialized = false;
+    bool moments_valid = false;   // fused path: M holds the moments of the current state
+    int variant = LBM_KERNEL_SPLIT, tx = 0, ty = 0, tz = 0;
+    int smem_bytes = 0;
+    std::string err;
+    Ops ops{};
+};
+
+namespace {
+
+int fail(lbm_ctx* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(lbm_ctx* h, cudaError_t e, const char* where)
+{
+    return fail(h, LBM_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA_CHECK(h, call)                                  \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+#define LBM_LAUNCH_CHECK(h, what)                                 \
+    do {                                                          \
+        cudaError_t e_ = cudaGetLastError();                      \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, (what)); \
+    } while (0)
+
+void* dev_alloc(lbm_ctx* h, size_t n) { return lbm_glue_alloc(n, (void*)h->stream); }
+
+// ---------------------------------------------------------------------------
+// Typed implementation of every operation for one (D, arithmetic, storage).
+// ---------------------------------------------------------------------------
+template <int D, typename R, typename S> struct Impl {
+    // carried moments of the fused path, double-buffered with the populations
+    static R* mbuf(lbm_ctx* h, int which) { return (R*)h->M + (size_t)which * M_NF * h->Ntot; }
+
+    static int nblocks(lbm_ctx* h) { return (int)h->table.size(); }
+
+    static int init(lbm_ctx* h, const double* rho, const double* u, const double* T)
+    {
+        k_init<D, R, S><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, rho, u, T, (S*)h->pop[0],
+                                                                   (R*)h->W, h->Ntot);
+        LBM_LAUNCH_CHECK(h, "k_init");
+        h->cur = 0;
+        h->moments_valid = false;
+        return LBM_OK;
+    }
+
+    static int split_step(lbm_ctx* h)
+    {
+        const int nb = nblocks(h);
+        S* src = (S*)h->pop[h->cur];
+        S* dst = (S*)h->pop[h->cur ^ 1];
+        k_moments<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, src, (R*)h->W, h->Ntot);
+        k_macro<D, R><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot, h->d_diag);
+        k_collide<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, src, dst, (const R*)h->W, h->Ntot);
+        LBM_LAUNCH_CHECK(h, "split step");
+        h->cur ^= 1;
+        h->moments_valid = false;
+        return LBM_OK;
+    }
+
+    static int fused_prepare(lbm_ctx* h)
+    {
+        // moments of the current state into M (one pull pass), before the first fused step
+        fused_moments_launch<D, R, S>(h->d_sims, h->d_table, nblocks(h), (const S*)h->pop[h->cur], (const R*)h->W,
+                                      mbuf(h, h->cur), h->Ntot, h->stream);
+        LBM_LAUNCH_CHECK(h, "fused moments");
+        h->moments_valid = true;
+        return LBM_OK;
+    }
+
+    static int fused_step(lbm_ctx* h)
+    {
+        if (!h->moments_valid) {
+            int rc = fused_prepare(h);
+            if (rc) return rc;
+        }
+        cudaError_t e = fused_step_launch<D, R, S>(h->d_sims, h->d_tiles, (int)h->tiles.size(), h->tx, h->ty, h->tz,
+                                                  (const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], mbuf(h, h->cur),
+                                                  mbuf(h, h->cur ^ 1), h->Ntot, h->d_diag, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "fused step");
+        h->cur ^= 1;
+        return LBM_OK;
+    }
+
+    static int step(lbm_ctx* h, int n)
+    {
+        for (int it = 0; it < n; ++it) {
+            int rc = h->variant == LBM_KERNEL_FUSED ? fused_step(h) : split_step(h);
+            if (rc) return rc;
+        }
+        return LBM_OK;
+    }
+
+    // moments and macroscopic fields of the current state into W (no counters)
+    static int macro(lbm_ctx* h)
+    {
+        const int nb = nblocks(h);
+        k_moments<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (const S*)h->pop[h->cur],
+                                                              (R*)h->W, h->Ntot);
+        k_macro<D, R><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot, nullptr);
+        LBM_LAUNCH_CHECK(h, "macro");
+        return LBM_OK;
+    }
+
+    static int export_moments(lbm_ctx* h, double* rho, double* u, double* T)
+    {
+        k_export_moments<D, R><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (const R*)h->W,
+                                                                          h->Ntot, rho, u, T);
+        LBM_LAUNCH_CHECK(h, "export moments");
+        return LBM_OK;
+    }
+
+    static int export_pops(lbm_ctx* h, double* f, double* g)
+    {
+        k_export_pops<D, R, S><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table,
+                                                                          (const S*)h->pop[h->cur], f, g);
+        LBM_LAUNCH_CHECK(h, "export populations");
+        return LBM_OK;
+    }
+
+    static int invariants(lbm_ctx* h, double* d_out)
+    {
+        const int nv = 2 * D + 3;
+        k_invariants<D, R><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (const R*)h->W, h->Ntot,
+                                                                      h->d_partials);
+        int nt = h->nsim * nv;
+        k_invariants_final<<<(nt + 127) / 128, 128, 0, h->stream>>>(h->d_partials, h->d_sim_block_start, h->nsim, nv,
+                                                                    d_out);
+        LBM_LAUNCH_CHECK(h, "invariants");
+        return LBM_OK;
+    }
+
+    static int fused_ok(lbm_ctx* h, int tx, int ty, int tz) { return fused_tile_ok<D, R, S>(tx, ty, tz) ? 1 : 0; }
+
+    static Ops ops() { return Ops{init, step, macro, export_moments, export_pops, invariants, fused_ok}; }
+};
+
+bool pick_ops(int dim, int storage, Ops& ops, size_t& rbytes, size_t& sbytes)
+{
+#define LBM_PICK(D, R, S)              \
+    do {                               \
+        ops = Impl<D, R, S>::ops();    \
+        rbytes = sizeof(R);            \
+        sbytes = sizeof(S);            \
+        return true;                   \
+    } while (0)
+    if (dim == 2) {
+        if (storage == LBM_F64) LBM_PICK(2, double, double);
+        if (storage == LBM_F32) LBM_PICK(2, float, float);
+        if (storage == LBM_BF16) LBM_PICK(2, float, __nv_bfloat16);
+        if (storage == LBM_F16) LBM_PICK(2, float, __half);
+    } else if (dim == 3) {
+        if (storage == LBM_F64) LBM_PICK(3, double, double);
+        if (storage == LBM_F32) LBM_PICK(3, float, float);
+        if (storage == LBM_BF16) LBM_PICK(3, float, __nv_bfloat16);
+        if (storage == LBM_F16) LBM_PICK(3, float, __half);
+    }
+#undef LBM_PICK
+    return false;
+}
+
+int check_lattice(const lbm_lattice* L, std::string& why)
+{
+    if (!L) { why = "lattice is NULL"; return LBM_E_INVALID; }
+    if (L->dim != 2 && L->dim != 3) { why = "dim must be 2 or 3"; return LBM_E_INVALID; }
+    if (L->nx < 1 || L->ny < 1 || L->nz < 1) { why = "nx, ny, nz must be >= 1"; return LBM_E_INVALID; }
+    if (L->dim == 2 && (L->nz != 1 || L->zwalls)) { why = "2-D lattices need nz = 1 and no z walls"; return LBM_E_INVALID; }
+    if ((long long)L->nx * L->ny * L->nz > (1LL << 31) - 1) { why = "more than 2^31 - 1 cells"; return LBM_E_INVALID; }
+    if (L->zwalls != 0 && L->zwalls != 1) { why = "zwalls must be 0 or 1"; return LBM_E_INVALID; }
+    if (L->storage < LBM_F64 || L->storage > LBM_F16) { why = "unknown storage"; return LBM_E_INVALID; }
+    if (L->phi_scheme != LBM_PHI_UPWIND && L->phi_scheme != LBM_PHI_CENTRAL) { why = "unknown phi_scheme"; return LBM_E_INVALID; }
+    return LBM_OK;
+}
+
+int fill_sim(SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, double tau_g, const lbm_force* F,
+             const lbm_heat* H, std::string& why)
+{
+    std::memset(&s, 0, sizeof(s));
+    if (!E) { why = "eos is NULL"; return LBM_E_INVALID; }
+    if (E->kind < LBM_IDEAL || E->kind > LBM_PR) { why = "unknown eos kind"; return LBM_E_INVALID; }
+    if (!(E->R > 0) || !(E->cv > 0)) { why = "R and cv must be > 0"; return LBM_E_INVALID; }
+    if (!(tau_f > 0) || !(tau_g > 0)) { why = "tau_f and tau_g must be > 0"; return LBM_E_INVALID; }
+    if (E->t_solver != LBM_T_NEWTON && E->t_solver != LBM_T_MLP) { why = "unknown t_solver"; return LBM_E_INVALID; }
+    s.nx = L->nx; s.ny = L->ny; s.nz = L->nz; s.zwalls = L->zwalls;
+    s.N = (long long)L->nx * L->ny * L->nz;
+    s.eos = E->kind;
+    s.phi_central = L->phi_scheme == LBM_PHI_CENTRAL;
+    s.t_solver = E->t_solver;
+    s.R = E->R; s.cv = E->cv; s.a = E->a; s.b = E->b; s.Tc = E->Tc;
+    if (E->kind == LBM_PR) {
+        if (!(E->Tc > 0)) { why = "Peng-Robinson needs Tc > 0"; return LBM_E_INVALID; }
+        if (E->a == 0.0) {
+            if (!(E->Pc > 0)) { why = "Peng-Robinson needs a, b or Pc > 0"; return LBM_E_INVALID; }
+            s.a = 0.45724 * E->R * E->R * E->Tc * E->Tc / E->Pc;
+            s.b = 0.07780 * E->R * E->Tc / E->Pc;
+        }
+        s.kw = 0.37464 + 1.54226 * E->omega - 0.26992 * E->omega * E->omega;
+        if (!(s.b > 0)) { why = "Peng-Robinson needs b > 0"; return LBM_E_INVALID; }
+    }
+    if (E->kind == LBM_VDW && (E->a < 0 || E->b < 0)) { why = "van der Waals needs a, b >= 0"; return LBM_E_INVALID; }
+    s.kappa = E->kappa; s.eta_mu = E->eta_over_mu; s.k_mu = E->k_over_mu;
+    s.beta_f = 1.0 / (2.0 * tau_f + 1.0);
+    s.beta_g = 1.0 / (2.0 * tau_g + 1.0);
+    if (F) { s.acc[0] = F->accel[0]; s.acc[1] = F->accel[1]; s.acc[2] = L->dim == 3 ? F->accel[2] : 0.0; }
+    s.inv_cv = 1.0 / s.cv;
+    s.inv_Tc = s.Tc > 0 ? 1.0 / s.Tc : 0.0;
+    s.lam_c = s.b > 0 ? 1.0 / (2.0 * std::sqrt(2.0) * s.b) : 0.0;
+    s.athe_c = (double)(L->dim + 2) / (double)L->dim - s.eta_mu;
+    if (H) { s.q = H->q; s.zlo = H->zmask_lo; s.zhi = H->zmask_hi; }
+    return LBM_OK;
+}
+
+void free_all(lbm_ctx* h)
+{
+    void* ptrs[] = {h->d_sims, h->d_table, h->d_sim_block_start, h->d_tiles, h->pop[0], h->pop[1],
+                    h->W, h->M, h->d_diag, h->d_partials};
+    for (void* p : ptrs) lbm_glue_free(p);
+    h->d_sims = nullptr; h->d_table = nullptr; h->d_sim_block_start = nullptr; h->d_tiles = nullptr;
+    h->pop[0] = h->pop[1] = nullptr; h->W = nullptr; h->M = nullptr; h->d_diag = nullptr; h->d_partials = nullptr;
+}
+
+int upload_sims(lbm_ctx* h)
+{
+    LBM_CUDA_CHECK(h, cudaMemcpyAsync(h->d_sims, h->sims.data(), h->sims.size() * sizeof(SimDev),
+                                      cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int build_tiles(lbm_ctx* h, int tx, int ty, int tz)
+{
+    h->tiles.clear();
+    for (int s = 0; s < h->nsim; ++s) {
+        const SimDev& d = h->sims[s];
+        int zt = h->dim == 3 ? tz : 1;
+        for (int z0 = 0; z0 < d.nz; z0 += zt)
+            for (int y0 = 0; y0 < d.ny; y0 += ty)
+                for (int x0 = 0; x0 < d.nx; x0 += tx) h->tiles.push_back(TileEntry{s, x0, y0, z0});
+    }
+    lbm_glue_free(h->d_tiles);
+    h->d_tiles = (TileEntry*)dev_alloc(h, h->tiles.size() * sizeof(TileEntry));
+    if (!h->d_tiles) return fail(h, LBM_E_NOMEM, "tile table allocation failed");
+    LBM_CUDA_CHECK(h, cudaMemcpyAsync(h->d_tiles, h->tiles.data(), h->tiles.size() * sizeof(TileEntry),
+                                      cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* tau_f, const double* tau_g,
+                const lbm_force* F, const lbm_heat* H, lbm_handle* out)
+{
+    if (!out) return fail(nullptr, LBM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (nsim < 1) return fail(nullptr, LBM_E_INVALID, "nsim must be >= 1");
+    if (!L || !E || !tau_f || !tau_g) return fail(nullptr, LBM_E_INVALID, "NULL argument");
+    std::string why;
+    for (int s = 0; s < nsim; ++s) {
+        int rc = check_lattice(&L[s], why);
+        if (rc) return fail(nullptr, rc, "simulation " + std::to_string(s) + ": " + why);
+        if (L[s].dim != L[0].dim || L[s].storage != L[0].storage)
+            return fail(nullptr, LBM_E_INVALID, "all simulations of a batch must share dim and storage");
+    }
+    lbm_ctx* h = new lbm_ctx();
+    h->nsim = nsim;
+    h->dim = L[0].dim;
+    h->Q = h->dim == 2 ? 9 : 27;
+    h->storage = L[0].storage;
+    if (!pick_ops(h->dim, h->storage, h->ops, h->rbytes, h->sbytes)) {
+        delete h;
+        return fail(nullptr, LBM_E_UNSUPPORTED, "lattice/storage combination not built");
+    }
+    h->sims.resize(nsim);
+    long long cells = 0, pops = 0;
+    for (int s = 0; s < nsim; ++s) {
+        int rc = fill_sim(h->sims[s], &L[s], &E[s], tau_f[s], tau_g[s], F ? &F[s] : nullptr, H ? &H[s] : nullptr, why);
+        if (rc) {
+            delete h;
+            return fail(nullptr, rc, "simulation " + std::to_string(s) + ": " + why);
+        }
+        h->sims[s].cell_off = cells;
+        h->sims[s].pop_off = pops;
+        cells += h->sims[s].N;
+        pops += 2LL * h->Q * h->sims[s].N;
+    }
+    h->Ntot = cells;
+    h->pop_elems = pops;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) {
+        delete h;
+        return fail(nullptr, LBM_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+    }
+    h->device = dev;
+    h->stream = (cudaStream_t)lbm_glue_current_stream(dev);
+
+    // block table of the per-cell kernels
+    for (int s = 0; s < nsim; ++s) {
+        h->sim_block_start.push_back((int)h->table.size());
+        for (long long k = 0; k < h->sims[s].N; k += kBlockCells) h->table.push_back(BlockEntry{s, (int)k});
+    }
+    h->sim_block_start.push_back((int)h->table.size());
+    const int nv = 2 * h->dim + 3;
+
+    h->d_sims = (SimDev*)dev_alloc(h, nsim * sizeof(SimDev));
+    h->d_table = (BlockEntry*)dev_alloc(h, h->table.size() * sizeof(BlockEntry));
+    h->d_sim_block_start = (int*)dev_alloc(h, h->sim_block_start.size() * sizeof(int));
+    h->pop[0] = dev_alloc(h, (size_t)pops * h->sbytes);
+    h->pop[1] = dev_alloc(h, (size_t)pops * h->sbytes);
+    h->W = dev_alloc(h, (size_t)W_NF * cells * h->rbytes);
+    h->M = dev_alloc(h, (size_t)2 * M_NF * cells * h->rbytes);
+    h->d_diag = (unsigned long long*)dev_alloc(h, 4 * sizeof(unsigned long long));
+    h->d_partials = (double*)dev_alloc(h, h->table.size() * nv * sizeof(double));
+    if (!h->d_sims || !h->d_table || !h->d_sim_block_start || !h->pop[0] || !h->pop[1] || !h->W || !h->M ||
+        !h->d_diag || !h->d_partials) {
+        free_all(h);
+        delete h;
+        return fail(nullptr, LBM_E_NOMEM,
+                    "device allocation failed (torch.cuda must be initialised; populations need " +
+                        std::to_string(2.0 * (double)pops * (double)h->sbytes * 1e-9) + " GB)");
+    }
+    int rc = LBM_OK;
+    auto chk = [&](cudaError_t e, const char* w) {
+        if (e != cudaSuccess && rc == LBM_OK) rc = cuda_fail(h, e, w);
+    };
+    chk(cudaMemcpyAsync(h->d_table, h->table.data(), h->table.size() * sizeof(BlockEntry), cudaMemcpyHostToDevice,
+                        h->stream), "table upload");
+    chk(cudaMemcpyAsync(h->d_sim_block_start, h->sim_block_start.data(), h->sim_block_start.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, h->stream), "table upload");
+    chk(cudaMemsetAsync(h->d_diag, 0, 4 * sizeof(unsigned long long), h->stream), "diag reset");
+    chk(cudaMemsetAsync(h->W, 0, (size_t)W_NF * cells * h->rbytes, h->stream), "work reset");
+    if (rc == LBM_OK) rc = upload_sims(h);
+    if (rc == LBM_OK) {
+        // default kernel: the fused one-pass step with its default tile when it runs this lattice
+        int dtx, dty, dtz;
+        fused_default_tile(h->dim, h->storage, dtx, dty, dtz);
+        if (h->ops.fused_ok(h, dtx, dty, dtz)) {
+            h->variant = LBM_KERNEL_FUSED;
+            h->tx = dtx; h->ty = dty; h->tz = dtz;
+            rc = build_tiles(h, dtx, dty, dtz);
+        } else {
+            h->variant = LBM_KERNEL_SPLIT;
+        }
+    }
+    if (rc != LBM_OK) {
+        g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_create(const lbm_lattice* lattice, const lbm_eos* eos, double tau_f, double tau_g, const lbm_force* force,
+               const lbm_heat* heat, lbm_handle* out)
+{
+    return create_impl(1, lattice, eos, &tau_f, &tau_g, force, heat, out);
+}
+
+int lbm_create_batch(int nsim, const lbm_lattice* lattices, const lbm_eos* eos, const double* tau_f,
+                     const double* tau_g, const lbm_force* force, const lbm_heat* heat, lbm_handle* out)
+{
+    return create_impl(nsim, lattices, eos, tau_f, tau_g, force, heat, out);
+}
+
+void lbm_destroy(lbm_handle h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+int lbm_set_stream(lbm_handle h, void* stream)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+    h->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T, int on_device)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (!rho || !u || !T) return fail(h, LBM_E_INVALID, "rho, u and T are required");
+    const long long N = h->Ntot;
+    const size_t nb_s = (size_t)N * sizeof(double), nb_v = (size_t)N * h->dim * sizeof(double);
+    std::vector<double> hr, hu, hT;
+    const double *dr = rho, *du = u, *dT = T;
+    void* tmp = nullptr;
+    if (!on_device || h->storage == LBM_BF16 || h->storage == LBM_F16) {
+        // host copies (inputs, or the means for the 16-bit storage offsets)
+        hr.resize(N); hu.resize((size_t)N * h->dim); hT.resize(N);
+        cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        LBM_CUDA_CHECK(h, cudaMemcpyAsync(hr.data(), rho, nb_s, kind, h->stream));
+        LBM_CUDA_CHECK(h, cudaMemcpyAsync(hu.data(), u, nb_v, kind, h->stream));
+        LBM_CUDA_CHECK(h, cudaMemcpyAsync(hT.data(), T, nb_s, kind, h->stream));
+        LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+        for (long long k = 0; k < N; ++k)
+            if (!(hr[k] > 0) || !(hT[k] > 0)) return fail(h, LBM_E_INVALID, "rho and T must be > 0 everywhere");
+    }
+    if (h->storage == LBM_BF16 || h->storage == LBM_F16) {
+        for (int s = 0; s < h->nsim; ++s) {
+            SimDev& d = h->sims[s];
+            double mr = 0, mT = 0;
+            for (long long k = 0; k < d.N; ++k) { mr += hr[d.cell_off + k]; mT += hT[d.cell_off + k]; }
+            mr /= (double)d.N;
+            mT /= (double)d.N;
+            RhoPart<double> p = rho_part<double>(d, mr);
+            double th = eos_P<double>(d, p, mT) / mr, e = eos_e<double>(d, p, mT), u0[3] = {0, 0, 0};
+            double f[27], g[27];
+            if (h->dim == 2) equilibria<2, double>(mr, u0, th, e, f, g);
+            else equilibria<3, double>(mr, u0, th, e, f, g);
+            for (int i = 0; i < h->Q; ++i) { d.fref[i] = (float)f[i]; d.gref[i] = (float)g[i]; }
+        }
+        int rc = upload_sims(h);
+        if (rc) return rc;
+    }
+    if (!on_device) {
+        tmp = dev_alloc(h, 2 * nb_s + nb_v);
+        if (!tmp) return fail(h, LBM_E_NOMEM, "staging allocation failed");
+        double* t = (double*)tmp;
+        LBM_CUDA_CHECK(h, cudaMemcpyAsync(t, hr.data(), nb_s, cudaMemcpyHostToDevice, h->stream));
+        LBM_CUDA_CHECK(h, cudaMemcpyAsync(t + N, hT.data(), nb_s, cudaMemcpyHostToDevice, h->stream));
+        LBM_CUDA_CHECK(h, cudaMemcpyAsync(t + 2 * N, hu.data(), nb_v, cudaMemcpyHostToDevice, h->stream));
+        dr = t; dT = t + N; du = t + 2 * N;
+    }
+    LBM_CUDA_CHECK(h, cudaMemsetAsync(h->d_diag, 0, 4 * sizeof(unsigned long long), h->stream));
+    int rc = h->ops.init(h, dr, du, dT);
+    cudaError_t se = cudaStreamSynchronize(h->stream);
+    lbm_glue_free(tmp);
+    if (rc) return rc;
+    if (se != cudaSuccess) return cuda_fail(h, se, "lbm_init");
+    h->initialized = true;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle h, int n)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (n < 0) return fail(h, LBM_E_INVALID, "n must be >= 0");
+    if (!h->initialized) return fail(h, LBM_E_STATE, "lbm_init has not been called");
+    return h->ops.step(h, n);
+}
+
+int lbm_moments(lbm_handle h, double* rho, double* u, double* T, int on_device)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (!h->initialized) return fail(h, LBM_E_STATE, "lbm_init has not been called");
+    int rc = h->ops.macro(h);
+    if (rc) return rc;
+    const long long N = h->Ntot;
+    if (on_device) {
+        rc = h->ops.export_moments(h, rho, u, T);
+        if (rc) return rc;
+        LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+        return LBM_OK;
+    }
+    const size_t nb_s = (size_t)N * sizeof(double), nb_v = (size_t)N * h->dim * sizeof(double);
+    double* t = (double*)dev_alloc(h, 2 * nb_s + nb_v);
+    if (!t) return fail(h, LBM_E_NOMEM, "staging allocation failed");
+    rc = h->ops.export_moments(h, t, t + 2 * N, t + N);
+    if (rc == LBM_OK) {
+        cudaError_t e = cudaSuccess;
+        if (rho && e == cudaSuccess) e = cudaMemcpyAsync(rho, t, nb_s, cudaMemcpyDeviceToHost, h->stream);
+        if (T && e == cudaSuccess) e = cudaMemcpyAsync(T, t + N, nb_s, cudaMemcpyDeviceToHost, h->stream);
+        if (u && e == cudaSuccess) e = cudaMemcpyAsync(u, t + 2 * N, nb_v, cudaMemcpyDeviceToHost, h->stream);
+        cudaError_t se = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = se;
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "lbm_moments copy");
+    }
+    lbm_glue_free(t);
+    return rc;
+}
+
+int lbm_populations(lbm_handle h, double* f, double* g, int on_device)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (!h->initialized) return fail(h, LBM_E_STATE, "lbm_init has not been called");
+    const size_t nb = (size_t)h->Ntot * h->Q * sizeof(double);
+    if (on_device) {
+        int rc = h->ops.export_pops(h, f, g);
+        if (rc) return rc;
+        LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+        return LBM_OK;
+    }
+    double* t = (double*)dev_alloc(h, 2 * nb);
+    if (!t) return fail(h, LBM_E_NOMEM, "staging allocation failed");
+    int rc = h->ops.export_pops(h, t, t + h->Ntot * h->Q);
+    if (rc == LBM_OK) {
+        cudaError_t e = cudaSuccess;
+        if (f) e = cudaMemcpyAsync(f, t, nb, cudaMemcpyDeviceToHost, h->stream);
+        if (g && e == cudaSuccess) e = cudaMemcpyAsync(g, t + h->Ntot * h->Q, nb, cudaMemcpyDeviceToHost, h->stream);
+        cudaError_t se = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = se;
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "lbm_populations copy");
+    }
+    lbm_glue_free(t);
+    return rc;
+}
+
+int lbm_invariants(lbm_handle h, double* out)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (!out) return fail(h, LBM_E_INVALID, "out is NULL");
+    if (!h->initialized) return fail(h, LBM_E_STATE, "lbm_init has not been called");
+    int rc = h->ops.macro(h);
+    if (rc) return rc;
+    const int nv = 2 * h->dim + 3;
+    double* t = (double*)dev_alloc(h, (size_t)h->nsim * nv * sizeof(double));
+    if (!t) return fail(h, LBM_E_NOMEM, "staging allocation failed");
+    rc = h->ops.invariants(h, t);
+    if (rc == LBM_OK) {
+        cudaError_t e = cudaMemcpyAsync(out, t, (size_t)h->nsim * nv * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        cudaError_t se = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = se;
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "lbm_invariants copy");
+    }
+    lbm_glue_free(t);
+    return rc;
+}
+
+int lbm_diagnostics(lbm_handle h, long long out[4])
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (!out) return fail(h, LBM_E_INVALID, "out is NULL");
+    unsigned long long v[4];
+    LBM_CUDA_CHECK(h, cudaMemcpyAsync(v, h->d_diag, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < 4; ++i) out[i] = (long long)v[i];
+    return LBM_OK;
+}
+
+int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (variant == LBM_KERNEL_SPLIT) {
+        h->variant = LBM_KERNEL_SPLIT;
+        return LBM_OK;
+    }
+    if (variant != LBM_KERNEL_FUSED && variant != LBM_KERNEL_AUTO) return fail(h, LBM_E_INVALID, "unknown variant");
+    int dtx, dty, dtz;
+    fused_default_tile(h->dim, h->storage, dtx, dty, dtz);
+    if (tx <= 0) tx = dtx;
+    if (ty <= 0) ty = dty;
+    if (tz <= 0) tz = h->dim == 3 ? dtz : 1;
+    if (h->dim == 2) tz = 1;
+    if (!h->ops.fused_ok(h, tx, ty, tz)) {
+        if (variant == LBM_KERNEL_AUTO) {
+            h->variant = LBM_KERNEL_SPLIT;
+            return LBM_OK;
+        }
+        return fail(h, LBM_E_INVALID, "the fused kernel cannot run this tile (shared memory or shape)");
+    }
+    LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+    int rc = build_tiles(h, tx, ty, tz);
+    if (rc) return rc;
+    h->variant = LBM_KERNEL_FUSED;
+    h->tx = tx; h->ty = ty; h->tz = tz;
+    return LBM_OK;
+}
+
+int lbm_get_kernel(lbm_handle h, int* variant, int* tx, int* ty, int* tz)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (variant) *variant = h->variant;
+    if (tx) *tx = h->tx;
+    if (ty) *ty = h->ty;
+    if (tz) *tz = h->tz;
+    return LBM_OK;
+}
+
+const char* lbm_last_error(lbm_handle h)
+{
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+}  // extern "C"

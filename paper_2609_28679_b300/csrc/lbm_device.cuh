@@ -1,0 +1,436 @@
+// Device building blocks of one time step of the consistent DDF lattice
+// Boltzmann scheme (arxiv 2609.28679, Sec. II): lattice, population storage
+// codecs, equations of state, per-cell macroscopic state and the collision.
+// Shared by the split (three-pass) and fused (one-pass) step kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Lattice (Eq. D3Q27c; D2Q9 is its restriction to two axes).  Direction i has
+// base-3 digits (d0, d1, d2); digit 0, 1, 2 means c = 0, +1, -1, which is also
+// the index into the per-axis factor triples below.
+// ---------------------------------------------------------------------------
+template <int D> struct Lat { static constexpr int Q = (D == 2) ? 9 : 27; };
+
+__host__ __device__ constexpr int dig(int i, int a) { return a == 0 ? i % 3 : (a == 1 ? (i / 3) % 3 : (i / 9) % 3); }
+__host__ __device__ constexpr int cval(int d) { return d == 0 ? 0 : (d == 1 ? 1 : -1); }
+__host__ __device__ constexpr int cc(int i, int a) { return cval(dig(i, a)); }
+__host__ __device__ constexpr int odig(int d) { return d == 0 ? 0 : 3 - d; }
+__host__ __device__ constexpr int opp(int i) { return odig(i % 3) + 3 * odig((i / 3) % 3) + 9 * odig((i / 9) % 3); }
+__host__ __device__ constexpr int cnorm2(int i) { return cc(i, 0) * cc(i, 0) + cc(i, 1) * cc(i, 1) + cc(i, 2) * cc(i, 2); }
+
+enum { EOS_IDEAL = 0, EOS_VDW = 1, EOS_PR = 2 };
+
+// Per-simulation constants, resident in device memory.
+struct SimDev {
+    int nx, ny, nz, zwalls;
+    long long N;         // cells
+    long long pop_off;   // element offset of this simulation's f block; g follows at +Q*N
+    long long cell_off;  // element offset of its cells in per-cell arrays
+    int eos, phi_central, t_solver, zlo, zhi;
+    int pad_;
+    double R, cv, a, b, Tc, kw;   // kw: Soave kappa(omega) for Peng-Robinson
+    double kappa, eta_mu, k_mu;   // Korteweg coefficient, eta/mu, k/mu
+    double beta_f, beta_g;        // 1/(2 tau + 1)
+    double acc[3], q;             // body acceleration, heat source
+    double inv_cv, inv_Tc, lam_c; // 1/cv, 1/Tc, 1/(2 sqrt2 b) (Peng-Robinson)
+    double athe_c;                // (D+2)/D - eta/mu
+    float fref[27], gref[27];     // storage offsets (16-bit storage only; zero otherwise)
+};
+
+// ---------------------------------------------------------------------------
+// Storage codecs: populations are stored as S, computed in R.
+// ---------------------------------------------------------------------------
+template <typename S, typename R> struct Codec;
+template <> struct Codec<double, double> {
+    static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+    static constexpr bool offset = false;
+};
+template <> struct Codec<float, float> {
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+    static constexpr bool offset = false;
+};
+template <> struct Codec<__nv_bfloat16, float> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    static constexpr bool offset = true;
+};
+template <> struct Codec<__half, float> {
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+    static constexpr bool offset = true;
+};
+
+// ---------------------------------------------------------------------------
+// Equations of state.  Per cell, the density-only parts are evaluated once
+// (RhoPart, with the reciprocals the T-dependent parts need), then P, e and
+// the derivatives as functions of T.
+// ---------------------------------------------------------------------------
+template <typename R> struct RhoPart {
+    R rho, id1, iden, lam;  // 1/(1 - b rho); 1/(1 + 2 b rho - b^2 rho^2); Lambda(rho) (Peng-Robinson)
+};
+
+template <typename R> __host__ __device__ __forceinline__ RhoPart<R> rho_part(const SimDev& s, R rho)
+{
+    RhoPart<R> p;
+    p.rho = rho;
+    p.id1 = R(1);
+    p.iden = R(1);
+    p.lam = R(0);
+    if (s.eos == EOS_IDEAL) return p;
+    const R b = (R)s.b;
+    p.id1 = R(1) / (R(1) - b * rho);
+    if (s.eos == EOS_PR) {
+        const R r2 = (R)1.4142135623730951;
+        const R br = b * rho;
+        p.iden = R(1) / (R(1) + R(2) * br - br * br);
+        // Lambda = int_0^rho dr/(1 + 2 b r - b^2 r^2) = ln[(1 + (1+sqrt2) b rho)/(1 + (1-sqrt2) b rho)] / (2 sqrt2 b)
+        p.lam = log((R(1) + (R(1) + r2) * br) / (R(1) + (R(1) - r2) * br)) * (R)s.lam_c;
+    }
+    return p;
+}
+
+template <typename R> __host__ __device__ __forceinline__ R pr_sq(const SimDev& s, R T) { return sqrt(T * (R)s.inv_Tc); }
+
+template <typename R> __host__ __device__ __forceinline__ R eos_P(const SimDev& s, const RhoPart<R>& p, R T)
+{
+    const R rho = p.rho;
+    if (s.eos == EOS_IDEAL) return rho * (R)s.R * T;
+    if (s.eos == EOS_VDW) return rho * (R)s.R * T * p.id1 - (R)s.a * rho * rho;
+    const R m = R(1) + (R)s.kw * (R(1) - pr_sq<R>(s, T));
+    return rho * (R)s.R * T * p.id1 - (R)s.a * m * m * rho * rho * p.iden;
+}
+
+template <typename R> __host__ __device__ __forceinline__ R eos_e(const SimDev& s, const RhoPart<R>& p, R T)
+{
+    if (s.eos == EOS_IDEAL) return (R)s.cv * T;
+    if (s.eos == EOS_VDW) return (R)s.cv * T - (R)s.a * p.rho;
+    const R k = (R)s.kw;
+    return (R)s.cv * T - (R)s.a * (R(1) + k) * (R(1) + k - k * pr_sq<R>(s, T)) * p.lam;
+}
+
+// c_v = (de/dT)_rho
+template <typename R> __host__ __device__ __forceinline__ R eos_cv(const SimDev& s, const RhoPart<R>& p, R T)
+{
+    if (s.eos != EOS_PR) return (R)s.cv;
+    const R k = (R)s.kw;
+    return (R)s.cv + (R)s.a * (R(1) + k) * k * p.lam * R(0.5) * (R)s.inv_Tc / pr_sq<R>(s, T);
+}
+
+// P, (dP/dT)_rho, (dP/drho)_T and c_v at (rho, T) with shared subexpressions
+template <typename R> struct Thermo {
+    R P, PT, Pr, cv;
+};
+
+template <typename R> __host__ __device__ __forceinline__ Thermo<R> thermo(const SimDev& s, const RhoPart<R>& p, R T)
+{
+    Thermo<R> t;
+    const R rho = p.rho, Rg = (R)s.R;
+    if (s.eos == EOS_IDEAL) {
+        t.PT = rho * Rg;
+        t.P = t.PT * T;
+        t.Pr = Rg * T;
+        t.cv = (R)s.cv;
+    } else if (s.eos == EOS_VDW) {
+        t.PT = rho * Rg * p.id1;
+        t.P = t.PT * T - (R)s.a * rho * rho;
+        t.Pr = Rg * T * p.id1 * p.id1 - R(2) * (R)s.a * rho;
+        t.cv = (R)s.cv;
+    } else {
+        const R k = (R)s.kw, b = (R)s.b, a = (R)s.a;
+        const R sq = pr_sq<R>(s, T), isq = R(1) / sq;
+        const R m = R(1) + k * (R(1) - sq);
+        const R q = rho * rho * p.iden;                       // rho^2 / den
+        const R dq = (R(2) * rho - q * (R(2) * b - R(2) * b * b * rho)) * p.iden;  // d(rho^2/den)/drho
+        const R dal = -m * k * isq * (R)s.inv_Tc;             // d alpha / dT
+        t.P = rho * Rg * T * p.id1 - a * m * m * q;
+        t.PT = rho * Rg * p.id1 - a * dal * q;
+        t.Pr = Rg * T * p.id1 * p.id1 - a * m * m * dq;
+        t.cv = (R)s.cv + a * (R(1) + k) * k * p.lam * R(0.5) * (R)s.inv_Tc * isq;
+    }
+    return t;
+}
+
+template <typename R> __device__ __forceinline__ R eos_dPdT(const SimDev& s, const RhoPart<R>& p, R T)
+{
+    return thermo<R>(s, p, T).PT;
+}
+
+template <typename R> __device__ __forceinline__ R eos_dPdrho(const SimDev& s, const RhoPart<R>& p, R T)
+{
+    return thermo<R>(s, p, T).Pr;
+}
+
+// Newton's method on e(rho, T) - e = 0 for Peng-Robinson, in precision W.
+// Returns the iteration count (cap + 1 when the cap was hit).
+template <typename W>
+__device__ __forceinline__ int pr_newton(const SimDev& s, const RhoPart<W>& p, W e, W& T, W tol, int cap)
+{
+    for (int it = 1; it <= cap; ++it) {
+        W r = eos_e<W>(s, p, T) - e;
+        W dT = -r / eos_cv<W>(s, p, T);
+        T += dT;
+        if (fabs(dT) <= tol * fabs(T)) return it;
+    }
+    return cap + 1;
+}
+
+// T(rho, e): explicit for ideal gas and van der Waals (Eqs. idealgasT,
+// lbm_temp); Peng-Robinson by Newton from Tguess -- in float64 for the
+// float64 path; in float32 with a float64 fallback for the float32 path.
+template <typename R>
+__device__ __forceinline__ R eos_T(const SimDev& s, const RhoPart<R>& p, R e, R Tguess, bool& capped)
+{
+    capped = false;
+    if (s.eos == EOS_IDEAL) return e * (R)s.inv_cv;
+    if (s.eos == EOS_VDW) return (e + (R)s.a * p.rho) * (R)s.inv_cv;
+    R T = Tguess > R(0) ? Tguess : e * (R)s.inv_cv;
+    if (sizeof(R) == 8) {
+        int it = pr_newton<R>(s, p, e, T, (R)1e-14, 50);
+        capped = it > 50;
+        return T;
+    }
+    int it = pr_newton<R>(s, p, e, T, (R)1e-6, 8);
+    if (it <= 8 && T > R(0)) return T;
+    RhoPart<double> pd = rho_part<double>(s, (double)p.rho);
+    double Td = (Tguess > R(0)) ? (double)Tguess : (double)e * s.inv_cv;
+    int itd = pr_newton<double>(s, pd, (double)e, Td, 1e-12, 50);
+    capped = itd > 50;
+    return (R)Td;
+}
+
+// ---------------------------------------------------------------------------
+// Macroscopic state of one cell (flowchart boxes 2-3): from the moments
+// rho, j = sum c f, G = sum g, the force F and source Q.
+// ---------------------------------------------------------------------------
+template <typename R> struct Macro {
+    R rho, ir, u[3], F[3], Q, T, P, theta, h, cv, icv, gam, athe, e;
+};
+
+template <int D, typename R>
+__device__ __forceinline__ Macro<R> macro_cell(const SimDev& s, R rho, const R* j, R G, const R* F, R Q, R Tguess,
+                                               unsigned& flags)
+{
+    Macro<R> m;
+    m.rho = rho;
+    m.ir = R(1) / rho;
+    m.Q = Q;
+    R uF = 0, u2 = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        m.F[a] = a < D ? F[a] : R(0);
+        m.u[a] = a < D ? (j[a] + R(0.5) * F[a]) * m.ir : R(0);  // Eq. def_u
+        uF += m.u[a] * m.F[a];
+        u2 += m.u[a] * m.u[a];
+    }
+    const R rhoE = G + R(0.5) * (uF + Q);  // Eq. def_E
+    const R e = rhoE * m.ir - R(0.5) * u2;
+    const RhoPart<R> p = rho_part<R>(s, rho);
+    bool capped;
+    const R T = eos_T<R>(s, p, e, Tguess, capped);
+    const Thermo<R> t = thermo<R>(s, p, T);
+    const R th = t.P * m.ir;  // Eq. theta
+    m.icv = s.eos == EOS_PR ? R(1) / t.cv : (R)s.inv_cv;
+    const R cs2 = t.Pr + T * t.PT * t.PT * m.ir * m.ir * m.icv;
+    m.T = T;
+    m.P = t.P;
+    m.theta = th;
+    m.h = e + th;  // Eq. enthalpy: h = e + P/rho
+    m.cv = t.cv;
+    m.gam = R(1) + t.PT * m.ir * m.icv;  // Eq. corr_heat_source
+    m.athe = (R)s.athe_c * th - cs2;     // alpha theta, Eq. corr_bulk: ((D+2)/D - eta/mu) theta - c_s^2
+    m.e = e;
+    if (capped) flags |= 4u;
+    if (!(th > R(0))) flags |= 2u;
+    if (!isfinite(rho) || !isfinite(T) || !isfinite(u2)) flags |= 1u;
+    return m;
+}
+
+// X_alpha = rho u_alpha^3 + 3 rho u_alpha (theta - 1/3), the flux whose
+// derivative is the Galilean correction Phi (Eq. correction).
+template <typename R> __device__ __forceinline__ R xflux(R rho, R u, R th)
+{
+    return rho * u * (u * u + R(3) * th - R(1));
+}
+
+// ---------------------------------------------------------------------------
+// Collision of one cell (Eqs. LBMeq, LBMstar, LBMeqG, LBMgstar, LBM_f, LBM_g).
+// f, g: pre-collision populations in, post-collision out.
+// ---------------------------------------------------------------------------
+template <typename R> __host__ __device__ __forceinline__ void psi3(R xi, R zeta, R* o)
+{
+    // Eq. phi at c = 0, +1, -1
+    o[0] = R(1) - zeta;
+    o[1] = R(0.5) * (zeta + xi);
+    o[2] = R(0.5) * (zeta - xi);
+}
+
+// Psi(c; O, O^2) applied to u^2/2, with O = theta d/du + u (Eq. Oa):
+// O(u^2/2) = theta u + u^3/2, O^2(u^2/2) = theta^2 + 5/2 theta u^2 + u^4/2.
+template <typename R> __host__ __device__ __forceinline__ void hpsi3(R u, R th, R* o)
+{
+    R u2 = u * u;
+    R o1 = th * u + R(0.5) * u2 * u;
+    R o2 = th * th + R(2.5) * th * u2 + R(0.5) * u2 * u2;
+    o[0] = R(0.5) * u2 - o2;
+    o[1] = R(0.5) * (o2 + o1);
+    o[2] = R(0.5) * (o2 - o1);
+}
+
+template <int D, typename R>
+__device__ __forceinline__ void collide_cell(const SimDev& s, const Macro<R>& m, R divu, const R* gh, const R* gT,
+                                             const R* Phi, R* f, R* g)
+{
+    constexpr int Q = Lat<D>::Q;
+    const R rho = m.rho;
+    // shifted states (Eqs. sh_vel_1, sh_temp_1, sh_T_1, qc_1), lambda = dt = 1
+    R us[3], qc[3], FF = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        us[a] = a < D ? m.u[a] + m.F[a] * m.ir : R(0);
+        FF += m.F[a] * m.F[a];
+        qc[a] = a < D ? m.P * (gh[a] - (R)s.k_mu * gT[a]) : R(0);
+    }
+    R ths = m.theta + m.athe * divu + (m.gam - R(1)) * m.Q * m.ir;
+    R Ts = m.T + (m.Q * m.ir - R(0.5) * FF * m.ir * m.ir) * m.icv;
+    RhoPart<R> p = rho_part<R>(s, rho);
+    R es = eos_e<R>(s, p, Ts);
+
+    // per-axis factors
+    R A0[3][3], As[3][3], B0[3][3], H0[3][3], Hs[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        psi3<R>(m.u[a], m.theta + m.u[a] * m.u[a], A0[a]);              // f^eq, g^eq
+        psi3<R>(us[a], ths + us[a] * us[a] + Phi[a], As[a]);            // f*
+        psi3<R>(us[a], ths + us[a] * us[a], B0[a]);                     // g* (no Phi)
+        hpsi3<R>(m.u[a], m.theta, H0[a]);
+        hpsi3<R>(us[a], ths, Hs[a]);
+    }
+    const R bf = (R)s.beta_f, bg = (R)s.beta_g;
+    const R cf0 = R(1) - R(2) * bf, cf1 = R(3) * bf - R(1), cf2 = R(1) - bf;
+    const R cg0 = R(1) - R(2) * bg, cg1 = R(3) * bg - R(1), cg2 = R(1) - bg;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int d0 = dig(i, 0), d1 = dig(i, 1), d2 = dig(i, 2);
+        R feq, fst, geq, gst;
+        if (D == 2) {
+            feq = rho * A0[0][d0] * A0[1][d1];
+            fst = rho * As[0][d0] * As[1][d1];
+            geq = rho * (m.e * A0[0][d0] * A0[1][d1] + H0[0][d0] * A0[1][d1] + A0[0][d0] * H0[1][d1]);
+            gst = rho * (es * B0[0][d0] * B0[1][d1] + Hs[0][d0] * B0[1][d1] + B0[0][d0] * Hs[1][d1]);
+        } else {
+            R a01 = A0[0][d0] * A0[1][d1];
+            feq = rho * a01 * A0[2][d2];
+            fst = rho * As[0][d0] * As[1][d1] * As[2][d2];
+            geq = rho * ((m.e * a01 + H0[0][d0] * A0[1][d1] + A0[0][d0] * H0[1][d1]) * A0[2][d2] + a01 * H0[2][d2]);
+            R b01 = B0[0][d0] * B0[1][d1];
+            gst = rho * ((es * b01 + Hs[0][d0] * B0[1][d1] + B0[0][d0] * Hs[1][d1]) * B0[2][d2] + b01 * Hs[2][d2]);
+        }
+        if (cnorm2(i) == 1) {
+            R cq = R(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) cq += R(cc(i, a)) * qc[a];
+            gst += R(0.5) * cq;
+        }
+        // f' = f + 2 beta (f^eq - f) + (1 - beta)(f* - f^eq)
+        f[i] = cf0 * f[i] + cf1 * feq + cf2 * fst;
+        g[i] = cg0 * g[i] + cg1 * geq + cg2 * gst;
+    }
+}
+
+// Rest equilibria (used for initialisation and the 16-bit storage offsets).
+template <int D, typename R>
+__host__ __device__ __forceinline__ void equilibria(R rho, const R* u, R theta, R e, R* f, R* g)
+{
+    constexpr int Q = Lat<D>::Q;
+    R A0[3][3], H0[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        psi3<R>(u[a], theta + u[a] * u[a], A0[a]);
+        hpsi3<R>(u[a], theta, H0[a]);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int d0 = dig(i, 0), d1 = dig(i, 1), d2 = dig(i, 2);
+        if (D == 2) {
+            f[i] = rho * A0[0][d0] * A0[1][d1];
+            g[i] = rho * (e * A0[0][d0] * A0[1][d1] + H0[0][d0] * A0[1][d1] + A0[0][d0] * H0[1][d1]);
+        } else {
+            R a01 = A0[0][d0] * A0[1][d1];
+            f[i] = rho * a01 * A0[2][d2];
+            g[i] = rho * ((e * a01 + H0[0][d0] * A0[1][d1] + A0[0][d0] * H0[1][d1]) * A0[2][d2] + a01 * H0[2][d2]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Addressing: periodic wrap in x, y (and z without walls); for macroscopic
+// stencils a cell beyond a z wall stands for its mirror image about the wall
+// (sign flips the velocity).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrapi(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+__device__ __forceinline__ int mirror_z(int z, int nz, bool& flip)
+{
+    flip = false;
+#pragma unroll 1
+    for (int k = 0; k < 4 && (z < 0 || z >= nz); ++k) {
+        z = z < 0 ? -1 - z : 2 * nz - 1 - z;
+        flip = !flip;
+    }
+    return z;
+}
+
+// cell index of the stencil neighbour, with the mirror flag
+__device__ __forceinline__ long long nb_index(const SimDev& s, int x, int y, int z, bool& flip)
+{
+    x = wrapi(x, s.nx);
+    y = wrapi(y, s.ny);
+    if (s.zwalls) {
+        z = mirror_z(z, s.nz, flip);
+    } else {
+        flip = false;
+        z = wrapi(z, s.nz);
+    }
+    return (long long)x + (long long)s.nx * ((long long)y + (long long)s.ny * (long long)z);
+}
+
+// Pull streaming: the pre-collision f_i(x) is f'_i(x - c_i); across a z wall
+// (half-way bounce-back) it is f'_opp(i)(x).  Returns the storage element
+// index within one distribution block and the direction whose offset applies.
+template <int D>
+__device__ __forceinline__ long long pull_index(const SimDev& s, int i, int x, int y, int z, int& isrc)
+{
+    int sx = wrapi(x - cc(i, 0), s.nx);
+    int sy = wrapi(y - cc(i, 1), s.ny);
+    int sz = z - (D == 3 ? cc(i, 2) : 0);
+    isrc = i;
+    if (D == 3) {
+        if (s.zwalls && (sz < 0 || sz >= s.nz)) {
+            sx = x;
+            sy = y;
+            sz = z;
+            isrc = opp(i);
+        } else {
+            sz = wrapi(sz, s.nz);
+        }
+    } else {
+        sz = 0;
+    }
+    long long k = (long long)sx + (long long)s.nx * ((long long)sy + (long long)s.ny * (long long)sz);
+    return (long long)isrc * s.N + k;
+}
+
+}  // namespace lbm

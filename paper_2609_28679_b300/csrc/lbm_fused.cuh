@@ -1,0 +1,480 @@
+// One-pass ("fused") time step on shared-memory tiles.
+//
+// The step needs the moments of every cell within 5 cells of the cells it
+// updates (rho for grad lap rho at radius 2 of the radius-3 macroscopic state
+// that the radius-2 stencils of Phi and the radius-1 gradients consume, plus
+// one ring of neighbours for the next moments).  Instead of a separate pass
+// that re-reads all populations to form those moments, every step carries
+// them: a CTA owning tile T
+//   1. loads rho on T+5 from the moment buffer of the current state,
+//   2. computes lap rho on T+4,
+//   3. computes u, e, T, P, theta, ... on T+3 (cells beyond a z wall are
+//      mirror copies of their images, velocity and X negated),
+//   4. pulls the populations of T+1 once, collides them, stores those of T,
+//      and adds each post-collision population of T+1 to the next-step moment
+//      (rho, j, G) of the cell it streams into, if that cell is in T,
+//   5. writes the next-step moments (and T as the next Newton guess) of T.
+// Populations are thus read and written once per step; the moment buffers
+// (6 values per cell) are double-buffered like the populations.  Tile shapes
+// are compile-time so that every region index is a constant-divisor
+// computation.
+#pragma once
+
+#include "lbm_device.cuh"
+#include "lbm_split.cuh"
+
+namespace lbm {
+
+struct TileEntry {
+    int sim, x0, y0, z0;
+};
+
+// carried per-cell values: rho, j (3), G, T (Newton guess)
+enum MField { M_RHO = 0, M_J = 1, M_G = 4, M_T = 5, M_NF = 6 };
+
+constexpr int kFusedThreads = 256;
+
+template <int D, int TX, int TY, int TZ> struct TileShape {
+    static constexpr int HZ = D == 3 ? 1 : 0;
+    static constexpr int tz = D == 3 ? TZ : 1;
+    __host__ __device__ static constexpr int w(int r) { return TX + 2 * r; }
+    __host__ __device__ static constexpr int h(int r) { return TY + 2 * r; }
+    __host__ __device__ static constexpr int d(int r) { return D == 3 ? TZ + 2 * r : 1; }
+    __host__ __device__ static constexpr int n(int r) { return w(r) * h(r) * d(r); }
+    // stencil fields on T+3: u (D), T, h, X (D); local fields on T+1: P, theta, cv, gamma, alpha theta, e
+    static constexpr int NS = 2 * D + 2, NL = 6;
+    static constexpr int U = 0, TT = D, H = D + 1, X = D + 2;
+    static constexpr int LP = 0, LTH = 1, LCV = 2, LGAM = 3, LATHE = 4, LE = 5;
+    __host__ __device__ static constexpr size_t elems()
+    {
+        return (size_t)n(5) + n(4) + (size_t)NS * n(3) + (size_t)NL * n(1) + (size_t)(D + 2) * n(0);
+    }
+};
+
+// periodic wrap of a coordinate at most one period outside [0, n), with a
+// general fallback for periods shorter than the halo
+__device__ __forceinline__ int wrapc(int v, int n)
+{
+    if (v < 0) v += n;
+    else if (v >= n) v -= n;
+    if ((unsigned)v >= (unsigned)n) v = ((v % n) + n) % n;
+    return v;
+}
+
+// coordinate of a stencil neighbour in z: periodic, or mirrored beyond walls
+__device__ __forceinline__ int zcoord(const SimDev& s, int z, bool& flip)
+{
+    flip = false;
+    if (!s.zwalls) return wrapc(z, s.nz);
+    return mirror_z(z, s.nz, flip);
+}
+
+template <int D, typename R, typename S, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 : 1)
+    k_fused(const SimDev* __restrict__ sims, const TileEntry* __restrict__ tiles, int ntiles,
+            const S* __restrict__ src, S* __restrict__ dst, const R* __restrict__ Min, R* __restrict__ Mout,
+            long long Ntot, unsigned long long* diag)
+{
+    using G = TileShape<D, TX, TY, TZ>;
+    constexpr int Q = Lat<D>::Q;
+    constexpr int HZ = G::HZ;
+    constexpr int n5 = G::n(5), n4 = G::n(4), n3 = G::n(3), n1 = G::n(1), n0 = G::n(0);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ SimDev s;
+    __shared__ int cur_sim;
+    R* s_rho = reinterpret_cast<R*>(smem_raw);
+    R* s_L = s_rho + n5;
+    R* s_st = s_L + n4;            // [NS][n3]
+    R* s_lo = s_st + G::NS * n3;   // [NL][n1]
+    R* s_acc = s_lo + G::NL * n1;  // [D+2][n0]
+    const int tid = threadIdx.x;
+    if (tid == 0) cur_sim = -1;
+    __syncthreads();
+
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileEntry te = tiles[t];
+        if (te.sim != cur_sim) {
+            __syncthreads();
+            const int nw = (int)(sizeof(SimDev) / sizeof(int));
+            const int* srcw = reinterpret_cast<const int*>(sims + te.sim);
+            for (int k = tid; k < nw; k += kFusedThreads) reinterpret_cast<int*>(&s)[k] = srcw[k];
+            if (tid == 0) cur_sim = te.sim;
+            __syncthreads();
+        }
+        const int nx = s.nx, ny = s.ny, nz = s.nz;
+        const bool walls = D == 3 && s.zwalls;
+        const long long off = s.cell_off;
+        const R* Mrho = Min + M_RHO * Ntot + off;
+
+        // ---- 1. rho on T+5 (ghosts beyond walls: the image's value); zero the accumulators
+        for (int k = tid; k < n5; k += kFusedThreads) {
+            const int lx = k % G::w(5), ly = (k / G::w(5)) % G::h(5), lz = k / (G::w(5) * G::h(5));
+            bool fl;
+            const int x = wrapc(te.x0 - 5 + lx, nx), y = wrapc(te.y0 - 5 + ly, ny);
+            const int z = D == 3 ? zcoord(s, te.z0 - 5 + lz, fl) : 0;
+            s_rho[k] = Mrho[x + (long long)nx * (y + (long long)ny * z)];
+        }
+        for (int k = tid; k < (D + 2) * n0; k += kFusedThreads) s_acc[k] = R(0);
+        __syncthreads();
+
+        // ---- 2. lap rho on T+4 (non-ghost cells; ghosts copied from images after)
+        for (int k = tid; k < n4; k += kFusedThreads) {
+            const int lx = k % G::w(4), ly = (k / G::w(4)) % G::h(4), lz = k / (G::w(4) * G::h(4));
+            const int z = te.z0 - 4 * HZ + lz;
+            if (walls && (z < 0 || z >= nz)) continue;
+            const int c = (lx + 1) + G::w(5) * ((ly + 1) + G::h(5) * (lz + HZ));
+            constexpr int sy = G::w(5), sz = G::w(5) * G::h(5);
+            R L = s_rho[c + 1] + s_rho[c - 1] + s_rho[c + sy] + s_rho[c - sy] - R(2 * D) * s_rho[c];
+            if (D == 3) L += s_rho[c + sz] + s_rho[c - sz];
+            s_L[k] = L;
+        }
+        __syncthreads();
+        if (walls && (te.z0 < 4 || te.z0 + G::tz + 4 > nz)) {
+            for (int k = tid; k < n4; k += kFusedThreads) {
+                const int lx = k % G::w(4), ly = (k / G::w(4)) % G::h(4), lz = k / (G::w(4) * G::h(4));
+                const int z = te.z0 - 4 * HZ + lz;
+                if (z >= 0 && z < nz) continue;
+                bool fl;
+                const int li = mirror_z(z, nz, fl) - (te.z0 - 4 * HZ);
+                s_L[k] = (li >= 0 && li < G::d(4)) ? s_L[lx + G::w(4) * (ly + G::h(4) * li)] : R(0);
+            }
+            __syncthreads();
+        }
+
+        // ---- 3. macroscopic state on T+3
+        constexpr int nb3 = (n3 + kFusedThreads - 1) / kFusedThreads;
+#pragma unroll 1
+        for (int it = 0; it < nb3; ++it) {
+            const int k = it * kFusedThreads + tid;
+            unsigned flags = 0;
+            bool owned = false;
+            if (k < n3) {
+                const int lx = k % G::w(3), ly = (k / G::w(3)) % G::h(3), lz = k / (G::w(3) * G::h(3));
+                const int zr = te.z0 - 3 * HZ + lz;
+                if (!(walls && (zr < 0 || zr >= nz))) {
+                    const int x = wrapc(te.x0 - 3 + lx, nx), y = wrapc(te.y0 - 3 + ly, ny);
+                    const int z = D == 3 ? wrapc(zr, nz) : 0;
+                    const long long gk = off + x + (long long)nx * (y + (long long)ny * z);
+                    const int c4 = (lx + 1) + G::w(4) * ((ly + 1) + G::h(4) * (lz + HZ));
+                    const R r = s_rho[(lx + 2) + G::w(5) * ((ly + 2) + G::h(5) * (lz + 2 * HZ))];
+                    constexpr int st4[3] = {1, G::w(4), G::w(4) * G::h(4)};
+                    R Fv[3] = {0, 0, 0}, j[3] = {0, 0, 0};
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        Fv[a] = r * ((R)s.acc[a] + (R)s.kappa * R(0.5) * (s_L[c4 + st4[a]] - s_L[c4 - st4[a]]));
+                        j[a] = Min[(M_J + a) * Ntot + gk];
+                    }
+                    const R Qh = (R)heat_at(s, z);
+                    const Macro<R> m = macro_cell<D, R>(s, r, j, Min[M_G * Ntot + gk], Fv, Qh, Min[M_T * Ntot + gk], flags);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        s_st[(G::U + a) * n3 + k] = m.u[a];
+                        s_st[(G::X + a) * n3 + k] = xflux<R>(r, m.u[a], m.theta);
+                    }
+                    s_st[G::TT * n3 + k] = m.T;
+                    s_st[G::H * n3 + k] = m.h;
+                    // local fields for the cells of T+1
+                    const int l1x = lx - 2, l1y = ly - 2, l1z = lz - 2 * HZ;
+                    if (l1x >= 0 && l1y >= 0 && l1z >= 0 && l1x < G::w(1) && l1y < G::h(1) && l1z < G::d(1)) {
+                        const int k1 = l1x + G::w(1) * (l1y + G::h(1) * l1z);
+                        s_lo[G::LP * n1 + k1] = m.P;
+                        s_lo[G::LTH * n1 + k1] = m.theta;
+                        s_lo[G::LCV * n1 + k1] = m.cv;
+                        s_lo[G::LGAM * n1 + k1] = m.gam;
+                        s_lo[G::LATHE * n1 + k1] = m.athe;
+                        s_lo[G::LE * n1 + k1] = m.e;
+                    }
+                    owned = lx >= 3 && ly >= 3 && lz >= 3 * HZ && lx < 3 + TX && ly < 3 + TY && lz < 3 * HZ + G::tz &&
+                            te.x0 - 3 + lx < nx && te.y0 - 3 + ly < ny && zr < nz;
+                }
+            }
+            if (diag) count_flags(owned ? flags : 0u, diag);
+        }
+        __syncthreads();
+        if (walls && (te.z0 < 3 || te.z0 + G::tz + 3 > nz)) {
+            for (int k = tid; k < n3; k += kFusedThreads) {
+                const int lx = k % G::w(3), ly = (k / G::w(3)) % G::h(3), lz = k / (G::w(3) * G::h(3));
+                const int z = te.z0 - 3 * HZ + lz;
+                if (z >= 0 && z < nz) continue;
+                bool fl;
+                const int li = mirror_z(z, nz, fl) - (te.z0 - 3 * HZ);
+                if (li < 0 || li >= G::d(3)) continue;  // image outside the tile's region: never read
+                const int ki = lx + G::w(3) * (ly + G::h(3) * li);
+#pragma unroll
+                for (int f = 0; f < G::NS; ++f) {
+                    const R v = s_st[f * n3 + ki];
+                    const bool odd = (f >= G::U && f < G::U + D) || (f >= G::X && f < G::X + D);
+                    s_st[f * n3 + k] = (odd && fl) ? -v : v;
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- 4. collide T+1, store T, accumulate the next moments of T
+        const S* fb = src + s.pop_off;
+        const S* gb = fb + (long long)Q * s.N;
+        S* fo = dst + s.pop_off;
+        S* go = fo + (long long)Q * s.N;
+        for (int k = tid; k < n1; k += kFusedThreads) {
+            const int lx = k % G::w(1), ly = (k / G::w(1)) % G::h(1), lz = k / (G::w(1) * G::h(1));
+            const int zr = te.z0 - HZ + lz;
+            if (walls && (zr < 0 || zr >= nz)) continue;
+            const int x = wrapc(te.x0 - 1 + lx, nx), y = wrapc(te.y0 - 1 + ly, ny);
+            const int z = D == 3 ? wrapc(zr, nz) : 0;
+            const int c3 = (lx + 2) + G::w(3) * ((ly + 2) + G::h(3) * (lz + 2 * HZ));
+            const int c4 = (lx + 3) + G::w(4) * ((ly + 3) + G::h(4) * (lz + 3 * HZ));
+            constexpr int st3[3] = {1, G::w(3), G::w(3) * G::h(3)};
+            constexpr int st4[3] = {1, G::w(4), G::w(4) * G::h(4)};
+            Macro<R> m;
+            m.rho = s_rho[(lx + 4) + G::w(5) * ((ly + 4) + G::h(5) * (lz + 4 * HZ))];
+            m.ir = R(1) / m.rho;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                m.u[a] = a < D ? s_st[(G::U + a) * n3 + c3] : R(0);
+                m.F[a] = a < D ? m.rho * ((R)s.acc[a] + (R)s.kappa * R(0.5) * (s_L[c4 + st4[a]] - s_L[c4 - st4[a]]))
+                               : R(0);
+            }
+            m.Q = (R)heat_at(s, z);
+            m.T = s_st[G::TT * n3 + c3];
+            m.h = s_st[G::H * n3 + c3];
+            m.P = s_lo[G::LP * n1 + k];
+            m.theta = s_lo[G::LTH * n1 + k];
+            m.cv = s_lo[G::LCV * n1 + k];
+            m.icv = s.eos == EOS_PR ? R(1) / m.cv : (R)s.inv_cv;
+            m.gam = s_lo[G::LGAM * n1 + k];
+            m.athe = s_lo[G::LATHE * n1 + k];
+            m.e = s_lo[G::LE * n1 + k];
+            R divu = 0, gh[3] = {0, 0, 0}, gT[3] = {0, 0, 0}, Phi[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const int sa = st3[a];
+                const R* ua = s_st + (G::U + a) * n3;
+                const R* Xa = s_st + (G::X + a) * n3;
+                divu += R(0.5) * (ua[c3 + sa] - ua[c3 - sa]);
+                gh[a] = R(0.5) * (s_st[G::H * n3 + c3 + sa] - s_st[G::H * n3 + c3 - sa]);
+                gT[a] = R(0.5) * (s_st[G::TT * n3 + c3 + sa] - s_st[G::TT * n3 + c3 - sa]);
+                R dX;
+                if (s.phi_central) {
+                    dX = R(0.5) * (Xa[c3 + sa] - Xa[c3 - sa]);
+                } else if (m.u[a] >= R(0)) {
+                    dX = R(0.5) * (R(3) * Xa[c3] - R(4) * Xa[c3 - sa] + Xa[c3 - 2 * sa]);
+                } else {
+                    dX = -R(0.5) * (R(3) * Xa[c3] - R(4) * Xa[c3 + sa] + Xa[c3 + 2 * sa]);
+                }
+                Phi[a] = -dX * m.ir;
+            }
+
+            // pull: f_i(x) = f'_i(x - c_i), or f'_opp(i)(x) across a z wall
+            const int xs[3] = {x, x == 0 ? nx - 1 : x - 1, x == nx - 1 ? 0 : x + 1};  // x - c for digit 0,1,2
+            const int ys[3] = {y, y == 0 ? ny - 1 : y - 1, y == ny - 1 ? 0 : y + 1};
+            int zs[3] = {z, 0, 0};
+            bool zwall[3] = {false, false, false};
+            if (D == 3) {
+                zs[1] = z - 1;
+                zs[2] = z + 1;
+                if (walls) {
+                    zwall[1] = zs[1] < 0;
+                    zwall[2] = zs[2] >= nz;
+                } else {
+                    zs[1] = z == 0 ? nz - 1 : z - 1;
+                    zs[2] = z == nz - 1 ? 0 : z + 1;
+                }
+            }
+            const long long self = x + (long long)nx * (y + (long long)ny * z);
+            R f[Q], gp[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int d0 = dig(i, 0), d1 = dig(i, 1), d2 = D == 3 ? dig(i, 2) : 0;
+                long long idx;
+                int isrc = i;
+                if (D == 3 && zwall[d2]) {
+                    isrc = opp(i);
+                    idx = (long long)isrc * s.N + self;
+                } else {
+                    idx = (long long)i * s.N + xs[d0] + (long long)nx * (ys[d1] + (long long)ny * zs[d2]);
+                }
+                f[i] = Codec<S, R>::ld(fb + idx);
+                gp[i] = Codec<S, R>::ld(gb + idx);
+                if (Codec<S, R>::offset) {
+                    f[i] += (R)s.fref[isrc];
+                    gp[i] += (R)s.gref[isrc];
+                }
+            }
+            collide_cell<D, R>(s, m, divu, gh, gT, Phi, f, gp);
+
+            const int tx = lx - 1, ty = ly - 1, tz = lz - HZ;
+            const bool inT = tx >= 0 && ty >= 0 && tz >= 0 && tx < TX && ty < TY && tz < G::tz;
+            const int gx = te.x0 + tx, gy = te.y0 + ty, gz = te.z0 + tz;
+            if (inT && gx < nx && gy < ny && gz < nz) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const R fr = Codec<S, R>::offset ? (R)s.fref[i] : R(0);
+                    const R gr = Codec<S, R>::offset ? (R)s.gref[i] : R(0);
+                    Codec<S, R>::st(fo + (long long)i * s.N + self, f[i] - fr);
+                    Codec<S, R>::st(go + (long long)i * s.N + self, gp[i] - gr);
+                }
+            }
+            // next-step moments: f'_i(x) becomes f_i(x + c_i), or f_opp(i)(x) across a z wall
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                int dx = tx + cc(i, 0), dy = ty + cc(i, 1), dz = tz + (D == 3 ? cc(i, 2) : 0);
+                R sgn = R(1);
+                if (walls) {
+                    const int zt = z + cc(i, 2);
+                    if (zt < 0 || zt >= nz) {
+                        dx = tx; dy = ty; dz = tz;
+                        sgn = R(-1);
+                    }
+                }
+                if (dx < 0 || dy < 0 || dz < 0 || dx >= TX || dy >= TY || dz >= G::tz) continue;
+                if (te.x0 + dx >= nx || te.y0 + dy >= ny || te.z0 + dz >= nz) continue;
+                const int dd = dx + TX * (dy + TY * dz);
+                atomicAdd(&s_acc[dd], f[i]);
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    if (cc(i, a) != 0) atomicAdd(&s_acc[(1 + a) * n0 + dd], sgn * R(cc(i, a)) * f[i]);
+                atomicAdd(&s_acc[(1 + D) * n0 + dd], gp[i]);
+            }
+        }
+        __syncthreads();
+
+        // ---- 5. next-step moments and Newton guess of T
+        for (int d = tid; d < n0; d += kFusedThreads) {
+            const int tx = d % TX, ty = (d / TX) % TY, tz = d / (TX * TY);
+            const int x = te.x0 + tx, y = te.y0 + ty, z = te.z0 + tz;
+            if (x >= nx || y >= ny || z >= nz) continue;
+            const long long kk = off + x + (long long)nx * (y + (long long)ny * z);
+            Mout[M_RHO * Ntot + kk] = s_acc[d];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Mout[(M_J + a) * Ntot + kk] = a < D ? s_acc[(1 + a) * n0 + d] : R(0);
+            Mout[M_G * Ntot + kk] = s_acc[(1 + D) * n0 + d];
+            Mout[M_T * Ntot + kk] = s_st[G::TT * n3 + (tx + 3) + G::w(3) * ((ty + 3) + G::h(3) * (tz + 3 * HZ))];
+        }
+        __syncthreads();
+    }
+}
+
+// Moments (and the Newton guess from the split path's T) of the current state,
+// before the first fused step after lbm_init or a split step.
+template <int D, typename R, typename S>
+__global__ void __launch_bounds__(kBlockCells) k_fused_prep(const SimDev* __restrict__ sims,
+                                                            const BlockEntry* __restrict__ table,
+                                                            const S* __restrict__ pop, const R* __restrict__ W,
+                                                            R* __restrict__ M, long long Ntot)
+{
+    constexpr int Q = Lat<D>::Q;
+    __shared__ SimDev s;
+    const BlockEntry be = table[blockIdx.x];
+    load_sim(s, sims, be.sim);
+    const long long k = (long long)be.start + threadIdx.x;
+    if (k >= s.N) return;
+    int x, y, z;
+    cell_xyz(s, k, x, y, z);
+    R f[Q], g[Q];
+    pull_cell<D, R, S>(s, pop, x, y, z, f, g);
+    R rho = 0, j[3] = {0, 0, 0}, G = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        rho += f[i];
+#pragma unroll
+        for (int a = 0; a < D; ++a) j[a] += R(cc(i, a)) * f[i];
+        G += g[i];
+    }
+    const long long gk = s.cell_off + k;
+    M[M_RHO * Ntot + gk] = rho;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) M[(M_J + a) * Ntot + gk] = j[a];
+    M[M_G * Ntot + gk] = G;
+    M[M_T * Ntot + gk] = W[W_T * Ntot + gk];
+}
+
+template <int D, typename R, typename S>
+void fused_moments_launch(const SimDev* sims, const BlockEntry* table, int nblocks, const S* pop, const R* W, R* M,
+                          long long Ntot, cudaStream_t stream)
+{
+    k_fused_prep<D, R, S><<<nblocks, kBlockCells, 0, stream>>>(sims, table, pop, W, M, Ntot);
+}
+
+// ---------------------------------------------------------------------------
+// Tile shapes built (the autotuner picks among them per lattice and storage).
+// ---------------------------------------------------------------------------
+#define LBM_FUSED_TILES_2D(X) X(32, 8, 1) X(32, 16, 1) X(32, 32, 1) X(64, 16, 1)
+#define LBM_FUSED_TILES_3D(X) X(8, 8, 4) X(16, 8, 4) X(8, 8, 8)
+
+inline void fused_default_tile(int dim, int storage, int& tx, int& ty, int& tz)
+{
+    if (dim == 2) {
+        tx = 32;
+        ty = storage == 0 ? 8 : 16;
+        tz = 1;
+    } else {
+        tx = 8;
+        ty = 8;
+        tz = 4;
+    }
+}
+
+template <int D, typename R, int TX, int TY, int TZ> constexpr size_t fused_smem()
+{
+    return TileShape<D, TX, TY, TZ>::elems() * sizeof(R);
+}
+
+template <int D, typename R, typename S> bool fused_tile_ok(int tx, int ty, int tz)
+{
+    bool ok = false;
+#define LBM_OK_2D(A, B, C) \
+    if (D == 2 && tx == A && ty == B && tz == C) ok = fused_smem<D, R, A, B, C>() <= 227u * 1024u;
+#define LBM_OK_3D(A, B, C) \
+    if (D == 3 && tx == A && ty == B && tz == C) ok = fused_smem<D, R, A, B, C>() <= 227u * 1024u;
+    LBM_FUSED_TILES_2D(LBM_OK_2D)
+    LBM_FUSED_TILES_3D(LBM_OK_3D)
+#undef LBM_OK_2D
+#undef LBM_OK_3D
+    return ok;
+}
+
+template <int D, typename R, typename S, int TX, int TY, int TZ>
+cudaError_t fused_launch_shape(const SimDev* sims, const TileEntry* tiles, int ntiles, const S* src, S* dst,
+                               const R* Min, R* Mout, long long Ntot, unsigned long long* diag, cudaStream_t stream)
+{
+    constexpr size_t smem = fused_smem<D, R, TX, TY, TZ>();
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused<D, R, S, TX, TY, TZ>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, dev = 0, nsm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, R, S, TX, TY, TZ>, kFusedThreads, smem);
+        if (e != cudaSuccess) return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        grid_cap = per_sm * nsm;
+    }
+    const int grid = ntiles < grid_cap ? ntiles : grid_cap;
+    k_fused<D, R, S, TX, TY, TZ><<<grid, kFusedThreads, smem, stream>>>(sims, tiles, ntiles, src, dst, Min, Mout, Ntot,
+                                                                        diag);
+    return cudaGetLastError();
+}
+
+template <int D, typename R, typename S>
+cudaError_t fused_step_launch(const SimDev* sims, const TileEntry* tiles, int ntiles, int tx, int ty, int tz,
+                              const S* src, S* dst, const R* Min, R* Mout, long long Ntot, unsigned long long* diag,
+                              cudaStream_t stream)
+{
+#define LBM_GO_2D(A, B, C)                                                                                  \
+    if (D == 2 && tx == A && ty == B)                                                                       \
+        if constexpr (D == 2 && fused_smem<2, R, A, B, C>() <= 227u * 1024u)                               \
+            return fused_launch_shape<D, R, S, A, B, C>(sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+#define LBM_GO_3D(A, B, C)                                                                                  \
+    if (D == 3 && tx == A && ty == B && tz == C)                                                            \
+        if constexpr (D == 3 && fused_smem<3, R, A, B, C>() <= 227u * 1024u)                               \
+            return fused_launch_shape<D, R, S, A, B, C>(sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    LBM_FUSED_TILES_2D(LBM_GO_2D)
+    LBM_FUSED_TILES_3D(LBM_GO_3D)
+#undef LBM_GO_2D
+#undef LBM_GO_3D
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

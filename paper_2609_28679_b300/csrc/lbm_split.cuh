@@ -1,0 +1,427 @@
+// Per-cell kernels: initialisation, the three-pass ("split") time step,
+// export of fields/populations and the float64 conservation reduction.
+//
+// Work arrays W are [NF][Ntot] in the arithmetic type R; field f of global
+// cell (cell_off + k) sits at W[f * Ntot + cell_off + k].  Kernels run over a
+// block table: block b handles cells [start, start + 256) of simulation sim.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+enum Field {
+    W_RHO = 0, W_J = 1, W_G = 4, W_U = 5, W_T = 8, W_H = 9, W_X = 10, W_F = 13,
+    W_P = 16, W_TH = 17, W_CV = 18, W_GAM = 19, W_ATHE = 20, W_E = 21, W_NF = 22
+};
+
+constexpr int kBlockCells = 256;
+
+struct BlockEntry {
+    int sim;
+    int start;
+};
+
+// Copy the simulation's constants to shared memory (one block = one simulation).
+__device__ __forceinline__ void load_sim(SimDev& dst, const SimDev* sims, int sim)
+{
+    const int n = (int)(sizeof(SimDev) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(sims + sim);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) d[t] = src[t];
+    __syncthreads();
+}
+
+__device__ __forceinline__ void cell_xyz(const SimDev& s, long long k, int& x, int& y, int& z)
+{
+    x = (int)(k % s.nx);
+    long long r = k / s.nx;
+    y = (int)(r % s.ny);
+    z = (int)(r / s.ny);
+}
+
+__device__ __forceinline__ double heat_at(const SimDev& s, int z)
+{
+    return (s.zhi <= 0 || (z >= s.zlo && z < s.zhi)) ? s.q : 0.0;
+}
+
+// Warp-aggregated diagnostic counters (bit 0: non-finite, 1: theta <= 0, 2: Newton cap).
+__device__ __forceinline__ void count_flags(unsigned flags, unsigned long long* diag)
+{
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        unsigned m = __ballot_sync(0xffffffffu, (flags >> b) & 1u);
+        if (lane == 0 && m) atomicAdd(diag + b, (unsigned long long)__popc(m));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state: f = f^eq(rho, u, theta), g = g^eq (flowchart, first box),
+// written where the first pull reads them.
+// ---------------------------------------------------------------------------
+template <int D, typename R, typename S>
+__global__ void __launch_bounds__(kBlockCells) k_init(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
+                                                      const double* __restrict__ rho_in, const double* __restrict__ u_in,
+                                                      const double* __restrict__ T_in, S* __restrict__ pop,
+                                                      R* __restrict__ W, long long Ntot)
+{
+    constexpr int Q = Lat<D>::Q;
+    __shared__ SimDev s;
+    const BlockEntry be = table[blockIdx.x];
+    load_sim(s, sims, be.sim);
+    const long long k = (long long)be.start + threadIdx.x;
+    if (k >= s.N) return;
+    int x, y, z;
+    cell_xyz(s, k, x, y, z);
+    const long long gk = s.cell_off + k;
+    R rho = (R)rho_in[gk], T = (R)T_in[gk], u[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) u[a] = (R)u_in[(long long)D * s.cell_off + (long long)a * s.N + k];
+    RhoPart<R> p = rho_part<R>(s, rho);
+    R th = eos_P<R>(s, p, T) / rho;
+    R e = eos_e<R>(s, p, T);
+    R f[Q], g[Q];
+    equilibria<D, R>(rho, u, th, e, f, g);
+    S* fb = pop + s.pop_off;
+    S* gb = fb + (long long)Q * s.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        // slot read by the pull of (x, i): (i, x - c_i), or (opp(i), x) across a wall
+        int sx = wrapi(x - cc(i, 0), s.nx), sy = wrapi(y - cc(i, 1), s.ny), sz = z - (D == 3 ? cc(i, 2) : 0);
+        int j = i;
+        if (D == 3 && s.zwalls && (sz < 0 || sz >= s.nz)) {
+            sx = x; sy = y; sz = z; j = opp(i);
+        } else if (D == 3) {
+            sz = wrapi(sz, s.nz);
+        } else {
+            sz = 0;
+        }
+        long long kk = (long long)sx + (long long)s.nx * ((long long)sy + (long long)s.ny * (long long)sz);
+        R fo = Codec<S, R>::offset ? (R)s.fref[j] : R(0);
+        R go = Codec<S, R>::offset ? (R)s.gref[j] : R(0);
+        Codec<S, R>::st(fb + (long long)j * s.N + kk, f[i] - fo);
+        Codec<S, R>::st(gb + (long long)j * s.N + kk, g[i] - go);
+    }
+    W[W_T * Ntot + gk] = T;
+}
+
+// Pre-collision populations of cell (x,y,z), decoded to R.
+template <int D, typename R, typename S>
+__device__ __forceinline__ void pull_cell(const SimDev& s, const S* __restrict__ pop, int x, int y, int z, R* f, R* g)
+{
+    constexpr int Q = Lat<D>::Q;
+    const S* fb = pop + s.pop_off;
+    const S* gb = fb + (long long)Q * s.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        int j;
+        long long idx = pull_index<D>(s, i, x, y, z, j);
+        f[i] = Codec<S, R>::ld(fb + idx);
+        g[i] = Codec<S, R>::ld(gb + idx);
+        if (Codec<S, R>::offset) {
+            f[i] += (R)s.fref[j];
+            g[i] += (R)s.gref[j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: moments rho = sum f (Eq. def_h), j = sum c f, G = sum g.
+// ---------------------------------------------------------------------------
+template <int D, typename R, typename S>
+__global__ void __launch_bounds__(kBlockCells) k_moments(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
+                                                         const S* __restrict__ pop, R* __restrict__ W, long long Ntot)
+{
+    constexpr int Q = Lat<D>::Q;
+    __shared__ SimDev s;
+    const BlockEntry be = table[blockIdx.x];
+    load_sim(s, sims, be.sim);
+    const long long k = (long long)be.start + threadIdx.x;
+    if (k >= s.N) return;
+    int x, y, z;
+    cell_xyz(s, k, x, y, z);
+    R f[Q], g[Q];
+    pull_cell<D, R, S>(s, pop, x, y, z, f, g);
+    R rho = 0, j[3] = {0, 0, 0}, G = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        rho += f[i];
+#pragma unroll
+        for (int a = 0; a < D; ++a) j[a] += R(cc(i, a)) * f[i];
+        G += g[i];
+    }
+    const long long gk = s.cell_off + k;
+    W[W_RHO * Ntot + gk] = rho;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) W[(W_J + a) * Ntot + gk] = j[a];
+    W[W_G * Ntot + gk] = G;
+}
+
+// lap rho at the image of (x,y,z) ((2D+1)-point stencil, mirrored beyond walls)
+template <int D, typename R>
+__device__ __forceinline__ R lap_at(const SimDev& s, const R* __restrict__ rho, int x, int y, int z)
+{
+    bool fl;
+    long long kc = nb_index(s, x, y, z, fl);
+    int ix, iy, iz;
+    cell_xyz(s, kc, ix, iy, iz);
+    R c = rho[kc], L = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        int e0 = a == 0, e1 = a == 1, e2 = a == 2;
+        L += rho[nb_index(s, ix + e0, iy + e1, iz + e2, fl)] - R(2) * c + rho[nb_index(s, ix - e0, iy - e1, iz - e2, fl)];
+    }
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: force, velocity, energy, temperature and closure scalars per cell.
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
+                                                       R* __restrict__ W, long long Ntot, unsigned long long* diag)
+{
+    __shared__ SimDev s;
+    const BlockEntry be = table[blockIdx.x];
+    load_sim(s, sims, be.sim);
+    const long long k = (long long)be.start + threadIdx.x;
+    const bool valid = k < s.N;
+    unsigned flags = 0;
+    if (valid) {
+        int x, y, z;
+        cell_xyz(s, k, x, y, z);
+        const long long gk = s.cell_off + k;
+        const R* rho = W + W_RHO * Ntot + s.cell_off;
+        R r = rho[k];
+        R F[3] = {0, 0, 0}, j[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            int e0 = a == 0, e1 = a == 1, e2 = a == 2;
+            R gl = R(0.5) * (lap_at<D, R>(s, rho, x + e0, y + e1, z + e2) - lap_at<D, R>(s, rho, x - e0, y - e1, z - e2));
+            F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl;  // Eqs. force_decomposition, korteweg_force
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) j[a] = W[(W_J + a) * Ntot + gk];
+        R Q = (R)heat_at(s, z);
+        Macro<R> m = macro_cell<D, R>(s, r, j, W[W_G * Ntot + gk], F, Q, W[W_T * Ntot + gk], flags);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            W[(W_U + a) * Ntot + gk] = m.u[a];
+            W[(W_F + a) * Ntot + gk] = m.F[a];
+            W[(W_X + a) * Ntot + gk] = a < D ? xflux<R>(r, m.u[a], m.theta) : R(0);
+        }
+        W[W_T * Ntot + gk] = m.T;
+        W[W_H * Ntot + gk] = m.h;
+        W[W_P * Ntot + gk] = m.P;
+        W[W_TH * Ntot + gk] = m.theta;
+        W[W_CV * Ntot + gk] = m.cv;
+        W[W_GAM * Ntot + gk] = m.gam;
+        W[W_ATHE * Ntot + gk] = m.athe;
+        W[W_E * Ntot + gk] = m.e;
+    }
+    if (diag) count_flags(flags, diag);
+}
+
+template <typename R>
+__device__ __forceinline__ R wget(const SimDev& s, const R* __restrict__ fld, int x, int y, int z, bool odd)
+{
+    bool fl;
+    long long kk = nb_index(s, x, y, z, fl);
+    R v = fld[kk];
+    return (odd && fl) ? -v : v;
+}
+
+// Stencil quantities of cell (x,y,z): div u, grad h, grad T (central) and
+// Phi (Eq. correction; upwind-biased or central derivative of X).
+template <int D, typename R>
+__device__ __forceinline__ void stencils(const SimDev& s, const R* __restrict__ W, long long Ntot, int x, int y, int z,
+                                         R rho, const R* u, R& divu, R* gh, R* gT, R* Phi)
+{
+    const long long off = s.cell_off;
+    divu = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { gh[a] = 0; gT[a] = 0; Phi[a] = 0; }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const int e0 = a == 0, e1 = a == 1, e2 = a == 2;
+        const R* ua = W + (W_U + a) * Ntot + off;
+        const R* h = W + W_H * Ntot + off;
+        const R* T = W + W_T * Ntot + off;
+        const R* X = W + (W_X + a) * Ntot + off;
+        divu += R(0.5) * (wget(s, ua, x + e0, y + e1, z + e2, true) - wget(s, ua, x - e0, y - e1, z - e2, true));
+        gh[a] = R(0.5) * (wget(s, h, x + e0, y + e1, z + e2, false) - wget(s, h, x - e0, y - e1, z - e2, false));
+        gT[a] = R(0.5) * (wget(s, T, x + e0, y + e1, z + e2, false) - wget(s, T, x - e0, y - e1, z - e2, false));
+        R dX;
+        if (s.phi_central) {
+            dX = R(0.5) * (wget(s, X, x + e0, y + e1, z + e2, true) - wget(s, X, x - e0, y - e1, z - e2, true));
+        } else {
+            R X0 = wget(s, X, x, y, z, true);
+            if (u[a] >= R(0))
+                dX = R(0.5) * (R(3) * X0 - R(4) * wget(s, X, x - e0, y - e1, z - e2, true) +
+                               wget(s, X, x - 2 * e0, y - 2 * e1, z - 2 * e2, true));
+            else
+                dX = -R(0.5) * (R(3) * X0 - R(4) * wget(s, X, x + e0, y + e1, z + e2, true) +
+                                wget(s, X, x + 2 * e0, y + 2 * e1, z + 2 * e2, true));
+        }
+        Phi[a] = -dX / rho;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 3: shifted states, equilibria, collision and pull streaming.
+// ---------------------------------------------------------------------------
+template <int D, typename R, typename S>
+__global__ void __launch_bounds__(kBlockCells) k_collide(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
+                                                         const S* __restrict__ src, S* __restrict__ dst,
+                                                         const R* __restrict__ W, long long Ntot)
+{
+    constexpr int Q = Lat<D>::Q;
+    __shared__ SimDev s;
+    const BlockEntry be = table[blockIdx.x];
+    load_sim(s, sims, be.sim);
+    const long long k = (long long)be.start + threadIdx.x;
+    if (k >= s.N) return;
+    int x, y, z;
+    cell_xyz(s, k, x, y, z);
+    const long long gk = s.cell_off + k;
+    Macro<R> m;
+    m.rho = W[W_RHO * Ntot + gk];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        m.u[a] = W[(W_U + a) * Ntot + gk];
+        m.F[a] = W[(W_F + a) * Ntot + gk];
+    }
+    m.Q = (R)heat_at(s, z);
+    m.T = W[W_T * Ntot + gk];
+    m.P = W[W_P * Ntot + gk];
+    m.theta = W[W_TH * Ntot + gk];
+    m.h = W[W_H * Ntot + gk];
+    m.cv = W[W_CV * Ntot + gk];
+    m.gam = W[W_GAM * Ntot + gk];
+    m.athe = W[W_ATHE * Ntot + gk];
+    m.e = W[W_E * Ntot + gk];
+    m.ir = R(1) / m.rho;
+    m.icv = R(1) / m.cv;
+    R divu, gh[3], gT[3], Phi[3];
+    stencils<D, R>(s, W, Ntot, x, y, z, m.rho, m.u, divu, gh, gT, Phi);
+    R f[Q], g[Q];
+    pull_cell<D, R, S>(s, src, x, y, z, f, g);
+    collide_cell<D, R>(s, m, divu, gh, gT, Phi, f, g);
+    S* fb = dst + s.pop_off;
+    S* gb = fb + (long long)Q * s.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        R fo = Codec<S, R>::offset ? (R)s.fref[i] : R(0);
+        R go = Codec<S, R>::offset ? (R)s.gref[i] : R(0);
+        Codec<S, R>::st(fb + (long long)i * s.N + k, f[i] - fo);
+        Codec<S, R>::st(gb + (long long)i * s.N + k, g[i] - go);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Float64 totals per block (after k_moments + k_macro of the current state):
+// [rho, rho u (D), rho E, F (D), u.F + Q].  Warp shuffles, then shared memory.
+// ---------------------------------------------------------------------------
+template <int D, typename R>
+__global__ void __launch_bounds__(kBlockCells) k_invariants(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
+                                                            const R* __restrict__ W, long long Ntot, double* __restrict__ partials)
+{
+    constexpr int NV = 2 * D + 3;
+    __shared__ SimDev s;
+    __shared__ double red[kBlockCells / 32][NV];
+    const BlockEntry be = table[blockIdx.x];
+    load_sim(s, sims, be.sim);
+    const long long k = (long long)be.start + threadIdx.x;
+    double v[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] = 0.0;
+    if (k < s.N) {
+        int x, y, z;
+        cell_xyz(s, k, x, y, z);
+        const long long gk = s.cell_off + k;
+        double r = (double)W[W_RHO * Ntot + gk], uF = 0.0;
+        v[0] = r;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double Fa = (double)W[(W_F + a) * Ntot + gk];
+            double ua = (double)W[(W_U + a) * Ntot + gk];
+            v[1 + a] = (double)W[(W_J + a) * Ntot + gk] + 0.5 * Fa;  // Eq. def_u
+            v[D + 2 + a] = Fa;
+            uF += ua * Fa;
+        }
+        double Q = heat_at(s, z);
+        v[D + 1] = (double)W[W_G * Ntot + gk] + 0.5 * (uF + Q);  // Eq. def_E
+        v[2 * D + 2] = uF + Q;
+    }
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+        double t = v[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double t = 0.0;
+        for (int w = 0; w < kBlockCells / 32; ++w) t += red[w][threadIdx.x];
+        partials[(long long)blockIdx.x * NV + threadIdx.x] = t;
+    }
+}
+
+// Fixed-order sum of the block partials of each simulation.
+__global__ void k_invariants_final(const double* __restrict__ partials, const int* __restrict__ sim_block_start, int nsim,
+                                   int nv, double* __restrict__ out)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nsim * nv) return;
+    int sim = t / nv, c = t % nv;
+    double acc = 0.0;
+    for (int b = sim_block_start[sim]; b < sim_block_start[sim + 1]; ++b) acc += partials[(long long)b * nv + c];
+    out[t] = acc;
+}
+
+// Export rho, u, T (float64, per-simulation field layout of the ABI).
+template <int D, typename R>
+__global__ void __launch_bounds__(kBlockCells) k_export_moments(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
+                                                                const R* __restrict__ W, long long Ntot, double* rho,
+                                                                double* u, double* T)
+{
+    __shared__ SimDev s;
+    const BlockEntry be = table[blockIdx.x];
+    load_sim(s, sims, be.sim);
+    const long long k = (long long)be.start + threadIdx.x;
+    if (k >= s.N) return;
+    const long long gk = s.cell_off + k;
+    if (rho) rho[gk] = (double)W[W_RHO * Ntot + gk];
+    if (T) T[gk] = (double)W[W_T * Ntot + gk];
+    if (u) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) u[(long long)D * s.cell_off + (long long)a * s.N + k] = (double)W[(W_U + a) * Ntot + gk];
+    }
+}
+
+// Export the pre-collision populations (pulled, decoded) as float64 [Q][N].
+template <int D, typename R, typename S>
+__global__ void __launch_bounds__(kBlockCells) k_export_pops(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
+                                                             const S* __restrict__ pop, double* f_out, double* g_out)
+{
+    constexpr int Q = Lat<D>::Q;
+    __shared__ SimDev s;
+    const BlockEntry be = table[blockIdx.x];
+    load_sim(s, sims, be.sim);
+    const long long k = (long long)be.start + threadIdx.x;
+    if (k >= s.N) return;
+    int x, y, z;
+    cell_xyz(s, k, x, y, z);
+    R f[Q], g[Q];
+    pull_cell<D, R, S>(s, pop, x, y, z, f, g);
+    const long long base = (long long)Q * s.cell_off;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (f_out) f_out[base + (long long)i * s.N + k] = (double)f[i];
+        if (g_out) g_out[base + (long long)i * s.N + k] = (double)g[i];
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,223 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on the
+same seeded inputs, element by element.
+
+Tolerances (relative L-infinity, max|x - x_ref| / max|x_ref| per field):
+  float64 storage and arithmetic: 1e-12 for populations, rho, T; u to 1e-12
+  of max(max|u_ref|, 1e-3) (u = (sum c f + F/2)/rho is a difference of O(rho)
+  momenta, so its rounding floor is absolute, ~1e-16 of the lattice speed);
+  float32: 1e-5 for populations, rho, T, and 1e-5 of the lattice speed c = 1
+  for u (the same cancellation at float32 precision);
+  16-bit storage: the bound follows from the stored precision (see below).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2609_28679_b300 import lbm
+from paper_2609_28679_b300 import workloads as wl
+from tests.util import oracle_params, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+SPLIT, FUSED = lbm.LBM_KERNEL_SPLIT, lbm.LBM_KERNEL_FUSED
+
+
+def _variants():
+    return [SPLIT, FUSED]
+
+
+def _run_pair(case, steps, variant, fields=None):
+    fields = fields if fields is not None else case.fields()
+    sim = lbm.Simulation(case)
+    if variant == FUSED:
+        try:
+            lbm.lbm_set_kernel(sim.h, FUSED)
+        except lbm.LbmError as e:
+            pytest.skip(f"fused kernel unavailable for this lattice: {e}")
+    sim.init(fields)
+    sim.step(steps)
+    o = orc.Oracle(oracle_params(case))
+    o.init(*fields)
+    o.step(steps)
+    return sim, o
+
+
+def _compare(sim, o, tol, f32=False):
+    f, g = sim.populations()
+    fr, gr = o.populations()
+    assert rel_linf(f, fr.ravel()) <= tol
+    assert rel_linf(g, gr.ravel()) <= tol
+    rho, u, T = sim.moments()
+    rr, ur, Tr = o.moments()
+    assert rel_linf(rho, rr) <= tol
+    assert rel_linf(T, Tr) <= tol
+    du = float(np.max(np.abs(u - ur.ravel()))) if u.size else 0.0
+    tol_u = tol if f32 else tol * max(float(np.max(np.abs(ur))) if ur.size else 0.0, 1e-3)
+    assert du <= tol_u, (du, tol_u)
+
+
+# ---------------------------------------------------------------------------
+# float64: 1e-12
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("variant", _variants())
+def test_f64_ideal_2d_acoustic_shear(variant):
+    c = wl.acoustic_shear(n=37, storage="f64")  # ragged: not a multiple of any tile
+    c.ny = 29
+    sim, o = _run_pair(c, 60, variant)
+    _compare(sim, o, 1e-12)
+
+
+@pytest.mark.parametrize("variant", _variants())
+def test_f64_vdw_2d_korteweg_gravity(variant):
+    c = wl.vdw_spinodal(n=45, ny=38, storage="f64")
+    sim, o = _run_pair(c, 40, variant)
+    _compare(sim, o, 1e-12)
+
+
+@pytest.mark.parametrize("variant", _variants())
+def test_f64_vdw_2d_upwind_phi(variant):
+    c = wl.vdw_spinodal(n=24, ny=20, storage="f64")
+    c.phi_central = 0
+    c.accel = (2e-4, -1e-4, 0.0)  # nonzero mean flow so both upwind branches are taken
+    sim, o = _run_pair(c, 15, variant)
+    _compare(sim, o, 1e-12)
+
+
+@pytest.mark.parametrize("variant", _variants())
+def test_f64_pr_3d_walls_heat_gravity(variant):
+    c = wl.pr_heated_slab(n=11, nz=13, storage="f64")
+    c.ny = 9
+    c.zhi = 4
+    sim, o = _run_pair(c, 12, variant)
+    _compare(sim, o, 1e-12)
+
+
+@pytest.mark.parametrize("variant", _variants())
+def test_f64_pr_3d_droplet_periodic(variant):
+    c = wl.pr_droplet(n=14, radius=4.0, storage="f64")
+    sim, o = _run_pair(c, 8, variant)
+    _compare(sim, o, 1e-12)
+
+
+def test_f64_invariants_match_oracle():
+    c = wl.vdw_spinodal(n=32, storage="f64")
+    c.q = 2e-6
+    sim, o = _run_pair(c, 25, SPLIT)
+    gi = sim.invariants()[0]
+    oi = o.invariants()
+    scale = np.maximum(np.abs(oi), 1e-30)
+    # sums over 1024 cells: rounding order differs; relative to the size of the summands
+    assert np.all(np.abs(gi - oi) <= 1e-12 * np.maximum(scale, np.abs(oi[0])))
+
+
+def test_f64_mass_drift_per_1000_steps():
+    c = wl.vdw_spinodal(n=64, storage="f64")
+    sim = lbm.Simulation(c)
+    sim.init()
+    m0 = sim.invariants()[0][0]
+    sim.step(1000)
+    m1 = sim.invariants()[0][0]
+    assert abs(m1 - m0) <= 1e-12 * m0
+
+
+def test_f64_batch_of_uneven_simulations():
+    cases = [wl.vdw_spinodal(n=n, ny=n + 3, storage="f64", seed=10 + n) for n in (17, 24, 9)]
+    cases[1] = wl.acoustic_shear(n=24, storage="f64")
+    sim = lbm.Simulation(cases)
+    sim.init()
+    sim.step(10)
+    rho, u, T = sim.moments()
+    off = 0
+    for c in cases:
+        o = orc.Oracle(oracle_params(c))
+        o.init(*c.fields())
+        o.step(10)
+        rr, ur, Tr = o.moments()
+        n = c.ncell
+        assert rel_linf(rho[off:off + n], rr) <= 1e-12
+        assert rel_linf(T[off:off + n], Tr) <= 1e-12
+        assert np.max(np.abs(u[2 * off:2 * off + 2 * n] - ur.ravel())) <= 1e-13
+        off += n
+
+
+# ---------------------------------------------------------------------------
+# float32: 1e-5
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("variant", _variants())
+def test_f32_vdw_2d(variant):
+    c = wl.vdw_spinodal(n=40, ny=33, storage="f32")
+    sim, o = _run_pair(c, 40, variant)
+    _compare(sim, o, 1e-5, f32=True)
+
+
+@pytest.mark.parametrize("variant", _variants())
+def test_f32_ideal_2d(variant):
+    c = wl.acoustic_shear(n=48, storage="f32")
+    sim, o = _run_pair(c, 50, variant)
+    _compare(sim, o, 1e-5, f32=True)
+
+
+@pytest.mark.parametrize("variant", _variants())
+def test_f32_pr_3d_walls(variant):
+    c = wl.pr_heated_slab(n=12, nz=10, storage="f32")
+    c.zhi = 3
+    sim, o = _run_pair(c, 10, variant)
+    _compare(sim, o, 1e-5, f32=True)
+
+
+# ---------------------------------------------------------------------------
+# 16-bit storage of f - f^ref, float32 arithmetic.  One rounding of the stored
+# deviation per step: |delta f| <= 2^-9 |f - f^ref| (bf16) or 2^-12 (f16) per
+# step; bounded here over a short horizon relative to the population scale.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("storage,tol", [("bf16", 2e-3), ("f16", 3e-4)])
+def test_16bit_storage_error_bound(storage, tol):
+    c = wl.pr_heated_slab(n=10, nz=8, storage=storage)
+    sim, o = _run_pair(c, 10, SPLIT)
+    f, g = sim.populations()
+    fr, gr = o.populations()
+    assert rel_linf(f, fr.ravel()) <= tol
+    assert rel_linf(g, gr.ravel()) <= tol
+    rho, u, T = sim.moments()
+    rr, ur, Tr = o.moments()
+    assert rel_linf(rho, rr) <= tol
+    assert rel_linf(T, Tr) <= tol
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------
+def test_zero_steps_returns_initial_equilibrium():
+    c = wl.acoustic_shear(n=8, storage="f64")
+    sim, o = _run_pair(c, 0, SPLIT)
+    _compare(sim, o, 1e-15)
+
+
+def test_single_cell_domain():
+    c = wl.Case(name="one", dim=2, nx=1, ny=1, eos="ideal", q=1e-4, accel=(1e-3, 0, 0), storage="f64",
+                init=dict(kind="uniform", rho0=1.3, T0=0.4))
+    sim, o = _run_pair(c, 5, SPLIT)
+    _compare(sim, o, 1e-13)
+
+
+def test_theta_nonpositive_is_counted():
+    # van der Waals with a = 9/49 at T/Tc = 0.8 and rho = 5.6 (rho/rho_c = 1.6): P < 0 in the spinodal
+    c = wl.Case(name="negP", dim=2, nx=8, ny=8, eos="vdw", a=9 / 49, b=2 / 21, storage="f64",
+                init=dict(kind="uniform", rho0=5.6, T0=0.8 * 4 / 7))
+    sim = lbm.Simulation(c)
+    sim.init()
+    sim.step(1)
+    d = sim.diagnostics()
+    assert d[1] == 64
+    assert d[0] == 0
+
+
+def test_init_rejects_nonpositive_density():
+    c = wl.acoustic_shear(n=8, storage="f64")
+    sim = lbm.Simulation(c)
+    rho, u, T = c.fields()
+    rho[5] = np.nan
+    with pytest.raises(lbm.LbmError):
+        sim.init((rho, u, T))
+    with pytest.raises(lbm.LbmError):
+        sim.step(1)  # still not initialised
