@@ -46,7 +46,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     tinc, tlib, cudart_dir, abi = _torch_dirs()
     cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
-    objs = []
+    objs, jobs = [], []
     for cu in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         obj = os.path.join(BUILD, os.path.basename(cu) + ".o")
         if force or _newer(obj, [cu] + headers):
@@ -54,8 +54,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
                    "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-c", cu, "-o", obj]
             if ptxas_verbose:
                 cmd.insert(1, "-Xptxas=-v")
-            _run(cmd, verbose)
+            jobs.append(cmd)
         objs.append(obj)
+    if jobs:
+        from concurrent.futures import ThreadPoolExecutor
+
+        with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+            list(ex.map(lambda c: _run(c, verbose), jobs))
     glue = os.path.join(CSRC, "lbm_glue.cpp")
     gobj = os.path.join(BUILD, "lbm_glue.cpp.o")
     if force or _newer(gobj, [glue]):

@@ -9,6 +9,7 @@
 
 #include "lbm.h"
 #include "lbm_fused.cuh"
+#include "lbm_fused_api.h"
 #include "lbm_split.cuh"
 
 extern "C" void* lbm_glue_alloc(size_t nbytes, void* stream);
@@ -91,6 +92,11 @@ int cuda_fail(lbm_ctx* h, cudaError_t e, const char* where)
 
 void* dev_alloc(lbm_ctx* h, size_t n) { return lbm_glue_alloc(n, (void*)h->stream); }
 
+cudaError_t fused_dispatch(int storage, int dim, int eos, int tx, int ty, int tz, const SimDev* sims,
+                           const TileEntry* tiles, int ntiles, const void* src, void* dst, const void* Min, void* Mout,
+                           long long Ntot, unsigned long long* diag, cudaStream_t stream);
+bool fused_shape(int storage, int dim, int tx, int ty, int tz);
+
 // ---------------------------------------------------------------------------
 // Typed implementation of every operation for one (D, arithmetic, storage).
 // ---------------------------------------------------------------------------
@@ -140,9 +146,9 @@ template <int D, typename R, typename S> struct Impl {
             int rc = fused_prepare(h);
             if (rc) return rc;
         }
-        cudaError_t e = fused_step_launch<D, R, S>(h->d_sims, h->d_tiles, (int)h->tiles.size(), h->tx, h->ty, h->tz,
-                                                  (const S*)h->pop[h->cur], (S*)h->pop[h->cur ^ 1], mbuf(h, h->cur),
-                                                  mbuf(h, h->cur ^ 1), h->Ntot, h->d_diag, h->stream);
+        cudaError_t e = fused_dispatch(h->storage, D, h->sims[0].eos, h->tx, h->ty, h->tz, h->d_sims, h->d_tiles,
+                                       (int)h->tiles.size(), h->pop[h->cur], h->pop[h->cur ^ 1], mbuf(h, h->cur),
+                                       mbuf(h, h->cur ^ 1), h->Ntot, h->d_diag, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "fused step");
         h->cur ^= 1;
         return LBM_OK;
@@ -196,10 +202,53 @@ template <int D, typename R, typename S> struct Impl {
         return LBM_OK;
     }
 
-    static int fused_ok(lbm_ctx* h, int tx, int ty, int tz) { return fused_tile_ok<D, R, S>(tx, ty, tz) ? 1 : 0; }
+    static int fused_ok(lbm_ctx* h, int tx, int ty, int tz)
+    {
+        for (const SimDev& d : h->sims)
+            if (d.eos != h->sims[0].eos) return 0;  // one equation of state per fused launch
+        return fused_shape(h->storage, D, tx, ty, tz) ? 1 : 0;
+    }
 
     static Ops ops() { return Ops{init, step, macro, export_moments, export_pops, invariants, fused_ok}; }
 };
+
+cudaError_t fused_dispatch(int storage, int dim, int eos, int tx, int ty, int tz, const SimDev* sims,
+                           const TileEntry* tiles, int ntiles, const void* src, void* dst, const void* Min, void* Mout,
+                           long long Ntot, unsigned long long* diag, cudaStream_t stream)
+{
+    switch (storage) {
+    case LBM_F64: return fused_dispatch_f64(dim, eos, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_F32: return fused_dispatch_f32(dim, eos, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_BF16: return fused_dispatch_bf16(dim, eos, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_F16: return fused_dispatch_f16(dim, eos, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool fused_shape(int storage, int dim, int tx, int ty, int tz)
+{
+    switch (storage) {
+    case LBM_F64: return fused_shape_f64(dim, tx, ty, tz);
+    case LBM_F32: return fused_shape_f32(dim, tx, ty, tz);
+    case LBM_BF16: return fused_shape_bf16(dim, tx, ty, tz);
+    case LBM_F16: return fused_shape_f16(dim, tx, ty, tz);
+    }
+    return false;
+}
+
+// default tile of the fused kernel per lattice and storage
+void fused_default_tile(int dim, int storage, int& tx, int& ty, int& tz)
+{
+    if (dim == 2) {
+        tx = 32;
+        ty = storage == LBM_F64 ? 8 : 16;
+        tz = 1;
+    } else {
+        tx = 8;
+        ty = 8;
+        tz = 4;
+    }
+}
 
 bool pick_ops(int dim, int storage, Ops& ops, size_t& rbytes, size_t& sbytes)
 {
@@ -231,7 +280,10 @@ int check_lattice(const lbm_lattice* L, std::string& why)
     if (L->dim != 2 && L->dim != 3) { why = "dim must be 2 or 3"; return LBM_E_INVALID; }
     if (L->nx < 1 || L->ny < 1 || L->nz < 1) { why = "nx, ny, nz must be >= 1"; return LBM_E_INVALID; }
     if (L->dim == 2 && (L->nz != 1 || L->zwalls)) { why = "2-D lattices need nz = 1 and no z walls"; return LBM_E_INVALID; }
-    if ((long long)L->nx * L->ny * L->nz > (1LL << 31) - 1) { why = "more than 2^31 - 1 cells"; return LBM_E_INVALID; }
+    if ((long long)L->nx * L->ny * L->nz * (L->dim == 2 ? 9 : 27) > 0xFFFFFFFFLL) {
+        why = "too many cells: Q * cells must stay below 2^32 per simulation";
+        return LBM_E_INVALID;
+    }
     if (L->zwalls != 0 && L->zwalls != 1) { why = "zwalls must be 0 or 1"; return LBM_E_INVALID; }
     if (L->storage < LBM_F64 || L->storage > LBM_F16) { why = "unknown storage"; return LBM_E_INVALID; }
     if (L->phi_scheme != LBM_PHI_UPWIND && L->phi_scheme != LBM_PHI_CENTRAL) { why = "unknown phi_scheme"; return LBM_E_INVALID; }

@@ -44,6 +44,28 @@ struct SimDev {
     float fref[27], gref[27];     // storage offsets (16-bit storage only; zero otherwise)
 };
 
+// The same constants in the arithmetic type R (built once per tile on the
+// device, so that float32 kernels never convert from float64 on the way).
+template <typename F> struct SimC {
+    int nx, ny, nz, zwalls;
+    long long N, pop_off, cell_off;
+    int eos, phi_central, t_solver, zlo, zhi;
+    F R, cv, a, b, Tc, kw, kappa, eta_mu, k_mu, beta_f, beta_g, acc[3], q, inv_cv, inv_Tc, lam_c, athe_c;
+    F fref[27], gref[27];
+};
+
+template <typename R> __device__ inline void simc_from(SimC<R>& d, const SimDev& s)
+{
+    d.nx = s.nx; d.ny = s.ny; d.nz = s.nz; d.zwalls = s.zwalls;
+    d.N = s.N; d.pop_off = s.pop_off; d.cell_off = s.cell_off;
+    d.eos = s.eos; d.phi_central = s.phi_central; d.t_solver = s.t_solver; d.zlo = s.zlo; d.zhi = s.zhi;
+    d.R = (R)s.R; d.cv = (R)s.cv; d.a = (R)s.a; d.b = (R)s.b; d.Tc = (R)s.Tc; d.kw = (R)s.kw;
+    d.kappa = (R)s.kappa; d.eta_mu = (R)s.eta_mu; d.k_mu = (R)s.k_mu; d.beta_f = (R)s.beta_f; d.beta_g = (R)s.beta_g;
+    for (int a = 0; a < 3; ++a) d.acc[a] = (R)s.acc[a];
+    d.q = (R)s.q; d.inv_cv = (R)s.inv_cv; d.inv_Tc = (R)s.inv_Tc; d.lam_c = (R)s.lam_c; d.athe_c = (R)s.athe_c;
+    for (int i = 0; i < 27; ++i) { d.fref[i] = (R)s.fref[i]; d.gref[i] = (R)s.gref[i]; }
+}
+
 // ---------------------------------------------------------------------------
 // Storage codecs: populations are stored as S, computed in R.
 // ---------------------------------------------------------------------------
@@ -78,7 +100,7 @@ template <typename R> struct RhoPart {
     R rho, id1, iden, lam;  // 1/(1 - b rho); 1/(1 + 2 b rho - b^2 rho^2); Lambda(rho) (Peng-Robinson)
 };
 
-template <typename R> __host__ __device__ __forceinline__ RhoPart<R> rho_part(const SimDev& s, R rho)
+template <typename R, typename C> __host__ __device__ __forceinline__ RhoPart<R> rho_part(const C& s, R rho)
 {
     RhoPart<R> p;
     p.rho = rho;
@@ -98,9 +120,9 @@ template <typename R> __host__ __device__ __forceinline__ RhoPart<R> rho_part(co
     return p;
 }
 
-template <typename R> __host__ __device__ __forceinline__ R pr_sq(const SimDev& s, R T) { return sqrt(T * (R)s.inv_Tc); }
+template <typename R, typename C> __host__ __device__ __forceinline__ R pr_sq(const C& s, R T) { return sqrt(T * (R)s.inv_Tc); }
 
-template <typename R> __host__ __device__ __forceinline__ R eos_P(const SimDev& s, const RhoPart<R>& p, R T)
+template <typename R, typename C> __host__ __device__ __forceinline__ R eos_P(const C& s, const RhoPart<R>& p, R T)
 {
     const R rho = p.rho;
     if (s.eos == EOS_IDEAL) return rho * (R)s.R * T;
@@ -109,7 +131,7 @@ template <typename R> __host__ __device__ __forceinline__ R eos_P(const SimDev& 
     return rho * (R)s.R * T * p.id1 - (R)s.a * m * m * rho * rho * p.iden;
 }
 
-template <typename R> __host__ __device__ __forceinline__ R eos_e(const SimDev& s, const RhoPart<R>& p, R T)
+template <typename R, typename C> __host__ __device__ __forceinline__ R eos_e(const C& s, const RhoPart<R>& p, R T)
 {
     if (s.eos == EOS_IDEAL) return (R)s.cv * T;
     if (s.eos == EOS_VDW) return (R)s.cv * T - (R)s.a * p.rho;
@@ -118,7 +140,7 @@ template <typename R> __host__ __device__ __forceinline__ R eos_e(const SimDev& 
 }
 
 // c_v = (de/dT)_rho
-template <typename R> __host__ __device__ __forceinline__ R eos_cv(const SimDev& s, const RhoPart<R>& p, R T)
+template <typename R, typename C> __host__ __device__ __forceinline__ R eos_cv(const C& s, const RhoPart<R>& p, R T)
 {
     if (s.eos != EOS_PR) return (R)s.cv;
     const R k = (R)s.kw;
@@ -130,7 +152,7 @@ template <typename R> struct Thermo {
     R P, PT, Pr, cv;
 };
 
-template <typename R> __host__ __device__ __forceinline__ Thermo<R> thermo(const SimDev& s, const RhoPart<R>& p, R T)
+template <typename R, typename C> __host__ __device__ __forceinline__ Thermo<R> thermo(const C& s, const RhoPart<R>& p, R T)
 {
     Thermo<R> t;
     const R rho = p.rho, Rg = (R)s.R;
@@ -159,20 +181,20 @@ template <typename R> __host__ __device__ __forceinline__ Thermo<R> thermo(const
     return t;
 }
 
-template <typename R> __device__ __forceinline__ R eos_dPdT(const SimDev& s, const RhoPart<R>& p, R T)
+template <typename R, typename C> __device__ __forceinline__ R eos_dPdT(const C& s, const RhoPart<R>& p, R T)
 {
     return thermo<R>(s, p, T).PT;
 }
 
-template <typename R> __device__ __forceinline__ R eos_dPdrho(const SimDev& s, const RhoPart<R>& p, R T)
+template <typename R, typename C> __device__ __forceinline__ R eos_dPdrho(const C& s, const RhoPart<R>& p, R T)
 {
     return thermo<R>(s, p, T).Pr;
 }
 
 // Newton's method on e(rho, T) - e = 0 for Peng-Robinson, in precision W.
 // Returns the iteration count (cap + 1 when the cap was hit).
-template <typename W>
-__device__ __forceinline__ int pr_newton(const SimDev& s, const RhoPart<W>& p, W e, W& T, W tol, int cap)
+template <typename W, typename C>
+__device__ __forceinline__ int pr_newton(const C& s, const RhoPart<W>& p, W e, W& T, W tol, int cap)
 {
     for (int it = 1; it <= cap; ++it) {
         W r = eos_e<W>(s, p, T) - e;
@@ -186,8 +208,8 @@ __device__ __forceinline__ int pr_newton(const SimDev& s, const RhoPart<W>& p, W
 // T(rho, e): explicit for ideal gas and van der Waals (Eqs. idealgasT,
 // lbm_temp); Peng-Robinson by Newton from Tguess -- in float64 for the
 // float64 path; in float32 with a float64 fallback for the float32 path.
-template <typename R>
-__device__ __forceinline__ R eos_T(const SimDev& s, const RhoPart<R>& p, R e, R Tguess, bool& capped)
+template <typename R, typename C>
+__device__ __forceinline__ R eos_T(const C& s, const RhoPart<R>& p, R e, R Tguess, bool& capped)
 {
     capped = false;
     if (s.eos == EOS_IDEAL) return e * (R)s.inv_cv;
@@ -215,8 +237,8 @@ template <typename R> struct Macro {
     R rho, ir, u[3], F[3], Q, T, P, theta, h, cv, icv, gam, athe, e;
 };
 
-template <int D, typename R>
-__device__ __forceinline__ Macro<R> macro_cell(const SimDev& s, R rho, const R* j, R G, const R* F, R Q, R Tguess,
+template <int D, typename R, typename C>
+__device__ __forceinline__ Macro<R> macro_cell(const C& s, R rho, const R* j, R G, const R* F, R Q, R Tguess,
                                                unsigned& flags)
 {
     Macro<R> m;
@@ -285,8 +307,8 @@ template <typename R> __host__ __device__ __forceinline__ void hpsi3(R u, R th, 
     o[2] = R(0.5) * (o2 - o1);
 }
 
-template <int D, typename R>
-__device__ __forceinline__ void collide_cell(const SimDev& s, const Macro<R>& m, R divu, const R* gh, const R* gT,
+template <int D, typename R, typename C>
+__device__ __forceinline__ void collide_cell(const C& s, const Macro<R>& m, R divu, const R* gh, const R* gT,
                                              const R* Phi, R* f, R* g)
 {
     constexpr int Q = Lat<D>::Q;
@@ -394,7 +416,8 @@ __device__ __forceinline__ int mirror_z(int z, int nz, bool& flip)
 }
 
 // cell index of the stencil neighbour, with the mirror flag
-__device__ __forceinline__ long long nb_index(const SimDev& s, int x, int y, int z, bool& flip)
+template <typename C>
+__device__ __forceinline__ long long nb_index(const C& s, int x, int y, int z, bool& flip)
 {
     x = wrapi(x, s.nx);
     y = wrapi(y, s.ny);
@@ -410,8 +433,8 @@ __device__ __forceinline__ long long nb_index(const SimDev& s, int x, int y, int
 // Pull streaming: the pre-collision f_i(x) is f'_i(x - c_i); across a z wall
 // (half-way bounce-back) it is f'_opp(i)(x).  Returns the storage element
 // index within one distribution block and the direction whose offset applies.
-template <int D>
-__device__ __forceinline__ long long pull_index(const SimDev& s, int i, int x, int y, int z, int& isrc)
+template <int D, typename C>
+__device__ __forceinline__ long long pull_index(const C& s, int i, int x, int y, int z, int& isrc)
 {
     int sx = wrapi(x - cc(i, 0), s.nx);
     int sy = wrapi(y - cc(i, 1), s.ny);

@@ -62,14 +62,21 @@ __device__ __forceinline__ int wrapc(int v, int n)
 }
 
 // coordinate of a stencil neighbour in z: periodic, or mirrored beyond walls
-__device__ __forceinline__ int zcoord(const SimDev& s, int z, bool& flip)
+template <typename C>
+__device__ __forceinline__ int zcoord(const C& s, int z, bool& flip)
 {
     flip = false;
     if (!s.zwalls) return wrapc(z, s.nz);
     return mirror_z(z, s.nz, flip);
 }
 
-template <int D, typename R, typename S, int TX, int TY, int TZ>
+// Constants with the equation of state fixed at compile time: every
+// `s.eos == ...` test in the shared helpers folds away.
+template <typename R, int EK> struct SimK : SimC<R> {
+    static constexpr int eos = EK;
+};
+
+template <int D, typename R, typename S, int EK, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 : 1)
     k_fused(const SimDev* __restrict__ sims, const TileEntry* __restrict__ tiles, int ntiles,
             const S* __restrict__ src, S* __restrict__ dst, const R* __restrict__ Min, R* __restrict__ Mout,
@@ -80,7 +87,7 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
     constexpr int HZ = G::HZ;
     constexpr int n5 = G::n(5), n4 = G::n(4), n3 = G::n(3), n1 = G::n(1), n0 = G::n(0);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ SimDev s;
+    __shared__ SimK<R, EK> s;
     __shared__ int cur_sim;
     R* s_rho = reinterpret_cast<R*>(smem_raw);
     R* s_L = s_rho + n5;
@@ -95,16 +102,23 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
         const TileEntry te = tiles[t];
         if (te.sim != cur_sim) {
             __syncthreads();
-            const int nw = (int)(sizeof(SimDev) / sizeof(int));
-            const int* srcw = reinterpret_cast<const int*>(sims + te.sim);
-            for (int k = tid; k < nw; k += kFusedThreads) reinterpret_cast<int*>(&s)[k] = srcw[k];
-            if (tid == 0) cur_sim = te.sim;
+            if (tid == 0) {
+                simc_from<R>(static_cast<SimC<R>&>(s), sims[te.sim]);
+                cur_sim = te.sim;
+            }
             __syncthreads();
         }
         const int nx = s.nx, ny = s.ny, nz = s.nz;
         const bool walls = D == 3 && s.zwalls;
         const long long off = s.cell_off;
+        const unsigned Ncell = (unsigned)s.N;
+        // owned extent of the tile (ragged at the domain's far edges)
+        const unsigned vx = (unsigned)min(TX, nx - te.x0), vy = (unsigned)min(TY, ny - te.y0);
+        const unsigned vz = (unsigned)min(G::tz, nz - te.z0);
         const R* Mrho = Min + M_RHO * Ntot + off;
+        const R* Mj = Min + M_J * Ntot + off;
+        const R* MG = Min + M_G * Ntot + off;
+        const R* MT = Min + M_T * Ntot + off;
 
         // ---- 1. rho on T+5 (ghosts beyond walls: the image's value); zero the accumulators
         for (int k = tid; k < n5; k += kFusedThreads) {
@@ -112,7 +126,7 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
             bool fl;
             const int x = wrapc(te.x0 - 5 + lx, nx), y = wrapc(te.y0 - 5 + ly, ny);
             const int z = D == 3 ? zcoord(s, te.z0 - 5 + lz, fl) : 0;
-            s_rho[k] = Mrho[x + (long long)nx * (y + (long long)ny * z)];
+            s_rho[k] = Mrho[(unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z)];
         }
         for (int k = tid; k < (D + 2) * n0; k += kFusedThreads) s_acc[k] = R(0);
         __syncthreads();
@@ -154,18 +168,18 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
                 if (!(walls && (zr < 0 || zr >= nz))) {
                     const int x = wrapc(te.x0 - 3 + lx, nx), y = wrapc(te.y0 - 3 + ly, ny);
                     const int z = D == 3 ? wrapc(zr, nz) : 0;
-                    const long long gk = off + x + (long long)nx * (y + (long long)ny * z);
+                    const unsigned gk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
                     const int c4 = (lx + 1) + G::w(4) * ((ly + 1) + G::h(4) * (lz + HZ));
                     const R r = s_rho[(lx + 2) + G::w(5) * ((ly + 2) + G::h(5) * (lz + 2 * HZ))];
                     constexpr int st4[3] = {1, G::w(4), G::w(4) * G::h(4)};
                     R Fv[3] = {0, 0, 0}, j[3] = {0, 0, 0};
 #pragma unroll
                     for (int a = 0; a < D; ++a) {
-                        Fv[a] = r * ((R)s.acc[a] + (R)s.kappa * R(0.5) * (s_L[c4 + st4[a]] - s_L[c4 - st4[a]]));
-                        j[a] = Min[(M_J + a) * Ntot + gk];
+                        Fv[a] = r * (s.acc[a] + s.kappa * R(0.5) * (s_L[c4 + st4[a]] - s_L[c4 - st4[a]]));
+                        j[a] = Mj[(size_t)a * Ntot + gk];
                     }
-                    const R Qh = (R)heat_at(s, z);
-                    const Macro<R> m = macro_cell<D, R>(s, r, j, Min[M_G * Ntot + gk], Fv, Qh, Min[M_T * Ntot + gk], flags);
+                    const R Qh = heat_q<R>(s, z);
+                    const Macro<R> m = macro_cell<D, R>(s, r, j, MG[gk], Fv, Qh, MT[gk], flags);
 #pragma unroll
                     for (int a = 0; a < D; ++a) {
                         s_st[(G::U + a) * n3 + k] = m.u[a];
@@ -212,9 +226,9 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
 
         // ---- 4. collide T+1, store T, accumulate the next moments of T
         const S* fb = src + s.pop_off;
-        const S* gb = fb + (long long)Q * s.N;
+        const S* gb = fb + (size_t)Q * s.N;
         S* fo = dst + s.pop_off;
-        S* go = fo + (long long)Q * s.N;
+        S* go = fo + (size_t)Q * s.N;
         for (int k = tid; k < n1; k += kFusedThreads) {
             const int lx = k % G::w(1), ly = (k / G::w(1)) % G::h(1), lz = k / (G::w(1) * G::h(1));
             const int zr = te.z0 - HZ + lz;
@@ -231,16 +245,16 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 m.u[a] = a < D ? s_st[(G::U + a) * n3 + c3] : R(0);
-                m.F[a] = a < D ? m.rho * ((R)s.acc[a] + (R)s.kappa * R(0.5) * (s_L[c4 + st4[a]] - s_L[c4 - st4[a]]))
+                m.F[a] = a < D ? m.rho * (s.acc[a] + s.kappa * R(0.5) * (s_L[c4 + st4[a]] - s_L[c4 - st4[a]]))
                                : R(0);
             }
-            m.Q = (R)heat_at(s, z);
+            m.Q = heat_q<R>(s, z);
             m.T = s_st[G::TT * n3 + c3];
             m.h = s_st[G::H * n3 + c3];
             m.P = s_lo[G::LP * n1 + k];
             m.theta = s_lo[G::LTH * n1 + k];
             m.cv = s_lo[G::LCV * n1 + k];
-            m.icv = s.eos == EOS_PR ? R(1) / m.cv : (R)s.inv_cv;
+            m.icv = s.eos == EOS_PR ? R(1) / m.cv : s.inv_cv;
             m.gam = s_lo[G::LGAM * n1 + k];
             m.athe = s_lo[G::LATHE * n1 + k];
             m.e = s_lo[G::LE * n1 + k];
@@ -280,24 +294,30 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
                     zs[2] = z == nz - 1 ? 0 : z + 1;
                 }
             }
-            const long long self = x + (long long)nx * (y + (long long)ny * z);
+            const unsigned self = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+            unsigned rows[3][3];  // row offsets (y, z) of the pull sources
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int c = 0; c < (D == 3 ? 3 : 1); ++c)
+                    rows[b][c] = (unsigned)nx * ((unsigned)ys[b] + (unsigned)ny * (unsigned)zs[c]);
             R f[Q], gp[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const int d0 = dig(i, 0), d1 = dig(i, 1), d2 = D == 3 ? dig(i, 2) : 0;
-                long long idx;
+                unsigned idx;
                 int isrc = i;
                 if (D == 3 && zwall[d2]) {
                     isrc = opp(i);
-                    idx = (long long)isrc * s.N + self;
+                    idx = (unsigned)isrc * Ncell + self;
                 } else {
-                    idx = (long long)i * s.N + xs[d0] + (long long)nx * (ys[d1] + (long long)ny * zs[d2]);
+                    idx = (unsigned)i * Ncell + (unsigned)xs[d0] + rows[d1][d2];
                 }
                 f[i] = Codec<S, R>::ld(fb + idx);
                 gp[i] = Codec<S, R>::ld(gb + idx);
                 if (Codec<S, R>::offset) {
-                    f[i] += (R)s.fref[isrc];
-                    gp[i] += (R)s.gref[isrc];
+                    f[i] += s.fref[isrc];
+                    gp[i] += s.gref[isrc];
                 }
             }
             collide_cell<D, R>(s, m, divu, gh, gT, Phi, f, gp);
@@ -308,32 +328,31 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
             if (inT && gx < nx && gy < ny && gz < nz) {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    const R fr = Codec<S, R>::offset ? (R)s.fref[i] : R(0);
-                    const R gr = Codec<S, R>::offset ? (R)s.gref[i] : R(0);
-                    Codec<S, R>::st(fo + (long long)i * s.N + self, f[i] - fr);
-                    Codec<S, R>::st(go + (long long)i * s.N + self, gp[i] - gr);
+                    const R fr = Codec<S, R>::offset ? s.fref[i] : R(0);
+                    const R gr = Codec<S, R>::offset ? s.gref[i] : R(0);
+                    Codec<S, R>::st(fo + (unsigned)i * Ncell + self, f[i] - fr);
+                    Codec<S, R>::st(go + (unsigned)i * Ncell + self, gp[i] - gr);
                 }
             }
-            // next-step moments: f'_i(x) becomes f_i(x + c_i), or f_opp(i)(x) across a z wall
+            // next-step moments: f'_i(x) becomes f_i(x + c_i), or f_opp(i)(x) across a z wall.
+            // Branch-free: a destination counts if it lies in the owned part of T.
+            const bool zlo_wall = walls && z == 0, zhi_wall = walls && z == nz - 1;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                int dx = tx + cc(i, 0), dy = ty + cc(i, 1), dz = tz + (D == 3 ? cc(i, 2) : 0);
-                R sgn = R(1);
-                if (walls) {
-                    const int zt = z + cc(i, 2);
-                    if (zt < 0 || zt >= nz) {
-                        dx = tx; dy = ty; dz = tz;
-                        sgn = R(-1);
-                    }
-                }
-                if (dx < 0 || dy < 0 || dz < 0 || dx >= TX || dy >= TY || dz >= G::tz) continue;
-                if (te.x0 + dx >= nx || te.y0 + dy >= ny || te.z0 + dz >= nz) continue;
-                const int dd = dx + TX * (dy + TY * dz);
-                atomicAdd(&s_acc[dd], f[i]);
+                const int ci0 = cc(i, 0), ci1 = cc(i, 1), ci2 = D == 3 ? cc(i, 2) : 0;
+                const bool bounce = (ci2 < 0 && zlo_wall) || (ci2 > 0 && zhi_wall);
+                const int dx = bounce ? tx : tx + ci0, dy = bounce ? ty : ty + ci1, dz = bounce ? tz : tz + ci2;
+                const bool ok = (unsigned)dx < vx && (unsigned)dy < vy && (D == 2 || (unsigned)dz < vz);
+                if (ok) {
+                    const int dd = dx + TX * (dy + TY * dz);
+                    atomicAdd(&s_acc[dd], f[i]);
 #pragma unroll
-                for (int a = 0; a < D; ++a)
-                    if (cc(i, a) != 0) atomicAdd(&s_acc[(1 + a) * n0 + dd], sgn * R(cc(i, a)) * f[i]);
-                atomicAdd(&s_acc[(1 + D) * n0 + dd], gp[i]);
+                    for (int a = 0; a < D; ++a) {
+                        const int ca = cc(i, a);
+                        if (ca != 0) atomicAdd(&s_acc[(1 + a) * n0 + dd], (ca > 0) != bounce ? f[i] : -f[i]);
+                    }
+                    atomicAdd(&s_acc[(1 + D) * n0 + dd], gp[i]);
+                }
             }
         }
         __syncthreads();
@@ -343,12 +362,13 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
             const int tx = d % TX, ty = (d / TX) % TY, tz = d / (TX * TY);
             const int x = te.x0 + tx, y = te.y0 + ty, z = te.z0 + tz;
             if (x >= nx || y >= ny || z >= nz) continue;
-            const long long kk = off + x + (long long)nx * (y + (long long)ny * z);
-            Mout[M_RHO * Ntot + kk] = s_acc[d];
+            const unsigned kk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+            R* Mo = Mout + off;
+            Mo[M_RHO * Ntot + kk] = s_acc[d];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) Mout[(M_J + a) * Ntot + kk] = a < D ? s_acc[(1 + a) * n0 + d] : R(0);
-            Mout[M_G * Ntot + kk] = s_acc[(1 + D) * n0 + d];
-            Mout[M_T * Ntot + kk] = s_st[G::TT * n3 + (tx + 3) + G::w(3) * ((ty + 3) + G::h(3) * (tz + 3 * HZ))];
+            for (int a = 0; a < 3; ++a) Mo[(M_J + a) * Ntot + kk] = a < D ? s_acc[(1 + a) * n0 + d] : R(0);
+            Mo[M_G * Ntot + kk] = s_acc[(1 + D) * n0 + d];
+            Mo[M_T * Ntot + kk] = s_st[G::TT * n3 + (tx + 3) + G::w(3) * ((ty + 3) + G::h(3) * (tz + 3 * HZ))];
         }
         __syncthreads();
     }
@@ -396,55 +416,28 @@ void fused_moments_launch(const SimDev* sims, const BlockEntry* table, int nbloc
 }
 
 // ---------------------------------------------------------------------------
-// Tile shapes built (the autotuner picks among them per lattice and storage).
+// Launch of one instantiated shape (persistent grid: resident CTAs x SMs).
 // ---------------------------------------------------------------------------
-#define LBM_FUSED_TILES_2D(X) X(32, 8, 1) X(32, 16, 1) X(32, 32, 1) X(64, 16, 1)
-#define LBM_FUSED_TILES_3D(X) X(8, 8, 4) X(16, 8, 4) X(8, 8, 8)
-
-inline void fused_default_tile(int dim, int storage, int& tx, int& ty, int& tz)
-{
-    if (dim == 2) {
-        tx = 32;
-        ty = storage == 0 ? 8 : 16;
-        tz = 1;
-    } else {
-        tx = 8;
-        ty = 8;
-        tz = 4;
-    }
-}
-
 template <int D, typename R, int TX, int TY, int TZ> constexpr size_t fused_smem()
 {
     return TileShape<D, TX, TY, TZ>::elems() * sizeof(R);
 }
 
-template <int D, typename R, typename S> bool fused_tile_ok(int tx, int ty, int tz)
-{
-    bool ok = false;
-#define LBM_OK_2D(A, B, C) \
-    if (D == 2 && tx == A && ty == B && tz == C) ok = fused_smem<D, R, A, B, C>() <= 227u * 1024u;
-#define LBM_OK_3D(A, B, C) \
-    if (D == 3 && tx == A && ty == B && tz == C) ok = fused_smem<D, R, A, B, C>() <= 227u * 1024u;
-    LBM_FUSED_TILES_2D(LBM_OK_2D)
-    LBM_FUSED_TILES_3D(LBM_OK_3D)
-#undef LBM_OK_2D
-#undef LBM_OK_3D
-    return ok;
-}
-
-template <int D, typename R, typename S, int TX, int TY, int TZ>
-cudaError_t fused_launch_shape(const SimDev* sims, const TileEntry* tiles, int ntiles, const S* src, S* dst,
-                               const R* Min, R* Mout, long long Ntot, unsigned long long* diag, cudaStream_t stream)
+template <int D, typename R, typename S, int EK, int TX, int TY, int TZ>
+cudaError_t fused_launch_shape(const SimDev* sims, const TileEntry* tiles, int ntiles, const void* src, void* dst,
+                               const void* Min, void* Mout, long long Ntot, unsigned long long* diag,
+                               cudaStream_t stream)
 {
     constexpr size_t smem = fused_smem<D, R, TX, TY, TZ>();
+    static_assert(smem <= 227u * 1024u, "tile does not fit in shared memory");
     static int grid_cap = 0;
     if (grid_cap == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<D, R, S, TX, TY, TZ>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<D, R, S, EK, TX, TY, TZ>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, nsm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, R, S, TX, TY, TZ>, kFusedThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, R, S, EK, TX, TY, TZ>, kFusedThreads,
+                                                          smem);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -452,29 +445,9 @@ cudaError_t fused_launch_shape(const SimDev* sims, const TileEntry* tiles, int n
         grid_cap = per_sm * nsm;
     }
     const int grid = ntiles < grid_cap ? ntiles : grid_cap;
-    k_fused<D, R, S, TX, TY, TZ><<<grid, kFusedThreads, smem, stream>>>(sims, tiles, ntiles, src, dst, Min, Mout, Ntot,
-                                                                        diag);
+    k_fused<D, R, S, EK, TX, TY, TZ><<<grid, kFusedThreads, smem, stream>>>(
+        sims, tiles, ntiles, (const S*)src, (S*)dst, (const R*)Min, (R*)Mout, Ntot, diag);
     return cudaGetLastError();
-}
-
-template <int D, typename R, typename S>
-cudaError_t fused_step_launch(const SimDev* sims, const TileEntry* tiles, int ntiles, int tx, int ty, int tz,
-                              const S* src, S* dst, const R* Min, R* Mout, long long Ntot, unsigned long long* diag,
-                              cudaStream_t stream)
-{
-#define LBM_GO_2D(A, B, C)                                                                                  \
-    if (D == 2 && tx == A && ty == B)                                                                       \
-        if constexpr (D == 2 && fused_smem<2, R, A, B, C>() <= 227u * 1024u)                               \
-            return fused_launch_shape<D, R, S, A, B, C>(sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
-#define LBM_GO_3D(A, B, C)                                                                                  \
-    if (D == 3 && tx == A && ty == B && tz == C)                                                            \
-        if constexpr (D == 3 && fused_smem<3, R, A, B, C>() <= 227u * 1024u)                               \
-            return fused_launch_shape<D, R, S, A, B, C>(sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
-    LBM_FUSED_TILES_2D(LBM_GO_2D)
-    LBM_FUSED_TILES_3D(LBM_GO_3D)
-#undef LBM_GO_2D
-#undef LBM_GO_3D
-    return cudaErrorInvalidValue;
 }
 
 }  // namespace lbm

@@ -1,0 +1,27 @@
+// Entry points of the fused-step instantiations.  Each storage type lives in
+// its own translation unit (lbm_fused_<storage>.cu) so that the kernels,
+// specialised per lattice, equation of state and tile shape, compile in
+// parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+struct SimDev;
+struct TileEntry;
+
+#define LBM_FUSED_DECL(NAME)                                                                                     \
+    cudaError_t fused_dispatch_##NAME(int dim, int eos, int tx, int ty, int tz, const SimDev* sims,              \
+                                      const TileEntry* tiles, int ntiles, const void* src, void* dst,            \
+                                      const void* Min, void* Mout, long long Ntot, unsigned long long* diag,     \
+                                      cudaStream_t stream);                                                      \
+    bool fused_shape_##NAME(int dim, int tx, int ty, int tz);
+
+LBM_FUSED_DECL(f64)
+LBM_FUSED_DECL(f32)
+LBM_FUSED_DECL(bf16)
+LBM_FUSED_DECL(f16)
+#undef LBM_FUSED_DECL
+
+}  // namespace lbm

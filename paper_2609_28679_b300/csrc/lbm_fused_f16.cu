@@ -1,0 +1,62 @@
+// Fused-step kernels for float16 (offset) population storage: every tile shape below,
+// for D2Q9 and D3Q27 and each equation of state.
+#include "lbm_fused.cuh"
+#include "lbm_fused_api.h"
+
+namespace lbm {
+
+#define TILES_2D(X) X(32, 16, 1) X(32, 32, 1)
+#define TILES_3D(X) X(8, 8, 4) X(16, 8, 4)
+
+namespace {
+
+template <int D, int EK>
+cudaError_t go(int tx, int ty, int tz, const SimDev* sims, const TileEntry* tiles, int ntiles, const void* src,
+               void* dst, const void* Min, void* Mout, long long Ntot, unsigned long long* diag, cudaStream_t stream)
+{
+#define CASE(A, B, C)                                                                                           \
+    if (tx == A && ty == B && tz == C)                                                                          \
+        return fused_launch_shape<D, float, __half, EK, A, B, C>(sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag,  \
+                                                         stream);
+    if constexpr (D == 2) {
+        TILES_2D(CASE)
+    } else {
+        TILES_3D(CASE)
+    }
+#undef CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t fused_dispatch_f16(int dim, int eos, int tx, int ty, int tz, const SimDev* sims, const TileEntry* tiles,
+                               int ntiles, const void* src, void* dst, const void* Min, void* Mout, long long Ntot,
+                               unsigned long long* diag, cudaStream_t stream)
+{
+#define ARGS tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream
+    if (dim == 2) {
+        if (eos == EOS_IDEAL) return go<2, EOS_IDEAL>(ARGS);
+        if (eos == EOS_VDW) return go<2, EOS_VDW>(ARGS);
+        if (eos == EOS_PR) return go<2, EOS_PR>(ARGS);
+    } else if (dim == 3) {
+        if (eos == EOS_IDEAL) return go<3, EOS_IDEAL>(ARGS);
+        if (eos == EOS_VDW) return go<3, EOS_VDW>(ARGS);
+        if (eos == EOS_PR) return go<3, EOS_PR>(ARGS);
+    }
+#undef ARGS
+    return cudaErrorInvalidValue;
+}
+
+bool fused_shape_f16(int dim, int tx, int ty, int tz)
+{
+#define HAS(A, B, C) if (tx == A && ty == B && tz == C) return true;
+    if (dim == 2) {
+        TILES_2D(HAS)
+    } else if (dim == 3) {
+        TILES_3D(HAS)
+    }
+#undef HAS
+    return false;
+}
+
+}  // namespace lbm

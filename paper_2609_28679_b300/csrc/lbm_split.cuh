@@ -32,7 +32,8 @@ __device__ __forceinline__ void load_sim(SimDev& dst, const SimDev* sims, int si
     __syncthreads();
 }
 
-__device__ __forceinline__ void cell_xyz(const SimDev& s, long long k, int& x, int& y, int& z)
+template <typename C>
+__device__ __forceinline__ void cell_xyz(const C& s, long long k, int& x, int& y, int& z)
 {
     x = (int)(k % s.nx);
     long long r = k / s.nx;
@@ -40,9 +41,17 @@ __device__ __forceinline__ void cell_xyz(const SimDev& s, long long k, int& x, i
     z = (int)(r / s.ny);
 }
 
-__device__ __forceinline__ double heat_at(const SimDev& s, int z)
+template <typename C>
+__device__ __forceinline__ double heat_at(const C& s, int z)
 {
-    return (s.zhi <= 0 || (z >= s.zlo && z < s.zhi)) ? s.q : 0.0;
+    return (s.zhi <= 0 || (z >= s.zlo && z < s.zhi)) ? (double)s.q : 0.0;
+}
+
+// heat source of a cell in the arithmetic type
+template <typename R, typename C>
+__device__ __forceinline__ R heat_q(const C& s, int z)
+{
+    return (s.zhi <= 0 || (z >= s.zlo && z < s.zhi)) ? (R)s.q : R(0);
 }
 
 // Warp-aggregated diagnostic counters (bit 0: non-finite, 1: theta <= 0, 2: Newton cap).
@@ -370,7 +379,7 @@ __global__ void __launch_bounds__(kBlockCells) k_invariants(const SimDev* __rest
 }
 
 // Fixed-order sum of the block partials of each simulation.
-__global__ void k_invariants_final(const double* __restrict__ partials, const int* __restrict__ sim_block_start, int nsim,
+static __global__ void k_invariants_final(const double* __restrict__ partials, const int* __restrict__ sim_block_start, int nsim,
                                    int nv, double* __restrict__ out)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
