@@ -174,8 +174,36 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz);
 /* The variant and tile that lbm_step uses now. */
 int lbm_get_kernel(lbm_handle h, int *variant, int *tx, int *ty, int *tz);
 
+/* One time step of float64 populations owned by the caller, allocating
+ * nothing.  The paper has no counterpart: this is a variant of the library's
+ * three-pass step for callers that cannot allocate device memory when they
+ * step -- code running inside a CUDA graph capture managed by someone else,
+ * hosts that give the library a fixed memory budget, callers outside
+ * PyTorch's allocator.  Its work arrays live in one fixed-size static device
+ * array (room for 65536 cells, about 11.5 MB, held on every GPU that loads the
+ * library until the process exits).
+ *
+ * f_in, g_in: pre-collision populations [Q][N] (device, float64, the layout
+ * of lbm_populations); f_out, g_out: the pre-collision populations of the
+ * next step (device, must not alias the inputs).  lattice->storage must be
+ * LBM_F64.  Peng-Robinson's Newton iteration starts from e/c_v (no guess is
+ * carried between calls).  Work is enqueued on `stream` (NULL: the legacy
+ * default stream); the call does not synchronise.
+ *
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls whose kernels overlap on the GPU (other
+ * streams, other threads) race and corrupt each other -- serialise them.
+ * Nothing carries over between calls: each one rewrites what it reads.
+ * Errors: LBM_E_INVALID (NULL pointers, bad sizes, more than 65536 cells,
+ * aliasing), LBM_E_UNSUPPORTED (storage other than float64), LBM_E_CUDA;
+ * lbm_last_error(NULL) describes the failure. */
+int lbm_step_static(const lbm_lattice *lattice, const lbm_eos *eos, double tau_f, double tau_g,
+                    const lbm_force *force, const lbm_heat *heat, const double *f_in, const double *g_in,
+                    double *f_out, double *g_out, void *stream);
+
 /* Message of the last failing call on h (or of the last failing lbm_create*
- * when h is NULL).  Valid until the next call on h. */
+ * or lbm_step_static when h is NULL).  Valid until the next call on h. */
 const char *lbm_last_error(lbm_handle h);
 
 #ifdef __cplusplus

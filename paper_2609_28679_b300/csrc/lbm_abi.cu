@@ -471,6 +471,9 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
 
 }  // namespace
 
+// message of a failing call that has no handle (lbm_create*, lbm_step_static)
+void lbm_set_global_error(const std::string& msg) { g_create_error = msg; }
+
 extern "C" {
 
 int lbm_create(const lbm_lattice* lattice, const lbm_eos* eos, double tau_f, double tau_g, const lbm_force* force,

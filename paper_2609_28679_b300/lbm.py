@@ -72,6 +72,10 @@ _SIGS = {
     "lbm_set_kernel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_get_kernel": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4),
     "lbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "lbm_step_static": (ctypes.c_int, [ctypes.POINTER(lbm_lattice), ctypes.POINTER(lbm_eos), ctypes.c_double,
+                                       ctypes.c_double, ctypes.POINTER(lbm_force), ctypes.POINTER(lbm_heat),
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
 }
 
 
@@ -193,6 +197,19 @@ def lbm_get_kernel(h):
     v = [ctypes.c_int() for _ in range(4)]
     _check(_lib.lbm_get_kernel(h, *[ctypes.byref(x) for x in v]), h)
     return tuple(x.value for x in v)
+
+
+def lbm_step_static(lattice: lbm_lattice, eos: lbm_eos, tau_f: float, tau_g: float, force, heat,
+                    f_in, g_in, f_out, g_out, stream: int | None = None) -> None:
+    """One float64 step of caller-owned device populations without any
+    allocation (see include/lbm.h); tensors are CUDA float64 [Q*N]."""
+    lib = _lib_gpu()
+    rc = lib.lbm_step_static(ctypes.byref(lattice), ctypes.byref(eos), tau_f, tau_g,
+                             ctypes.byref(force) if force is not None else None,
+                             ctypes.byref(heat) if heat is not None else None,
+                             _ptr(f_in), _ptr(g_in), _ptr(f_out), _ptr(g_out),
+                             ctypes.c_void_p(stream) if stream else None)
+    _check(rc, None)
 
 
 def lbm_last_error(h) -> str:
