@@ -171,6 +171,23 @@ int lbm_diagnostics(lbm_handle h, long long out[4]);
  * the variant cannot run. */
 int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz);
 
+/* Replay lbm_step's time steps as CUDA graphs of `steps_per_graph` steps (an
+ * even number >= 2; 0 turns graphs off).  lbm_step(h, n) then runs one eager
+ * step, n-1 steps as whole graphs and the remainder eagerly.  The graph is
+ * captured on the first such call and kept until the kernel or stream
+ * changes.  Needs a created stream (lbm_set_stream), not the legacy default
+ * stream: LBM_E_STATE otherwise. */
+int lbm_set_graph(lbm_handle h, int steps_per_graph);
+
+/* Autotuner: time trial_steps steps (after 2 warm-up steps) of the split path
+ * and of every built fused tile for this lattice, storage and equation of
+ * state, select the fastest, and restore the state as it was (populations,
+ * Newton guess and diagnostic counters; the step count does not advance).
+ * Outputs (any may be NULL): the chosen variant and tile, its ms per step.
+ * Synchronises; allocates one snapshot of the populations for the duration
+ * of the call. */
+int lbm_autotune(lbm_handle h, int trial_steps, int *variant, int *tx, int *ty, int *tz, double *ms_per_step);
+
 /* The variant and tile that lbm_step uses now. */
 int lbm_get_kernel(lbm_handle h, int *variant, int *tx, int *ty, int *tz);
 

@@ -60,6 +60,8 @@ struct lbm_ctx {
     bool moments_valid = false;   // fused path: M holds the moments of the current state
     int variant = LBM_KERNEL_SPLIT, tx = 0, ty = 0, tz = 0;
     int smem_bytes = 0;
+    int graph_steps = 0;               // steps per captured CUDA graph (0: launch eagerly)
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};  // per starting buffer parity
     std::string err;
     Ops ops{};
 };
@@ -328,8 +330,17 @@ int fill_sim(SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, do
     return LBM_OK;
 }
 
+void drop_graph(lbm_ctx* h)
+{
+    for (int p = 0; p < 2; ++p) {
+        if (h->graph_exec[p]) cudaGraphExecDestroy(h->graph_exec[p]);
+        h->graph_exec[p] = nullptr;
+    }
+}
+
 void free_all(lbm_ctx* h)
 {
+    drop_graph(h);
     void* ptrs[] = {h->d_sims, h->d_table, h->d_sim_block_start, h->d_tiles, h->pop[0], h->pop[1],
                     h->W, h->M, h->d_diag, h->d_partials};
     for (void* p : ptrs) lbm_glue_free(p);
@@ -500,6 +511,8 @@ int lbm_set_stream(lbm_handle h, void* stream)
 {
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
     LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+    drop_graph(h);
+    h->graph_steps = 0;
     h->stream = (cudaStream_t)stream;
     return LBM_OK;
 }
@@ -560,12 +573,62 @@ int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T, 
     return LBM_OK;
 }
 
+// Capture graph_steps steps (an even number, so the buffers return to the
+// same parity) into an executable graph on the handle's stream.
+static int capture_graph(lbm_ctx* h)
+{
+    cudaGraph_t g = nullptr;
+    LBM_CUDA_CHECK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    const int cur0 = h->cur;
+    int rc = h->ops.step(h, h->graph_steps);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->cur = cur0;  // nothing ran yet: the steps run when the graph is launched
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph_exec[cur0], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph_exec[cur0] = nullptr;
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    return LBM_OK;
+}
+
 int lbm_step(lbm_handle h, int n)
 {
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
     if (n < 0) return fail(h, LBM_E_INVALID, "n must be >= 0");
     if (!h->initialized) return fail(h, LBM_E_STATE, "lbm_init has not been called");
-    return h->ops.step(h, n);
+    if (h->graph_steps < 2 || n < h->graph_steps) return h->ops.step(h, n);
+    // one eager step first: it prepares the carried moments and the kernels'
+    // launch attributes, which must not happen inside a capture
+    int rc = h->ops.step(h, 1);
+    if (rc) return rc;
+    int left = n - 1;
+    if (h->variant == LBM_KERNEL_FUSED && !h->moments_valid) return fail(h, LBM_E_STATE, "moments not prepared");
+    if (!h->graph_exec[h->cur]) {
+        rc = capture_graph(h);
+        if (rc) return rc;
+    }
+    for (; left >= h->graph_steps; left -= h->graph_steps) {
+        LBM_CUDA_CHECK(h, cudaGraphLaunch(h->graph_exec[h->cur], h->stream));
+    }
+    return left ? h->ops.step(h, left) : LBM_OK;
+}
+
+int lbm_set_graph(lbm_handle h, int steps_per_graph)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (steps_per_graph != 0 && (steps_per_graph < 2 || steps_per_graph % 2))
+        return fail(h, LBM_E_INVALID, "steps_per_graph must be 0 or an even number >= 2");
+    if (steps_per_graph && (h->stream == nullptr || h->stream == cudaStreamLegacy || h->stream == cudaStreamPerThread))
+        return fail(h, LBM_E_STATE, "CUDA graphs need a created stream: call lbm_set_stream first");
+    drop_graph(h);
+    h->graph_steps = steps_per_graph;
+    return LBM_OK;
 }
 
 int lbm_moments(lbm_handle h, double* rho, double* u, double* T, int on_device)
@@ -659,6 +722,7 @@ int lbm_diagnostics(lbm_handle h, long long out[4])
 int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
 {
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    drop_graph(h);
     if (variant == LBM_KERNEL_SPLIT) {
         h->variant = LBM_KERNEL_SPLIT;
         return LBM_OK;
@@ -682,6 +746,82 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
     if (rc) return rc;
     h->variant = LBM_KERNEL_FUSED;
     h->tx = tx; h->ty = ty; h->tz = tz;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle h, int trial_steps, int* variant, int* tx, int* ty, int* tz, double* ms_per_step)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (!h->initialized) return fail(h, LBM_E_STATE, "lbm_init has not been called");
+    if (trial_steps < 1) trial_steps = 4;
+    // snapshot of the state (populations of the current buffer, T guess) to restore afterwards
+    const size_t pbytes = (size_t)h->pop_elems * h->sbytes, wbytes = (size_t)h->Ntot * h->rbytes;
+    void* snap = dev_alloc(h, pbytes + wbytes);
+    if (!snap) return fail(h, LBM_E_NOMEM, "autotune snapshot allocation failed");
+    void* wT = (unsigned char*)h->W + (size_t)W_T * h->Ntot * h->rbytes;
+    int rc = LBM_OK;
+    const int cur0 = h->cur, var0 = h->variant, tx0 = h->tx, ty0 = h->ty, tz0 = h->tz, g0 = h->graph_steps;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto restore = [&]() {
+        cudaMemcpyAsync(h->pop[cur0], snap, pbytes, cudaMemcpyDeviceToDevice, h->stream);
+        cudaMemcpyAsync(wT, (unsigned char*)snap + pbytes, wbytes, cudaMemcpyDeviceToDevice, h->stream);
+        h->cur = cur0;
+        h->moments_valid = false;
+    };
+    if (cudaMemcpyAsync(snap, h->pop[cur0], pbytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync((unsigned char*)snap + pbytes, wT, wbytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = fail(h, LBM_E_CUDA, "autotune setup failed");
+    }
+    // candidates: the split path and every built fused tile of this lattice and storage
+    struct Cand { int v, x, y, z; };
+    std::vector<Cand> cands{{LBM_KERNEL_SPLIT, 0, 0, 0}};
+    const int shapes2[][3] = {{32, 8, 1}, {32, 16, 1}, {32, 32, 1}, {64, 16, 1}};
+    const int shapes3[][3] = {{8, 8, 4}, {16, 8, 4}, {8, 8, 8}};
+    if (h->dim == 2) {
+        for (auto& t : shapes2)
+            if (h->ops.fused_ok(h, t[0], t[1], t[2])) cands.push_back({LBM_KERNEL_FUSED, t[0], t[1], t[2]});
+    } else {
+        for (auto& t : shapes3)
+            if (h->ops.fused_ok(h, t[0], t[1], t[2])) cands.push_back({LBM_KERNEL_FUSED, t[0], t[1], t[2]});
+    }
+    h->graph_steps = 0;
+    drop_graph(h);
+    double best = 1e300;
+    Cand pick{var0, tx0, ty0, tz0};
+    unsigned long long diag_save[4];
+    cudaMemcpyAsync(diag_save, h->d_diag, sizeof(diag_save), cudaMemcpyDeviceToHost, h->stream);
+    for (size_t c = 0; c < cands.size() && rc == LBM_OK; ++c) {
+        rc = lbm_set_kernel(h, cands[c].v, cands[c].x, cands[c].y, cands[c].z);
+        if (rc) break;
+        restore();
+        rc = h->ops.step(h, 2);  // warm-up (and launch set-up)
+        if (rc) break;
+        cudaEventRecord(e0, h->stream);
+        rc = h->ops.step(h, trial_steps);
+        cudaEventRecord(e1, h->stream);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(h, LBM_E_CUDA, "autotune timing failed"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / trial_steps;
+        if (per < best) { best = per; pick = cands[c]; }
+    }
+    restore();
+    cudaMemcpyAsync(h->d_diag, diag_save, sizeof(diag_save), cudaMemcpyHostToDevice, h->stream);
+    cudaStreamSynchronize(h->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    lbm_glue_free(snap);
+    if (rc == LBM_OK) rc = lbm_set_kernel(h, pick.v, pick.x, pick.y, pick.z);
+    else lbm_set_kernel(h, var0, tx0, ty0, tz0);
+    h->graph_steps = g0;
+    if (rc) return rc;
+    if (variant) *variant = pick.v;
+    if (tx) *tx = pick.x;
+    if (ty) *ty = pick.y;
+    if (tz) *tz = pick.z;
+    if (ms_per_step) *ms_per_step = best;
     return LBM_OK;
 }
 

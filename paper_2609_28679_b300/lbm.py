@@ -72,6 +72,9 @@ _SIGS = {
     "lbm_set_kernel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_get_kernel": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4),
     "lbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "lbm_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lbm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4 +
+                     [ctypes.POINTER(ctypes.c_double)]),
     "lbm_step_static": (ctypes.c_int, [ctypes.POINTER(lbm_lattice), ctypes.POINTER(lbm_eos), ctypes.c_double,
                                        ctypes.c_double, ctypes.POINTER(lbm_force), ctypes.POINTER(lbm_heat),
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -193,6 +196,17 @@ def lbm_set_kernel(h, variant: int, tx: int = 0, ty: int = 0, tz: int = 0) -> No
     _check(_lib.lbm_set_kernel(h, variant, tx, ty, tz), h)
 
 
+def lbm_set_graph(h, steps_per_graph: int) -> None:
+    _check(_lib.lbm_set_graph(h, int(steps_per_graph)), h)
+
+
+def lbm_autotune(h, trial_steps: int = 5):
+    v = [ctypes.c_int() for _ in range(4)]
+    ms = ctypes.c_double()
+    _check(_lib.lbm_autotune(h, int(trial_steps), *[ctypes.byref(x) for x in v], ctypes.byref(ms)), h)
+    return tuple(x.value for x in v), ms.value
+
+
 def lbm_get_kernel(h):
     v = [ctypes.c_int() for _ in range(4)]
     _check(_lib.lbm_get_kernel(h, *[ctypes.byref(x) for x in v]), h)
@@ -297,3 +311,11 @@ class Simulation:
 
     def kernel(self):
         return lbm_get_kernel(self.h)
+
+    def autotune(self, trial_steps: int = 5):
+        return lbm_autotune(self.h, trial_steps)
+
+    def use_graphs(self, steps_per_graph: int, stream) -> None:
+        """Step through CUDA graphs on `stream` (a torch.cuda.Stream)."""
+        lbm_set_stream(self.h, stream.cuda_stream)
+        lbm_set_graph(self.h, steps_per_graph)
