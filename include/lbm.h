@@ -219,6 +219,36 @@ int lbm_step_static(const lbm_lattice *lattice, const lbm_eos *eos, double tau_f
                     const lbm_force *force, const lbm_heat *heat, const double *f_in, const double *g_in,
                     double *f_out, double *g_out, void *stream);
 
+/* Learned temperature inversion T(rho, e) for Peng-Robinson (the form that
+ * stands in for the per-cell Newton solve, falling back to Newton).  Network
+ * 2 -> 64 -> 64 -> 1 with tanh hidden units; the 64 x 64 layer runs on the
+ * tensor cores in bfloat16 with float32 accumulation.  Parameters are
+ * lbm_mlp_nparams() floats:
+ *   [c_rho, s_rho, c_e, s_e, c_T, s_T | W1 (64x2) | b1 (64) | W2 (64x64, [out][in]) | b2 (64) | W3 (64) | b3]
+ * with inputs ((log rho - c_rho)/s_rho, (e - c_e)/s_e) and T_hat = c_T + s_T y. */
+int lbm_mlp_nparams(void);
+
+/* Train on nsamples samples drawn on the GPU: rho log-uniform over
+ * [box[0], box[1]], T uniform over [box[2], box[3]] * Tc, e = e(rho, T), and
+ * the target T re-solved from (rho, e) by float64 Newton.  `steps` Adam steps
+ * (lr; beta 0.9/0.999) of minibatches of `batch` samples (counter-based
+ * sampling with `seed`).  params (host, float32) is read as the start point,
+ * or first initialised when init != 0 (normalisation from the box and the
+ * samples' e range, weights uniform in +-1/sqrt(fan_in)); it receives the
+ * trained network.  loss_hist (host, `steps` doubles) may be NULL.  eos must
+ * be Peng-Robinson.  Synchronises `stream`. */
+int lbm_mlp_train(const lbm_eos *eos, const double box[4], long long nsamples, int steps, int batch, double lr,
+                  unsigned long long seed, int init, float *params, double *loss_hist, void *stream);
+
+/* Loss (mean of (y - t)^2/2 over the n samples, t = (T - c_T)/s_T) and its
+ * gradient with respect to the parameters (normalisation entries 0), from
+ * the training kernel, for the host arrays rho, e, T of n samples. */
+int lbm_mlp_grad(const float *params, const double *rho, const double *e, const double *T, long long n,
+                 float *grad, double *loss);
+
+/* T_hat for n (rho, e) pairs (host arrays) through the in-step inference routine. */
+int lbm_mlp_predict(const float *params, const double *rho, const double *e, long long n, double *T_out);
+
 /* Message of the last failing call on h (or of the last failing lbm_create*
  * or lbm_step_static when h is NULL).  Valid until the next call on h. */
 const char *lbm_last_error(lbm_handle h);

@@ -45,8 +45,9 @@
  *  - Peng-Robinson: the paper names the model only.  The textbook form with the
  *    Soave alpha(T) and a constant ideal-part c_v is used; e(rho,T) follows by
  *    integrating Eq. de_rho at constant T from rho = 0.  T(rho,e) is found by
- *    Newton's method in T from the previous step's T, stopping at
- *    |dT| <= 1e-14 T, at most 50 iterations (hits of the cap are counted).
+ *    Newton's method in T from the previous step's T (from Tc when there is
+ *    none), stopping at |dT| <= 1e-14 T, at most 50 iterations (hits of the
+ *    cap are counted).
  *  - c_v in Eq. sh_T_1 is the local (de/dT)_rho.
  */
 #include <math.h>
@@ -299,7 +300,8 @@ double orc_eos_T(const orc_params *p, double rho, double e, double T_guess, int 
     case ORC_VDW:
         return (e + p->a * rho) / p->cv;
     default: {
-        double T = T_guess > 0.0 ? T_guess : e / p->cv;
+        /* without a previous T (T_guess <= 0) start from the critical temperature */
+        double T = T_guess > 0.0 ? T_guess : p->Tc;
         int it;
         for (it = 1; it <= 50; ++it) {
             double r = orc_eos_e(p, rho, T) - e;

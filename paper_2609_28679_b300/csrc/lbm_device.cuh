@@ -214,7 +214,8 @@ __device__ __forceinline__ R eos_T(const C& s, const RhoPart<R>& p, R e, R Tgues
     capped = false;
     if (s.eos == EOS_IDEAL) return e * (R)s.inv_cv;
     if (s.eos == EOS_VDW) return (e + (R)s.a * p.rho) * (R)s.inv_cv;
-    R T = Tguess > R(0) ? Tguess : e * (R)s.inv_cv;
+    // without a previous T (Tguess <= 0) start from the critical temperature
+    R T = Tguess > R(0) ? Tguess : (R)s.Tc;
     if (sizeof(R) == 8) {
         int it = pr_newton<R>(s, p, e, T, (R)1e-14, 50);
         capped = it > 50;
@@ -223,7 +224,7 @@ __device__ __forceinline__ R eos_T(const C& s, const RhoPart<R>& p, R e, R Tgues
     int it = pr_newton<R>(s, p, e, T, (R)1e-6, 8);
     if (it <= 8 && T > R(0)) return T;
     RhoPart<double> pd = rho_part<double>(s, (double)p.rho);
-    double Td = (Tguess > R(0)) ? (double)Tguess : (double)e * s.inv_cv;
+    double Td = (Tguess > R(0)) ? (double)Tguess : (double)s.Tc;
     int itd = pr_newton<double>(s, pd, (double)e, Td, 1e-12, 50);
     capped = itd > 50;
     return (R)Td;

@@ -75,6 +75,12 @@ _SIGS = {
     "lbm_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4 +
                      [ctypes.POINTER(ctypes.c_double)]),
+    "lbm_mlp_nparams": (ctypes.c_int, []),
+    "lbm_mlp_train": (ctypes.c_int, [ctypes.POINTER(lbm_eos), ctypes.POINTER(ctypes.c_double), ctypes.c_longlong,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_mlp_grad": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_mlp_predict": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_longlong, ctypes.c_void_p]),
     "lbm_step_static": (ctypes.c_int, [ctypes.POINTER(lbm_lattice), ctypes.POINTER(lbm_eos), ctypes.c_double,
                                        ctypes.c_double, ctypes.POINTER(lbm_force), ctypes.POINTER(lbm_heat),
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -224,6 +230,42 @@ def lbm_step_static(lattice: lbm_lattice, eos: lbm_eos, tau_f: float, tau_g: flo
                              _ptr(f_in), _ptr(g_in), _ptr(f_out), _ptr(g_out),
                              ctypes.c_void_p(stream) if stream else None)
     _check(rc, None)
+
+
+def lbm_mlp_nparams() -> int:
+    return int(load_library().lbm_mlp_nparams())
+
+
+def _f32(a: np.ndarray):
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
+        raise LbmError("parameter arrays must be C-contiguous float32")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def lbm_mlp_train(eos: lbm_eos, box, nsamples: int, steps: int, batch: int, lr: float, seed: int,
+                  init: bool, params: np.ndarray, loss_hist: np.ndarray | None = None, stream: int | None = None):
+    lib = _lib_gpu()
+    b = (ctypes.c_double * 4)(*box)
+    rc = lib.lbm_mlp_train(ctypes.byref(eos), b, int(nsamples), int(steps), int(batch), float(lr), int(seed),
+                           int(bool(init)), _f32(params), _ptr(loss_hist) if loss_hist is not None else None,
+                           ctypes.c_void_p(stream) if stream else None)
+    _check(rc, None)
+
+
+def lbm_mlp_grad(params: np.ndarray, rho, e, T):
+    lib = _lib_gpu()
+    g = np.zeros(lbm_mlp_nparams(), dtype=np.float32)
+    loss = ctypes.c_double()
+    rc = lib.lbm_mlp_grad(_f32(params), _ptr(rho), _ptr(e), _ptr(T), len(rho), _f32(g), ctypes.byref(loss))
+    _check(rc, None)
+    return loss.value, g
+
+
+def lbm_mlp_predict(params: np.ndarray, rho, e) -> np.ndarray:
+    lib = _lib_gpu()
+    out = np.zeros(len(rho))
+    _check(lib.lbm_mlp_predict(_f32(params), _ptr(rho), _ptr(e), len(rho), _ptr(out)), None)
+    return out
 
 
 def lbm_last_error(h) -> str:
