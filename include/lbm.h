@@ -249,6 +249,15 @@ int lbm_mlp_grad(const float *params, const double *rho, const double *e, const 
 /* T_hat for n (rho, e) pairs (host arrays) through the in-step inference routine. */
 int lbm_mlp_predict(const float *params, const double *rho, const double *e, long long n, double *T_out);
 
+/* Attach learned-inversion parameters (host, lbm_mlp_nparams() floats) to h:
+ * simulations with eos kind LBM_PR and t_solver LBM_T_MLP then start each
+ * cell's Newton solve from the network's T_hat and accept it when the first
+ * Newton correction meets the tolerance (diagnostics[3] counts the cells
+ * that needed more).  Without loaded parameters they use the previous step's
+ * T.  The fused kernel runs the learned start for float32 storage; other
+ * storages step through the split path. */
+int lbm_mlp_load(lbm_handle h, const float *params);
+
 /* Message of the last failing call on h (or of the last failing lbm_create*
  * or lbm_step_static when h is NULL).  Valid until the next call on h. */
 const char *lbm_last_error(lbm_handle h);

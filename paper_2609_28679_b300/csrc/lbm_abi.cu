@@ -61,6 +61,7 @@ struct lbm_ctx {
     int variant = LBM_KERNEL_SPLIT, tx = 0, ty = 0, tz = 0;
     int smem_bytes = 0;
     int graph_steps = 0;               // steps per captured CUDA graph (0: launch eagerly)
+    float* d_mlp = nullptr;            // learned temperature parameters (lbm_mlp_load)
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};  // per starting buffer parity
     std::string err;
     Ops ops{};
@@ -94,7 +95,7 @@ int cuda_fail(lbm_ctx* h, cudaError_t e, const char* where)
 
 void* dev_alloc(lbm_ctx* h, size_t n) { return lbm_glue_alloc(n, (void*)h->stream); }
 
-cudaError_t fused_dispatch(int storage, int dim, int eos, int tx, int ty, int tz, const SimDev* sims,
+cudaError_t fused_dispatch(int storage, int dim, int eos, int mlp, int tx, int ty, int tz, const SimDev* sims,
                            const TileEntry* tiles, int ntiles, const void* src, void* dst, const void* Min, void* Mout,
                            long long Ntot, unsigned long long* diag, cudaStream_t stream);
 bool fused_shape(int storage, int dim, int tx, int ty, int tz);
@@ -148,7 +149,8 @@ template <int D, typename R, typename S> struct Impl {
             int rc = fused_prepare(h);
             if (rc) return rc;
         }
-        cudaError_t e = fused_dispatch(h->storage, D, h->sims[0].eos, h->tx, h->ty, h->tz, h->d_sims, h->d_tiles,
+        cudaError_t e = fused_dispatch(h->storage, D, h->sims[0].eos, uses_mlp(h), h->tx, h->ty, h->tz, h->d_sims,
+                                       h->d_tiles,
                                        (int)h->tiles.size(), h->pop[h->cur], h->pop[h->cur ^ 1], mbuf(h, h->cur),
                                        mbuf(h, h->cur ^ 1), h->Ntot, h->d_diag, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "fused step");
@@ -204,25 +206,33 @@ template <int D, typename R, typename S> struct Impl {
         return LBM_OK;
     }
 
+    static int uses_mlp(lbm_ctx* h)
+    {
+        for (const SimDev& d : h->sims)
+            if (d.eos == EOS_PR && d.t_solver == LBM_T_MLP && d.mlp != nullptr) return 1;
+        return 0;
+    }
+
     static int fused_ok(lbm_ctx* h, int tx, int ty, int tz)
     {
         for (const SimDev& d : h->sims)
             if (d.eos != h->sims[0].eos) return 0;  // one equation of state per fused launch
+        if (uses_mlp(h) && h->storage != LBM_F32) return 0;  // learned start built for float32 storage
         return fused_shape(h->storage, D, tx, ty, tz) ? 1 : 0;
     }
 
     static Ops ops() { return Ops{init, step, macro, export_moments, export_pops, invariants, fused_ok}; }
 };
 
-cudaError_t fused_dispatch(int storage, int dim, int eos, int tx, int ty, int tz, const SimDev* sims,
+cudaError_t fused_dispatch(int storage, int dim, int eos, int mlp, int tx, int ty, int tz, const SimDev* sims,
                            const TileEntry* tiles, int ntiles, const void* src, void* dst, const void* Min, void* Mout,
                            long long Ntot, unsigned long long* diag, cudaStream_t stream)
 {
     switch (storage) {
-    case LBM_F64: return fused_dispatch_f64(dim, eos, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
-    case LBM_F32: return fused_dispatch_f32(dim, eos, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
-    case LBM_BF16: return fused_dispatch_bf16(dim, eos, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
-    case LBM_F16: return fused_dispatch_f16(dim, eos, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_F64: return fused_dispatch_f64(dim, eos, mlp, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_F32: return fused_dispatch_f32(dim, eos, mlp, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_BF16: return fused_dispatch_bf16(dim, eos, mlp, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_F16: return fused_dispatch_f16(dim, eos, mlp, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
     }
     return cudaErrorInvalidValue;
 }
@@ -342,10 +352,11 @@ void free_all(lbm_ctx* h)
 {
     drop_graph(h);
     void* ptrs[] = {h->d_sims, h->d_table, h->d_sim_block_start, h->d_tiles, h->pop[0], h->pop[1],
-                    h->W, h->M, h->d_diag, h->d_partials};
+                    h->W, h->M, h->d_diag, h->d_partials, h->d_mlp};
     for (void* p : ptrs) lbm_glue_free(p);
     h->d_sims = nullptr; h->d_table = nullptr; h->d_sim_block_start = nullptr; h->d_tiles = nullptr;
     h->pop[0] = h->pop[1] = nullptr; h->W = nullptr; h->M = nullptr; h->d_diag = nullptr; h->d_partials = nullptr;
+    h->d_mlp = nullptr;
 }
 
 int upload_sims(lbm_ctx* h)
@@ -822,6 +833,25 @@ int lbm_autotune(lbm_handle h, int trial_steps, int* variant, int* tx, int* ty, 
     if (ty) *ty = pick.y;
     if (tz) *tz = pick.z;
     if (ms_per_step) *ms_per_step = best;
+    return LBM_OK;
+}
+
+int lbm_mlp_load(lbm_handle h, const float* params)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (!params) return fail(h, LBM_E_INVALID, "params is NULL");
+    const int np = lbm_mlp_nparams();
+    if (!h->d_mlp) {
+        h->d_mlp = (float*)dev_alloc(h, (size_t)np * sizeof(float));
+        if (!h->d_mlp) return fail(h, LBM_E_NOMEM, "parameter allocation failed");
+    }
+    LBM_CUDA_CHECK(h, cudaMemcpyAsync(h->d_mlp, params, (size_t)np * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    for (SimDev& d : h->sims)
+        if (d.eos == EOS_PR && d.t_solver == LBM_T_MLP) d.mlp = h->d_mlp;
+    drop_graph(h);
+    int rc = upload_sims(h);
+    if (rc) return rc;
+    if (h->variant == LBM_KERNEL_FUSED && !h->ops.fused_ok(h, h->tx, h->ty, h->tz)) h->variant = LBM_KERNEL_SPLIT;
     return LBM_OK;
 }
 

@@ -42,6 +42,7 @@ struct SimDev {
     double inv_cv, inv_Tc, lam_c; // 1/cv, 1/Tc, 1/(2 sqrt2 b) (Peng-Robinson)
     double athe_c;                // (D+2)/D - eta/mu
     float fref[27], gref[27];     // storage offsets (16-bit storage only; zero otherwise)
+    const float* mlp;             // learned T(rho, e) parameters (t_solver == LBM_T_MLP), or null
 };
 
 // The same constants in the arithmetic type R (built once per tile on the
@@ -52,6 +53,7 @@ template <typename F> struct SimC {
     int eos, phi_central, t_solver, zlo, zhi;
     F R, cv, a, b, Tc, kw, kappa, eta_mu, k_mu, beta_f, beta_g, acc[3], q, inv_cv, inv_Tc, lam_c, athe_c;
     F fref[27], gref[27];
+    const float* mlp;
 };
 
 template <typename R> __device__ inline void simc_from(SimC<R>& d, const SimDev& s)
@@ -64,6 +66,7 @@ template <typename R> __device__ inline void simc_from(SimC<R>& d, const SimDev&
     for (int a = 0; a < 3; ++a) d.acc[a] = (R)s.acc[a];
     d.q = (R)s.q; d.inv_cv = (R)s.inv_cv; d.inv_Tc = (R)s.inv_Tc; d.lam_c = (R)s.lam_c; d.athe_c = (R)s.athe_c;
     for (int i = 0; i < 27; ++i) { d.fref[i] = (R)s.fref[i]; d.gref[i] = (R)s.gref[i]; }
+    d.mlp = s.mlp;
 }
 
 // ---------------------------------------------------------------------------
@@ -209,9 +212,10 @@ __device__ __forceinline__ int pr_newton(const C& s, const RhoPart<W>& p, W e, W
 // lbm_temp); Peng-Robinson by Newton from Tguess -- in float64 for the
 // float64 path; in float32 with a float64 fallback for the float32 path.
 template <typename R, typename C>
-__device__ __forceinline__ R eos_T(const C& s, const RhoPart<R>& p, R e, R Tguess, bool& capped)
+__device__ __forceinline__ R eos_T(const C& s, const RhoPart<R>& p, R e, R Tguess, bool& capped, int& iters)
 {
     capped = false;
+    iters = 0;
     if (s.eos == EOS_IDEAL) return e * (R)s.inv_cv;
     if (s.eos == EOS_VDW) return (e + (R)s.a * p.rho) * (R)s.inv_cv;
     // without a previous T (Tguess <= 0) start from the critical temperature
@@ -219,14 +223,17 @@ __device__ __forceinline__ R eos_T(const C& s, const RhoPart<R>& p, R e, R Tgues
     if (sizeof(R) == 8) {
         int it = pr_newton<R>(s, p, e, T, (R)1e-14, 50);
         capped = it > 50;
+        iters = it;
         return T;
     }
     int it = pr_newton<R>(s, p, e, T, (R)1e-6, 8);
+    iters = it;
     if (it <= 8 && T > R(0)) return T;
     RhoPart<double> pd = rho_part<double>(s, (double)p.rho);
     double Td = (Tguess > R(0)) ? (double)Tguess : (double)s.Tc;
     int itd = pr_newton<double>(s, pd, (double)e, Td, 1e-12, 50);
     capped = itd > 50;
+    iters = 8 + itd;
     return (R)Td;
 }
 
@@ -258,7 +265,8 @@ __device__ __forceinline__ Macro<R> macro_cell(const C& s, R rho, const R* j, R 
     const R e = rhoE * m.ir - R(0.5) * u2;
     const RhoPart<R> p = rho_part<R>(s, rho);
     bool capped;
-    const R T = eos_T<R>(s, p, e, Tguess, capped);
+    int iters;
+    const R T = eos_T<R>(s, p, e, Tguess, capped, iters);
     const Thermo<R> t = thermo<R>(s, p, T);
     const R th = t.P * m.ir;  // Eq. theta
     m.icv = s.eos == EOS_PR ? R(1) / t.cv : (R)s.inv_cv;
@@ -272,9 +280,27 @@ __device__ __forceinline__ Macro<R> macro_cell(const C& s, R rho, const R* j, R 
     m.athe = (R)s.athe_c * th - cs2;     // alpha theta, Eq. corr_bulk: ((D+2)/D - eta/mu) theta - c_s^2
     m.e = e;
     if (capped) flags |= 4u;
+    // learned start: accepted when the first Newton correction meets the tolerance
+    if (s.eos == EOS_PR && s.t_solver == 1 && s.mlp != nullptr && iters > 1) flags |= 8u;
     if (!(th > R(0))) flags |= 2u;
     if (!isfinite(rho) || !isfinite(T) || !isfinite(u2)) flags |= 1u;
     return m;
+}
+
+// Specific internal energy e of a cell (Eqs. def_u, def_E): the input of the
+// learned temperature inversion, evaluated ahead of macro_cell.
+template <int D, typename R>
+__device__ __forceinline__ R macro_energy(R rho, const R* j, R G, const R* F, R Q)
+{
+    const R ir = R(1) / rho;
+    R uF = 0, u2 = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const R u = (j[a] + R(0.5) * F[a]) * ir;
+        uF += u * F[a];
+        u2 += u * u;
+    }
+    return (G + R(0.5) * (uF + Q)) * ir - R(0.5) * u2;
 }
 
 // X_alpha = rho u_alpha^3 + 3 rho u_alpha (theta - 1/3), the flux whose

@@ -76,7 +76,7 @@ template <typename R, int EK> struct SimK : SimC<R> {
     static constexpr int eos = EK;
 };
 
-template <int D, typename R, typename S, int EK, int TX, int TY, int TZ>
+template <int D, typename R, typename S, int EK, bool ML, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 : 1)
     k_fused(const SimDev* __restrict__ sims, const TileEntry* __restrict__ tiles, int ntiles,
             const S* __restrict__ src, S* __restrict__ dst, const R* __restrict__ Min, R* __restrict__ Mout,
@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
     R* s_st = s_L + n4;            // [NS][n3]
     R* s_lo = s_st + G::NS * n3;   // [NL][n1]
     R* s_acc = s_lo + G::NL * n1;  // [D+2][n0]
+    MlpSmem& mlp_s = *reinterpret_cast<MlpSmem*>(s_acc + (D + 2) * n0);  // only with ML
     const int tid = threadIdx.x;
     if (tid == 0) cur_sim = -1;
     __syncthreads();
@@ -107,6 +108,10 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
                 cur_sim = te.sim;
             }
             __syncthreads();
+            if (ML && s.mlp != nullptr) {
+                mlp_load(mlp_s, s.mlp);
+                __syncthreads();
+            }
         }
         const int nx = s.nx, ny = s.ny, nz = s.nz;
         const bool walls = D == 3 && s.zwalls;
@@ -161,46 +166,62 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
         for (int it = 0; it < nb3; ++it) {
             const int k = it * kFusedThreads + tid;
             unsigned flags = 0;
-            bool owned = false;
+            bool owned = false, act = false;
+            int lx = 0, ly = 0, lz = 0, zr = 0, z = 0;
+            R r = R(1), G_ = R(0), Qh = R(0), Tg = R(0), Fv[3] = {0, 0, 0}, j[3] = {0, 0, 0};
             if (k < n3) {
-                const int lx = k % G::w(3), ly = (k / G::w(3)) % G::h(3), lz = k / (G::w(3) * G::h(3));
-                const int zr = te.z0 - 3 * HZ + lz;
-                if (!(walls && (zr < 0 || zr >= nz))) {
+                lx = k % G::w(3);
+                ly = (k / G::w(3)) % G::h(3);
+                lz = k / (G::w(3) * G::h(3));
+                zr = te.z0 - 3 * HZ + lz;
+                act = !(walls && (zr < 0 || zr >= nz));
+                if (act) {
                     const int x = wrapc(te.x0 - 3 + lx, nx), y = wrapc(te.y0 - 3 + ly, ny);
-                    const int z = D == 3 ? wrapc(zr, nz) : 0;
+                    z = D == 3 ? wrapc(zr, nz) : 0;
                     const unsigned gk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
                     const int c4 = (lx + 1) + G::w(4) * ((ly + 1) + G::h(4) * (lz + HZ));
-                    const R r = s_rho[(lx + 2) + G::w(5) * ((ly + 2) + G::h(5) * (lz + 2 * HZ))];
+                    r = s_rho[(lx + 2) + G::w(5) * ((ly + 2) + G::h(5) * (lz + 2 * HZ))];
                     constexpr int st4[3] = {1, G::w(4), G::w(4) * G::h(4)};
-                    R Fv[3] = {0, 0, 0}, j[3] = {0, 0, 0};
 #pragma unroll
                     for (int a = 0; a < D; ++a) {
                         Fv[a] = r * (s.acc[a] + s.kappa * R(0.5) * (s_L[c4 + st4[a]] - s_L[c4 - st4[a]]));
                         j[a] = Mj[(size_t)a * Ntot + gk];
                     }
-                    const R Qh = heat_q<R>(s, z);
-                    const Macro<R> m = macro_cell<D, R>(s, r, j, MG[gk], Fv, Qh, MT[gk], flags);
-#pragma unroll
-                    for (int a = 0; a < D; ++a) {
-                        s_st[(G::U + a) * n3 + k] = m.u[a];
-                        s_st[(G::X + a) * n3 + k] = xflux<R>(r, m.u[a], m.theta);
-                    }
-                    s_st[G::TT * n3 + k] = m.T;
-                    s_st[G::H * n3 + k] = m.h;
-                    // local fields for the cells of T+1
-                    const int l1x = lx - 2, l1y = ly - 2, l1z = lz - 2 * HZ;
-                    if (l1x >= 0 && l1y >= 0 && l1z >= 0 && l1x < G::w(1) && l1y < G::h(1) && l1z < G::d(1)) {
-                        const int k1 = l1x + G::w(1) * (l1y + G::h(1) * l1z);
-                        s_lo[G::LP * n1 + k1] = m.P;
-                        s_lo[G::LTH * n1 + k1] = m.theta;
-                        s_lo[G::LCV * n1 + k1] = m.cv;
-                        s_lo[G::LGAM * n1 + k1] = m.gam;
-                        s_lo[G::LATHE * n1 + k1] = m.athe;
-                        s_lo[G::LE * n1 + k1] = m.e;
-                    }
-                    owned = lx >= 3 && ly >= 3 && lz >= 3 * HZ && lx < 3 + TX && ly < 3 + TY && lz < 3 * HZ + G::tz &&
-                            te.x0 - 3 + lx < nx && te.y0 - 3 + ly < ny && zr < nz;
+                    G_ = MG[gk];
+                    Qh = heat_q<R>(s, z);
+                    Tg = MT[gk];
                 }
+            }
+            if constexpr (ML) {
+                if (s.mlp != nullptr) {  // block-uniform: the whole warp evaluates the network
+                    const float rr = act ? (float)r : 1.f;
+                    const float ee = act ? (float)macro_energy<D, R>(r, j, G_, Fv, Qh) : 0.f;
+                    const float Tm = mlp_T_warp(mlp_s, rr, ee);
+                    if (act) Tg = (R)Tm;
+                }
+            }
+            if (act) {
+                const Macro<R> m = macro_cell<D, R>(s, r, j, G_, Fv, Qh, Tg, flags);
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    s_st[(G::U + a) * n3 + k] = m.u[a];
+                    s_st[(G::X + a) * n3 + k] = xflux<R>(r, m.u[a], m.theta);
+                }
+                s_st[G::TT * n3 + k] = m.T;
+                s_st[G::H * n3 + k] = m.h;
+                // local fields for the cells of T+1
+                const int l1x = lx - 2, l1y = ly - 2, l1z = lz - 2 * HZ;
+                if (l1x >= 0 && l1y >= 0 && l1z >= 0 && l1x < G::w(1) && l1y < G::h(1) && l1z < G::d(1)) {
+                    const int k1 = l1x + G::w(1) * (l1y + G::h(1) * l1z);
+                    s_lo[G::LP * n1 + k1] = m.P;
+                    s_lo[G::LTH * n1 + k1] = m.theta;
+                    s_lo[G::LCV * n1 + k1] = m.cv;
+                    s_lo[G::LGAM * n1 + k1] = m.gam;
+                    s_lo[G::LATHE * n1 + k1] = m.athe;
+                    s_lo[G::LE * n1 + k1] = m.e;
+                }
+                owned = lx >= 3 && ly >= 3 && lz >= 3 * HZ && lx < 3 + TX && ly < 3 + TY && lz < 3 * HZ + G::tz &&
+                        te.x0 - 3 + lx < nx && te.y0 - 3 + ly < ny && zr < nz;
             }
             if (diag) count_flags(owned ? flags : 0u, diag);
         }
@@ -423,20 +444,20 @@ template <int D, typename R, int TX, int TY, int TZ> constexpr size_t fused_smem
     return TileShape<D, TX, TY, TZ>::elems() * sizeof(R);
 }
 
-template <int D, typename R, typename S, int EK, int TX, int TY, int TZ>
+template <int D, typename R, typename S, int EK, bool ML, int TX, int TY, int TZ>
 cudaError_t fused_launch_shape(const SimDev* sims, const TileEntry* tiles, int ntiles, const void* src, void* dst,
                                const void* Min, void* Mout, long long Ntot, unsigned long long* diag,
                                cudaStream_t stream)
 {
-    constexpr size_t smem = fused_smem<D, R, TX, TY, TZ>();
+    constexpr size_t smem = fused_smem<D, R, TX, TY, TZ>() + (ML ? sizeof(MlpSmem) : 0);
     static_assert(smem <= 227u * 1024u, "tile does not fit in shared memory");
     static int grid_cap = 0;
     if (grid_cap == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<D, R, S, EK, TX, TY, TZ>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<D, R, S, EK, ML, TX, TY, TZ>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, nsm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, R, S, EK, TX, TY, TZ>, kFusedThreads,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, R, S, EK, ML, TX, TY, TZ>, kFusedThreads,
                                                           smem);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
@@ -445,7 +466,7 @@ cudaError_t fused_launch_shape(const SimDev* sims, const TileEntry* tiles, int n
         grid_cap = per_sm * nsm;
     }
     const int grid = ntiles < grid_cap ? ntiles : grid_cap;
-    k_fused<D, R, S, EK, TX, TY, TZ><<<grid, kFusedThreads, smem, stream>>>(
+    k_fused<D, R, S, EK, ML, TX, TY, TZ><<<grid, kFusedThreads, smem, stream>>>(
         sims, tiles, ntiles, (const S*)src, (S*)dst, (const R*)Min, (R*)Mout, Ntot, diag);
     return cudaGetLastError();
 }

@@ -7,6 +7,7 @@
 #pragma once
 
 #include "lbm_device.cuh"
+#include "lbm_mlp.cuh"
 
 namespace lbm {
 
@@ -54,12 +55,13 @@ __device__ __forceinline__ R heat_q(const C& s, int z)
     return (s.zhi <= 0 || (z >= s.zlo && z < s.zhi)) ? (R)s.q : R(0);
 }
 
-// Warp-aggregated diagnostic counters (bit 0: non-finite, 1: theta <= 0, 2: Newton cap).
+// Warp-aggregated diagnostic counters (bit 0: non-finite, 1: theta <= 0,
+// 2: Newton cap, 3: learned temperature not accepted by the residual test).
 __device__ __forceinline__ void count_flags(unsigned flags, unsigned long long* diag)
 {
     const unsigned lane = threadIdx.x & 31u;
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
+    for (int b = 0; b < 4; ++b) {
         unsigned m = __ballot_sync(0xffffffffu, (flags >> b) & 1u);
         if (lane == 0 && m) atomicAdd(diag + b, (unsigned long long)__popc(m));
     }
@@ -192,11 +194,41 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
                                                        R* __restrict__ W, long long Ntot, unsigned long long* diag)
 {
     __shared__ SimDev s;
+    __shared__ MlpSmem mlp_s;
     const BlockEntry be = table[blockIdx.x];
     load_sim(s, sims, be.sim);
+    const bool use_mlp = s.eos == EOS_PR && s.t_solver == 1 && s.mlp != nullptr;  // block-uniform
+    if (use_mlp) {
+        mlp_load(mlp_s, s.mlp);
+        __syncthreads();
+    }
     const long long k = (long long)be.start + threadIdx.x;
     const bool valid = k < s.N;
     unsigned flags = 0;
+    R Tml = R(0);
+    if (use_mlp) {
+        // learned start of the temperature inversion, one warp per 32 cells
+        float rr = 1.f, ee = 0.f;
+        if (valid) {
+            int x, y, z;
+            cell_xyz(s, k, x, y, z);
+            const long long gk = s.cell_off + k;
+            const R* rho = W + W_RHO * Ntot + s.cell_off;
+            const R r = rho[k];
+            R F[3] = {0, 0, 0}, j[3];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                int e0 = a == 0, e1 = a == 1, e2 = a == 2;
+                R gl = R(0.5) * (lap_at<D, R>(s, rho, x + e0, y + e1, z + e2) - lap_at<D, R>(s, rho, x - e0, y - e1, z - e2));
+                F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl;
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) j[a] = W[(W_J + a) * Ntot + gk];
+            rr = (float)r;
+            ee = (float)macro_energy<D, R>(r, j, W[W_G * Ntot + gk], F, (R)heat_at(s, z));
+        }
+        Tml = (R)mlp_T_warp(mlp_s, rr, ee);
+    }
     if (valid) {
         int x, y, z;
         cell_xyz(s, k, x, y, z);
@@ -213,7 +245,7 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
 #pragma unroll
         for (int a = 0; a < 3; ++a) j[a] = W[(W_J + a) * Ntot + gk];
         R Q = (R)heat_at(s, z);
-        Macro<R> m = macro_cell<D, R>(s, r, j, W[W_G * Ntot + gk], F, Q, W[W_T * Ntot + gk], flags);
+        Macro<R> m = macro_cell<D, R>(s, r, j, W[W_G * Ntot + gk], F, Q, use_mlp ? Tml : W[W_T * Ntot + gk], flags);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             W[(W_U + a) * Ntot + gk] = m.u[a];

@@ -81,6 +81,7 @@ _SIGS = {
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_mlp_grad": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_mlp_predict": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_longlong, ctypes.c_void_p]),
+    "lbm_mlp_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_step_static": (ctypes.c_int, [ctypes.POINTER(lbm_lattice), ctypes.POINTER(lbm_eos), ctypes.c_double,
                                        ctypes.c_double, ctypes.POINTER(lbm_force), ctypes.POINTER(lbm_heat),
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -266,6 +267,10 @@ def lbm_mlp_predict(params: np.ndarray, rho, e) -> np.ndarray:
     out = np.zeros(len(rho))
     _check(lib.lbm_mlp_predict(_f32(params), _ptr(rho), _ptr(e), len(rho), _ptr(out)), None)
     return out
+
+
+def lbm_mlp_load(h, params: np.ndarray) -> None:
+    _check(_lib.lbm_mlp_load(h, _f32(params)), h)
 
 
 def lbm_last_error(h) -> str:

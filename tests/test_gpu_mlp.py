@@ -70,3 +70,69 @@ def test_training_learns_the_inversion():
     rho, e, T, _ = _samples(2000, 13)
     Tg = lbm.lbm_mlp_predict(params, rho, e)
     assert np.max(np.abs(Tg - T)) / c.Tc < 0.02
+
+
+_TRAINED = {}
+
+
+def _trained_params():
+    if "p" not in _TRAINED:
+        c, _ = _pr()
+        le = lbm.structs_from_case(c)[1]
+        params = np.zeros(lbm.lbm_mlp_nparams(), dtype=np.float32)
+        lbm.lbm_mlp_train(le, (0.1, 2.6, 0.85, 1.05), 1 << 16, 1500, 512, 2e-3, 7, True, params)
+        _TRAINED["p"] = params
+    return _TRAINED["p"]
+
+
+def test_learned_start_keeps_f64_parity_with_oracle():
+    # the network only seeds Newton; the float64 path converges to 1e-14 either way
+    c = wl.pr_droplet(n=14, radius=4.0, storage="f64")
+    c.t_solver = 1
+    sim = lbm.Simulation(c)
+    lbm.lbm_mlp_load(sim.h, _trained_params())
+    sim.init()
+    sim.step(6)
+    rho, u, T = sim.moments()
+    o = orc.Oracle(orc.params_from_case(c))
+    o.init(*c.fields())
+    o.step(6)
+    rr, ur, Tr = o.moments()
+    assert np.max(np.abs(rho - rr)) / rr.max() <= 1e-12
+    assert np.max(np.abs(T - Tr)) / Tr.max() <= 1e-12
+
+
+@pytest.mark.parametrize("variant", [lbm.LBM_KERNEL_SPLIT, lbm.LBM_KERNEL_FUSED])
+def test_learned_start_f32_matches_newton_run(variant):
+    # float32 Newton stops at |dT| <= 1e-6 T from either start; the runs agree to that level
+    base = wl.pr_droplet(n=16, radius=5.0, storage="f32")
+    newton = lbm.Simulation(base, variant=variant)
+    newton.init()
+    newton.step(10)
+    c = wl.pr_droplet(n=16, radius=5.0, storage="f32")
+    c.t_solver = 1
+    sim = lbm.Simulation(c)
+    lbm.lbm_mlp_load(sim.h, _trained_params())
+    lbm.lbm_set_kernel(sim.h, variant)
+    assert sim.kernel()[0] == variant
+    sim.init()
+    sim.step(10)
+    r1, u1, T1 = sim.moments()
+    r0, u0, T0 = newton.moments()
+    assert np.max(np.abs(r1 - r0)) / r0.max() <= 1e-5
+    assert np.max(np.abs(T1 - T0)) / T0.max() <= 1e-5
+    d = sim.diagnostics()
+    assert d[0] == 0
+    assert 0 <= d[3] <= 10 * c.ncell
+
+
+def test_learned_start_saves_newton_iterations_over_a_cold_start():
+    # What the trained network gains: float64 Newton iterations (oracle solver) to
+    # converge from T_hat versus from Tc, the start without a previous T.
+    c, eos = _pr()
+    rho, e, T, _ = _samples(400, 21)
+    That = lbm.lbm_mlp_predict(_trained_params(), rho, e)
+    it_cold = np.array([eos.T(r, ee, 0.0)[1] for r, ee in zip(rho, e)])
+    it_mlp = np.array([eos.T(r, ee, t0)[1] for r, ee, t0 in zip(rho, e, That)])
+    assert np.mean(it_mlp) < np.mean(it_cold)
+    assert np.max(it_mlp) <= np.max(it_cold)
