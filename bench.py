@@ -143,6 +143,116 @@ def _oracle_mlups(case, steps_budget_s: float, threads: int | None = None):
     return case.ncell * n / dt / 1e6, n, dt, orc.get_threads()
 
 
+def max_over_ranks(x: float) -> float:
+    """Maximum of x over the ranks of the default process group (x itself
+    without one): the timed region of a weak-scaling replica run is the
+    slowest rank's."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(cells_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job MLUPS of `world` replicas timed over max_ms."""
+    return world * cells_per_rank * steps / (max_ms * 1e-3) / 1e6
+
+
+def _time_steps(torch, sim, steps, stream=None):
+    """ms per step over `steps` steps (device events), L2 flushed before."""
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    st = stream or torch.cuda.current_stream()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    sim.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    del flush
+    return e0.elapsed_time(e1) / steps
+
+
+def _form(lbm, torch, case, steps, storage_bytes, graphs=0, mlp=None, tune=True, warm=3):
+    """MLUPS, ms per step and HBM fraction of one workload form."""
+    sim = lbm.Simulation(case)
+    stream = None
+    if graphs:
+        stream = torch.cuda.Stream()
+        sim.use_graphs(graphs, stream)
+    if mlp is not None:
+        lbm.lbm_mlp_load(sim.h, mlp)
+    ctx = torch.cuda.stream(stream) if stream is not None else _null()
+    with ctx:
+        sim.init()
+        if tune:
+            sim.autotune(3)
+        sim.step(warm)
+        ms = _time_steps(torch, sim, steps, stream)
+        rho, u, T = sim.moments()
+        diag = sim.diagnostics()
+    n = sum(c.ncell for c in sim.cases)
+    Q = 3 ** sim.dim
+    alg = 4 * Q * storage_bytes * n
+    peak, _ = _peaks()
+    out = {"cells": n, "ms_per_step": ms, "mlups": n / (ms * 1e3), "hbm_frac": alg / (ms * 1e-3) / 1e9 / peak,
+           "kernel": list(sim.kernel()), "steps_timed": steps, "diagnostics": [int(v) for v in diag]}
+    sim.close()
+    return out, (rho, T)
+
+
+class _null:
+    def __enter__(self):
+        return None
+
+    def __exit__(self, *a):
+        return False
+
+
+def _measure_forms(lbm, wl, torch, steps):
+    """The other forms on their full-size workloads (few steps each)."""
+    res = {}
+    try:
+        r, _ = _form(lbm, torch, wl.acoustic_shear(128, storage="f64"), steps, 8)
+        res["f64_ideal_2d_128"] = r
+        base, (r0, T0) = _form(lbm, torch, wl.pr_heated_slab(256, storage="f32"), steps, 4, warm=0)
+        res["f32_pr_slab_256"] = base
+        for st, sb in (("bf16", 2), ("f16", 2)):
+            r, (r1, T1) = _form(lbm, torch, wl.pr_heated_slab(256, storage=st), steps, sb, warm=0)
+            r["rel_dev_vs_f32"] = {"rho": float(np.max(np.abs(r1 - r0)) / np.max(np.abs(r0))),
+                                   "T": float(np.max(np.abs(T1 - T0)) / np.max(np.abs(T0)))}
+            r["speedup_vs_f32"] = base["ms_per_step"] / r["ms_per_step"]
+            res[f"{st}_pr_slab_256"] = r
+        r, _ = _form(lbm, torch, wl.vdw_batch(64, storage="f32"), steps, 4, graphs=10)
+        res["f32_vdw_batch_64"] = r
+        drop = wl.pr_droplet(384, storage="f32")
+        newton, (rn, Tn) = _form(lbm, torch, drop, max(4, steps // 2), 4, warm=0)
+        res["f32_pr_droplet_384_newton"] = newton
+        le = lbm.structs_from_case(drop)[1]
+        params = np.zeros(lbm.lbm_mlp_nparams(), dtype=np.float32)
+        t0 = time.perf_counter()
+        lbm.lbm_mlp_train(le, (0.1, 2.6, 0.85, 1.05), 1_000_000, 2000, 1024, 2e-3, 7, True, params)
+        train_s = time.perf_counter() - t0
+        drop_m = wl.pr_droplet(384, storage="f32")
+        drop_m.t_solver = 1
+        r, (rm, Tm) = _form(lbm, torch, drop_m, max(4, steps // 2), 4, mlp=params, warm=0)
+        r["train_s"] = train_s
+        r["rel_dev_vs_newton"] = {"rho": float(np.max(np.abs(rm - rn)) / np.max(np.abs(rn))),
+                                  "T": float(np.max(np.abs(Tm - Tn)) / np.max(np.abs(Tn)))}
+        r["speedup_vs_newton"] = newton["ms_per_step"] / r["ms_per_step"]
+        res["f32_pr_droplet_384_mlp"] = r
+        # the plain float64 path on the 3-D slab, the baseline of the reduced-precision forms
+        r, _ = _form(lbm, torch, wl.pr_heated_slab(128, storage="f64"), max(4, steps // 2), 8, warm=0)
+        res["f64_pr_slab_128"] = r
+    except Exception as e:  # report what was measured
+        res["error"] = f"{type(e).__name__}: {e}"
+    return res
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -183,6 +293,14 @@ def run_ours(args):
     case = wl.vdw_spinodal(512, storage="f32")
     sim = lbm.Simulation(case)
     sim.init()
+    if args.kernel == "auto":
+        # warm-up includes the autotuner (kernel variant and tile for this workload; state restored)
+        sim.autotune(5)
+    else:
+        kind, _, tile = args.kernel.partition(":")
+        t = [int(v) for v in tile.split("x")] if tile else [0, 0, 0]
+        lbm.lbm_set_kernel(sim.h, lbm.LBM_KERNEL_FUSED if kind == "fused" else lbm.LBM_KERNEL_SPLIT,
+                           *(t + [0] * (3 - len(t))))
     variant, tx, ty, tz = sim.kernel()
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -215,12 +333,7 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms)
     diag = sim.diagnostics()
 
     # end to end through the C ABI with host buffers: upload the state, one step, read the fields back
@@ -247,13 +360,17 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     sim.close()
 
+    forms = None
+    if not args.no_forms:
+        forms = _measure_forms(lbm, wl, torch, min(args.steps, 20))
+
     Q = 9
     alg_bytes = 4 * Q * 4 * case.ncell  # read + write f and g once, float32
     avg_ms = total_ms / args.steps
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     peak, peak_src = _peaks()
     kname = "k_fused" if variant == lbm.LBM_KERNEL_FUSED else "k_collide"
-    value = world * case.ncell * args.steps / (total_ms * 1e-3) / 1e6
+    value = aggregate_mlups(case.ncell, args.steps, world, total_ms)
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -278,10 +395,11 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(rho_h.nbytes + u_h.nbytes + T_h.nbytes),
                     "d2h_bytes_per_step": int(out_r.nbytes + out_u.nbytes + out_T.nbytes),
                     "what": "lbm_init from pinned host fields + lbm_step(1) + lbm_moments to pinned host, per step"},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * (1 if variant == lbm.LBM_KERNEL_FUSED else 3),
             "clocks": clk,
             "cpu_baseline": cpu,
             "diagnostics": {"nonfinite": int(diag[0]), "theta_le_0": int(diag[1]), "newton_cap": int(diag[2])},
+            "forms": forms,
             "wall_s_timed_region": t_wall,
         }
         print(json.dumps(line), flush=True)
@@ -299,6 +417,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the per-form measurements")
+    ap.add_argument("--kernel", default="auto",
+                    help="auto (autotuned), split, or fused:TXxTY[xTZ] (pinned, e.g. for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
