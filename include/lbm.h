@@ -77,6 +77,7 @@ extern "C" {
 #define LBM_KERNEL_AUTO 0  /* the library's choice (autotuned when a cache entry exists) */
 #define LBM_KERNEL_SPLIT 1 /* moments, macroscopic, collide-stream: three passes         */
 #define LBM_KERNEL_FUSED 2 /* one pass per step, shared-memory halo tiles                */
+#define LBM_KERNEL_ZMARCH 3 /* D3Q27: macroscopic pass + z-marching collide-stream pass   */
 
 typedef struct lbm_ctx *lbm_handle;
 
@@ -166,9 +167,10 @@ int lbm_invariants(lbm_handle h, double *out);
  * Host pointer; synchronises. */
 int lbm_diagnostics(lbm_handle h, long long out[4]);
 
-/* Kernel selection: variant LBM_KERNEL_AUTO / SPLIT / FUSED; tx, ty, tz the
- * tile of the fused variant (0: default).  Errors: LBM_E_INVALID for a tile
- * the variant cannot run. */
+/* Kernel selection: variant LBM_KERNEL_AUTO / SPLIT / FUSED / ZMARCH; tx, ty,
+ * tz the tile of the fused variant, or for ZMARCH (3-D only) the xy tile and
+ * the number of z planes each CTA marches through (0: default).  Errors:
+ * LBM_E_INVALID for a tile the variant cannot run. */
 int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz);
 
 /* Replay lbm_step's time steps as CUDA graphs of `steps_per_graph` steps (an

@@ -99,6 +99,10 @@ cudaError_t fused_dispatch(int storage, int dim, int eos, int mlp, int tx, int t
                            const TileEntry* tiles, int ntiles, const void* src, void* dst, const void* Min, void* Mout,
                            long long Ntot, unsigned long long* diag, cudaStream_t stream);
 bool fused_shape(int storage, int dim, int tx, int ty, int tz);
+cudaError_t zmarch_dispatch(int storage, int eos, int tx, int ty, int zl, const SimDev* sims, const TileEntry* tiles,
+                            int ntiles, const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                            cudaStream_t stream);
+bool zmarch_shape(int storage, int tx, int ty);
 
 // ---------------------------------------------------------------------------
 // Typed implementation of every operation for one (D, arithmetic, storage).
@@ -158,10 +162,30 @@ template <int D, typename R, typename S> struct Impl {
         return LBM_OK;
     }
 
+    // D3Q27: macroscopic pass from the carried moments, then the z-marching collide-stream pass
+    static int zmarch_step(lbm_ctx* h)
+    {
+        if (D != 3) return fail(h, LBM_E_UNSUPPORTED, "the z-march kernel is built for D3Q27");
+        if (!h->moments_valid) {
+            int rc = fused_prepare(h);
+            if (rc) return rc;
+        }
+        k_macro<D, R, true><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot,
+                                                                       h->d_diag, mbuf(h, h->cur));
+        LBM_LAUNCH_CHECK(h, "z-march macroscopic pass");
+        cudaError_t e = zmarch_dispatch(h->storage, h->sims[0].eos, h->tx, h->ty, h->tz, h->d_sims, h->d_tiles,
+                                        (int)h->tiles.size(), h->pop[h->cur], h->pop[h->cur ^ 1], h->W,
+                                        mbuf(h, h->cur ^ 1), h->Ntot, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "z-march step");
+        h->cur ^= 1;
+        return LBM_OK;
+    }
+
     static int step(lbm_ctx* h, int n)
     {
         for (int it = 0; it < n; ++it) {
-            int rc = h->variant == LBM_KERNEL_FUSED ? fused_step(h) : split_step(h);
+            int rc = h->variant == LBM_KERNEL_FUSED ? fused_step(h)
+                     : h->variant == LBM_KERNEL_ZMARCH ? zmarch_step(h) : split_step(h);
             if (rc) return rc;
         }
         return LBM_OK;
@@ -244,6 +268,30 @@ bool fused_shape(int storage, int dim, int tx, int ty, int tz)
     case LBM_F32: return fused_shape_f32(dim, tx, ty, tz);
     case LBM_BF16: return fused_shape_bf16(dim, tx, ty, tz);
     case LBM_F16: return fused_shape_f16(dim, tx, ty, tz);
+    }
+    return false;
+}
+
+cudaError_t zmarch_dispatch(int storage, int eos, int tx, int ty, int zl, const SimDev* sims, const TileEntry* tiles,
+                            int ntiles, const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                            cudaStream_t stream)
+{
+    switch (storage) {
+    case LBM_F64: return zmarch_dispatch_f64(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    case LBM_F32: return zmarch_dispatch_f32(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    case LBM_BF16: return zmarch_dispatch_bf16(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    case LBM_F16: return zmarch_dispatch_f16(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool zmarch_shape(int storage, int tx, int ty)
+{
+    switch (storage) {
+    case LBM_F64: return zmarch_shape_f64(tx, ty);
+    case LBM_F32: return zmarch_shape_f32(tx, ty);
+    case LBM_BF16: return zmarch_shape_bf16(tx, ty);
+    case LBM_F16: return zmarch_shape_f16(tx, ty);
     }
     return false;
 }
@@ -473,7 +521,13 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
         // default kernel: the fused one-pass step with its default tile when it runs this lattice
         int dtx, dty, dtz;
         fused_default_tile(h->dim, h->storage, dtx, dty, dtz);
-        if (h->ops.fused_ok(h, dtx, dty, dtz)) {
+        bool same_eos = true;
+        for (const SimDev& d : h->sims) same_eos = same_eos && d.eos == h->sims[0].eos;
+        if (h->dim == 3 && same_eos && zmarch_shape(h->storage, 30, 14)) {
+            h->variant = LBM_KERNEL_ZMARCH;
+            h->tx = 30; h->ty = 14; h->tz = 32;
+            rc = build_tiles(h, 30, 14, 32);
+        } else if (h->ops.fused_ok(h, dtx, dty, dtz)) {
             h->variant = LBM_KERNEL_FUSED;
             h->tx = dtx; h->ty = dty; h->tz = dtz;
             rc = build_tiles(h, dtx, dty, dtz);
@@ -738,6 +792,20 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
         h->variant = LBM_KERNEL_SPLIT;
         return LBM_OK;
     }
+    if (variant == LBM_KERNEL_ZMARCH) {
+        if (h->dim != 3) return fail(h, LBM_E_INVALID, "the z-march kernel runs D3Q27 lattices");
+        if (tx <= 0 || ty <= 0) { tx = 30; ty = 14; }
+        if (tz <= 0) tz = 32;
+        for (const SimDev& d : h->sims)
+            if (d.eos != h->sims[0].eos) return fail(h, LBM_E_INVALID, "one equation of state per z-march launch");
+        if (!zmarch_shape(h->storage, tx, ty)) return fail(h, LBM_E_INVALID, "z-march tile not built");
+        LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+        int rc = build_tiles(h, tx, ty, tz);
+        if (rc) return rc;
+        h->variant = LBM_KERNEL_ZMARCH;
+        h->tx = tx; h->ty = ty; h->tz = tz;
+        return LBM_OK;
+    }
     if (variant != LBM_KERNEL_FUSED && variant != LBM_KERNEL_AUTO) return fail(h, LBM_E_INVALID, "unknown variant");
     int dtx, dty, dtz;
     fused_default_tile(h->dim, h->storage, dtx, dty, dtz);
@@ -795,6 +863,11 @@ int lbm_autotune(lbm_handle h, int trial_steps, int* variant, int* tx, int* ty, 
     } else {
         for (auto& t : shapes3)
             if (h->ops.fused_ok(h, t[0], t[1], t[2])) cands.push_back({LBM_KERNEL_FUSED, t[0], t[1], t[2]});
+        const int zshapes[][3] = {{30, 14, 32}, {62, 14, 32}, {32, 16, 32}, {30, 6, 32}, {30, 14, 64}, {30, 14, 16}};
+        bool same_eos = true;
+        for (const SimDev& d : h->sims) same_eos = same_eos && d.eos == h->sims[0].eos;
+        for (auto& t : zshapes)
+            if (same_eos && zmarch_shape(h->storage, t[0], t[1])) cands.push_back({LBM_KERNEL_ZMARCH, t[0], t[1], t[2]});
     }
     h->graph_steps = 0;
     drop_graph(h);

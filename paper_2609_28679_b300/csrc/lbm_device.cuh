@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbm {
 
 // ---------------------------------------------------------------------------
@@ -392,6 +394,98 @@ __device__ __forceinline__ void collide_cell(const C& s, const Macro<R>& m, R di
         // f' = f + 2 beta (f^eq - f) + (1 - beta)(f* - f^eq)
         f[i] = cf0 * f[i] + cf1 * feq + cf2 * fst;
         g[i] = cg0 * g[i] + cg1 * geq + cg2 * gst;
+    }
+}
+
+// The same collision split per population: the per-axis factors are formed
+// once (Coll::make) and each f_i, g_i is relaxed on its own (Coll::f, ::g),
+// so that a kernel can stream f and then g through the registers.
+template <int D, typename R> struct Coll {
+    R rho, e, es, qc[3];
+    R A0[3][3], As[3][3], B0[3][3], H0[3][3], Hs[3][3];
+    R cf0, cf1, cf2, cg0, cg1, cg2;
+
+    template <typename C>
+    __device__ __forceinline__ static Coll make(const C& s, const Macro<R>& m, R divu, const R* gh, const R* gT,
+                                                const R* Phi)
+    {
+        Coll c;
+        c.rho = m.rho;
+        c.e = m.e;
+        R us[3], FF = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            us[a] = a < D ? m.u[a] + m.F[a] * m.ir : R(0);
+            FF += m.F[a] * m.F[a];
+            c.qc[a] = a < D ? m.P * (gh[a] - (R)s.k_mu * gT[a]) : R(0);
+        }
+        const R ths = m.theta + m.athe * divu + (m.gam - R(1)) * m.Q * m.ir;
+        const R Ts = m.T + (m.Q * m.ir - R(0.5) * FF * m.ir * m.ir) * m.icv;
+        const RhoPart<R> p = rho_part<R>(s, m.rho);
+        c.es = eos_e<R>(s, p, Ts);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            psi3<R>(m.u[a], m.theta + m.u[a] * m.u[a], c.A0[a]);
+            psi3<R>(us[a], ths + us[a] * us[a] + Phi[a], c.As[a]);
+            psi3<R>(us[a], ths + us[a] * us[a], c.B0[a]);
+            hpsi3<R>(m.u[a], m.theta, c.H0[a]);
+            hpsi3<R>(us[a], ths, c.Hs[a]);
+        }
+        const R bf = (R)s.beta_f, bg = (R)s.beta_g;
+        c.cf0 = R(1) - R(2) * bf;
+        c.cf1 = R(3) * bf - R(1);
+        c.cf2 = R(1) - bf;
+        c.cg0 = R(1) - R(2) * bg;
+        c.cg1 = R(3) * bg - R(1);
+        c.cg2 = R(1) - bg;
+        return c;
+    }
+
+    // post-collision f_i from pre-collision f_i
+    template <int I> __device__ __forceinline__ R f(R fi) const
+    {
+        constexpr int d0 = dig(I, 0), d1 = dig(I, 1), d2 = dig(I, 2);
+        R feq, fst;
+        if (D == 2) {
+            feq = rho * A0[0][d0] * A0[1][d1];
+            fst = rho * As[0][d0] * As[1][d1];
+        } else {
+            feq = rho * A0[0][d0] * A0[1][d1] * A0[2][d2];
+            fst = rho * As[0][d0] * As[1][d1] * As[2][d2];
+        }
+        return cf0 * fi + cf1 * feq + cf2 * fst;
+    }
+
+    // post-collision g_i from pre-collision g_i
+    template <int I> __device__ __forceinline__ R g(R gi) const
+    {
+        constexpr int d0 = dig(I, 0), d1 = dig(I, 1), d2 = dig(I, 2);
+        R geq, gst;
+        if (D == 2) {
+            geq = rho * (e * A0[0][d0] * A0[1][d1] + H0[0][d0] * A0[1][d1] + A0[0][d0] * H0[1][d1]);
+            gst = rho * (es * B0[0][d0] * B0[1][d1] + Hs[0][d0] * B0[1][d1] + B0[0][d0] * Hs[1][d1]);
+        } else {
+            const R a01 = A0[0][d0] * A0[1][d1];
+            geq = rho * ((e * a01 + H0[0][d0] * A0[1][d1] + A0[0][d0] * H0[1][d1]) * A0[2][d2] + a01 * H0[2][d2]);
+            const R b01 = B0[0][d0] * B0[1][d1];
+            gst = rho * ((es * b01 + Hs[0][d0] * B0[1][d1] + B0[0][d0] * Hs[1][d1]) * B0[2][d2] + b01 * Hs[2][d2]);
+        }
+        if (cnorm2(I) == 1) {
+            R cq = R(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) cq += R(cc(I, a)) * qc[a];
+            gst += R(0.5) * cq;
+        }
+        return cg0 * gi + cg1 * geq + cg2 * gst;
+    }
+};
+
+// compile-time loop over the populations
+template <int I, int N, typename F> __device__ __forceinline__ void static_for(F&& fn)
+{
+    if constexpr (I < N) {
+        fn(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(fn);
     }
 }
 

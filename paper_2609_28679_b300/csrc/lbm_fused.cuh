@@ -29,9 +29,6 @@ struct TileEntry {
     int sim, x0, y0, z0;
 };
 
-// carried per-cell values: rho, j (3), G, T (Newton guess)
-enum MField { M_RHO = 0, M_J = 1, M_G = 4, M_T = 5, M_NF = 6 };
-
 constexpr int kFusedThreads = 256;
 
 template <int D, int TX, int TY, int TZ> struct TileShape {

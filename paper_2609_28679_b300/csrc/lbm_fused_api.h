@@ -16,7 +16,11 @@ struct TileEntry;
                                       const TileEntry* tiles, int ntiles, const void* src, void* dst,            \
                                       const void* Min, void* Mout, long long Ntot, unsigned long long* diag,     \
                                       cudaStream_t stream);                                                      \
-    bool fused_shape_##NAME(int dim, int tx, int ty, int tz);
+    bool fused_shape_##NAME(int dim, int tx, int ty, int tz);                                                   \
+    cudaError_t zmarch_dispatch_##NAME(int eos, int tx, int ty, int zl, const SimDev* sims, const TileEntry* tiles, \
+                                       int ntiles, const void* src, void* dst, const void* W, void* Mout,          \
+                                       long long Ntot, cudaStream_t stream);                                      \
+    bool zmarch_shape_##NAME(int tx, int ty);
 
 LBM_FUSED_DECL(f64)
 LBM_FUSED_DECL(f32)

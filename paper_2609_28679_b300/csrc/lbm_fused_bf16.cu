@@ -2,6 +2,7 @@
 // for D2Q9 and D3Q27 and each equation of state.
 #include "lbm_fused.cuh"
 #include "lbm_fused_api.h"
+#include "lbm_zmarch.cuh"
 
 namespace lbm {
 
@@ -57,6 +58,40 @@ bool fused_shape_bf16(int dim, int tx, int ty, int tz)
         TILES_3D(HAS)
     }
 #undef HAS
+    return false;
+}
+
+// z-march shapes (xy tile; the z range is a launch parameter)
+#define ZTILES(X) X(30, 14) X(62, 14) X(32, 16) X(30, 6)
+
+namespace {
+template <int EK>
+cudaError_t zgo(int tx, int ty, int zl, const SimDev* sims, const TileEntry* tiles, int ntiles, const void* src,
+                void* dst, const void* W, void* Mout, long long Ntot, cudaStream_t stream)
+{
+#define ZCASE(A, B) \
+    if (tx == A && ty == B) return zmarch_launch_shape<float, __nv_bfloat16, EK, A, B>(sims, tiles, ntiles, zl, src, dst, W, Mout, Ntot, stream);
+    ZTILES(ZCASE)
+#undef ZCASE
+    return cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t zmarch_dispatch_bf16(int eos, int tx, int ty, int zl, const SimDev* sims, const TileEntry* tiles,
+                                int ntiles, const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                                cudaStream_t stream)
+{
+    if (eos == EOS_IDEAL) return zgo<EOS_IDEAL>(tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    if (eos == EOS_VDW) return zgo<EOS_VDW>(tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    if (eos == EOS_PR) return zgo<EOS_PR>(tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    return cudaErrorInvalidValue;
+}
+
+bool zmarch_shape_bf16(int tx, int ty)
+{
+#define ZHAS(A, B) if (tx == A && ty == B) return true;
+    ZTILES(ZHAS)
+#undef ZHAS
     return false;
 }
 

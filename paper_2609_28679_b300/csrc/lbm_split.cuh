@@ -16,6 +16,9 @@ enum Field {
     W_P = 16, W_TH = 17, W_CV = 18, W_GAM = 19, W_ATHE = 20, W_E = 21, W_NF = 22
 };
 
+// carried per-cell values of the one-pass and z-march paths: rho, j (3), G, T (Newton guess)
+enum MField { M_RHO = 0, M_J = 1, M_G = 4, M_T = 5, M_NF = 6 };
+
 constexpr int kBlockCells = 256;
 
 struct BlockEntry {
@@ -189,9 +192,12 @@ __device__ __forceinline__ R lap_at(const SimDev& s, const R* __restrict__ rho, 
 // ---------------------------------------------------------------------------
 // Pass 2: force, velocity, energy, temperature and closure scalars per cell.
 // ---------------------------------------------------------------------------
-template <int D, typename R>
+// FROM_M: rho, j, G come from the carried moments M (z-march path) and rho is
+// copied into W; otherwise from W (written by k_moments).
+template <int D, typename R, bool FROM_M = false>
 __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
-                                                       R* __restrict__ W, long long Ntot, unsigned long long* diag)
+                                                       R* __restrict__ W, long long Ntot, unsigned long long* diag,
+                                                       const R* __restrict__ M = nullptr)
 {
     __shared__ SimDev s;
     __shared__ MlpSmem mlp_s;
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
             int x, y, z;
             cell_xyz(s, k, x, y, z);
             const long long gk = s.cell_off + k;
-            const R* rho = W + W_RHO * Ntot + s.cell_off;
+            const R* rho = (FROM_M ? M + M_RHO * Ntot : W + W_RHO * Ntot) + s.cell_off;
             const R r = rho[k];
             R F[3] = {0, 0, 0}, j[3];
 #pragma unroll
@@ -223,9 +229,10 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
                 F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl;
             }
 #pragma unroll
-            for (int a = 0; a < 3; ++a) j[a] = W[(W_J + a) * Ntot + gk];
+            for (int a = 0; a < 3; ++a) j[a] = FROM_M ? M[(M_J + a) * Ntot + gk] : W[(W_J + a) * Ntot + gk];
             rr = (float)r;
-            ee = (float)macro_energy<D, R>(r, j, W[W_G * Ntot + gk], F, (R)heat_at(s, z));
+            ee = (float)macro_energy<D, R>(r, j, FROM_M ? M[M_G * Ntot + gk] : W[W_G * Ntot + gk], F,
+                                            (R)heat_at(s, z));
         }
         Tml = (R)mlp_T_warp(mlp_s, rr, ee);
     }
@@ -233,7 +240,7 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
         int x, y, z;
         cell_xyz(s, k, x, y, z);
         const long long gk = s.cell_off + k;
-        const R* rho = W + W_RHO * Ntot + s.cell_off;
+        const R* rho = (FROM_M ? M + M_RHO * Ntot : W + W_RHO * Ntot) + s.cell_off;
         R r = rho[k];
         R F[3] = {0, 0, 0}, j[3];
 #pragma unroll
@@ -243,9 +250,11 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
             F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl;  // Eqs. force_decomposition, korteweg_force
         }
 #pragma unroll
-        for (int a = 0; a < 3; ++a) j[a] = W[(W_J + a) * Ntot + gk];
+        for (int a = 0; a < 3; ++a) j[a] = FROM_M ? M[(M_J + a) * Ntot + gk] : W[(W_J + a) * Ntot + gk];
         R Q = (R)heat_at(s, z);
-        Macro<R> m = macro_cell<D, R>(s, r, j, W[W_G * Ntot + gk], F, Q, use_mlp ? Tml : W[W_T * Ntot + gk], flags);
+        Macro<R> m = macro_cell<D, R>(s, r, j, FROM_M ? M[M_G * Ntot + gk] : W[W_G * Ntot + gk], F, Q,
+                                      use_mlp ? Tml : W[W_T * Ntot + gk], flags);
+        if (FROM_M) W[W_RHO * Ntot + gk] = r;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             W[(W_U + a) * Ntot + gk] = m.u[a];

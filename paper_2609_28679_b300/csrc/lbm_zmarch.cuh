@@ -1,0 +1,271 @@
+// z-marching collide-stream pass for D3Q27 (second pass of the 3-D step).
+//
+// The first pass (k_macro<3, R, true>) evaluates the macroscopic state of
+// every cell once from the carried moments (rho, j, G) and writes the fields
+// the stencils and the collision read.  This pass owns an xy tile of TX x TY
+// cells and a range of ZL planes and marches along z: for each plane zc from
+// z0 - 1 to z0 + ZL it collides the xy tile plus its one-cell rim (pulling
+// every population once, f and then g through the registers), stores the
+// post-collision populations of its own cells, and adds every post-collision
+// population to the next-step moment of the cell it streams into, kept in a
+// ring of three planes in shared memory; a plane's moments are complete, and
+// written, once the plane above it has been collided.  The rim collisions are
+// the only repeated work: (TX+2)(TY+2)/(TX TY) in xy and (ZL+2)/ZL in z.
+#pragma once
+
+#include "lbm_device.cuh"
+#include "lbm_fused.cuh"
+#include "lbm_split.cuh"
+
+namespace lbm {
+
+constexpr int kZThreads = 256;
+
+template <typename R, typename S, int EK, int TX, int TY>
+__global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
+    k_zmarch(const SimDev* __restrict__ sims, const TileEntry* __restrict__ tiles, int ntiles, int ZL,
+             const S* __restrict__ src, S* __restrict__ dst, const R* __restrict__ W, R* __restrict__ Mout,
+             long long Ntot)
+{
+    constexpr int Q = 27;
+    constexpr int W1 = TX + 2, H1 = TY + 2, N1 = W1 * H1, N0 = TX * TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* acc = reinterpret_cast<R*>(smem_raw);  // [3 planes][5: rho, j (3), G][N0]
+    __shared__ SimK<R, EK> s;
+    __shared__ int cur_sim;
+    const int tid = threadIdx.x;
+    if (tid == 0) cur_sim = -1;
+    __syncthreads();
+
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileEntry te = tiles[t];
+        if (te.sim != cur_sim) {
+            __syncthreads();
+            if (tid == 0) {
+                simc_from<R>(static_cast<SimC<R>&>(s), sims[te.sim]);
+                cur_sim = te.sim;
+            }
+            __syncthreads();
+        }
+        const int nx = s.nx, ny = s.ny, nz = s.nz;
+        const bool walls = s.zwalls != 0;
+        const unsigned Ncell = (unsigned)s.N;
+        const R* Wc = W + s.cell_off;
+        const S* fb = src + s.pop_off;
+        const S* gb = fb + (size_t)Q * s.N;
+        S* fo = dst + s.pop_off;
+        S* go = fo + (size_t)Q * s.N;
+        R* Mo = Mout + s.cell_off;
+        const int zend = min(te.z0 + ZL, nz);
+        const unsigned vx = (unsigned)min(TX, nx - te.x0), vy = (unsigned)min(TY, ny - te.y0);
+        for (int k = tid; k < 15 * N0; k += kZThreads) acc[k] = R(0);
+        __syncthreads();
+
+        for (int zc = te.z0 - 1; zc <= zend; ++zc) {
+            const bool ghost_plane = walls && (zc < 0 || zc >= nz);
+            if (!ghost_plane) {
+                const int z = wrapc(zc, nz);
+                // z neighbours of the stencils: periodic, or mirrored beyond walls (flip: odd fields change sign)
+                int zn[5];
+                bool zf[5];
+#pragma unroll
+                for (int o = -2; o <= 2; ++o) {
+                    if (walls) zn[o + 2] = mirror_z(zc + o, nz, zf[o + 2]);
+                    else {
+                        zn[o + 2] = wrapc(zc + o, nz);
+                        zf[o + 2] = false;
+                    }
+                }
+                for (int k = tid; k < N1; k += kZThreads) {
+                    const int lx = k % W1, ly = k / W1;
+                    const int tx = lx - 1, ty = ly - 1;
+                    const int x = wrapc(te.x0 + tx, nx), y = wrapc(te.y0 + ty, ny);
+                    const int xm1 = x == 0 ? nx - 1 : x - 1, xp1 = x == nx - 1 ? 0 : x + 1;
+                    const int ym1 = y == 0 ? ny - 1 : y - 1, yp1 = y == ny - 1 ? 0 : y + 1;
+                    auto cell = [&](int xx, int yy, int zz) {
+                        return (unsigned)xx + (unsigned)nx * ((unsigned)yy + (unsigned)ny * (unsigned)zz);
+                    };
+                    const unsigned gk = cell(x, y, z);
+                    auto Wf = [&](int f, unsigned c) { return Wc[(size_t)f * Ntot + c]; };
+
+                    Macro<R> m;
+                    m.rho = Wf(W_RHO, gk);
+                    m.ir = R(1) / m.rho;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        m.u[a] = Wf(W_U + a, gk);
+                        m.F[a] = Wf(W_F + a, gk);
+                    }
+                    m.Q = heat_q<R>(s, z);
+                    m.T = Wf(W_T, gk);
+                    m.P = Wf(W_P, gk);
+                    m.theta = Wf(W_TH, gk);
+                    m.h = Wf(W_H, gk);
+                    m.cv = Wf(W_CV, gk);
+                    m.icv = EK == EOS_PR ? R(1) / m.cv : s.inv_cv;
+                    m.gam = Wf(W_GAM, gk);
+                    m.athe = Wf(W_ATHE, gk);
+                    m.e = Wf(W_E, gk);
+
+                    // stencils: div u, grad h, grad T (central) and Phi (Eq. correction)
+                    R divu, gh[3], gT[3], Phi[3];
+                    {
+                        const unsigned cxm = cell(xm1, y, z), cxp = cell(xp1, y, z);
+                        const unsigned cym = cell(x, ym1, z), cyp = cell(x, yp1, z);
+                        const unsigned czm = cell(x, y, zn[1]), czp = cell(x, y, zn[3]);
+                        const R szm = zf[1] ? R(-1) : R(1), szp = zf[3] ? R(-1) : R(1);
+                        divu = R(0.5) * ((Wf(W_U, cxp) - Wf(W_U, cxm)) + (Wf(W_U + 1, cyp) - Wf(W_U + 1, cym)) +
+                                         (szp * Wf(W_U + 2, czp) - szm * Wf(W_U + 2, czm)));
+                        gh[0] = R(0.5) * (Wf(W_H, cxp) - Wf(W_H, cxm));
+                        gh[1] = R(0.5) * (Wf(W_H, cyp) - Wf(W_H, cym));
+                        gh[2] = R(0.5) * (Wf(W_H, czp) - Wf(W_H, czm));
+                        gT[0] = R(0.5) * (Wf(W_T, cxp) - Wf(W_T, cxm));
+                        gT[1] = R(0.5) * (Wf(W_T, cyp) - Wf(W_T, cym));
+                        gT[2] = R(0.5) * (Wf(W_T, czp) - Wf(W_T, czm));
+                        R dX[3];
+                        if (s.phi_central) {
+                            dX[0] = R(0.5) * (Wf(W_X, cxp) - Wf(W_X, cxm));
+                            dX[1] = R(0.5) * (Wf(W_X + 1, cyp) - Wf(W_X + 1, cym));
+                            dX[2] = R(0.5) * (szp * Wf(W_X + 2, czp) - szm * Wf(W_X + 2, czm));
+                        } else {
+                            // second-order one-sided by the sign of u_alpha (u >= 0: backward)
+                            const R X0x = Wf(W_X, gk), X0y = Wf(W_X + 1, gk), X0z = Wf(W_X + 2, gk);
+                            if (m.u[0] >= R(0))
+                                dX[0] = R(0.5) * (R(3) * X0x - R(4) * Wf(W_X, cxm) +
+                                                  Wf(W_X, cell(wrapc(x - 2, nx), y, z)));
+                            else
+                                dX[0] = -R(0.5) * (R(3) * X0x - R(4) * Wf(W_X, cxp) +
+                                                   Wf(W_X, cell(wrapc(x + 2, nx), y, z)));
+                            if (m.u[1] >= R(0))
+                                dX[1] = R(0.5) * (R(3) * X0y - R(4) * Wf(W_X + 1, cym) +
+                                                  Wf(W_X + 1, cell(x, wrapc(y - 2, ny), z)));
+                            else
+                                dX[1] = -R(0.5) * (R(3) * X0y - R(4) * Wf(W_X + 1, cyp) +
+                                                   Wf(W_X + 1, cell(x, wrapc(y + 2, ny), z)));
+                            if (m.u[2] >= R(0)) {
+                                const R s2 = zf[0] ? R(-1) : R(1);
+                                dX[2] = R(0.5) * (R(3) * X0z - R(4) * szm * Wf(W_X + 2, czm) +
+                                                  s2 * Wf(W_X + 2, cell(x, y, zn[0])));
+                            } else {
+                                const R s2 = zf[4] ? R(-1) : R(1);
+                                dX[2] = -R(0.5) * (R(3) * X0z - R(4) * szp * Wf(W_X + 2, czp) +
+                                                   s2 * Wf(W_X + 2, cell(x, y, zn[4])));
+                            }
+                        }
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) Phi[a] = -dX[a] * m.ir;
+                    }
+                    const Coll<3, R> cl = Coll<3, R>::make(s, m, divu, gh, gT, Phi);
+
+                    // pull sources: f_i(x) = f'_i(x - c_i), or f'_opp(i)(x) across a z wall
+                    const int xs[3] = {x, xm1, xp1}, ys[3] = {y, ym1, yp1};
+                    int zs[3] = {z, z == 0 ? nz - 1 : z - 1, z == nz - 1 ? 0 : z + 1};
+                    bool zw[3] = {false, false, false};
+                    if (walls) {
+                        zw[1] = z == 0;
+                        zw[2] = z == nz - 1;
+                    }
+                    unsigned rows[3][3];
+#pragma unroll
+                    for (int b = 0; b < 3; ++b)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) rows[b][c] = (unsigned)nx * ((unsigned)ys[b] + (unsigned)ny * (unsigned)zs[c]);
+                    const bool own = tx >= 0 && ty >= 0 && tx < TX && ty < TY && (unsigned)tx < vx && (unsigned)ty < vy &&
+                                     zc >= te.z0 && zc < zend;
+                    const bool zlo_wall = walls && z == 0, zhi_wall = walls && z == nz - 1;
+                    // destinations of f'_i: cell (tx + c, ty + c, zc + c), or (tx, ty, zc) as opp(i) across a wall
+                    auto scatter = [&](auto I, int field_base, R v) {
+                        constexpr int i = decltype(I)::value;
+                        constexpr int c0 = cc(i, 0), c1 = cc(i, 1), c2 = cc(i, 2);
+                        const bool bounce = (c2 < 0 && zlo_wall) || (c2 > 0 && zhi_wall);
+                        const int dx = bounce ? tx : tx + c0, dy = bounce ? ty : ty + c1, zd = bounce ? zc : zc + c2;
+                        if ((unsigned)dx < vx && (unsigned)dy < vy && zd >= te.z0 && zd < zend) {
+                            R* a = acc + (zd % 3) * 5 * N0 + dx + TX * dy;
+                            if (field_base == 0) {
+                                atomicAdd(a, v);
+                                if (c0 != 0) atomicAdd(a + 1 * N0, (c0 > 0) != bounce ? v : -v);
+                                if (c1 != 0) atomicAdd(a + 2 * N0, (c1 > 0) != bounce ? v : -v);
+                                if (c2 != 0) atomicAdd(a + 3 * N0, (c2 > 0) != bounce ? v : -v);
+                            } else {
+                                atomicAdd(a + 4 * N0, v);
+                            }
+                        }
+                    };
+                    // f: pull, relax, store, scatter
+                    static_for<0, Q>([&](auto I) {
+                        constexpr int i = decltype(I)::value;
+                        constexpr int d0 = dig(i, 0), d1 = dig(i, 1), d2 = dig(i, 2);
+                        const bool wall_src = zw[d2];
+                        const int isrc = wall_src ? opp(i) : i;
+                        const unsigned idx = wall_src ? (unsigned)isrc * Ncell + gk
+                                                      : (unsigned)i * Ncell + (unsigned)xs[d0] + rows[d1][d2];
+                        R v = Codec<S, R>::ld(fb + idx);
+                        if (Codec<S, R>::offset) v += s.fref[isrc];
+                        v = cl.template f<i>(v);
+                        if (own) Codec<S, R>::st(fo + (unsigned)i * Ncell + gk, v - (Codec<S, R>::offset ? s.fref[i] : R(0)));
+                        scatter(I, 0, v);
+                    });
+                    // g: pull, relax, store, scatter
+                    static_for<0, Q>([&](auto I) {
+                        constexpr int i = decltype(I)::value;
+                        constexpr int d0 = dig(i, 0), d1 = dig(i, 1), d2 = dig(i, 2);
+                        const bool wall_src = zw[d2];
+                        const int isrc = wall_src ? opp(i) : i;
+                        const unsigned idx = wall_src ? (unsigned)isrc * Ncell + gk
+                                                      : (unsigned)i * Ncell + (unsigned)xs[d0] + rows[d1][d2];
+                        R v = Codec<S, R>::ld(gb + idx);
+                        if (Codec<S, R>::offset) v += s.gref[isrc];
+                        v = cl.template g<i>(v);
+                        if (own) Codec<S, R>::st(go + (unsigned)i * Ncell + gk, v - (Codec<S, R>::offset ? s.gref[i] : R(0)));
+                        scatter(I, 1, v);
+                    });
+                }
+            }
+            __syncthreads();
+            // plane zc - 1 has all its contributions: write its moments and clear its slot
+            const int zfin = zc - 1;
+            if (zfin >= te.z0 && zfin < zend) {
+                R* a = acc + (zfin % 3) * 5 * N0;
+                for (int d = tid; d < N0; d += kZThreads) {
+                    const int tx = d % TX, ty = d / TX;
+                    const R r = a[d], j0 = a[N0 + d], j1 = a[2 * N0 + d], j2 = a[3 * N0 + d], Gv = a[4 * N0 + d];
+                    a[d] = a[N0 + d] = a[2 * N0 + d] = a[3 * N0 + d] = a[4 * N0 + d] = R(0);
+                    if ((unsigned)tx >= vx || (unsigned)ty >= vy) continue;
+                    const unsigned kk = (unsigned)(te.x0 + tx) + (unsigned)nx * ((unsigned)(te.y0 + ty) + (unsigned)ny * (unsigned)zfin);
+                    Mo[M_RHO * Ntot + kk] = r;
+                    Mo[(M_J + 0) * Ntot + kk] = j0;
+                    Mo[(M_J + 1) * Ntot + kk] = j1;
+                    Mo[(M_J + 2) * Ntot + kk] = j2;
+                    Mo[M_G * Ntot + kk] = Gv;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename R, typename S, int EK, int TX, int TY>
+cudaError_t zmarch_launch_shape(const SimDev* sims, const TileEntry* tiles, int ntiles, int ZL, const void* src,
+                                void* dst, const void* W, void* Mout, long long Ntot, cudaStream_t stream)
+{
+    constexpr size_t smem = (size_t)15 * TX * TY * sizeof(R);
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_zmarch<R, S, EK, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, dev = 0, nsm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_zmarch<R, S, EK, TX, TY>, kZThreads, smem);
+        if (e != cudaSuccess) return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        grid_cap = per_sm * nsm;
+    }
+    const int grid = ntiles < grid_cap ? ntiles : grid_cap;
+    k_zmarch<R, S, EK, TX, TY><<<grid, kZThreads, smem, stream>>>(sims, tiles, ntiles, ZL, (const S*)src, (S*)dst,
+                                                                  (const R*)W, (R*)Mout, Ntot);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

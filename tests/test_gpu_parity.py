@@ -19,21 +19,30 @@ from tests.util import oracle_params, rel_linf
 
 pytestmark = pytest.mark.gpu
 
-SPLIT, FUSED = lbm.LBM_KERNEL_SPLIT, lbm.LBM_KERNEL_FUSED
+SPLIT, FUSED, ZMARCH = lbm.LBM_KERNEL_SPLIT, lbm.LBM_KERNEL_FUSED, lbm.LBM_KERNEL_ZMARCH
 
 
 def _variants():
     return [SPLIT, FUSED]
 
 
+def _variants3():
+    # z-march with the default range and with 4-plane ranges (several ranges per column)
+    return [SPLIT, FUSED, (ZMARCH, (30, 14, 32)), (ZMARCH, (30, 6, 4))]
+
+
 def _run_pair(case, steps, variant, fields=None):
     fields = fields if fields is not None else case.fields()
     sim = lbm.Simulation(case)
-    if variant == FUSED:
+    tile = (0, 0, 0)
+    if isinstance(variant, tuple):
+        variant, tile = variant
+    if variant != SPLIT:
         try:
-            lbm.lbm_set_kernel(sim.h, FUSED)
+            lbm.lbm_set_kernel(sim.h, variant, *tile)
         except lbm.LbmError as e:
-            pytest.skip(f"fused kernel unavailable for this lattice: {e}")
+            pytest.skip(f"kernel unavailable for this lattice: {e}")
+        assert sim.kernel()[0] == variant
     sim.init(fields)
     sim.step(steps)
     o = orc.Oracle(oracle_params(case))
@@ -83,7 +92,7 @@ def test_f64_vdw_2d_upwind_phi(variant):
     _compare(sim, o, 1e-12)
 
 
-@pytest.mark.parametrize("variant", _variants())
+@pytest.mark.parametrize("variant", _variants3())
 def test_f64_pr_3d_walls_heat_gravity(variant):
     c = wl.pr_heated_slab(n=11, nz=13, storage="f64")
     c.ny = 9
@@ -92,10 +101,19 @@ def test_f64_pr_3d_walls_heat_gravity(variant):
     _compare(sim, o, 1e-12)
 
 
-@pytest.mark.parametrize("variant", _variants())
+@pytest.mark.parametrize("variant", _variants3())
 def test_f64_pr_3d_droplet_periodic(variant):
     c = wl.pr_droplet(n=14, radius=4.0, storage="f64")
     sim, o = _run_pair(c, 8, variant)
+    _compare(sim, o, 1e-12)
+
+
+@pytest.mark.parametrize("variant", _variants3())
+def test_f64_vdw_3d_periodic_upwind_korteweg(variant):
+    c = wl.Case(name="vdw3", dim=3, nx=13, ny=10, nz=9, eos="vdw", R=1.0, cv=2.5, a=wl.VDW_A, b=wl.VDW_B,
+                kappa=wl.VDW_KAPPA, eta_over_mu=wl.VDW_ETA, k_over_mu=3.5, accel=(2e-4, -1e-4, 3e-4), q=1e-6,
+                storage="f64", init=dict(kind="noisy_density", rho0=2.0, amp=0.01, T0=1.1 * wl.VDW_TC, seed=8))
+    sim, o = _run_pair(c, 10, variant)
     _compare(sim, o, 1e-12)
 
 
@@ -157,7 +175,7 @@ def test_f32_ideal_2d(variant):
     _compare(sim, o, 1e-5, f32=True)
 
 
-@pytest.mark.parametrize("variant", _variants())
+@pytest.mark.parametrize("variant", _variants3())
 def test_f32_pr_3d_walls(variant):
     c = wl.pr_heated_slab(n=12, nz=10, storage="f32")
     c.zhi = 3
@@ -171,9 +189,10 @@ def test_f32_pr_3d_walls(variant):
 # step; bounded here over a short horizon relative to the population scale.
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("storage,tol", [("bf16", 2e-3), ("f16", 3e-4)])
-def test_16bit_storage_error_bound(storage, tol):
+@pytest.mark.parametrize("variant", [SPLIT, (ZMARCH, (30, 6, 4))])
+def test_16bit_storage_error_bound(storage, tol, variant):
     c = wl.pr_heated_slab(n=10, nz=8, storage=storage)
-    sim, o = _run_pair(c, 10, SPLIT)
+    sim, o = _run_pair(c, 10, variant)
     f, g = sim.populations()
     fr, gr = o.populations()
     assert rel_linf(f, fr.ravel()) <= tol
