@@ -855,7 +855,7 @@ int lbm_autotune(lbm_handle h, int trial_steps, int* variant, int* tx, int* ty, 
     // candidates: the split path and every built fused tile of this lattice and storage
     struct Cand { int v, x, y, z; };
     std::vector<Cand> cands{{LBM_KERNEL_SPLIT, 0, 0, 0}};
-    const int shapes2[][3] = {{32, 8, 1}, {32, 16, 1}, {32, 32, 1}, {64, 16, 1}};
+    const int shapes2[][3] = {{32, 8, 1}, {32, 16, 1}, {32, 32, 1}, {64, 16, 1}, {64, 14, 1}};
     const int shapes3[][3] = {{8, 8, 4}, {16, 8, 4}, {8, 8, 8}};
     if (h->dim == 2) {
         for (auto& t : shapes2)

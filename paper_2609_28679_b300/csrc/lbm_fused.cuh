@@ -73,8 +73,18 @@ template <typename R, int EK> struct SimK : SimC<R> {
     static constexpr int eos = EK;
 };
 
+// CTAs per SM that the tile's shared memory leaves room for (float32 2-D
+// tiles; at most 3): the register budget the compiler may use follows from it.
+template <int D, typename R, int TX, int TY, int TZ> constexpr int fused_min_blocks()
+{
+    if (!(D == 2 && sizeof(R) == 4)) return 1;
+    constexpr size_t bytes = TileShape<D, TX, TY, TZ>::elems() * sizeof(R) + 1024;
+    constexpr int n = (int)((size_t)232448 / bytes);
+    return n < 1 ? 1 : (n > 3 ? 3 : n);
+}
+
 template <int D, typename R, typename S, int EK, bool ML, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 : 1)
+__global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY, TZ>()))
     k_fused(const SimDev* __restrict__ sims, const TileEntry* __restrict__ tiles, int ntiles,
             const S* __restrict__ src, S* __restrict__ dst, const R* __restrict__ Min, R* __restrict__ Mout,
             long long Ntot, unsigned long long* diag)
@@ -122,6 +132,31 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
         const R* MG = Min + M_G * Ntot + off;
         const R* MT = Min + M_T * Ntot + off;
 
+        // global inputs of the macroscopic state of cell k of T+3, fetched one
+        // iteration ahead so that their latency overlaps the work before use
+        struct In3 {
+            R j[3], Gm, T;
+        };
+        auto fetch3 = [&](int k) {
+            In3 v;
+            v.j[0] = v.j[1] = v.j[2] = v.Gm = v.T = R(0);
+            if (k < n3) {
+                const int lx = k % G::w(3), ly = (k / G::w(3)) % G::h(3), lz = k / (G::w(3) * G::h(3));
+                const int zr = te.z0 - 3 * HZ + lz;
+                if (!(walls && (zr < 0 || zr >= nz))) {
+                    const int x = wrapc(te.x0 - 3 + lx, nx), y = wrapc(te.y0 - 3 + ly, ny);
+                    const int z = D == 3 ? wrapc(zr, nz) : 0;
+                    const unsigned gk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) v.j[a] = Mj[(size_t)a * Ntot + gk];
+                    v.Gm = MG[gk];
+                    v.T = MT[gk];
+                }
+            }
+            return v;
+        };
+        In3 nxt3 = fetch3(tid);
+
         // ---- 1. rho on T+5 (ghosts beyond walls: the image's value); zero the accumulators
         for (int k = tid; k < n5; k += kFusedThreads) {
             const int lx = k % G::w(5), ly = (k / G::w(5)) % G::h(5), lz = k / (G::w(5) * G::h(5));
@@ -157,11 +192,75 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
             __syncthreads();
         }
 
+        const S* fb = src + s.pop_off;
+        const S* gb = fb + (size_t)Q * s.N;
+        S* fo = dst + s.pop_off;
+        S* go = fo + (size_t)Q * s.N;
+        // pre-collision populations of cell k of T+1: f_i(x) = f'_i(x - c_i),
+        // or f'_opp(i)(x) across a z wall (16-bit storage: offsets added back)
+        auto fetch4 = [&](int k, R* f, R* gp) {
+            if (k >= n1) return;
+            const int lx = k % G::w(1), ly = (k / G::w(1)) % G::h(1), lz = k / (G::w(1) * G::h(1));
+            const int zr = te.z0 - HZ + lz;
+            if (walls && (zr < 0 || zr >= nz)) return;
+            const int x = wrapc(te.x0 - 1 + lx, nx), y = wrapc(te.y0 - 1 + ly, ny);
+            const int z = D == 3 ? wrapc(zr, nz) : 0;
+            // pull: f_i(x) = f'_i(x - c_i), or f'_opp(i)(x) across a z wall
+            const int xs[3] = {x, x == 0 ? nx - 1 : x - 1, x == nx - 1 ? 0 : x + 1};  // x - c for digit 0,1,2
+            const int ys[3] = {y, y == 0 ? ny - 1 : y - 1, y == ny - 1 ? 0 : y + 1};
+            int zs[3] = {z, 0, 0};
+            bool zwall[3] = {false, false, false};
+            if (D == 3) {
+                zs[1] = z - 1;
+                zs[2] = z + 1;
+                if (walls) {
+                    zwall[1] = zs[1] < 0;
+                    zwall[2] = zs[2] >= nz;
+                } else {
+                    zs[1] = z == 0 ? nz - 1 : z - 1;
+                    zs[2] = z == nz - 1 ? 0 : z + 1;
+                }
+            }
+            const unsigned self = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+            unsigned rows[3][3];  // row offsets (y, z) of the pull sources
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int c = 0; c < (D == 3 ? 3 : 1); ++c)
+                    rows[b][c] = (unsigned)nx * ((unsigned)ys[b] + (unsigned)ny * (unsigned)zs[c]);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int d0 = dig(i, 0), d1 = dig(i, 1), d2 = D == 3 ? dig(i, 2) : 0;
+                unsigned idx;
+                int isrc = i;
+                if (D == 3 && zwall[d2]) {
+                    isrc = opp(i);
+                    idx = (unsigned)isrc * Ncell + self;
+                } else {
+                    idx = (unsigned)i * Ncell + (unsigned)xs[d0] + rows[d1][d2];
+                }
+                f[i] = Codec<S, R>::ld(fb + idx);
+                gp[i] = Codec<S, R>::ld(gb + idx);
+                if (Codec<S, R>::offset) {
+                    f[i] += s.fref[isrc];
+                    gp[i] += s.gref[isrc];
+                }
+            }
+        };
+        // 2-D: the populations of the next cell are fetched while this one collides
+        constexpr bool kAhead = D == 2;
+        R fn[Q], gn[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fn[i] = gn[i] = R(0);
+        if (kAhead) fetch4(tid, fn, gn);  // first cell of phase 4, in flight during phase 3
+
         // ---- 3. macroscopic state on T+3
         constexpr int nb3 = (n3 + kFusedThreads - 1) / kFusedThreads;
 #pragma unroll 1
         for (int it = 0; it < nb3; ++it) {
             const int k = it * kFusedThreads + tid;
+            const In3 in3 = nxt3;
+            if (it + 1 < nb3) nxt3 = fetch3(k + kFusedThreads);
             unsigned flags = 0;
             bool owned = false, act = false;
             int lx = 0, ly = 0, lz = 0, zr = 0, z = 0;
@@ -173,20 +272,18 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
                 zr = te.z0 - 3 * HZ + lz;
                 act = !(walls && (zr < 0 || zr >= nz));
                 if (act) {
-                    const int x = wrapc(te.x0 - 3 + lx, nx), y = wrapc(te.y0 - 3 + ly, ny);
                     z = D == 3 ? wrapc(zr, nz) : 0;
-                    const unsigned gk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
                     const int c4 = (lx + 1) + G::w(4) * ((ly + 1) + G::h(4) * (lz + HZ));
                     r = s_rho[(lx + 2) + G::w(5) * ((ly + 2) + G::h(5) * (lz + 2 * HZ))];
                     constexpr int st4[3] = {1, G::w(4), G::w(4) * G::h(4)};
 #pragma unroll
                     for (int a = 0; a < D; ++a) {
                         Fv[a] = r * (s.acc[a] + s.kappa * R(0.5) * (s_L[c4 + st4[a]] - s_L[c4 - st4[a]]));
-                        j[a] = Mj[(size_t)a * Ntot + gk];
+                        j[a] = in3.j[a];
                     }
-                    G_ = MG[gk];
+                    G_ = in3.Gm;
                     Qh = heat_q<R>(s, z);
-                    Tg = MT[gk];
+                    Tg = in3.T;
                 }
             }
             if constexpr (ML) {
@@ -243,11 +340,16 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
         }
 
         // ---- 4. collide T+1, store T, accumulate the next moments of T
-        const S* fb = src + s.pop_off;
-        const S* gb = fb + (size_t)Q * s.N;
-        S* fo = dst + s.pop_off;
-        S* go = fo + (size_t)Q * s.N;
         for (int k = tid; k < n1; k += kFusedThreads) {
+            R f[Q], gp[Q];
+            if (kAhead) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    f[i] = fn[i];
+                    gp[i] = gn[i];
+                }
+                fetch4(k + kFusedThreads, fn, gn);
+            }
             const int lx = k % G::w(1), ly = (k / G::w(1)) % G::h(1), lz = k / (G::w(1) * G::h(1));
             const int zr = te.z0 - HZ + lz;
             if (walls && (zr < 0 || zr >= nz)) continue;
@@ -296,48 +398,8 @@ __global__ void __launch_bounds__(kFusedThreads, (D == 2 && sizeof(R) == 4) ? 3 
                 Phi[a] = -dX * m.ir;
             }
 
-            // pull: f_i(x) = f'_i(x - c_i), or f'_opp(i)(x) across a z wall
-            const int xs[3] = {x, x == 0 ? nx - 1 : x - 1, x == nx - 1 ? 0 : x + 1};  // x - c for digit 0,1,2
-            const int ys[3] = {y, y == 0 ? ny - 1 : y - 1, y == ny - 1 ? 0 : y + 1};
-            int zs[3] = {z, 0, 0};
-            bool zwall[3] = {false, false, false};
-            if (D == 3) {
-                zs[1] = z - 1;
-                zs[2] = z + 1;
-                if (walls) {
-                    zwall[1] = zs[1] < 0;
-                    zwall[2] = zs[2] >= nz;
-                } else {
-                    zs[1] = z == 0 ? nz - 1 : z - 1;
-                    zs[2] = z == nz - 1 ? 0 : z + 1;
-                }
-            }
+            if (!kAhead) fetch4(k, f, gp);
             const unsigned self = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
-            unsigned rows[3][3];  // row offsets (y, z) of the pull sources
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-                for (int c = 0; c < (D == 3 ? 3 : 1); ++c)
-                    rows[b][c] = (unsigned)nx * ((unsigned)ys[b] + (unsigned)ny * (unsigned)zs[c]);
-            R f[Q], gp[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int d0 = dig(i, 0), d1 = dig(i, 1), d2 = D == 3 ? dig(i, 2) : 0;
-                unsigned idx;
-                int isrc = i;
-                if (D == 3 && zwall[d2]) {
-                    isrc = opp(i);
-                    idx = (unsigned)isrc * Ncell + self;
-                } else {
-                    idx = (unsigned)i * Ncell + (unsigned)xs[d0] + rows[d1][d2];
-                }
-                f[i] = Codec<S, R>::ld(fb + idx);
-                gp[i] = Codec<S, R>::ld(gb + idx);
-                if (Codec<S, R>::offset) {
-                    f[i] += s.fref[isrc];
-                    gp[i] += s.gref[isrc];
-                }
-            }
             collide_cell<D, R>(s, m, divu, gh, gT, Phi, f, gp);
 
             const int tx = lx - 1, ty = ly - 1, tz = lz - HZ;

@@ -6,7 +6,7 @@
 
 namespace lbm {
 
-#define TILES_2D(X) X(32, 8, 1) X(32, 16, 1) X(32, 32, 1) X(64, 16, 1)
+#define TILES_2D(X) X(32, 8, 1) X(32, 16, 1) X(32, 32, 1) X(64, 16, 1) X(64, 14, 1)
 #define TILES_3D(X) X(8, 8, 4) X(16, 8, 4) X(8, 8, 8)
 
 namespace {
