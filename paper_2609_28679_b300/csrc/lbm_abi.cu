@@ -103,6 +103,8 @@ cudaError_t zmarch_dispatch(int storage, int eos, int tx, int ty, int zl, const 
                             int ntiles, const void* src, void* dst, const void* W, void* Mout, long long Ntot,
                             cudaStream_t stream);
 bool zmarch_shape(int storage, int tx, int ty);
+cudaError_t zmacro_dispatch(int storage, int eos, int mlp, const SimDev* sims, const BlockEntry* table, int nblocks,
+                            const void* M, void* W, long long Ntot, unsigned long long* diag, cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Typed implementation of every operation for one (D, arithmetic, storage).
@@ -170,9 +172,15 @@ template <int D, typename R, typename S> struct Impl {
             int rc = fused_prepare(h);
             if (rc) return rc;
         }
-        k_macro<D, R, true><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot,
-                                                                       h->d_diag, mbuf(h, h->cur));
-        LBM_LAUNCH_CHECK(h, "z-march macroscopic pass");
+        if (uses_mlp(h) && h->storage != LBM_F32) {  // learned start with 16-bit or float64 storage: generic pass
+            k_macro<D, R, true><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot,
+                                                                           h->d_diag, mbuf(h, h->cur));
+            LBM_LAUNCH_CHECK(h, "z-march macroscopic pass");
+        } else {
+            cudaError_t e = zmacro_dispatch(h->storage, h->sims[0].eos, uses_mlp(h), h->d_sims, h->d_table,
+                                            nblocks(h), mbuf(h, h->cur), h->W, h->Ntot, h->d_diag, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "z-march macroscopic pass");
+        }
         cudaError_t e = zmarch_dispatch(h->storage, h->sims[0].eos, h->tx, h->ty, h->tz, h->d_sims, h->d_tiles,
                                         (int)h->tiles.size(), h->pop[h->cur], h->pop[h->cur ^ 1], h->W,
                                         mbuf(h, h->cur ^ 1), h->Ntot, h->stream);
@@ -281,6 +289,18 @@ cudaError_t zmarch_dispatch(int storage, int eos, int tx, int ty, int zl, const 
     case LBM_F32: return zmarch_dispatch_f32(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
     case LBM_BF16: return zmarch_dispatch_bf16(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
     case LBM_F16: return zmarch_dispatch_f16(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t zmacro_dispatch(int storage, int eos, int mlp, const SimDev* sims, const BlockEntry* table, int nblocks,
+                            const void* M, void* W, long long Ntot, unsigned long long* diag, cudaStream_t stream)
+{
+    switch (storage) {
+    case LBM_F64: return zmacro_dispatch_f64(eos, mlp, sims, table, nblocks, M, W, Ntot, diag, stream);
+    case LBM_F32: return zmacro_dispatch_f32(eos, mlp, sims, table, nblocks, M, W, Ntot, diag, stream);
+    case LBM_BF16: return zmacro_dispatch_bf16(eos, mlp, sims, table, nblocks, M, W, Ntot, diag, stream);
+    case LBM_F16: return zmacro_dispatch_f16(eos, mlp, sims, table, nblocks, M, W, Ntot, diag, stream);
     }
     return cudaErrorInvalidValue;
 }

@@ -397,11 +397,13 @@ __device__ __forceinline__ void collide_cell(const C& s, const Macro<R>& m, R di
     }
 }
 
-// The same collision split per population: the per-axis factors are formed
-// once (Coll::make) and each f_i, g_i is relaxed on its own (Coll::f, ::g),
-// so that a kernel can stream f and then g through the registers.
+// The same collision split per population, so that a kernel can stream f
+// and then g through the registers: make() forms the per-axis factors of
+// f^eq and f* (and keeps the few scalars g needs), f<I>() relaxes f_I;
+// prepare_g() forms the factors of g^eq and g*, and g<I>() relaxes g_I.
 template <int D, typename R> struct Coll {
     R rho, e, es, qc[3];
+    R u[3], th, us[3], ths;
     R A0[3][3], As[3][3], B0[3][3], H0[3][3], Hs[3][3];
     R cf0, cf1, cf2, cg0, cg1, cg2;
 
@@ -412,24 +414,23 @@ template <int D, typename R> struct Coll {
         Coll c;
         c.rho = m.rho;
         c.e = m.e;
-        R us[3], FF = 0;
+        c.th = m.theta;
+        R FF = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            us[a] = a < D ? m.u[a] + m.F[a] * m.ir : R(0);
+            c.u[a] = m.u[a];
+            c.us[a] = a < D ? m.u[a] + m.F[a] * m.ir : R(0);
             FF += m.F[a] * m.F[a];
             c.qc[a] = a < D ? m.P * (gh[a] - (R)s.k_mu * gT[a]) : R(0);
         }
-        const R ths = m.theta + m.athe * divu + (m.gam - R(1)) * m.Q * m.ir;
+        c.ths = m.theta + m.athe * divu + (m.gam - R(1)) * m.Q * m.ir;
         const R Ts = m.T + (m.Q * m.ir - R(0.5) * FF * m.ir * m.ir) * m.icv;
         const RhoPart<R> p = rho_part<R>(s, m.rho);
         c.es = eos_e<R>(s, p, Ts);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             psi3<R>(m.u[a], m.theta + m.u[a] * m.u[a], c.A0[a]);
-            psi3<R>(us[a], ths + us[a] * us[a] + Phi[a], c.As[a]);
-            psi3<R>(us[a], ths + us[a] * us[a], c.B0[a]);
-            hpsi3<R>(m.u[a], m.theta, c.H0[a]);
-            hpsi3<R>(us[a], ths, c.Hs[a]);
+            psi3<R>(c.us[a], c.ths + c.us[a] * c.us[a] + Phi[a], c.As[a]);
         }
         const R bf = (R)s.beta_f, bg = (R)s.beta_g;
         c.cf0 = R(1) - R(2) * bf;
@@ -439,6 +440,16 @@ template <int D, typename R> struct Coll {
         c.cg1 = R(3) * bg - R(1);
         c.cg2 = R(1) - bg;
         return c;
+    }
+
+    __device__ __forceinline__ void prepare_g()
+    {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            psi3<R>(us[a], ths + us[a] * us[a], B0[a]);
+            hpsi3<R>(u[a], th, H0[a]);
+            hpsi3<R>(us[a], ths, Hs[a]);
+        }
     }
 
     // post-collision f_i from pre-collision f_i
@@ -456,7 +467,7 @@ template <int D, typename R> struct Coll {
         return cf0 * fi + cf1 * feq + cf2 * fst;
     }
 
-    // post-collision g_i from pre-collision g_i
+    // post-collision g_i from pre-collision g_i (after prepare_g)
     template <int I> __device__ __forceinline__ R g(R gi) const
     {
         constexpr int d0 = dig(I, 0), d1 = dig(I, 1), d2 = dig(I, 2);

@@ -10,6 +10,7 @@ namespace lbm {
 
 struct SimDev;
 struct TileEntry;
+struct BlockEntry;
 
 #define LBM_FUSED_DECL(NAME)                                                                                     \
     cudaError_t fused_dispatch_##NAME(int dim, int eos, int mlp, int tx, int ty, int tz, const SimDev* sims,              \
@@ -20,7 +21,10 @@ struct TileEntry;
     cudaError_t zmarch_dispatch_##NAME(int eos, int tx, int ty, int zl, const SimDev* sims, const TileEntry* tiles, \
                                        int ntiles, const void* src, void* dst, const void* W, void* Mout,          \
                                        long long Ntot, cudaStream_t stream);                                      \
-    bool zmarch_shape_##NAME(int tx, int ty);
+    bool zmarch_shape_##NAME(int tx, int ty);                                                                   \
+    cudaError_t zmacro_dispatch_##NAME(int eos, int mlp, const SimDev* sims, const BlockEntry* table, int nblocks, \
+                                       const void* M, void* W, long long Ntot, unsigned long long* diag,          \
+                                       cudaStream_t stream);
 
 LBM_FUSED_DECL(f64)
 LBM_FUSED_DECL(f32)

@@ -87,6 +87,12 @@ cudaError_t zmarch_dispatch_f64(int eos, int tx, int ty, int zl, const SimDev* s
     return cudaErrorInvalidValue;
 }
 
+cudaError_t zmacro_dispatch_f64(int eos, int mlp, const SimDev* sims, const BlockEntry* table, int nblocks,
+                                  const void* M, void* W, long long Ntot, unsigned long long* diag, cudaStream_t stream)
+{
+    return zmacro_dispatch_t<double, false>(eos, mlp, sims, table, nblocks, M, W, Ntot, diag, stream);
+}
+
 bool zmarch_shape_f64(int tx, int ty)
 {
 #define ZHAS(A, B) if (tx == A && ty == B) return true;

@@ -172,21 +172,56 @@ __global__ void __launch_bounds__(kBlockCells) k_moments(const SimDev* __restric
     W[W_G * Ntot + gk] = G;
 }
 
-// lap rho at the image of (x,y,z) ((2D+1)-point stencil, mirrored beyond walls)
-template <int D, typename R>
-__device__ __forceinline__ R lap_at(const SimDev& s, const R* __restrict__ rho, int x, int y, int z)
+// Coordinate v + o (|o| small) of an in-domain coordinate v: periodic, or,
+// with mirror set, the image about the walls of a cell beyond them.
+__device__ __forceinline__ int nb_coord(int v, int o, int n, bool mirror)
 {
-    bool fl;
-    long long kc = nb_index(s, x, y, z, fl);
-    int ix, iy, iz;
-    cell_xyz(s, kc, ix, iy, iz);
-    R c = rho[kc], L = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        int e0 = a == 0, e1 = a == 1, e2 = a == 2;
-        L += rho[nb_index(s, ix + e0, iy + e1, iz + e2, fl)] - R(2) * c + rho[nb_index(s, ix - e0, iy - e1, iz - e2, fl)];
+    int w = v + o;
+    if (mirror) {
+        if (w < 0) w = -1 - w;
+        else if (w >= n) w = 2 * n - 1 - w;
+        if ((unsigned)w >= (unsigned)n) {
+            bool fl;
+            w = mirror_z(v + o, n, fl);
+        }
+    } else {
+        if (w < 0) w += n;
+        else if (w >= n) w -= n;
+        if ((unsigned)w >= (unsigned)n) w = wrapi(v + o, n);
     }
+    return w;
+}
+
+// lap rho at the in-domain cell (ix, iy, iz): (2D+1)-point stencil, with
+// neighbours beyond a z wall taken from their mirror images
+template <int D, typename R>
+__device__ __forceinline__ R lap_img(const R* __restrict__ rho, int ix, int iy, int iz, int nx, int ny, int nz,
+                                     bool walls)
+{
+    auto at = [&](int x, int y, int z) {
+        return rho[(long long)x + (long long)nx * ((long long)y + (long long)ny * (long long)z)];
+    };
+    const R c = at(ix, iy, iz);
+    R L = 0;
+    L += at(nb_coord(ix, 1, nx, false), iy, iz) - R(2) * c + at(nb_coord(ix, -1, nx, false), iy, iz);
+    L += at(ix, nb_coord(iy, 1, ny, false), iz) - R(2) * c + at(ix, nb_coord(iy, -1, ny, false), iz);
+    if (D == 3) L += at(ix, iy, nb_coord(iz, 1, nz, walls)) - R(2) * c + at(ix, iy, nb_coord(iz, -1, nz, walls));
     return L;
+}
+
+// Korteweg gradient of lap rho at (x, y, z) (central difference of lap rho
+// between the images of the two neighbours along each axis)
+template <int D, typename R>
+__device__ __forceinline__ void grad_lap(const R* __restrict__ rho, int x, int y, int z, int nx, int ny, int nz,
+                                         bool walls, R* gl)
+{
+    gl[0] = R(0.5) * (lap_img<D, R>(rho, nb_coord(x, 1, nx, false), y, z, nx, ny, nz, walls) -
+                      lap_img<D, R>(rho, nb_coord(x, -1, nx, false), y, z, nx, ny, nz, walls));
+    gl[1] = R(0.5) * (lap_img<D, R>(rho, x, nb_coord(y, 1, ny, false), z, nx, ny, nz, walls) -
+                      lap_img<D, R>(rho, x, nb_coord(y, -1, ny, false), z, nx, ny, nz, walls));
+    gl[2] = D == 3 ? R(0.5) * (lap_img<D, R>(rho, x, y, nb_coord(z, 1, nz, walls), nx, ny, nz, walls) -
+                               lap_img<D, R>(rho, x, y, nb_coord(z, -1, nz, walls), nx, ny, nz, walls))
+                   : R(0);
 }
 
 // ---------------------------------------------------------------------------
@@ -221,13 +256,10 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
             const long long gk = s.cell_off + k;
             const R* rho = (FROM_M ? M + M_RHO * Ntot : W + W_RHO * Ntot) + s.cell_off;
             const R r = rho[k];
-            R F[3] = {0, 0, 0}, j[3];
+            R F[3] = {0, 0, 0}, j[3], gl[3];
+            grad_lap<D, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls != 0, gl);
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-                int e0 = a == 0, e1 = a == 1, e2 = a == 2;
-                R gl = R(0.5) * (lap_at<D, R>(s, rho, x + e0, y + e1, z + e2) - lap_at<D, R>(s, rho, x - e0, y - e1, z - e2));
-                F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl;
-            }
+            for (int a = 0; a < D; ++a) F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl[a];
 #pragma unroll
             for (int a = 0; a < 3; ++a) j[a] = FROM_M ? M[(M_J + a) * Ntot + gk] : W[(W_J + a) * Ntot + gk];
             rr = (float)r;
@@ -242,13 +274,10 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
         const long long gk = s.cell_off + k;
         const R* rho = (FROM_M ? M + M_RHO * Ntot : W + W_RHO * Ntot) + s.cell_off;
         R r = rho[k];
-        R F[3] = {0, 0, 0}, j[3];
+        R F[3] = {0, 0, 0}, j[3], gl[3];
+        grad_lap<D, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls != 0, gl);
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            int e0 = a == 0, e1 = a == 1, e2 = a == 2;
-            R gl = R(0.5) * (lap_at<D, R>(s, rho, x + e0, y + e1, z + e2) - lap_at<D, R>(s, rho, x - e0, y - e1, z - e2));
-            F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl;  // Eqs. force_decomposition, korteweg_force
-        }
+        for (int a = 0; a < D; ++a) F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl[a];  // Eqs. force_decomposition, korteweg_force
 #pragma unroll
         for (int a = 0; a < 3; ++a) j[a] = FROM_M ? M[(M_J + a) * Ntot + gk] : W[(W_J + a) * Ntot + gk];
         R Q = (R)heat_at(s, z);

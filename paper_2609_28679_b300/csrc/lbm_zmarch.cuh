@@ -1,6 +1,6 @@
 // z-marching collide-stream pass for D3Q27 (second pass of the 3-D step).
 //
-// The first pass (k_macro<3, R, true>) evaluates the macroscopic state of
+// The first pass (k_zmacro below) evaluates the macroscopic state of
 // every cell once from the carried moments (rho, j, G) and writes the fields
 // the stencils and the collision read.  This pass owns an xy tile of TX x TY
 // cells and a range of ZL planes and marches along z: for each plane zc from
@@ -15,7 +15,10 @@
 
 #include "lbm_device.cuh"
 #include "lbm_fused.cuh"
+#include "lbm_mlp.cuh"
 #include "lbm_split.cuh"
+
+#include <type_traits>
 
 namespace lbm {
 
@@ -155,7 +158,8 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
 #pragma unroll
                         for (int a = 0; a < 3; ++a) Phi[a] = -dX[a] * m.ir;
                     }
-                    const Coll<3, R> cl = Coll<3, R>::make(s, m, divu, gh, gT, Phi);
+                    Coll<3, R> cl = Coll<3, R>::make(s, m, divu, gh, gT, Phi);
+                    cl.prepare_g();
 
                     // pull sources: f_i(x) = f'_i(x - c_i), or f'_opp(i)(x) across a z wall
                     const int xs[3] = {x, xm1, xp1}, ys[3] = {y, ym1, yp1};
@@ -242,6 +246,103 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
             __syncthreads();
         }
     }
+}
+
+// First pass of the z-march step: the macroscopic state of every cell
+// (Eqs. def_u, def_E, the EoS and its closure scalars, the flux X of
+// Eq. correction) from the carried moments rho, j, G, with last step's T as
+// the Newton start (or the learned start, ML), written to the field buffer W.
+// One thread per cell, constants of the simulation typed and with the EoS
+// fixed at compile time.
+template <typename R, int EK, bool ML>
+__global__ void __launch_bounds__(kBlockCells) k_zmacro(const SimDev* __restrict__ sims,
+                                                        const BlockEntry* __restrict__ table, const R* __restrict__ M,
+                                                        R* __restrict__ W, long long Ntot, unsigned long long* diag)
+{
+    __shared__ SimK<R, EK> s;
+    __shared__ std::conditional_t<ML, MlpSmem, int> mlp_s;
+    const BlockEntry be = table[blockIdx.x];
+    if (threadIdx.x == 0) simc_from<R>(static_cast<SimC<R>&>(s), sims[be.sim]);
+    __syncthreads();
+    if constexpr (ML) {
+        if (s.mlp != nullptr) {
+            mlp_load(mlp_s, s.mlp);
+            __syncthreads();
+        }
+    }
+    const long long k = (long long)be.start + threadIdx.x;
+    const bool valid = k < s.N;
+    const long long gk = s.cell_off + k;
+    int x = 0, y = 0, z = 0;
+    R r = R(1), F[3] = {0, 0, 0}, j[3] = {0, 0, 0}, Gm = R(0), Tg = R(0), Qh = R(0);
+    if (valid) {
+        cell_xyz(s, k, x, y, z);
+        const R* rho = M + M_RHO * Ntot + s.cell_off;
+        r = rho[k];
+        R gl[3];
+        grad_lap<3, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls != 0, gl);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            F[a] = r * s.acc[a] + s.kappa * r * gl[a];  // Eqs. force_decomposition, korteweg_force
+            j[a] = M[(M_J + a) * Ntot + gk];
+        }
+        Gm = M[M_G * Ntot + gk];
+        Tg = W[W_T * Ntot + gk];
+        Qh = heat_q<R>(s, z);
+    }
+    if constexpr (ML) {
+        if (s.mlp != nullptr) {  // block-uniform: whole warps evaluate the network
+            const float Tm = mlp_T_warp(mlp_s, valid ? (float)r : 1.f,
+                                        valid ? (float)macro_energy<3, R>(r, j, Gm, F, Qh) : 0.f);
+            if (valid) Tg = (R)Tm;
+        }
+    }
+    unsigned flags = 0;
+    if (valid) {
+        const Macro<R> m = macro_cell<3, R>(s, r, j, Gm, F, Qh, Tg, flags);
+        W[W_RHO * Ntot + gk] = r;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            W[(W_U + a) * Ntot + gk] = m.u[a];
+            W[(W_F + a) * Ntot + gk] = m.F[a];
+            W[(W_X + a) * Ntot + gk] = xflux<R>(r, m.u[a], m.theta);
+        }
+        W[W_T * Ntot + gk] = m.T;
+        W[W_H * Ntot + gk] = m.h;
+        W[W_P * Ntot + gk] = m.P;
+        W[W_TH * Ntot + gk] = m.theta;
+        W[W_CV * Ntot + gk] = m.cv;
+        W[W_GAM * Ntot + gk] = m.gam;
+        W[W_ATHE * Ntot + gk] = m.athe;
+        W[W_E * Ntot + gk] = m.e;
+    }
+    if (diag) count_flags(flags, diag);
+}
+
+template <typename R, int EK, bool ML>
+cudaError_t zmacro_launch(const SimDev* sims, const BlockEntry* table, int nblocks, const void* M, void* W,
+                          long long Ntot, unsigned long long* diag, cudaStream_t stream)
+{
+    k_zmacro<R, EK, ML><<<nblocks, kBlockCells, 0, stream>>>(sims, table, (const R*)M, (R*)W, Ntot, diag);
+    return cudaGetLastError();
+}
+
+// the first pass for one arithmetic type, by equation of state (ML: learned
+// temperature start, Peng-Robinson only)
+template <typename R, bool WITH_ML>
+cudaError_t zmacro_dispatch_t(int eos, int mlp, const SimDev* sims, const BlockEntry* table, int nblocks,
+                              const void* M, void* W, long long Ntot, unsigned long long* diag, cudaStream_t stream)
+{
+    if (mlp) {
+        if constexpr (WITH_ML) {
+            if (eos == EOS_PR) return zmacro_launch<R, EOS_PR, true>(sims, table, nblocks, M, W, Ntot, diag, stream);
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (eos == EOS_IDEAL) return zmacro_launch<R, EOS_IDEAL, false>(sims, table, nblocks, M, W, Ntot, diag, stream);
+    if (eos == EOS_VDW) return zmacro_launch<R, EOS_VDW, false>(sims, table, nblocks, M, W, Ntot, diag, stream);
+    if (eos == EOS_PR) return zmacro_launch<R, EOS_PR, false>(sims, table, nblocks, M, W, Ntot, diag, stream);
+    return cudaErrorInvalidValue;
 }
 
 template <typename R, typename S, int EK, int TX, int TY>
