@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
     constexpr int n5 = G::n(5), n4 = G::n(4), n3 = G::n(3), n1 = G::n(1), n0 = G::n(0);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SimK<R, EK> s;
+    __shared__ SimDev s_dev;  // raw constants of simulation dev_sim, converted into s when a tile needs them
     __shared__ int cur_sim;
     R* s_rho = reinterpret_cast<R*>(smem_raw);
     R* s_L = s_rho + n5;
@@ -104,14 +105,28 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
     MlpSmem& mlp_s = *reinterpret_cast<MlpSmem*>(s_acc + (D + 2) * n0);  // only with ML
     const int tid = threadIdx.x;
     if (tid == 0) cur_sim = -1;
+    // the constants of simulation 0 are fetched by all threads at once, in
+    // parallel with the first tile entry (other simulations on demand)
+    auto fetch_sim = [&](int sim) {
+        const int* src = reinterpret_cast<const int*>(sims + sim);
+        int* d = reinterpret_cast<int*>(&s_dev);
+        for (int w = tid; w < (int)(sizeof(SimDev) / sizeof(int)); w += kFusedThreads) d[w] = src[w];
+    };
+    int dev_sim = 0;
+    fetch_sim(0);
     __syncthreads();
 
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const TileEntry te = tiles[t];
         if (te.sim != cur_sim) {
             __syncthreads();
+            if (te.sim != dev_sim) {  // block-uniform
+                fetch_sim(te.sim);
+                dev_sim = te.sim;
+                __syncthreads();
+            }
             if (tid == 0) {
-                simc_from<R>(static_cast<SimC<R>&>(s), sims[te.sim]);
+                simc_from<R>(static_cast<SimC<R>&>(s), s_dev);
                 cur_sim = te.sim;
             }
             __syncthreads();
@@ -157,13 +172,29 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
         };
         In3 nxt3 = fetch3(tid);
 
-        // ---- 1. rho on T+5 (ghosts beyond walls: the image's value); zero the accumulators
-        for (int k = tid; k < n5; k += kFusedThreads) {
-            const int lx = k % G::w(5), ly = (k / G::w(5)) % G::h(5), lz = k / (G::w(5) * G::h(5));
-            bool fl;
-            const int x = wrapc(te.x0 - 5 + lx, nx), y = wrapc(te.y0 - 5 + ly, ny);
-            const int z = D == 3 ? zcoord(s, te.z0 - 5 + lz, fl) : 0;
-            s_rho[k] = Mrho[(unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z)];
+        // ---- 1. rho on T+5 (ghosts beyond walls: the image's value); zero the accumulators.
+        // All of a thread's loads are issued before the first store, so the
+        // phase waits for one memory round trip rather than one per element.
+        {
+            constexpr int nb5 = (n5 + kFusedThreads - 1) / kFusedThreads;
+            R rv[nb5];
+#pragma unroll
+            for (int it = 0; it < nb5; ++it) {
+                const int k = it * kFusedThreads + tid;
+                rv[it] = R(0);
+                if (k < n5) {
+                    const int lx = k % G::w(5), ly = (k / G::w(5)) % G::h(5), lz = k / (G::w(5) * G::h(5));
+                    bool fl;
+                    const int x = wrapc(te.x0 - 5 + lx, nx), y = wrapc(te.y0 - 5 + ly, ny);
+                    const int z = D == 3 ? zcoord(s, te.z0 - 5 + lz, fl) : 0;
+                    rv[it] = Mrho[(unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z)];
+                }
+            }
+#pragma unroll
+            for (int it = 0; it < nb5; ++it) {
+                const int k = it * kFusedThreads + tid;
+                if (k < n5) s_rho[k] = rv[it];
+            }
         }
         for (int k = tid; k < (D + 2) * n0; k += kFusedThreads) s_acc[k] = R(0);
         __syncthreads();
@@ -256,7 +287,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
 
         // ---- 3. macroscopic state on T+3
         constexpr int nb3 = (n3 + kFusedThreads - 1) / kFusedThreads;
-#pragma unroll 1
+#pragma unroll 2
         for (int it = 0; it < nb3; ++it) {
             const int k = it * kFusedThreads + tid;
             const In3 in3 = nxt3;
