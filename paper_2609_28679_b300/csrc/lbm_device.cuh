@@ -4,6 +4,8 @@
 // Shared by the split (three-pass) and fused (one-pass) step kernels.
 #pragma once
 
+#include <cstddef>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -69,6 +71,27 @@ template <typename R> __device__ inline void simc_from(SimC<R>& d, const SimDev&
     d.q = (R)s.q; d.inv_cv = (R)s.inv_cv; d.inv_Tc = (R)s.inv_Tc; d.lam_c = (R)s.lam_c; d.athe_c = (R)s.athe_c;
     for (int i = 0; i < 27; ++i) { d.fref[i] = (R)s.fref[i]; d.gref[i] = (R)s.gref[i]; }
     d.mlp = s.mlp;
+}
+
+// The same conversion shared out over a block's threads (one field each):
+// the nineteen float64 scalars from R to athe_c are consecutive members in both
+// structures, as are the two offset tables.  The caller synchronises after.
+template <typename R> __device__ inline void simc_from_coop(SimC<R>& d, const SimDev& s, int tid)
+{
+    static_assert(offsetof(SimDev, athe_c) - offsetof(SimDev, R) == 18 * sizeof(double), "SimDev scalar layout");
+    static_assert(offsetof(SimC<R>, athe_c) - offsetof(SimC<R>, R) == 18 * sizeof(R), "SimC scalar layout");
+    static_assert(offsetof(SimDev, gref) - offsetof(SimDev, fref) == 27 * sizeof(float), "SimDev table layout");
+    static_assert(offsetof(SimC<R>, gref) - offsetof(SimC<R>, fref) == 27 * sizeof(R), "SimC table layout");
+    if (tid < 19) {
+        (&d.R)[tid] = (R)(&s.R)[tid];
+    } else if (tid < 73) {
+        (&d.fref[0])[tid - 19] = (R)(&s.fref[0])[tid - 19];
+    } else if (tid == 73) {
+        d.nx = s.nx; d.ny = s.ny; d.nz = s.nz; d.zwalls = s.zwalls;
+        d.N = s.N; d.pop_off = s.pop_off; d.cell_off = s.cell_off;
+        d.eos = s.eos; d.phi_central = s.phi_central; d.t_solver = s.t_solver; d.zlo = s.zlo; d.zhi = s.zhi;
+        d.mlp = s.mlp;
+    }
 }
 
 // ---------------------------------------------------------------------------

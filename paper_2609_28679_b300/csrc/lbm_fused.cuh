@@ -29,7 +29,6 @@ struct TileEntry {
     int sim, x0, y0, z0;
 };
 
-constexpr int kFusedThreads = 256;
 
 template <int D, int TX, int TY, int TZ> struct TileShape {
     static constexpr int HZ = D == 3 ? 1 : 0;
@@ -73,6 +72,14 @@ template <typename R, int EK> struct SimK : SimC<R> {
     static constexpr int eos = EK;
 };
 
+// Threads of the fused kernel (one place to change it per tile shape; 288
+// threads for 64x14, which would spare the collide phase its nearly empty
+// fifth pass, measured slower: the register cap of 96 made the kernel spill).
+template <int D, int TX, int TY, int TZ> constexpr int fused_threads()
+{
+    return 256;
+}
+
 // CTAs per SM that the tile's shared memory leaves room for (float32 2-D
 // tiles; at most 3): the register budget the compiler may use follows from it.
 template <int D, typename R, int TX, int TY, int TZ> constexpr int fused_min_blocks()
@@ -84,12 +91,13 @@ template <int D, typename R, int TX, int TY, int TZ> constexpr int fused_min_blo
 }
 
 template <int D, typename R, typename S, int EK, bool ML, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY, TZ>()))
+__global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_blocks<D, R, TX, TY, TZ>()))
     k_fused(const SimDev* __restrict__ sims, const TileEntry* __restrict__ tiles, int ntiles,
             const S* __restrict__ src, S* __restrict__ dst, const R* __restrict__ Min, R* __restrict__ Mout,
             long long Ntot, unsigned long long* diag)
 {
     using G = TileShape<D, TX, TY, TZ>;
+    constexpr int NT = fused_threads<D, TX, TY, TZ>();
     constexpr int Q = Lat<D>::Q;
     constexpr int HZ = G::HZ;
     constexpr int n5 = G::n(5), n4 = G::n(4), n3 = G::n(3), n1 = G::n(1), n0 = G::n(0);
@@ -110,7 +118,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
     auto fetch_sim = [&](int sim) {
         const int* src = reinterpret_cast<const int*>(sims + sim);
         int* d = reinterpret_cast<int*>(&s_dev);
-        for (int w = tid; w < (int)(sizeof(SimDev) / sizeof(int)); w += kFusedThreads) d[w] = src[w];
+        for (int w = tid; w < (int)(sizeof(SimDev) / sizeof(int)); w += NT) d[w] = src[w];
     };
     int dev_sim = 0;
     fetch_sim(0);
@@ -125,10 +133,8 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
                 dev_sim = te.sim;
                 __syncthreads();
             }
-            if (tid == 0) {
-                simc_from<R>(static_cast<SimC<R>&>(s), s_dev);
-                cur_sim = te.sim;
-            }
+            simc_from_coop<R>(static_cast<SimC<R>&>(s), s_dev, tid);
+            if (tid == 0) cur_sim = te.sim;
             __syncthreads();
             if (ML && s.mlp != nullptr) {
                 mlp_load(mlp_s, s.mlp);
@@ -176,11 +182,11 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
         // All of a thread's loads are issued before the first store, so the
         // phase waits for one memory round trip rather than one per element.
         {
-            constexpr int nb5 = (n5 + kFusedThreads - 1) / kFusedThreads;
+            constexpr int nb5 = (n5 + NT - 1) / NT;
             R rv[nb5];
 #pragma unroll
             for (int it = 0; it < nb5; ++it) {
-                const int k = it * kFusedThreads + tid;
+                const int k = it * NT + tid;
                 rv[it] = R(0);
                 if (k < n5) {
                     const int lx = k % G::w(5), ly = (k / G::w(5)) % G::h(5), lz = k / (G::w(5) * G::h(5));
@@ -192,15 +198,15 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
             }
 #pragma unroll
             for (int it = 0; it < nb5; ++it) {
-                const int k = it * kFusedThreads + tid;
+                const int k = it * NT + tid;
                 if (k < n5) s_rho[k] = rv[it];
             }
         }
-        for (int k = tid; k < (D + 2) * n0; k += kFusedThreads) s_acc[k] = R(0);
+        for (int k = tid; k < (D + 2) * n0; k += NT) s_acc[k] = R(0);
         __syncthreads();
 
         // ---- 2. lap rho on T+4 (non-ghost cells; ghosts copied from images after)
-        for (int k = tid; k < n4; k += kFusedThreads) {
+        for (int k = tid; k < n4; k += NT) {
             const int lx = k % G::w(4), ly = (k / G::w(4)) % G::h(4), lz = k / (G::w(4) * G::h(4));
             const int z = te.z0 - 4 * HZ + lz;
             if (walls && (z < 0 || z >= nz)) continue;
@@ -212,7 +218,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
         }
         __syncthreads();
         if (walls && (te.z0 < 4 || te.z0 + G::tz + 4 > nz)) {
-            for (int k = tid; k < n4; k += kFusedThreads) {
+            for (int k = tid; k < n4; k += NT) {
                 const int lx = k % G::w(4), ly = (k / G::w(4)) % G::h(4), lz = k / (G::w(4) * G::h(4));
                 const int z = te.z0 - 4 * HZ + lz;
                 if (z >= 0 && z < nz) continue;
@@ -286,12 +292,12 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
         if (kAhead) fetch4(tid, fn, gn);  // first cell of phase 4, in flight during phase 3
 
         // ---- 3. macroscopic state on T+3
-        constexpr int nb3 = (n3 + kFusedThreads - 1) / kFusedThreads;
+        constexpr int nb3 = (n3 + NT - 1) / NT;
 #pragma unroll 2
         for (int it = 0; it < nb3; ++it) {
-            const int k = it * kFusedThreads + tid;
+            const int k = it * NT + tid;
             const In3 in3 = nxt3;
-            if (it + 1 < nb3) nxt3 = fetch3(k + kFusedThreads);
+            if (it + 1 < nb3) nxt3 = fetch3(k + NT);
             unsigned flags = 0;
             bool owned = false, act = false;
             int lx = 0, ly = 0, lz = 0, zr = 0, z = 0;
@@ -352,7 +358,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
         }
         __syncthreads();
         if (walls && (te.z0 < 3 || te.z0 + G::tz + 3 > nz)) {
-            for (int k = tid; k < n3; k += kFusedThreads) {
+            for (int k = tid; k < n3; k += NT) {
                 const int lx = k % G::w(3), ly = (k / G::w(3)) % G::h(3), lz = k / (G::w(3) * G::h(3));
                 const int z = te.z0 - 3 * HZ + lz;
                 if (z >= 0 && z < nz) continue;
@@ -371,7 +377,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
         }
 
         // ---- 4. collide T+1, store T, accumulate the next moments of T
-        for (int k = tid; k < n1; k += kFusedThreads) {
+        for (int k = tid; k < n1; k += NT) {
             R f[Q], gp[Q];
             if (kAhead) {
 #pragma unroll
@@ -379,7 +385,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
                     f[i] = fn[i];
                     gp[i] = gn[i];
                 }
-                fetch4(k + kFusedThreads, fn, gn);
+                fetch4(k + NT, fn, gn);
             }
             const int lx = k % G::w(1), ly = (k / G::w(1)) % G::h(1), lz = k / (G::w(1) * G::h(1));
             const int zr = te.z0 - HZ + lz;
@@ -469,7 +475,7 @@ __global__ void __launch_bounds__(kFusedThreads, (fused_min_blocks<D, R, TX, TY,
         __syncthreads();
 
         // ---- 5. next-step moments and Newton guess of T
-        for (int d = tid; d < n0; d += kFusedThreads) {
+        for (int d = tid; d < n0; d += NT) {
             const int tx = d % TX, ty = (d / TX) % TY, tz = d / (TX * TY);
             const int x = te.x0 + tx, y = te.y0 + ty, z = te.z0 + tz;
             if (x >= nx || y >= ny || z >= nz) continue;
@@ -547,7 +553,7 @@ cudaError_t fused_launch_shape(const SimDev* sims, const TileEntry* tiles, int n
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, nsm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, R, S, EK, ML, TX, TY, TZ>, kFusedThreads,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, R, S, EK, ML, TX, TY, TZ>, fused_threads<D, TX, TY, TZ>(),
                                                           smem);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
@@ -556,7 +562,7 @@ cudaError_t fused_launch_shape(const SimDev* sims, const TileEntry* tiles, int n
         grid_cap = per_sm * nsm;
     }
     const int grid = ntiles < grid_cap ? ntiles : grid_cap;
-    k_fused<D, R, S, EK, ML, TX, TY, TZ><<<grid, kFusedThreads, smem, stream>>>(
+    k_fused<D, R, S, EK, ML, TX, TY, TZ><<<grid, fused_threads<D, TX, TY, TZ>(), smem, stream>>>(
         sims, tiles, ntiles, (const S*)src, (S*)dst, (const R*)Min, (R*)Mout, Ntot, diag);
     return cudaGetLastError();
 }

@@ -260,9 +260,11 @@ __global__ void __launch_bounds__(kBlockCells) k_zmacro(const SimDev* __restrict
                                                         R* __restrict__ W, long long Ntot, unsigned long long* diag)
 {
     __shared__ SimK<R, EK> s;
+    __shared__ SimDev s_dev;
     __shared__ std::conditional_t<ML, MlpSmem, int> mlp_s;
     const BlockEntry be = table[blockIdx.x];
-    if (threadIdx.x == 0) simc_from<R>(static_cast<SimC<R>&>(s), sims[be.sim]);
+    load_sim(s_dev, sims, be.sim);
+    simc_from_coop<R>(static_cast<SimC<R>&>(s), s_dev, threadIdx.x);
     __syncthreads();
     if constexpr (ML) {
         if (s.mlp != nullptr) {
