@@ -95,7 +95,7 @@ int cuda_fail(lbm_ctx* h, cudaError_t e, const char* where)
 
 void* dev_alloc(lbm_ctx* h, size_t n) { return lbm_glue_alloc(n, (void*)h->stream); }
 
-cudaError_t fused_dispatch(int storage, int dim, int eos, int mlp, int tx, int ty, int tz, const SimDev* sims,
+cudaError_t fused_dispatch(int storage, int dim, int eos, int mlp, int pc, int tx, int ty, int tz, const SimDev* sims,
                            const TileEntry* tiles, int ntiles, const void* src, void* dst, const void* Min, void* Mout,
                            long long Ntot, unsigned long long* diag, cudaStream_t stream);
 bool fused_shape(int storage, int dim, int tx, int ty, int tz);
@@ -155,7 +155,8 @@ template <int D, typename R, typename S> struct Impl {
             int rc = fused_prepare(h);
             if (rc) return rc;
         }
-        cudaError_t e = fused_dispatch(h->storage, D, h->sims[0].eos, uses_mlp(h), h->tx, h->ty, h->tz, h->d_sims,
+        cudaError_t e = fused_dispatch(h->storage, D, h->sims[0].eos, uses_mlp(h), all_central(h), h->tx, h->ty, h->tz,
+                                       h->d_sims,
                                        h->d_tiles,
                                        (int)h->tiles.size(), h->pop[h->cur], h->pop[h->cur ^ 1], mbuf(h, h->cur),
                                        mbuf(h, h->cur ^ 1), h->Ntot, h->d_diag, h->stream);
@@ -238,6 +239,14 @@ template <int D, typename R, typename S> struct Impl {
         return LBM_OK;
     }
 
+    // every simulation takes the central derivative in Phi (narrower halos)
+    static int all_central(lbm_ctx* h)
+    {
+        for (const SimDev& d : h->sims)
+            if (!d.phi_central) return 0;
+        return 1;
+    }
+
     static int uses_mlp(lbm_ctx* h)
     {
         for (const SimDev& d : h->sims)
@@ -256,15 +265,15 @@ template <int D, typename R, typename S> struct Impl {
     static Ops ops() { return Ops{init, step, macro, export_moments, export_pops, invariants, fused_ok}; }
 };
 
-cudaError_t fused_dispatch(int storage, int dim, int eos, int mlp, int tx, int ty, int tz, const SimDev* sims,
+cudaError_t fused_dispatch(int storage, int dim, int eos, int mlp, int pc, int tx, int ty, int tz, const SimDev* sims,
                            const TileEntry* tiles, int ntiles, const void* src, void* dst, const void* Min, void* Mout,
                            long long Ntot, unsigned long long* diag, cudaStream_t stream)
 {
     switch (storage) {
-    case LBM_F64: return fused_dispatch_f64(dim, eos, mlp, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
-    case LBM_F32: return fused_dispatch_f32(dim, eos, mlp, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
-    case LBM_BF16: return fused_dispatch_bf16(dim, eos, mlp, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
-    case LBM_F16: return fused_dispatch_f16(dim, eos, mlp, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_F64: return fused_dispatch_f64(dim, eos, mlp, pc, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_F32: return fused_dispatch_f32(dim, eos, mlp, pc, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_BF16: return fused_dispatch_bf16(dim, eos, mlp, pc, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_F16: return fused_dispatch_f16(dim, eos, mlp, pc, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
     }
     return cudaErrorInvalidValue;
 }

@@ -30,7 +30,10 @@ struct TileEntry {
 };
 
 
-template <int D, int TX, int TY, int TZ> struct TileShape {
+// RB: radius of the rho halo (5; 4 when Phi takes the central derivative and
+// the macroscopic state is needed on T+2 only); lap rho on T+(RB-1) and the
+// macroscopic state on T+(RB-2).
+template <int D, int TX, int TY, int TZ, int RB = 5> struct TileShape {
     static constexpr int HZ = D == 3 ? 1 : 0;
     static constexpr int tz = D == 3 ? TZ : 1;
     __host__ __device__ static constexpr int w(int r) { return TX + 2 * r; }
@@ -43,7 +46,7 @@ template <int D, int TX, int TY, int TZ> struct TileShape {
     static constexpr int LP = 0, LTH = 1, LCV = 2, LGAM = 3, LATHE = 4, LE = 5;
     __host__ __device__ static constexpr size_t elems()
     {
-        return (size_t)n(5) + n(4) + (size_t)NS * n(3) + (size_t)NL * n(1) + (size_t)(D + 2) * n(0);
+        return (size_t)n(RB) + n(RB - 1) + (size_t)NS * n(RB - 2) + (size_t)NL * n(1) + (size_t)(D + 2) * n(0);
     }
 };
 
@@ -82,25 +85,28 @@ template <int D, int TX, int TY, int TZ> constexpr int fused_threads()
 
 // CTAs per SM that the tile's shared memory leaves room for (float32 2-D
 // tiles; at most 3): the register budget the compiler may use follows from it.
-template <int D, typename R, int TX, int TY, int TZ> constexpr int fused_min_blocks()
+template <int D, typename R, int TX, int TY, int TZ, bool PC> constexpr int fused_min_blocks()
 {
     if (!(D == 2 && sizeof(R) == 4)) return 1;
-    constexpr size_t bytes = TileShape<D, TX, TY, TZ>::elems() * sizeof(R) + 1024;
+    constexpr size_t bytes = TileShape<D, TX, TY, TZ, PC ? 4 : 5>::elems() * sizeof(R) + 1024;
     constexpr int n = (int)((size_t)232448 / bytes);
     return n < 1 ? 1 : (n > 3 ? 3 : n);
 }
 
-template <int D, typename R, typename S, int EK, bool ML, int TX, int TY, int TZ>
-__global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_blocks<D, R, TX, TY, TZ>()))
+// PC: Phi from the central derivative of X for every simulation of the
+// launch, so the halos shrink by one cell (see TileShape)
+template <int D, typename R, typename S, int EK, bool ML, int TX, int TY, int TZ, bool PC>
+__global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_blocks<D, R, TX, TY, TZ, PC>()))
     k_fused(const SimDev* __restrict__ sims, const TileEntry* __restrict__ tiles, int ntiles,
             const S* __restrict__ src, S* __restrict__ dst, const R* __restrict__ Min, R* __restrict__ Mout,
             long long Ntot, unsigned long long* diag)
 {
-    using G = TileShape<D, TX, TY, TZ>;
+    constexpr int RB = PC ? 4 : 5, RLP = RB - 1, RM = RB - 2;  // halo radii of rho, lap rho, the macroscopic state
+    using G = TileShape<D, TX, TY, TZ, RB>;
     constexpr int NT = fused_threads<D, TX, TY, TZ>();
     constexpr int Q = Lat<D>::Q;
     constexpr int HZ = G::HZ;
-    constexpr int n5 = G::n(5), n4 = G::n(4), n3 = G::n(3), n1 = G::n(1), n0 = G::n(0);
+    constexpr int n5 = G::n(RB), n4 = G::n(RLP), n3 = G::n(RM), n1 = G::n(1), n0 = G::n(0);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SimK<R, EK> s;
     __shared__ SimDev s_dev;  // raw constants of simulation dev_sim, converted into s when a tile needs them
@@ -162,10 +168,10 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
             In3 v;
             v.j[0] = v.j[1] = v.j[2] = v.Gm = v.T = R(0);
             if (k < n3) {
-                const int lx = k % G::w(3), ly = (k / G::w(3)) % G::h(3), lz = k / (G::w(3) * G::h(3));
-                const int zr = te.z0 - 3 * HZ + lz;
+                const int lx = k % G::w(RM), ly = (k / G::w(RM)) % G::h(RM), lz = k / (G::w(RM) * G::h(RM));
+                const int zr = te.z0 - RM * HZ + lz;
                 if (!(walls && (zr < 0 || zr >= nz))) {
-                    const int x = wrapc(te.x0 - 3 + lx, nx), y = wrapc(te.y0 - 3 + ly, ny);
+                    const int x = wrapc(te.x0 - RM + lx, nx), y = wrapc(te.y0 - RM + ly, ny);
                     const int z = D == 3 ? wrapc(zr, nz) : 0;
                     const unsigned gk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
 #pragma unroll
@@ -189,10 +195,10 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
                 const int k = it * NT + tid;
                 rv[it] = R(0);
                 if (k < n5) {
-                    const int lx = k % G::w(5), ly = (k / G::w(5)) % G::h(5), lz = k / (G::w(5) * G::h(5));
+                    const int lx = k % G::w(RB), ly = (k / G::w(RB)) % G::h(RB), lz = k / (G::w(RB) * G::h(RB));
                     bool fl;
-                    const int x = wrapc(te.x0 - 5 + lx, nx), y = wrapc(te.y0 - 5 + ly, ny);
-                    const int z = D == 3 ? zcoord(s, te.z0 - 5 + lz, fl) : 0;
+                    const int x = wrapc(te.x0 - RB + lx, nx), y = wrapc(te.y0 - RB + ly, ny);
+                    const int z = D == 3 ? zcoord(s, te.z0 - RB + lz, fl) : 0;
                     rv[it] = Mrho[(unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z)];
                 }
             }
@@ -207,24 +213,24 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
 
         // ---- 2. lap rho on T+4 (non-ghost cells; ghosts copied from images after)
         for (int k = tid; k < n4; k += NT) {
-            const int lx = k % G::w(4), ly = (k / G::w(4)) % G::h(4), lz = k / (G::w(4) * G::h(4));
-            const int z = te.z0 - 4 * HZ + lz;
+            const int lx = k % G::w(RLP), ly = (k / G::w(RLP)) % G::h(RLP), lz = k / (G::w(RLP) * G::h(RLP));
+            const int z = te.z0 - RLP * HZ + lz;
             if (walls && (z < 0 || z >= nz)) continue;
-            const int c = (lx + 1) + G::w(5) * ((ly + 1) + G::h(5) * (lz + HZ));
-            constexpr int sy = G::w(5), sz = G::w(5) * G::h(5);
+            const int c = (lx + 1) + G::w(RB) * ((ly + 1) + G::h(RB) * (lz + HZ));
+            constexpr int sy = G::w(RB), sz = G::w(RB) * G::h(RB);
             R L = s_rho[c + 1] + s_rho[c - 1] + s_rho[c + sy] + s_rho[c - sy] - R(2 * D) * s_rho[c];
             if (D == 3) L += s_rho[c + sz] + s_rho[c - sz];
             s_L[k] = L;
         }
         __syncthreads();
-        if (walls && (te.z0 < 4 || te.z0 + G::tz + 4 > nz)) {
+        if (walls && (te.z0 < RLP || te.z0 + G::tz + RLP > nz)) {
             for (int k = tid; k < n4; k += NT) {
-                const int lx = k % G::w(4), ly = (k / G::w(4)) % G::h(4), lz = k / (G::w(4) * G::h(4));
-                const int z = te.z0 - 4 * HZ + lz;
+                const int lx = k % G::w(RLP), ly = (k / G::w(RLP)) % G::h(RLP), lz = k / (G::w(RLP) * G::h(RLP));
+                const int z = te.z0 - RLP * HZ + lz;
                 if (z >= 0 && z < nz) continue;
                 bool fl;
-                const int li = mirror_z(z, nz, fl) - (te.z0 - 4 * HZ);
-                s_L[k] = (li >= 0 && li < G::d(4)) ? s_L[lx + G::w(4) * (ly + G::h(4) * li)] : R(0);
+                const int li = mirror_z(z, nz, fl) - (te.z0 - RLP * HZ);
+                s_L[k] = (li >= 0 && li < G::d(RLP)) ? s_L[lx + G::w(RLP) * (ly + G::h(RLP) * li)] : R(0);
             }
             __syncthreads();
         }
@@ -303,16 +309,16 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
             int lx = 0, ly = 0, lz = 0, zr = 0, z = 0;
             R r = R(1), G_ = R(0), Qh = R(0), Tg = R(0), Fv[3] = {0, 0, 0}, j[3] = {0, 0, 0};
             if (k < n3) {
-                lx = k % G::w(3);
-                ly = (k / G::w(3)) % G::h(3);
-                lz = k / (G::w(3) * G::h(3));
-                zr = te.z0 - 3 * HZ + lz;
+                lx = k % G::w(RM);
+                ly = (k / G::w(RM)) % G::h(RM);
+                lz = k / (G::w(RM) * G::h(RM));
+                zr = te.z0 - RM * HZ + lz;
                 act = !(walls && (zr < 0 || zr >= nz));
                 if (act) {
                     z = D == 3 ? wrapc(zr, nz) : 0;
-                    const int c4 = (lx + 1) + G::w(4) * ((ly + 1) + G::h(4) * (lz + HZ));
-                    r = s_rho[(lx + 2) + G::w(5) * ((ly + 2) + G::h(5) * (lz + 2 * HZ))];
-                    constexpr int st4[3] = {1, G::w(4), G::w(4) * G::h(4)};
+                    const int c4 = (lx + 1) + G::w(RLP) * ((ly + 1) + G::h(RLP) * (lz + HZ));
+                    r = s_rho[(lx + 2) + G::w(RB) * ((ly + 2) + G::h(RB) * (lz + 2 * HZ))];
+                    constexpr int st4[3] = {1, G::w(RLP), G::w(RLP) * G::h(RLP)};
 #pragma unroll
                     for (int a = 0; a < D; ++a) {
                         Fv[a] = r * (s.acc[a] + s.kappa * R(0.5) * (s_L[c4 + st4[a]] - s_L[c4 - st4[a]]));
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
                 s_st[G::TT * n3 + k] = m.T;
                 s_st[G::H * n3 + k] = m.h;
                 // local fields for the cells of T+1
-                const int l1x = lx - 2, l1y = ly - 2, l1z = lz - 2 * HZ;
+                const int l1x = lx - (RM - 1), l1y = ly - (RM - 1), l1z = lz - (RM - 1) * HZ;
                 if (l1x >= 0 && l1y >= 0 && l1z >= 0 && l1x < G::w(1) && l1y < G::h(1) && l1z < G::d(1)) {
                     const int k1 = l1x + G::w(1) * (l1y + G::h(1) * l1z);
                     s_lo[G::LP * n1 + k1] = m.P;
@@ -351,21 +357,21 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
                     s_lo[G::LATHE * n1 + k1] = m.athe;
                     s_lo[G::LE * n1 + k1] = m.e;
                 }
-                owned = lx >= 3 && ly >= 3 && lz >= 3 * HZ && lx < 3 + TX && ly < 3 + TY && lz < 3 * HZ + G::tz &&
-                        te.x0 - 3 + lx < nx && te.y0 - 3 + ly < ny && zr < nz;
+                owned = lx >= RM && ly >= RM && lz >= RM * HZ && lx < RM + TX && ly < RM + TY && lz < RM * HZ + G::tz &&
+                        te.x0 - RM + lx < nx && te.y0 - RM + ly < ny && zr < nz;
             }
             if (diag) count_flags(owned ? flags : 0u, diag);
         }
         __syncthreads();
-        if (walls && (te.z0 < 3 || te.z0 + G::tz + 3 > nz)) {
+        if (walls && (te.z0 < RM || te.z0 + G::tz + RM > nz)) {
             for (int k = tid; k < n3; k += NT) {
-                const int lx = k % G::w(3), ly = (k / G::w(3)) % G::h(3), lz = k / (G::w(3) * G::h(3));
-                const int z = te.z0 - 3 * HZ + lz;
+                const int lx = k % G::w(RM), ly = (k / G::w(RM)) % G::h(RM), lz = k / (G::w(RM) * G::h(RM));
+                const int z = te.z0 - RM * HZ + lz;
                 if (z >= 0 && z < nz) continue;
                 bool fl;
-                const int li = mirror_z(z, nz, fl) - (te.z0 - 3 * HZ);
-                if (li < 0 || li >= G::d(3)) continue;  // image outside the tile's region: never read
-                const int ki = lx + G::w(3) * (ly + G::h(3) * li);
+                const int li = mirror_z(z, nz, fl) - (te.z0 - RM * HZ);
+                if (li < 0 || li >= G::d(RM)) continue;  // image outside the tile's region: never read
+                const int ki = lx + G::w(RM) * (ly + G::h(RM) * li);
 #pragma unroll
                 for (int f = 0; f < G::NS; ++f) {
                     const R v = s_st[f * n3 + ki];
@@ -392,12 +398,12 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
             if (walls && (zr < 0 || zr >= nz)) continue;
             const int x = wrapc(te.x0 - 1 + lx, nx), y = wrapc(te.y0 - 1 + ly, ny);
             const int z = D == 3 ? wrapc(zr, nz) : 0;
-            const int c3 = (lx + 2) + G::w(3) * ((ly + 2) + G::h(3) * (lz + 2 * HZ));
-            const int c4 = (lx + 3) + G::w(4) * ((ly + 3) + G::h(4) * (lz + 3 * HZ));
-            constexpr int st3[3] = {1, G::w(3), G::w(3) * G::h(3)};
-            constexpr int st4[3] = {1, G::w(4), G::w(4) * G::h(4)};
+            const int c3 = (lx + RM - 1) + G::w(RM) * ((ly + RM - 1) + G::h(RM) * (lz + (RM - 1) * HZ));
+            const int c4 = (lx + RLP - 1) + G::w(RLP) * ((ly + RLP - 1) + G::h(RLP) * (lz + (RLP - 1) * HZ));
+            constexpr int st3[3] = {1, G::w(RM), G::w(RM) * G::h(RM)};
+            constexpr int st4[3] = {1, G::w(RLP), G::w(RLP) * G::h(RLP)};
             Macro<R> m;
-            m.rho = s_rho[(lx + 4) + G::w(5) * ((ly + 4) + G::h(5) * (lz + 4 * HZ))];
+            m.rho = s_rho[(lx + RB - 1) + G::w(RB) * ((ly + RB - 1) + G::h(RB) * (lz + (RB - 1) * HZ))];
             m.ir = R(1) / m.rho;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -425,7 +431,7 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
                 gh[a] = R(0.5) * (s_st[G::H * n3 + c3 + sa] - s_st[G::H * n3 + c3 - sa]);
                 gT[a] = R(0.5) * (s_st[G::TT * n3 + c3 + sa] - s_st[G::TT * n3 + c3 - sa]);
                 R dX;
-                if (s.phi_central) {
+                if (PC || s.phi_central) {
                     dX = R(0.5) * (Xa[c3 + sa] - Xa[c3 - sa]);
                 } else if (m.u[a] >= R(0)) {
                     dX = R(0.5) * (R(3) * Xa[c3] - R(4) * Xa[c3 - sa] + Xa[c3 - 2 * sa]);
@@ -485,7 +491,7 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
 #pragma unroll
             for (int a = 0; a < 3; ++a) Mo[(M_J + a) * Ntot + kk] = a < D ? s_acc[(1 + a) * n0 + d] : R(0);
             Mo[M_G * Ntot + kk] = s_acc[(1 + D) * n0 + d];
-            Mo[M_T * Ntot + kk] = s_st[G::TT * n3 + (tx + 3) + G::w(3) * ((ty + 3) + G::h(3) * (tz + 3 * HZ))];
+            Mo[M_T * Ntot + kk] = s_st[G::TT * n3 + (tx + RM) + G::w(RM) * ((ty + RM) + G::h(RM) * (tz + RM * HZ))];
         }
         __syncthreads();
     }
@@ -535,26 +541,25 @@ void fused_moments_launch(const SimDev* sims, const BlockEntry* table, int nbloc
 // ---------------------------------------------------------------------------
 // Launch of one instantiated shape (persistent grid: resident CTAs x SMs).
 // ---------------------------------------------------------------------------
-template <int D, typename R, int TX, int TY, int TZ> constexpr size_t fused_smem()
+template <int D, typename R, int TX, int TY, int TZ, bool PC> constexpr size_t fused_smem()
 {
-    return TileShape<D, TX, TY, TZ>::elems() * sizeof(R);
+    return TileShape<D, TX, TY, TZ, PC ? 4 : 5>::elems() * sizeof(R);
 }
 
-template <int D, typename R, typename S, int EK, bool ML, int TX, int TY, int TZ>
-cudaError_t fused_launch_shape(const SimDev* sims, const TileEntry* tiles, int ntiles, const void* src, void* dst,
-                               const void* Min, void* Mout, long long Ntot, unsigned long long* diag,
-                               cudaStream_t stream)
+template <int D, typename R, typename S, int EK, bool ML, int TX, int TY, int TZ, bool PC>
+cudaError_t fused_launch_pc(const SimDev* sims, const TileEntry* tiles, int ntiles, const void* src, void* dst,
+                            const void* Min, void* Mout, long long Ntot, unsigned long long* diag, cudaStream_t stream)
 {
-    constexpr size_t smem = fused_smem<D, R, TX, TY, TZ>() + (ML ? sizeof(MlpSmem) : 0);
+    constexpr size_t smem = fused_smem<D, R, TX, TY, TZ, PC>() + (ML ? sizeof(MlpSmem) : 0);
+    constexpr int nt = fused_threads<D, TX, TY, TZ>();
     static_assert(smem <= 227u * 1024u, "tile does not fit in shared memory");
     static int grid_cap = 0;
     if (grid_cap == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<D, R, S, EK, ML, TX, TY, TZ>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<D, R, S, EK, ML, TX, TY, TZ, PC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, nsm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, R, S, EK, ML, TX, TY, TZ>, fused_threads<D, TX, TY, TZ>(),
-                                                          smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, R, S, EK, ML, TX, TY, TZ, PC>, nt, smem);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -562,9 +567,25 @@ cudaError_t fused_launch_shape(const SimDev* sims, const TileEntry* tiles, int n
         grid_cap = per_sm * nsm;
     }
     const int grid = ntiles < grid_cap ? ntiles : grid_cap;
-    k_fused<D, R, S, EK, ML, TX, TY, TZ><<<grid, fused_threads<D, TX, TY, TZ>(), smem, stream>>>(
-        sims, tiles, ntiles, (const S*)src, (S*)dst, (const R*)Min, (R*)Mout, Ntot, diag);
+    k_fused<D, R, S, EK, ML, TX, TY, TZ, PC><<<grid, nt, smem, stream>>>(sims, tiles, ntiles, (const S*)src, (S*)dst,
+                                                                        (const R*)Min, (R*)Mout, Ntot, diag);
     return cudaGetLastError();
+}
+
+// pc: every simulation of the launch takes the central Phi (2-D tiles then
+// use the narrower halos)
+template <int D, typename R, typename S, int EK, bool ML, int TX, int TY, int TZ>
+cudaError_t fused_launch_shape(int pc, const SimDev* sims, const TileEntry* tiles, int ntiles, const void* src,
+                               void* dst, const void* Min, void* Mout, long long Ntot, unsigned long long* diag,
+                               cudaStream_t stream)
+{
+    if constexpr (D == 2) {
+        if (pc)
+            return fused_launch_pc<D, R, S, EK, ML, TX, TY, TZ, true>(sims, tiles, ntiles, src, dst, Min, Mout, Ntot,
+                                                                     diag, stream);
+    }
+    return fused_launch_pc<D, R, S, EK, ML, TX, TY, TZ, false>(sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag,
+                                                              stream);
 }
 
 }  // namespace lbm

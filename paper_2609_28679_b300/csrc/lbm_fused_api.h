@@ -13,7 +13,7 @@ struct TileEntry;
 struct BlockEntry;
 
 #define LBM_FUSED_DECL(NAME)                                                                                     \
-    cudaError_t fused_dispatch_##NAME(int dim, int eos, int mlp, int tx, int ty, int tz, const SimDev* sims,              \
+    cudaError_t fused_dispatch_##NAME(int dim, int eos, int mlp, int pc, int tx, int ty, int tz, const SimDev* sims,              \
                                       const TileEntry* tiles, int ntiles, const void* src, void* dst,            \
                                       const void* Min, void* Mout, long long Ntot, unsigned long long* diag,     \
                                       cudaStream_t stream);                                                      \

@@ -12,12 +12,12 @@ namespace lbm {
 namespace {
 
 template <int D, int EK, bool ML>
-cudaError_t go(int tx, int ty, int tz, const SimDev* sims, const TileEntry* tiles, int ntiles, const void* src,
+cudaError_t go(int pc, int tx, int ty, int tz, const SimDev* sims, const TileEntry* tiles, int ntiles, const void* src,
                void* dst, const void* Min, void* Mout, long long Ntot, unsigned long long* diag, cudaStream_t stream)
 {
 #define CASE(A, B, C)                                                                                           \
     if (tx == A && ty == B && tz == C)                                                                          \
-        return fused_launch_shape<D, float, __nv_bfloat16, EK, ML, A, B, C>(sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag,  \
+        return fused_launch_shape<D, float, __nv_bfloat16, EK, ML, A, B, C>(pc, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag,  \
                                                          stream);
     if constexpr (D == 2) {
         TILES_2D(CASE)
@@ -30,11 +30,11 @@ cudaError_t go(int tx, int ty, int tz, const SimDev* sims, const TileEntry* tile
 
 }  // namespace
 
-cudaError_t fused_dispatch_bf16(int dim, int eos, int mlp, int tx, int ty, int tz, const SimDev* sims, const TileEntry* tiles,
+cudaError_t fused_dispatch_bf16(int dim, int eos, int mlp, int pc, int tx, int ty, int tz, const SimDev* sims, const TileEntry* tiles,
                                int ntiles, const void* src, void* dst, const void* Min, void* Mout, long long Ntot,
                                unsigned long long* diag, cudaStream_t stream)
 {
-#define ARGS tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream
+#define ARGS pc, tx, ty, tz, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream
     if (mlp) return cudaErrorInvalidValue;  // the learned start is built for float32 storage
     if (dim == 2) {
         if (eos == EOS_IDEAL) return go<2, EOS_IDEAL, false>(ARGS);
