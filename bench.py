@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS (million lattice-cell updates per second, f and g populations)"
 UNIT = "MLUPS"
 FALLBACK_HBM_GBS = 6400.0
+NOMINAL_HBM_GBS = 8000.0  # B300 HBM3e, nominal (context for the measured fraction)
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -62,19 +63,19 @@ def _kernel_source_hash() -> str:
 
 
 def _ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    """DRAM bytes and ncu duration (us) per launch from the committed ncu
+    summary, if it was taken on the current kernel source (else None, None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
-        return None
+        return None, None
     src = _kernel_source_hash()
     with open(path) as fh:
         for line in fh:
             parts = line.split()
             if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload \
                     and parts[2] == src:
-                return float(parts[3])
-    return None
+                return float(parts[3]), (float(parts[4]) if len(parts) >= 5 else None)
+    return None, None
 
 
 class ClockSampler:
@@ -150,6 +151,23 @@ def _oracle_mlups(case, steps_budget_s: float, threads: int | None = None):
     o.step(n)
     dt = time.perf_counter() - t0
     return case.ncell * n / dt / 1e6, n, dt, orc.get_threads()
+
+
+def _oracle_threads(n: int) -> None:
+    from oracle import oracle as orc
+
+    orc.set_threads(n)
+
+
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def max_over_ranks(x: float) -> float:
@@ -380,13 +398,18 @@ def run_ours(args):
     peak, peak_src = _peaks()
     kname = "k_fused" if variant == lbm.LBM_KERNEL_FUSED else "k_collide"
     value = aggregate_mlups(case.ncell, args.steps, world, total_ms)
+    traffic, ncu_us = _ncu_traffic(kname, "vdw_spinodal_512_f32")
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cb_case = wl.vdw_spinodal(512, storage="f64")
             cv, n, dt, cores = _oracle_mlups(cb_case, 15.0)
+            cv1, n1, dt1, _ = _oracle_mlups(cb_case, 8.0, threads=1)
+            _oracle_threads(cores)
             cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"{n} full time steps of the same 512x512 workload ({dt:.1f} s, FP64 C oracle, OpenMP)"}
+                   "sample": f"{n} full time steps of the same 512x512 workload ({dt:.1f} s, FP64 C oracle, OpenMP)",
+                   "single_core": {"value": cv1, "unit": UNIT, "sample": f"{n1} full time steps ({dt1:.1f} s)"},
+                   "cpu_model": _cpu_model(), "nproc": os.cpu_count()}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak",
@@ -397,8 +420,10 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MiB write outside the event pairs)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": _ncu_traffic(kname, "vdw_spinodal_512_f32"),
+                         "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,
+                         "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
+                         "ncu_dram_gbs": (traffic / (ncu_us * 1e-6) / 1e9) if traffic and ncu_us else None,
                          "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": avg_ms},
             "e2e": {"value": case.ncell * e2e_steps / e2e_s / 1e6, "unit": UNIT,
                     "h2d_bytes_per_step": int(rho_h.nbytes + u_h.nbytes + T_h.nbytes),

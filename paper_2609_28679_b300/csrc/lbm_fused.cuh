@@ -459,22 +459,44 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
             }
             // next-step moments: f'_i(x) becomes f_i(x + c_i), or f_opp(i)(x) across a z wall.
             // Branch-free: a destination counts if it lies in the owned part of T.
-            const bool zlo_wall = walls && z == 0, zhi_wall = walls && z == nz - 1;
+            if constexpr (D == 2) {
+                // per axis, whether the neighbour at c = 0, +1, -1 is owned
+                bool okx[3], oky[3];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int ci0 = cc(i, 0), ci1 = cc(i, 1), ci2 = D == 3 ? cc(i, 2) : 0;
-                const bool bounce = (ci2 < 0 && zlo_wall) || (ci2 > 0 && zhi_wall);
-                const int dx = bounce ? tx : tx + ci0, dy = bounce ? ty : ty + ci1, dz = bounce ? tz : tz + ci2;
-                const bool ok = (unsigned)dx < vx && (unsigned)dy < vy && (D == 2 || (unsigned)dz < vz);
-                if (ok) {
-                    const int dd = dx + TX * (dy + TY * dz);
-                    atomicAdd(&s_acc[dd], f[i]);
+                for (int d = 0; d < 3; ++d) {
+                    okx[d] = (unsigned)(tx + cval(d)) < vx;
+                    oky[d] = (unsigned)(ty + cval(d)) < vy;
+                }
+                const int dbase = tx + TX * ty;
 #pragma unroll
-                    for (int a = 0; a < D; ++a) {
-                        const int ca = cc(i, a);
-                        if (ca != 0) atomicAdd(&s_acc[(1 + a) * n0 + dd], (ca > 0) != bounce ? f[i] : -f[i]);
+                for (int i = 0; i < Q; ++i) {
+                    const int ci0 = cc(i, 0), ci1 = cc(i, 1);
+                    if (okx[dig(i, 0)] && oky[dig(i, 1)]) {
+                        const int dd = dbase + ci0 + TX * ci1;
+                        atomicAdd(&s_acc[dd], f[i]);
+                        if (ci0 != 0) atomicAdd(&s_acc[n0 + dd], ci0 > 0 ? f[i] : -f[i]);
+                        if (ci1 != 0) atomicAdd(&s_acc[2 * n0 + dd], ci1 > 0 ? f[i] : -f[i]);
+                        atomicAdd(&s_acc[3 * n0 + dd], gp[i]);
                     }
-                    atomicAdd(&s_acc[(1 + D) * n0 + dd], gp[i]);
+                }
+            } else {
+                const bool zlo_wall = walls && z == 0, zhi_wall = walls && z == nz - 1;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int ci0 = cc(i, 0), ci1 = cc(i, 1), ci2 = cc(i, 2);
+                    const bool bounce = (ci2 < 0 && zlo_wall) || (ci2 > 0 && zhi_wall);
+                    const int dx = bounce ? tx : tx + ci0, dy = bounce ? ty : ty + ci1, dz = bounce ? tz : tz + ci2;
+                    const bool ok = (unsigned)dx < vx && (unsigned)dy < vy && (unsigned)dz < vz;
+                    if (ok) {
+                        const int dd = dx + TX * (dy + TY * dz);
+                        atomicAdd(&s_acc[dd], f[i]);
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            const int ca = cc(i, a);
+                            if (ca != 0) atomicAdd(&s_acc[(1 + a) * n0 + dd], (ca > 0) != bounce ? f[i] : -f[i]);
+                        }
+                        atomicAdd(&s_acc[(1 + D) * n0 + dd], gp[i]);
+                    }
                 }
             }
         }
