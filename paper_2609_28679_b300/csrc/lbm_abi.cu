@@ -817,6 +817,7 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
 {
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
     drop_graph(h);
+    h->moments_valid = false;  // the carried moments depend on the kernel and its tile
     if (variant == LBM_KERNEL_SPLIT) {
         h->variant = LBM_KERNEL_SPLIT;
         return LBM_OK;
