@@ -190,10 +190,23 @@ def aggregate_mlups(cells_per_rank: int, steps: int, world: int, max_ms: float) 
     return world * cells_per_rank * steps / (max_ms * 1e-3) / 1e6
 
 
-def _time_steps(torch, sim, steps, stream=None):
-    """ms per step over `steps` steps (device events), L2 flushed before."""
+def _time_steps(torch, sim, steps, stream=None, per_step=True):
+    """ms per step over `steps` steps (device events).  per_step: one event
+    pair per step with L2 flushed before each (workloads that fit in L2);
+    else one pair around all steps, L2 flushed once (inputs larger than L2,
+    or steps replayed as CUDA graphs)."""
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     st = stream or torch.cuda.current_stream()
+    if per_step:
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(st)
+            sim.step(1)
+            b.record(st)
+        torch.cuda.synchronize()
+        del flush
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
     flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
@@ -219,7 +232,10 @@ def _form(lbm, torch, case, steps, storage_bytes, graphs=0, mlp=None, tune=True,
         if tune:
             sim.autotune(3)
         sim.step(warm)
-        ms = _time_steps(torch, sim, steps, stream)
+        # population bytes of one step; below the 126 MB L2 every timed step starts cold
+        Q = 3 ** sim.dim
+        pop_bytes = 4 * Q * storage_bytes * sum(c.ncell for c in sim.cases)
+        ms = _time_steps(torch, sim, steps, stream, per_step=(not graphs and pop_bytes < 4 * L2_FLUSH_BYTES))
         rho, u, T = sim.moments()
         diag = sim.diagnostics()
     n = sum(c.ncell for c in sim.cases)
@@ -240,24 +256,55 @@ class _null:
         return False
 
 
+def _rel_dev(a, b) -> float:
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _vs_f64(ref, ref_fields, r, fields):
+    """Speed-up over the float64 GPU run of the same workload, and the
+    deviation from it after the same steps from the same state."""
+    r["speedup_vs_f64_gpu"] = ref["ms_per_step"] / r["ms_per_step"]
+    r["rel_dev_vs_f64_gpu"] = {"rho": _rel_dev(fields[0], ref_fields[0]), "T": _rel_dev(fields[1], ref_fields[1])}
+
+
 def _measure_forms(lbm, wl, torch, steps):
-    """The other forms on their full-size workloads (few steps each)."""
+    """Every form on its full-size workload (few steps each), next to the
+    plain float64 GPU path of the same workload: MLUPS, HBM fraction, speed-up
+    and deviation from float64 after the same steps."""
     res = {}
     try:
         r, _ = _form(lbm, torch, wl.acoustic_shear(128, storage="f64"), steps, 8)
         res["f64_ideal_2d_128"] = r
-        base, (r0, T0) = _form(lbm, torch, wl.pr_heated_slab(256, storage="f32"), steps, 4, warm=0)
-        res["f32_pr_slab_256"] = base
-        for st, sb in (("bf16", 2), ("f16", 2)):
-            r, (r1, T1) = _form(lbm, torch, wl.pr_heated_slab(256, storage=st), steps, sb, warm=0)
-            r["rel_dev_vs_f32"] = {"rho": float(np.max(np.abs(r1 - r0)) / np.max(np.abs(r0))),
-                                   "T": float(np.max(np.abs(T1 - T0)) / np.max(np.abs(T0)))}
-            r["speedup_vs_f32"] = base["ms_per_step"] / r["ms_per_step"]
-            res[f"{st}_pr_slab_256"] = r
-        r, _ = _form(lbm, torch, wl.vdw_batch(64, storage="f32"), steps, 4, graphs=10)
+        # the 512^2 van der Waals quench (the bench workload)
+        r64, f64 = _form(lbm, torch, wl.vdw_spinodal(512, storage="f64"), steps, 8, warm=0)
+        res["f64_vdw_512"] = r64
+        r, fr = _form(lbm, torch, wl.vdw_spinodal(512, storage="f32"), steps, 4, warm=0)
+        _vs_f64(r64, f64, r, fr)
+        res["f32_vdw_512"] = r
+        # 64 simulations per launch under CUDA graphs
+        b64, fb64 = _form(lbm, torch, wl.vdw_batch(64, storage="f64"), steps, 8, graphs=10, warm=0)
+        res["f64_vdw_batch_64"] = b64
+        r, fr = _form(lbm, torch, wl.vdw_batch(64, storage="f32"), steps, 4, graphs=10, warm=0)
+        _vs_f64(b64, fb64, r, fr)
         res["f32_vdw_batch_64"] = r
+        torch.cuda.empty_cache()
+        # 3-D heated slab: float64, float32, and 16-bit storage with offsets
+        s64, fs64 = _form(lbm, torch, wl.pr_heated_slab(256, storage="f64"), steps, 8, warm=0)
+        res["f64_pr_slab_256"] = s64
+        for st, sb in (("f32", 4), ("bf16", 2), ("f16", 2)):
+            r, fr = _form(lbm, torch, wl.pr_heated_slab(256, storage=st), steps, sb, warm=0)
+            _vs_f64(s64, fs64, r, fr)
+            res[f"{st}_pr_slab_256"] = r
+        del fs64
+        torch.cuda.empty_cache()
+        # 3-D droplet: Newton in float64 and float32, and the learned temperature start
+        nd = max(4, steps // 2)
+        d64, fd64 = _form(lbm, torch, wl.pr_droplet(384, storage="f64"), nd, 8, warm=0)
+        res["f64_pr_droplet_384_newton"] = d64
+        torch.cuda.empty_cache()
         drop = wl.pr_droplet(384, storage="f32")
-        newton, (rn, Tn) = _form(lbm, torch, drop, max(4, steps // 2), 4, warm=0)
+        newton, fdn = _form(lbm, torch, drop, nd, 4, warm=0)
+        _vs_f64(d64, fd64, newton, fdn)
         res["f32_pr_droplet_384_newton"] = newton
         le = lbm.structs_from_case(drop)[1]
         params = np.zeros(lbm.lbm_mlp_nparams(), dtype=np.float32)
@@ -266,15 +313,13 @@ def _measure_forms(lbm, wl, torch, steps):
         train_s = time.perf_counter() - t0
         drop_m = wl.pr_droplet(384, storage="f32")
         drop_m.t_solver = 1
-        r, (rm, Tm) = _form(lbm, torch, drop_m, max(4, steps // 2), 4, mlp=params, warm=0)
+        r, fr = _form(lbm, torch, drop_m, nd, 4, mlp=params, warm=0)
+        _vs_f64(d64, fd64, r, fr)
         r["train_s"] = train_s
-        r["rel_dev_vs_newton"] = {"rho": float(np.max(np.abs(rm - rn)) / np.max(np.abs(rn))),
-                                  "T": float(np.max(np.abs(Tm - Tn)) / np.max(np.abs(Tn)))}
-        r["speedup_vs_newton"] = newton["ms_per_step"] / r["ms_per_step"]
+        r["speedup_vs_f32_newton"] = newton["ms_per_step"] / r["ms_per_step"]
+        r["rel_dev_vs_f32_newton"] = {"rho": _rel_dev(fr[0], fdn[0]), "T": _rel_dev(fr[1], fdn[1])}
         res["f32_pr_droplet_384_mlp"] = r
-        # the plain float64 path on the 3-D slab, the baseline of the reduced-precision forms
-        r, _ = _form(lbm, torch, wl.pr_heated_slab(128, storage="f64"), max(4, steps // 2), 8, warm=0)
-        res["f64_pr_slab_128"] = r
+        torch.cuda.empty_cache()
     except Exception as e:  # report what was measured
         res["error"] = f"{type(e).__name__}: {e}"
     return res
