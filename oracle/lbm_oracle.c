@@ -27,7 +27,10 @@
  * Readings of points the paper leaves open (each also listed in the design doc):
  *  - beta = 1/(2 tau + 1) with a constant tau per distribution (Eq. beta); the
  *    shear viscosity mu = tau P then follows the local pressure.  eta and k
- *    enter only through the ratios eta/mu and k/mu.
+ *    enter only through the ratios eta/mu and k/mu.  With mu > 0 the paper's
+ *    own parameterisation is used instead: tau = mu / P of the cell (Sec. II.C,
+ *    the relation after Eq. theta), the same tau for f and g, and beta per
+ *    cell in the collision (flowchart, last box).
  *  - alpha*theta is evaluated as ((D+2)/D - eta/mu) theta - c_s^2, which equals
  *    alpha*theta of Eq. corr_bulk with theta = P/rho but has no removable
  *    singularity where P = 0 (spinodal region of van der Waals / Peng-Robinson).
@@ -77,6 +80,8 @@ typedef struct {
     double q;           /* volumetric heat source Q */
     int zlo, zhi;       /* Q acts where zlo <= z < zhi; zhi <= 0 means everywhere */
     int phi_central;    /* 0: upwind-biased derivative in Phi; 1: central difference */
+    double mu;          /* > 0: the paper's tau = mu / P per cell (Sec. II.C), one tau for f and g;
+                           0: constant tau_f, tau_g */
 } orc_params;
 
 typedef struct {
@@ -630,11 +635,18 @@ static void one_step(orc_state *s)
                     if (c2 == 1) gst[i] += 0.5 * cq;                      /* Eq. LBMgstar, correction */
                 }
 
+                /* beta (Eq. beta): constant, or from tau = mu / P of this cell */
+                double bf = beta_f, bg = beta_g;
+                if (p->mu > 0.0) {
+                    double tau = p->mu / P;
+                    bf = bg = 1.0 / (2.0 * tau + 1.0);
+                }
+
                 /* collide (Eqs. LBM_f, LBM_g with lambda = dt) and stream (push) */
                 for (int i = 0; i < Q; ++i) {
                     double fi = s->f[(long)i * N + k], gi = s->g[(long)i * N + k];
-                    double fo = fi + 2.0 * beta_f * (feq[i] - fi) + (1.0 - beta_f) * (fst[i] - feq[i]);
-                    double go = gi + 2.0 * beta_g * (geq[i] - gi) + (1.0 - beta_g) * (gst[i] - geq[i]);
+                    double fo = fi + 2.0 * bf * (feq[i] - fi) + (1.0 - bf) * (fst[i] - feq[i]);
+                    double go = gi + 2.0 * bg * (geq[i] - gi) + (1.0 - bg) * (gst[i] - geq[i]);
                     int zt = z + s->c[i][2];
                     if (p->zwalls && (zt < 0 || zt >= nz)) {
                         /* half-way bounce-back: returns to this cell reversed */

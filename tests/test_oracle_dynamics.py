@@ -120,6 +120,41 @@ def test_shear_wave_decay_rate():
     assert rate == pytest.approx(tau * T0 * k * k, rel=0.01)
 
 
+def test_shear_wave_decay_rate_constant_mu():
+    # The paper's own parameterisation tau = mu / P per cell (Sec. II.C): the kinematic viscosity is
+    # nu = mu / rho, here at rho0 = 2 so that a tau taken as mu itself (nu = mu theta) would fail.
+    nx, mu, rho0, T0 = 48, 0.48, 2.0, 0.3
+    c = wl.Case(name="shear_mu", dim=2, nx=nx, ny=1, eos="ideal", R=1.0, cv=2.5, k_over_mu=3.5 / 0.71,
+                mu=mu, init=dict(kind="waves", rho0=rho0, amp_rho=0.0, amp_u=1e-4, T0=T0))
+    o = run_oracle(c, 0)
+    amps, ts = [], [50, 150, 250, 350]
+    t = 0
+    for tt in ts:
+        o.step(tt - t)
+        t = tt
+        amps.append(_mode_amplitude(o.moments()[1][1], nx))
+    rate = -np.polyfit(ts, np.log(amps), 1)[0]
+    k = 2 * math.pi / nx
+    assert rate == pytest.approx(mu / rho0 * k * k, rel=0.01)
+
+
+def test_constant_mu_equals_constant_tau_at_uniform_pressure():
+    # With P uniform and constant in time (a state at rest), tau = mu / P is the constant mu / P0,
+    # so both parameterisations take the same steps (to rounding of beta).
+    base = dict(dim=2, nx=6, ny=5, eos="vdw", R=1.0, cv=2.5, a=9 / 49, b=2 / 21, k_over_mu=3.5,
+                init=dict(kind="uniform", rho0=1.3, T0=0.8))
+    ca = wl.Case(name="tau", tau_f=0.7, tau_g=0.7, **base)
+    oa = run_oracle(ca, 0)
+    P0 = orc.EoS(orc.params_from_case(ca)).P(1.3, 0.8)
+    cb = wl.Case(name="mu", mu=0.7 * P0, **base)
+    ob = run_oracle(cb, 0)
+    oa.step(30)
+    ob.step(30)
+    fa, ga = oa.populations()
+    fb, gb = ob.populations()
+    assert np.max(np.abs(fa - fb)) <= 1e-14 and np.max(np.abs(ga - gb)) <= 1e-14
+
+
 def test_sound_speed_and_acoustic_damping():
     # Uniform-T density pulse: the acoustic part oscillates at c_s k with c_s^2 = gamma R T (ideal gas)
     # and decays at Gamma = k^2/2 [2(D-1)/D nu + (gamma - 1) chi] (eta = 0), chi = k_cond/(rho c_p).
@@ -185,6 +220,19 @@ def test_poiseuille_between_bounce_back_walls():
     assert A == pytest.approx(a / (2 * nu), rel=0.01)
     assert abs(B) <= 0.05 * A * shape.max()
     assert np.max(np.abs(u[0] - (A * shape + B))) <= 1e-3 * A * shape.max()
+
+
+def test_poiseuille_constant_mu():
+    # Poiseuille curvature a / (2 nu) with nu = mu / rho for tau = mu / P per cell (Sec. II.C, III.A).
+    nz, a, mu, rho0, T0 = 16, 1e-6, 0.36, 1.5, 0.3
+    c = wl.Case(name="pois_mu", dim=3, nx=1, ny=1, nz=nz, zwalls=1, eos="ideal", R=1.0, cv=2.5,
+                k_over_mu=3.5 / 0.71, mu=mu, accel=(a, 0.0, 0.0), init=dict(kind="uniform", rho0=rho0, T0=T0))
+    o = run_oracle(c, 6000)
+    rho, u, T = o.moments()
+    z = np.arange(nz)
+    shape = (z + 0.5) * (nz - 0.5 - z)
+    A, B = np.polyfit(shape, u[0], 1)
+    assert A == pytest.approx(a / (2 * mu / rho0), rel=0.01)
 
 
 def _maxwell(eos, T):
