@@ -101,6 +101,10 @@ typedef struct {
     double eta_over_mu; /* bulk / shear viscosity (Eq. corr_bulk)                */
     double k_over_mu;   /* thermal conductivity / shear viscosity (Eq. qc_1)    */
     int t_solver;       /* LBM_T_NEWTON | LBM_T_MLP                              */
+    double mu;          /* shear viscosity of the paper's tau = mu / P (Sec. II.C):
+                           > 0: tau and beta (Eq. beta) per cell from the cell's
+                           pressure, one tau for f and g (tau_f, tau_g unused);
+                           0: constant tau_f, tau_g                              */
 } lbm_eos;
 
 typedef struct {
@@ -114,7 +118,8 @@ typedef struct {
 } lbm_heat;
 
 /* Create one simulation.  tau_f, tau_g are the paper's relaxation time tau of
- * f and g (beta = 1/(2 tau + 1), Eq. beta; tau > 0).  force and heat may be
+ * f and g (beta = 1/(2 tau + 1), Eq. beta; tau > 0), used when eos->mu is 0
+ * (eos->mu > 0: tau = mu / P per cell instead).  force and heat may be
  * NULL (no body force / no heat source).  Allocates 2 x 2 x Q x N populations
  * of the storage type plus work arrays.  Errors: LBM_E_INVALID (dim not 2/3,
  * sizes < 1, nz != 1 in 2-D, walls in 2-D, kind/storage/scheme out of range,

@@ -45,6 +45,7 @@ struct SimDev {
     double acc[3], q;             // body acceleration, heat source
     double inv_cv, inv_Tc, lam_c; // 1/cv, 1/Tc, 1/(2 sqrt2 b) (Peng-Robinson)
     double athe_c;                // (D+2)/D - eta/mu
+    double mu;                    // > 0: tau = mu / P per cell (beta per cell); 0: beta_f, beta_g
     float fref[27], gref[27];     // storage offsets (16-bit storage only; zero otherwise)
     const float* mlp;             // learned T(rho, e) parameters (t_solver == LBM_T_MLP), or null
 };
@@ -55,7 +56,7 @@ template <typename F> struct SimC {
     int nx, ny, nz, zwalls;
     long long N, pop_off, cell_off;
     int eos, phi_central, t_solver, zlo, zhi;
-    F R, cv, a, b, Tc, kw, kappa, eta_mu, k_mu, beta_f, beta_g, acc[3], q, inv_cv, inv_Tc, lam_c, athe_c;
+    F R, cv, a, b, Tc, kw, kappa, eta_mu, k_mu, beta_f, beta_g, acc[3], q, inv_cv, inv_Tc, lam_c, athe_c, mu;
     F fref[27], gref[27];
     const float* mlp;
 };
@@ -69,24 +70,25 @@ template <typename R> __device__ inline void simc_from(SimC<R>& d, const SimDev&
     d.kappa = (R)s.kappa; d.eta_mu = (R)s.eta_mu; d.k_mu = (R)s.k_mu; d.beta_f = (R)s.beta_f; d.beta_g = (R)s.beta_g;
     for (int a = 0; a < 3; ++a) d.acc[a] = (R)s.acc[a];
     d.q = (R)s.q; d.inv_cv = (R)s.inv_cv; d.inv_Tc = (R)s.inv_Tc; d.lam_c = (R)s.lam_c; d.athe_c = (R)s.athe_c;
+    d.mu = (R)s.mu;
     for (int i = 0; i < 27; ++i) { d.fref[i] = (R)s.fref[i]; d.gref[i] = (R)s.gref[i]; }
     d.mlp = s.mlp;
 }
 
 // The same conversion shared out over a block's threads (one field each):
-// the nineteen float64 scalars from R to athe_c are consecutive members in both
+// the twenty float64 scalars from R to mu are consecutive members in both
 // structures, as are the two offset tables.  The caller synchronises after.
 template <typename R> __device__ inline void simc_from_coop(SimC<R>& d, const SimDev& s, int tid)
 {
-    static_assert(offsetof(SimDev, athe_c) - offsetof(SimDev, R) == 18 * sizeof(double), "SimDev scalar layout");
-    static_assert(offsetof(SimC<R>, athe_c) - offsetof(SimC<R>, R) == 18 * sizeof(R), "SimC scalar layout");
+    static_assert(offsetof(SimDev, mu) - offsetof(SimDev, R) == 19 * sizeof(double), "SimDev scalar layout");
+    static_assert(offsetof(SimC<R>, mu) - offsetof(SimC<R>, R) == 19 * sizeof(R), "SimC scalar layout");
     static_assert(offsetof(SimDev, gref) - offsetof(SimDev, fref) == 27 * sizeof(float), "SimDev table layout");
     static_assert(offsetof(SimC<R>, gref) - offsetof(SimC<R>, fref) == 27 * sizeof(R), "SimC table layout");
-    if (tid < 19) {
+    if (tid < 20) {
         (&d.R)[tid] = (R)(&s.R)[tid];
-    } else if (tid < 73) {
-        (&d.fref[0])[tid - 19] = (R)(&s.fref[0])[tid - 19];
-    } else if (tid == 73) {
+    } else if (tid < 74) {
+        (&d.fref[0])[tid - 20] = (R)(&s.fref[0])[tid - 20];
+    } else if (tid == 74) {
         d.nx = s.nx; d.ny = s.ny; d.nz = s.nz; d.zwalls = s.zwalls;
         d.N = s.N; d.pop_off = s.pop_off; d.cell_off = s.cell_off;
         d.eos = s.eos; d.phi_central = s.phi_central; d.t_solver = s.t_solver; d.zlo = s.zlo; d.zhi = s.zhi;
@@ -335,6 +337,13 @@ template <typename R> __device__ __forceinline__ R xflux(R rho, R u, R th)
     return rho * u * (u * u + R(3) * th - R(1));
 }
 
+// beta of a cell (Eq. beta, dt = 1) under the paper's tau = mu / P (Sec. II.C)
+template <typename R, typename C> __device__ __forceinline__ R relax_beta(const C& s, R P)
+{
+    const R tau = (R)s.mu / P;
+    return R(1) / (R(2) * tau + R(1));
+}
+
 // ---------------------------------------------------------------------------
 // Collision of one cell (Eqs. LBMeq, LBMstar, LBMeqG, LBMgstar, LBM_f, LBM_g).
 // f, g: pre-collision populations in, post-collision out.
@@ -388,7 +397,8 @@ __device__ __forceinline__ void collide_cell(const C& s, const Macro<R>& m, R di
         hpsi3<R>(m.u[a], m.theta, H0[a]);
         hpsi3<R>(us[a], ths, Hs[a]);
     }
-    const R bf = (R)s.beta_f, bg = (R)s.beta_g;
+    R bf = (R)s.beta_f, bg = (R)s.beta_g;
+    if (s.mu > 0) bf = bg = relax_beta<R>(s, m.P);
     const R cf0 = R(1) - R(2) * bf, cf1 = R(3) * bf - R(1), cf2 = R(1) - bf;
     const R cg0 = R(1) - R(2) * bg, cg1 = R(3) * bg - R(1), cg2 = R(1) - bg;
     //   f'_i = cf0 f_i + cf1 f^eq_i + cf2 f*_i,  g'_i = cg0 g_i + cg1 g^eq_i + cg2 g*_i
@@ -477,7 +487,8 @@ template <int D, typename R> struct Coll {
             psi3<R>(m.u[a], m.theta + m.u[a] * m.u[a], c.A0[a]);
             psi3<R>(c.us[a], c.ths + c.us[a] * c.us[a] + Phi[a], c.As[a]);
         }
-        const R bf = (R)s.beta_f, bg = (R)s.beta_g;
+        R bf = (R)s.beta_f, bg = (R)s.beta_g;
+        if (s.mu > 0) bf = bg = relax_beta<R>(s, m.P);
         c.cf0 = R(1) - R(2) * bf;
         c.cf1 = R(3) * bf - R(1);
         c.cf2 = R(1) - bf;

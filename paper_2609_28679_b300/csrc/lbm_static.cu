@@ -17,6 +17,7 @@
 // host threads) race on it and produce garbage; serialise them.  Each call
 // rewrites all of the array it reads, so no state carries from one call to
 // the next.
+#include <cmath>
 #include <cstring>
 #include <string>
 
@@ -194,7 +195,9 @@ int lbm_step_static(const lbm_lattice* lattice, const lbm_eos* eos, double tau_f
         }
         s.kw = 0.37464 + 1.54226 * eos->omega - 0.26992 * eos->omega * eos->omega;
     }
+    if (!(eos->mu >= 0) || !std::isfinite(eos->mu)) return fail(LBM_E_INVALID, "mu must be finite and >= 0");
     s.kappa = eos->kappa; s.eta_mu = eos->eta_over_mu; s.k_mu = eos->k_over_mu;
+    s.mu = eos->mu;
     s.beta_f = 1.0 / (2.0 * tau_f + 1.0);
     s.beta_g = 1.0 / (2.0 * tau_g + 1.0);
     if (force) { s.acc[0] = force->accel[0]; s.acc[1] = force->accel[1]; s.acc[2] = L.dim == 3 ? force->accel[2] : 0.0; }

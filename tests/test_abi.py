@@ -43,7 +43,7 @@ def test_struct_layout_matches_header():
 #include "lbm.h"
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(lbm_lattice), sizeof(lbm_eos), sizeof(lbm_force), sizeof(lbm_heat));
-  printf("%zu %zu %zu\n", offsetof(lbm_eos, kappa), offsetof(lbm_eos, t_solver), offsetof(lbm_lattice, phi_scheme));
+  printf("%zu %zu %zu %zu\n", offsetof(lbm_eos, kappa), offsetof(lbm_eos, t_solver), offsetof(lbm_lattice, phi_scheme), offsetof(lbm_eos, mu));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -58,6 +58,7 @@ int main(void) {
     assert sizes[4] == lbm.lbm_eos.kappa.offset
     assert sizes[5] == lbm.lbm_eos.t_solver.offset
     assert sizes[6] == lbm.lbm_lattice.phi_scheme.offset
+    assert sizes[7] == lbm.lbm_eos.mu.offset
 
 
 def _create(lib, lat, eos, tau=0.8):
@@ -77,6 +78,8 @@ def _create(lib, lat, eos, tau=0.8):
     ({}, dict(R=0.0), 0.8, "R"),
     ({}, {}, 0.0, "tau"),
     ({}, dict(kind=lbm.LBM_PR, Tc=0.0), 0.8, "Tc"),
+    ({}, dict(mu=-1.0), 0.8, "mu"),
+    ({}, dict(mu=float("nan")), 0.8, "mu nan"),
 ])
 def test_invalid_arguments_rejected_without_device(lib, lat_kw, eos_kw, tau, why):
     lat = lbm.lbm_lattice(**{**dict(dim=2, nx=8, ny=8, nz=1, zwalls=0, storage=0, phi_scheme=0), **lat_kw})

@@ -117,6 +117,43 @@ def test_f64_vdw_3d_periodic_upwind_korteweg(variant):
     _compare(sim, o, 1e-12)
 
 
+def _with_mu(c, rho0, T0, tau=0.8):
+    # the paper's tau = mu / P per cell, with mu set so that tau = 0.8 at the mean state
+    c.mu = tau * orc.EoS(oracle_params(c)).P(rho0, T0)
+    return c
+
+
+@pytest.mark.parametrize("variant", _variants())
+def test_f64_vdw_2d_constant_mu(variant):
+    c = wl.Case(name="vdw2mu", dim=2, nx=33, ny=26, eos="vdw", R=1.0, cv=2.5, a=wl.VDW_A, b=wl.VDW_B,
+                kappa=wl.VDW_KAPPA, eta_over_mu=wl.VDW_ETA, k_over_mu=3.5, accel=(2e-4, -1e-4, 0.0),
+                phi_central=1, storage="f64",
+                init=dict(kind="noisy_density", rho0=2.0, amp=0.02, T0=1.1 * wl.VDW_TC, seed=12))
+    _with_mu(c, 2.0, 1.1 * wl.VDW_TC)
+    sim, o = _run_pair(c, 25, variant)
+    _compare(sim, o, 1e-12)
+
+
+@pytest.mark.parametrize("variant", _variants3())
+def test_f64_pr_3d_walls_constant_mu(variant):
+    c = wl.pr_heated_slab(n=11, nz=13, storage="f64")
+    c.ny = 9
+    c.zhi = 4
+    _with_mu(c, c.init["rho0"], c.init["T0"])
+    sim, o = _run_pair(c, 12, variant)
+    _compare(sim, o, 1e-12)
+
+
+def test_f32_vdw_2d_constant_mu():
+    c = wl.Case(name="vdw2mu", dim=2, nx=70, ny=40, eos="vdw", R=1.0, cv=2.5, a=wl.VDW_A, b=wl.VDW_B,
+                kappa=wl.VDW_KAPPA, eta_over_mu=wl.VDW_ETA, k_over_mu=3.5, accel=(0.0, -1e-4, 0.0),
+                phi_central=1, storage="f32",
+                init=dict(kind="noisy_density", rho0=2.0, amp=0.02, T0=1.1 * wl.VDW_TC, seed=13))
+    _with_mu(c, 2.0, 1.1 * wl.VDW_TC)
+    sim, o = _run_pair(c, 25, FUSED)
+    _compare(sim, o, 1e-5, f32=True)
+
+
 def test_f64_invariants_match_oracle():
     c = wl.vdw_spinodal(n=32, storage="f64")
     c.q = 2e-6
