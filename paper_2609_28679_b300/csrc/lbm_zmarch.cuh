@@ -195,33 +195,45 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
                             }
                         }
                     };
-                    // f: pull, relax, store, scatter
-                    static_for<0, Q>([&](auto I) {
+                    // Pull, relax, store, scatter: f, then g, nine populations (one c_z layer)
+                    // at a time.  Each layer's loads are issued together, ahead of the shared-
+                    // memory atomics of the scatter, which the compiler does not move loads across.
+                    auto pull = [&](auto I, const S* base, const R* ref) {
                         constexpr int i = decltype(I)::value;
                         constexpr int d0 = dig(i, 0), d1 = dig(i, 1), d2 = dig(i, 2);
                         const bool wall_src = zw[d2];
                         const int isrc = wall_src ? opp(i) : i;
                         const unsigned idx = wall_src ? (unsigned)isrc * Ncell + gk
                                                       : (unsigned)i * Ncell + (unsigned)xs[d0] + rows[d1][d2];
-                        R v = Codec<S, R>::ld(fb + idx);
-                        if (Codec<S, R>::offset) v += s.fref[isrc];
-                        v = cl.template f<i>(v);
-                        if (own) Codec<S, R>::st(fo + (unsigned)i * Ncell + gk, v - (Codec<S, R>::offset ? s.fref[i] : R(0)));
-                        scatter(I, 0, v);
+                        R v = Codec<S, R>::ld(base + idx);
+                        if (Codec<S, R>::offset) v += ref[isrc];
+                        return v;
+                    };
+                    static_for<0, 3>([&](auto L) {
+                        constexpr int l = decltype(L)::value;
+                        R v[9];
+                        static_for<0, 9>([&](auto J) {
+                            v[decltype(J)::value] = pull(std::integral_constant<int, 9 * l + decltype(J)::value>{}, fb, s.fref);
+                        });
+                        static_for<0, 9>([&](auto J) {
+                            constexpr int i = 9 * l + decltype(J)::value;
+                            const R w = cl.template f<i>(v[decltype(J)::value]);
+                            if (own) Codec<S, R>::st(fo + (unsigned)i * Ncell + gk, w - (Codec<S, R>::offset ? s.fref[i] : R(0)));
+                            scatter(std::integral_constant<int, i>{}, 0, w);
+                        });
                     });
-                    // g: pull, relax, store, scatter
-                    static_for<0, Q>([&](auto I) {
-                        constexpr int i = decltype(I)::value;
-                        constexpr int d0 = dig(i, 0), d1 = dig(i, 1), d2 = dig(i, 2);
-                        const bool wall_src = zw[d2];
-                        const int isrc = wall_src ? opp(i) : i;
-                        const unsigned idx = wall_src ? (unsigned)isrc * Ncell + gk
-                                                      : (unsigned)i * Ncell + (unsigned)xs[d0] + rows[d1][d2];
-                        R v = Codec<S, R>::ld(gb + idx);
-                        if (Codec<S, R>::offset) v += s.gref[isrc];
-                        v = cl.template g<i>(v);
-                        if (own) Codec<S, R>::st(go + (unsigned)i * Ncell + gk, v - (Codec<S, R>::offset ? s.gref[i] : R(0)));
-                        scatter(I, 1, v);
+                    static_for<0, 3>([&](auto L) {
+                        constexpr int l = decltype(L)::value;
+                        R v[9];
+                        static_for<0, 9>([&](auto J) {
+                            v[decltype(J)::value] = pull(std::integral_constant<int, 9 * l + decltype(J)::value>{}, gb, s.gref);
+                        });
+                        static_for<0, 9>([&](auto J) {
+                            constexpr int i = 9 * l + decltype(J)::value;
+                            const R w = cl.template g<i>(v[decltype(J)::value]);
+                            if (own) Codec<S, R>::st(go + (unsigned)i * Ncell + gk, w - (Codec<S, R>::offset ? s.gref[i] : R(0)));
+                            scatter(std::integral_constant<int, i>{}, 1, w);
+                        });
                     });
                 }
             }
