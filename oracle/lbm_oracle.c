@@ -31,6 +31,9 @@
  *    own parameterisation is used instead: tau = mu / P of the cell (Sec. II.C,
  *    the relation after Eq. theta), the same tau for f and g, and beta per
  *    cell in the collision (flowchart, last box).
+ *  - isothermal = 1 follows the isothermal tests of Sec. III.A, where the g
+ *    equation is not solved: each cell keeps its initial temperature, the
+ *    specific energy is e(rho, T) of the EoS, and g is left as initialised.
  *  - alpha*theta is evaluated as ((D+2)/D - eta/mu) theta - c_s^2, which equals
  *    alpha*theta of Eq. corr_bulk with theta = P/rho but has no removable
  *    singularity where P = 0 (spinodal region of van der Waals / Peng-Robinson).
@@ -82,6 +85,8 @@ typedef struct {
     int phi_central;    /* 0: upwind-biased derivative in Phi; 1: central difference */
     double mu;          /* > 0: the paper's tau = mu / P per cell (Sec. II.C), one tau for f and g;
                            0: constant tau_f, tau_g */
+    int isothermal;     /* 1: the g equation is not solved (Sec. III.A, isothermal tests); every cell
+                           keeps its initial temperature, e = e(rho, T) from the EoS */
 } orc_params;
 
 typedef struct {
@@ -529,12 +534,20 @@ static void macro_fields(orc_state *s)
             u2 += uu[a] * uu[a];
         }
         for (int a = 0; a < 3; ++a) s->u[(long)a * N + k] = uu[a];
-        double rhoE = s->G[k] + 0.5 * (uF + s->Qs[k]);
-        double E = rhoE / r;
-        double e = E - 0.5 * u2;
-        int it;
-        double T = orc_eos_T(p, r, e, s->T[k], &it);
-        if (p->eos == ORC_PR && it >= 50) caps++;
+        double e, T, E;
+        if (p->isothermal) {
+            /* isothermal: T stays at its initial value; e follows from the EoS */
+            T = s->T[k];
+            e = orc_eos_e(p, r, T);
+            E = e + 0.5 * u2;
+        } else {
+            double rhoE = s->G[k] + 0.5 * (uF + s->Qs[k]);
+            E = rhoE / r;
+            e = E - 0.5 * u2;
+            int it;
+            T = orc_eos_T(p, r, e, s->T[k], &it);
+            if (p->eos == ORC_PR && it >= 50) caps++;
+        }
         double P = orc_eos_P(p, r, T);
         double th = P / r;
         if (!(th > 0.0)) nonpos++;
@@ -651,18 +664,18 @@ static void one_step(orc_state *s)
                     if (p->zwalls && (zt < 0 || zt >= nz)) {
                         /* half-way bounce-back: returns to this cell reversed */
                         s->fn[(long)s->opp[i] * N + k] = fo;
-                        s->gn[(long)s->opp[i] * N + k] = go;
+                        if (!p->isothermal) s->gn[(long)s->opp[i] * N + k] = go;
                     } else {
                         long kt = cidx(s, wrap(x + s->c[i][0], nx), wrap(y + s->c[i][1], ny), wrap(zt, nz));
                         s->fn[(long)i * N + kt] = fo;
-                        s->gn[(long)i * N + kt] = go;
+                        if (!p->isothermal) s->gn[(long)i * N + kt] = go;
                     }
                 }
             }
 
     double *t;
     t = s->f; s->f = s->fn; s->fn = t;
-    t = s->g; s->g = s->gn; s->gn = t;
+    if (!p->isothermal) { t = s->g; s->g = s->gn; s->gn = t; }  /* isothermal: g is not evolved */
 }
 
 int orc_step(orc_state *s, int n)

@@ -47,6 +47,7 @@ class OrcParams(ctypes.Structure):
         ("q", ctypes.c_double), ("zlo", ctypes.c_int), ("zhi", ctypes.c_int),
         ("phi_central", ctypes.c_int),
         ("mu", ctypes.c_double),
+        ("isothermal", ctypes.c_int),
     ]
 
 
@@ -99,7 +100,7 @@ def _dp(a: np.ndarray):
 def make_params(dim=2, nx=8, ny=8, nz=1, zwalls=0, eos="ideal", R=1.0, cv=2.5, a=0.0, b=0.0,
                 Tc=1.0, omega=0.0, Pc=None, kappa=0.0, eta_over_mu=0.0, k_over_mu=0.0,
                 tau_f=0.8, tau_g=0.8, accel=(0.0, 0.0, 0.0), q=0.0, zlo=0, zhi=0,
-                phi_central=0, mu=0.0) -> OrcParams:
+                phi_central=0, mu=0.0, isothermal=0) -> OrcParams:
     """Build the oracle's parameter struct.  For Peng-Robinson with ``Pc`` given
     and ``a == 0``, a and b follow from (Tc, Pc) by the oracle's own helper."""
     kind = _EOS_NAMES[eos] if isinstance(eos, str) else int(eos)
@@ -115,6 +116,7 @@ def make_params(dim=2, nx=8, ny=8, nz=1, zwalls=0, eos="ideal", R=1.0, cv=2.5, a
     p.q, p.zlo, p.zhi = q, zlo, zhi
     p.phi_central = int(phi_central)
     p.mu = float(mu)
+    p.isothermal = int(isothermal)
     return p
 
 
@@ -268,4 +270,5 @@ def params_from_case(case) -> OrcParams:
                        eos=case.eos, R=case.R, cv=case.cv, a=a, b=b, Tc=case.Tc, omega=case.omega,
                        kappa=case.kappa, eta_over_mu=case.eta_over_mu, k_over_mu=case.k_over_mu,
                        tau_f=case.tau_f, tau_g=case.tau_g, accel=case.accel, q=case.q,
-                       zlo=case.zlo, zhi=case.zhi, phi_central=case.phi_central, mu=getattr(case, "mu", 0.0))
+                       zlo=case.zlo, zhi=case.zhi, phi_central=case.phi_central, mu=getattr(case, "mu", 0.0),
+                       isothermal=getattr(case, "isothermal", 0))

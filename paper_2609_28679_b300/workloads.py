@@ -61,6 +61,7 @@ class Case:
     zhi: int = 0                  # <= 0: heat source everywhere
     phi_central: int = 0          # derivative in the Galilean correction: 0 upwind-biased, 1 central
     mu: float = 0.0               # > 0: tau = mu / P per cell (one tau for f and g); 0: tau_f, tau_g
+    isothermal: int = 0           # 1: g not evolved, every cell keeps its initial T
     t_solver: int = 0             # Peng-Robinson T(rho, e): 0 Newton, 1 learned start + Newton
     storage: str = "f64"          # f64 | f32 | bf16 | f16
     steps: int = 100

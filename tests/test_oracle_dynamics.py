@@ -235,6 +235,46 @@ def test_poiseuille_constant_mu():
     assert A == pytest.approx(a / (2 * mu / rho0), rel=0.01)
 
 
+def test_isothermal_poiseuille():
+    # Isothermal mode (Sec. III.A: the g equation is not solved): force-driven flow between half-way
+    # bounce-back walls keeps the curvature a / (2 nu), nu = tau theta, and the temperature stays put.
+    nz, a, tau, T0 = 16, 1e-6, 0.8, 0.3
+    c = wl.Case(name="pois_iso", dim=3, nx=1, ny=1, nz=nz, zwalls=1, eos="ideal", R=1.0, cv=2.5,
+                k_over_mu=3.5 / 0.71, tau_f=tau, tau_g=tau, accel=(a, 0.0, 0.0), isothermal=1,
+                init=dict(kind="uniform", rho0=1.0, T0=T0))
+    o = run_oracle(c, 6000)
+    rho, u, T = o.moments()
+    z = np.arange(nz)
+    shape = (z + 0.5) * (nz - 0.5 - z)
+    A, B = np.polyfit(shape, u[0], 1)
+    assert A == pytest.approx(a / (2 * tau * T0), rel=0.01)
+    assert np.all(T == T0)
+
+
+def test_isothermal_sound_speed():
+    # Without the energy equation a density wave travels at the isothermal sound speed
+    # c_T = sqrt((dP/drho)_T) = sqrt(R T) of the ideal gas, not the adiabatic sqrt(gamma R T).
+    nx, tau, T0 = 48, 0.8, 0.3
+    c = wl.Case(name="sound_iso", dim=2, nx=nx, ny=1, eos="ideal", R=1.0, cv=2.5, k_over_mu=3.5 / 0.71,
+                tau_f=tau, tau_g=tau, isothermal=1,
+                init=dict(kind="waves", rho0=1.0, amp_rho=1e-4, amp_u=0.0, T0=T0))
+    o = run_oracle(c, 0)
+    x = np.arange(nx)
+    ts, sig = np.arange(0, 300), []
+    for t in ts:
+        rho = o.moments()[0]
+        sig.append(2.0 / nx * np.sum((rho - rho.mean()) * np.sin(2 * math.pi * x / nx)))
+        o.step(1)
+    sig = np.array(sig)
+    k = 2 * math.pi / nx
+
+    def model(t, A, w, G):
+        return A * np.cos(w * t) * np.exp(-G * t)
+
+    popt, _ = optimize.curve_fit(model, ts, sig, p0=[1e-4, math.sqrt(T0) * k, 1e-3], maxfev=20000)
+    assert popt[1] == pytest.approx(math.sqrt(T0) * k, rel=0.01)
+
+
 def _maxwell(eos, T):
     # equal-area construction on the oracle's own pressure: P(rv) = P(rl) = Ps, int_{vl}^{vv} P dv = Ps (vv - vl)
     from scipy import integrate
