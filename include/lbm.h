@@ -105,6 +105,12 @@ typedef struct {
                            > 0: tau and beta (Eq. beta) per cell from the cell's
                            pressure, one tau for f and g (tau_f, tau_g unused);
                            0: constant tau_f, tau_g                              */
+    int isothermal;     /* 1: the g equation is not solved, as in the paper's
+                           isothermal tests (Sec. III.A): every cell keeps the
+                           temperature lbm_init gave it, e = e(rho, T), and the
+                           g populations and the energy invariant are left
+                           undefined; needs no heat source and t_solver
+                           LBM_T_NEWTON; not for lbm_step_static.  0: full model */
 } lbm_eos;
 
 typedef struct {
@@ -220,7 +226,8 @@ int lbm_get_kernel(lbm_handle h, int *variant, int *tx, int *ty, int *tz);
  * streams, other threads) race and corrupt each other -- serialise them.
  * Nothing carries over between calls: each one rewrites what it reads.
  * Errors: LBM_E_INVALID (NULL pointers, bad sizes, more than 65536 cells,
- * aliasing), LBM_E_UNSUPPORTED (storage other than float64), LBM_E_CUDA;
+ * aliasing), LBM_E_UNSUPPORTED (storage other than float64, the isothermal
+ * mode, which needs the temperature a handle carries), LBM_E_CUDA;
  * lbm_last_error(NULL) describes the failure. */
 int lbm_step_static(const lbm_lattice *lattice, const lbm_eos *eos, double tau_f, double tau_g,
                     const lbm_force *force, const lbm_heat *heat, const double *f_in, const double *g_in,

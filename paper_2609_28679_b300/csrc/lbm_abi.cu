@@ -389,6 +389,9 @@ int fill_sim(SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, do
     if (!(tau_f > 0) || !(tau_g > 0)) { why = "tau_f and tau_g must be > 0"; return LBM_E_INVALID; }
     if (E->t_solver != LBM_T_NEWTON && E->t_solver != LBM_T_MLP) { why = "unknown t_solver"; return LBM_E_INVALID; }
     if (!(E->mu >= 0) || !std::isfinite(E->mu)) { why = "mu must be finite and >= 0"; return LBM_E_INVALID; }
+    if (E->isothermal != 0 && E->isothermal != 1) { why = "isothermal must be 0 or 1"; return LBM_E_INVALID; }
+    if (E->isothermal && E->t_solver == LBM_T_MLP) { why = "isothermal runs invert no temperature"; return LBM_E_INVALID; }
+    if (E->isothermal && H && H->q != 0.0) { why = "isothermal runs take no heat source"; return LBM_E_INVALID; }
     s.nx = L->nx; s.ny = L->ny; s.nz = L->nz; s.zwalls = L->zwalls;
     s.N = (long long)L->nx * L->ny * L->nz;
     s.eos = E->kind;
@@ -408,6 +411,7 @@ int fill_sim(SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, do
     if (E->kind == LBM_VDW && (E->a < 0 || E->b < 0)) { why = "van der Waals needs a, b >= 0"; return LBM_E_INVALID; }
     s.kappa = E->kappa; s.eta_mu = E->eta_over_mu; s.k_mu = E->k_over_mu;
     s.mu = E->mu;
+    s.iso = E->isothermal;
     s.beta_f = 1.0 / (2.0 * tau_f + 1.0);
     s.beta_g = 1.0 / (2.0 * tau_g + 1.0);
     if (F) { s.acc[0] = F->accel[0]; s.acc[1] = F->accel[1]; s.acc[2] = L->dim == 3 ? F->accel[2] : 0.0; }

@@ -38,7 +38,7 @@ struct SimDev {
     long long pop_off;   // element offset of this simulation's f block; g follows at +Q*N
     long long cell_off;  // element offset of its cells in per-cell arrays
     int eos, phi_central, t_solver, zlo, zhi;
-    int pad_;
+    int iso;                      // 1: isothermal, g not evolved, T kept at its initial value
     double R, cv, a, b, Tc, kw;   // kw: Soave kappa(omega) for Peng-Robinson
     double kappa, eta_mu, k_mu;   // Korteweg coefficient, eta/mu, k/mu
     double beta_f, beta_g;        // 1/(2 tau + 1)
@@ -55,7 +55,7 @@ struct SimDev {
 template <typename F> struct SimC {
     int nx, ny, nz, zwalls;
     long long N, pop_off, cell_off;
-    int eos, phi_central, t_solver, zlo, zhi;
+    int eos, phi_central, t_solver, zlo, zhi, iso;
     F R, cv, a, b, Tc, kw, kappa, eta_mu, k_mu, beta_f, beta_g, acc[3], q, inv_cv, inv_Tc, lam_c, athe_c, mu;
     F fref[27], gref[27];
     const float* mlp;
@@ -66,6 +66,7 @@ template <typename R> __device__ inline void simc_from(SimC<R>& d, const SimDev&
     d.nx = s.nx; d.ny = s.ny; d.nz = s.nz; d.zwalls = s.zwalls;
     d.N = s.N; d.pop_off = s.pop_off; d.cell_off = s.cell_off;
     d.eos = s.eos; d.phi_central = s.phi_central; d.t_solver = s.t_solver; d.zlo = s.zlo; d.zhi = s.zhi;
+    d.iso = s.iso;
     d.R = (R)s.R; d.cv = (R)s.cv; d.a = (R)s.a; d.b = (R)s.b; d.Tc = (R)s.Tc; d.kw = (R)s.kw;
     d.kappa = (R)s.kappa; d.eta_mu = (R)s.eta_mu; d.k_mu = (R)s.k_mu; d.beta_f = (R)s.beta_f; d.beta_g = (R)s.beta_g;
     for (int a = 0; a < 3; ++a) d.acc[a] = (R)s.acc[a];
@@ -92,6 +93,7 @@ template <typename R> __device__ inline void simc_from_coop(SimC<R>& d, const Si
         d.nx = s.nx; d.ny = s.ny; d.nz = s.nz; d.zwalls = s.zwalls;
         d.N = s.N; d.pop_off = s.pop_off; d.cell_off = s.cell_off;
         d.eos = s.eos; d.phi_central = s.phi_central; d.t_solver = s.t_solver; d.zlo = s.zlo; d.zhi = s.zhi;
+    d.iso = s.iso;
         d.mlp = s.mlp;
     }
 }
@@ -288,12 +290,19 @@ __device__ __forceinline__ Macro<R> macro_cell(const C& s, R rho, const R* j, R 
         uF += m.u[a] * m.F[a];
         u2 += m.u[a] * m.u[a];
     }
-    const R rhoE = G + R(0.5) * (uF + Q);  // Eq. def_E
-    const R e = rhoE * m.ir - R(0.5) * u2;
     const RhoPart<R> p = rho_part<R>(s, rho);
-    bool capped;
-    int iters;
-    const R T = eos_T<R>(s, p, e, Tguess, capped, iters);
+    bool capped = false;
+    int iters = 0;
+    R e, T;
+    if (s.iso) {
+        // isothermal (g not evolved): the carried temperature is the cell's initial one
+        T = Tguess;
+        e = eos_e<R>(s, p, T);
+    } else {
+        const R rhoE = G + R(0.5) * (uF + Q);  // Eq. def_E
+        e = rhoE * m.ir - R(0.5) * u2;
+        T = eos_T<R>(s, p, e, Tguess, capped, iters);
+    }
     const Thermo<R> t = thermo<R>(s, p, T);
     const R th = t.P * m.ir;  // Eq. theta
     m.icv = s.eos == EOS_PR ? R(1) / t.cv : (R)s.inv_cv;
@@ -424,9 +433,11 @@ __device__ __forceinline__ void collide_cell(const C& s, const Macro<R>& m, R di
         for (int i = 0; i < Q; ++i) {
             const int d0 = dig(i, 0), d1 = dig(i, 1);
             f[i] = cf0 * f[i] + fa[d0] * A0[1][d1] + fs[d0] * As[1][d1];
-            R gi = cg0 * g[i] + ga[d0] * A0[1][d1] + gh0[d0] * H0[1][d1] + gb[d0] * B0[1][d1] + gk[d0] * Hs[1][d1];
-            if (cnorm2(i) == 1) gi += cc(i, 0) != 0 ? R(cc(i, 0)) * hq[0] : R(cc(i, 1)) * hq[1];
-            g[i] = gi;
+            if (!s.iso) {  // isothermal: g is not evolved
+                R gi = cg0 * g[i] + ga[d0] * A0[1][d1] + gh0[d0] * H0[1][d1] + gb[d0] * B0[1][d1] + gk[d0] * Hs[1][d1];
+                if (cnorm2(i) == 1) gi += cc(i, 0) != 0 ? R(cc(i, 0)) * hq[0] : R(cc(i, 1)) * hq[1];
+                g[i] = gi;
+            }
         }
     } else {
         // 3-D: per population (folding the xy products costs registers that the
@@ -447,7 +458,7 @@ __device__ __forceinline__ void collide_cell(const C& s, const Macro<R>& m, R di
                 gst += R(0.5) * cq;
             }
             f[i] = cf0 * f[i] + cf1 * feq + cf2 * fst;
-            g[i] = cg0 * g[i] + cg1 * geq + cg2 * gst;
+            if (!s.iso) g[i] = cg0 * g[i] + cg1 * geq + cg2 * gst;
         }
     }
 }

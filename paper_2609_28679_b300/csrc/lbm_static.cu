@@ -196,6 +196,7 @@ int lbm_step_static(const lbm_lattice* lattice, const lbm_eos* eos, double tau_f
         s.kw = 0.37464 + 1.54226 * eos->omega - 0.26992 * eos->omega * eos->omega;
     }
     if (!(eos->mu >= 0) || !std::isfinite(eos->mu)) return fail(LBM_E_INVALID, "mu must be finite and >= 0");
+    if (eos->isothermal) return fail(LBM_E_UNSUPPORTED, "the isothermal mode needs the temperature a handle carries");
     s.kappa = eos->kappa; s.eta_mu = eos->eta_over_mu; s.k_mu = eos->k_over_mu;
     s.mu = eos->mu;
     s.beta_f = 1.0 / (2.0 * tau_f + 1.0);

@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
                         for (int a = 0; a < 3; ++a) Phi[a] = -dX[a] * m.ir;
                     }
                     Coll<3, R> cl = Coll<3, R>::make(s, m, divu, gh, gT, Phi);
-                    cl.prepare_g();
+                    if (!s.iso) cl.prepare_g();
 
                     // pull sources: f_i(x) = f'_i(x - c_i), or f'_opp(i)(x) across a z wall
                     const int xs[3] = {x, xm1, xp1}, ys[3] = {y, ym1, yp1};
@@ -222,19 +222,21 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
                             scatter(std::integral_constant<int, i>{}, 0, w);
                         });
                     });
-                    static_for<0, 3>([&](auto L) {
-                        constexpr int l = decltype(L)::value;
-                        R v[9];
-                        static_for<0, 9>([&](auto J) {
-                            v[decltype(J)::value] = pull(std::integral_constant<int, 9 * l + decltype(J)::value>{}, gb, s.gref);
+                    if (!s.iso) {  // isothermal: g is not evolved
+                        static_for<0, 3>([&](auto L) {
+                            constexpr int l = decltype(L)::value;
+                            R v[9];
+                            static_for<0, 9>([&](auto J) {
+                                v[decltype(J)::value] = pull(std::integral_constant<int, 9 * l + decltype(J)::value>{}, gb, s.gref);
+                            });
+                            static_for<0, 9>([&](auto J) {
+                                constexpr int i = 9 * l + decltype(J)::value;
+                                const R w = cl.template g<i>(v[decltype(J)::value]);
+                                if (own) Codec<S, R>::st(go + (unsigned)i * Ncell + gk, w - (Codec<S, R>::offset ? s.gref[i] : R(0)));
+                                scatter(std::integral_constant<int, i>{}, 1, w);
+                            });
                         });
-                        static_for<0, 9>([&](auto J) {
-                            constexpr int i = 9 * l + decltype(J)::value;
-                            const R w = cl.template g<i>(v[decltype(J)::value]);
-                            if (own) Codec<S, R>::st(go + (unsigned)i * Ncell + gk, w - (Codec<S, R>::offset ? s.gref[i] : R(0)));
-                            scatter(std::integral_constant<int, i>{}, 1, w);
-                        });
-                    });
+                    }
                 }
             }
             __syncthreads();

@@ -40,7 +40,8 @@ class lbm_eos(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("R", ctypes.c_double), ("cv", ctypes.c_double),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("Tc", ctypes.c_double), ("Pc", ctypes.c_double),
                 ("omega", ctypes.c_double), ("kappa", ctypes.c_double), ("eta_over_mu", ctypes.c_double),
-                ("k_over_mu", ctypes.c_double), ("t_solver", ctypes.c_int), ("mu", ctypes.c_double)]
+                ("k_over_mu", ctypes.c_double), ("t_solver", ctypes.c_int), ("mu", ctypes.c_double),
+                ("isothermal", ctypes.c_int)]
 
 
 class lbm_force(ctypes.Structure):
@@ -284,7 +285,8 @@ def structs_from_case(case):
     lat = lbm_lattice(case.dim, case.nx, case.ny, case.nz, case.zwalls, STORAGE[case.storage],
                       LBM_PHI_CENTRAL if case.phi_central else LBM_PHI_UPWIND)
     eos = lbm_eos(EOS[case.eos], case.R, case.cv, case.a, case.b, case.Tc, case.Pc, case.omega, case.kappa,
-                  case.eta_over_mu, case.k_over_mu, getattr(case, "t_solver", LBM_T_NEWTON), getattr(case, "mu", 0.0))
+                  case.eta_over_mu, case.k_over_mu, getattr(case, "t_solver", LBM_T_NEWTON), getattr(case, "mu", 0.0),
+                  getattr(case, "isothermal", 0))
     force = lbm_force((ctypes.c_double * 3)(*case.accel))
     heat = lbm_heat(case.q, case.zlo, case.zhi)
     return lat, eos, force, heat

@@ -43,7 +43,7 @@ def test_struct_layout_matches_header():
 #include "lbm.h"
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(lbm_lattice), sizeof(lbm_eos), sizeof(lbm_force), sizeof(lbm_heat));
-  printf("%zu %zu %zu %zu\n", offsetof(lbm_eos, kappa), offsetof(lbm_eos, t_solver), offsetof(lbm_lattice, phi_scheme), offsetof(lbm_eos, mu));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(lbm_eos, kappa), offsetof(lbm_eos, t_solver), offsetof(lbm_lattice, phi_scheme), offsetof(lbm_eos, mu), offsetof(lbm_eos, isothermal));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -59,6 +59,7 @@ int main(void) {
     assert sizes[5] == lbm.lbm_eos.t_solver.offset
     assert sizes[6] == lbm.lbm_lattice.phi_scheme.offset
     assert sizes[7] == lbm.lbm_eos.mu.offset
+    assert sizes[8] == lbm.lbm_eos.isothermal.offset
 
 
 def _create(lib, lat, eos, tau=0.8):
@@ -80,6 +81,8 @@ def _create(lib, lat, eos, tau=0.8):
     ({}, dict(kind=lbm.LBM_PR, Tc=0.0), 0.8, "Tc"),
     ({}, dict(mu=-1.0), 0.8, "mu"),
     ({}, dict(mu=float("nan")), 0.8, "mu nan"),
+    ({}, dict(isothermal=2), 0.8, "isothermal flag"),
+    ({}, dict(kind=lbm.LBM_PR, Tc=0.5, Pc=0.15, t_solver=lbm.LBM_T_MLP, isothermal=1), 0.8, "isothermal learned"),
 ])
 def test_invalid_arguments_rejected_without_device(lib, lat_kw, eos_kw, tau, why):
     lat = lbm.lbm_lattice(**{**dict(dim=2, nx=8, ny=8, nz=1, zwalls=0, storage=0, phi_scheme=0), **lat_kw})
@@ -88,6 +91,15 @@ def test_invalid_arguments_rejected_without_device(lib, lat_kw, eos_kw, tau, why
     assert rc == lbm.LBM_E_INVALID
     assert not h.value
     assert lib.lbm_last_error(None)
+
+
+def test_isothermal_with_heat_source_rejected_without_device(lib):
+    lat = lbm.lbm_lattice(dim=2, nx=8, ny=8, nz=1, zwalls=0, storage=0, phi_scheme=0)
+    eos = lbm.lbm_eos(kind=0, R=1.0, cv=2.5, isothermal=1)
+    heat = lbm.lbm_heat(1e-6, 0, 0)
+    h = ctypes.c_void_p()
+    rc = lib.lbm_create(ctypes.byref(lat), ctypes.byref(eos), 0.8, 0.8, None, ctypes.byref(heat), ctypes.byref(h))
+    assert rc == lbm.LBM_E_INVALID and not h.value
 
 
 def test_null_handle_calls_fail_cleanly(lib):

@@ -154,6 +154,54 @@ def test_f32_vdw_2d_constant_mu():
     _compare(sim, o, 1e-5, f32=True)
 
 
+def _compare_isothermal(sim, o, tol, f32=False):
+    # the isothermal mode evolves f only: g is left undefined, T stays at its initial field
+    f, _ = sim.populations()
+    fr, _ = o.populations()
+    assert rel_linf(f, fr.ravel()) <= tol
+    rho, u, T = sim.moments()
+    rr, ur, Tr = o.moments()
+    assert rel_linf(rho, rr) <= tol
+    assert rel_linf(T, Tr) <= tol
+    du = float(np.max(np.abs(u - ur.ravel())))
+    tol_u = tol if f32 else tol * max(float(np.max(np.abs(ur))), 1e-3)
+    assert du <= tol_u, (du, tol_u)
+
+
+@pytest.mark.parametrize("variant", _variants())
+def test_f64_vdw_2d_isothermal(variant):
+    c = wl.vdw_spinodal(n=33, ny=26, storage="f64")
+    c.isothermal = 1
+    sim, o = _run_pair(c, 30, variant)
+    _compare_isothermal(sim, o, 1e-12)
+
+
+@pytest.mark.parametrize("variant", _variants3())
+def test_f64_pr_3d_walls_isothermal(variant):
+    c = wl.pr_heated_slab(n=11, nz=13, storage="f64")
+    c.ny = 9
+    c.q = 0.0
+    c.isothermal = 1
+    sim, o = _run_pair(c, 12, variant)
+    _compare_isothermal(sim, o, 1e-12)
+
+
+def test_f32_vdw_2d_isothermal_fused():
+    c = wl.vdw_spinodal(n=70, ny=40, storage="f32")
+    c.isothermal = 1
+    sim, o = _run_pair(c, 25, FUSED)
+    _compare_isothermal(sim, o, 1e-5, f32=True)
+
+
+@pytest.mark.parametrize("tile", [(30, 14, 32), (30, 6, 4)])
+def test_f32_pr_3d_isothermal_zmarch(tile):
+    c = wl.pr_heated_slab(n=12, nz=10, storage="f32")
+    c.q = 0.0
+    c.isothermal = 1
+    sim, o = _run_pair(c, 10, (ZMARCH, tile))
+    _compare_isothermal(sim, o, 1e-5, f32=True)
+
+
 def test_f64_invariants_match_oracle():
     c = wl.vdw_spinodal(n=32, storage="f64")
     c.q = 2e-6
