@@ -217,8 +217,9 @@ def _time_steps(torch, sim, steps, stream=None, per_step=True):
     return e0.elapsed_time(e1) / steps
 
 
-def _form(lbm, torch, case, steps, storage_bytes, graphs=0, mlp=None, tune=True, warm=3):
-    """MLUPS, ms per step and HBM fraction of one workload form."""
+def _form(lbm, torch, case, steps, storage_bytes, graphs=0, mlp=None, tune=True, warm=3, pops=2):
+    """MLUPS, ms per step and HBM fraction of one workload form (pops: population
+    sets read and written per step, 2 for f and g, 1 in the isothermal mode)."""
     sim = lbm.Simulation(case)
     stream = None
     if graphs:
@@ -234,13 +235,13 @@ def _form(lbm, torch, case, steps, storage_bytes, graphs=0, mlp=None, tune=True,
         sim.step(warm)
         # population bytes of one step; below the 126 MB L2 every timed step starts cold
         Q = 3 ** sim.dim
-        pop_bytes = 4 * Q * storage_bytes * sum(c.ncell for c in sim.cases)
+        pop_bytes = 2 * pops * Q * storage_bytes * sum(c.ncell for c in sim.cases)
         ms = _time_steps(torch, sim, steps, stream, per_step=(not graphs and pop_bytes < 4 * L2_FLUSH_BYTES))
         rho, u, T = sim.moments()
         diag = sim.diagnostics()
     n = sum(c.ncell for c in sim.cases)
     Q = 3 ** sim.dim
-    alg = 4 * Q * storage_bytes * n
+    alg = 2 * pops * Q * storage_bytes * n
     peak, _ = _peaks()
     out = {"cells": n, "ms_per_step": ms, "mlups": n / (ms * 1e3), "hbm_frac": alg / (ms * 1e-3) / 1e9 / peak,
            "kernel": list(sim.kernel()), "steps_timed": steps, "diagnostics": [int(v) for v in diag]}
@@ -281,6 +282,12 @@ def _measure_forms(lbm, wl, torch, steps):
         r, fr = _form(lbm, torch, wl.vdw_spinodal(512, storage="f32"), steps, 4, warm=0)
         _vs_f64(r64, f64, r, fr)
         res["f32_vdw_512"] = r
+        # the isothermal mode (f only; algorithmic bytes 2 Q s) beside the full model
+        iso = wl.vdw_spinodal(512, storage="f32")
+        iso.isothermal = 1
+        ri, _ = _form(lbm, torch, iso, steps, 4, warm=0, pops=1)
+        ri["speedup_vs_full_model"] = r["ms_per_step"] / ri["ms_per_step"]
+        res["f32_vdw_512_isothermal"] = ri
         # 64 simulations per launch under CUDA graphs
         b64, fb64 = _form(lbm, torch, wl.vdw_batch(64, storage="f64"), steps, 8, graphs=10, warm=0)
         res["f64_vdw_batch_64"] = b64
@@ -295,6 +302,11 @@ def _measure_forms(lbm, wl, torch, steps):
             r, fr = _form(lbm, torch, wl.pr_heated_slab(256, storage=st), steps, sb, warm=0)
             _vs_f64(s64, fs64, r, fr)
             res[f"{st}_pr_slab_256"] = r
+        iso = wl.pr_heated_slab(256, storage="f32")
+        iso.isothermal, iso.q = 1, 0.0
+        ri, _ = _form(lbm, torch, iso, steps, 4, warm=0, pops=1)
+        ri["speedup_vs_full_model"] = res["f32_pr_slab_256"]["ms_per_step"] / ri["ms_per_step"]
+        res["f32_pr_slab_256_isothermal"] = ri
         del fs64
         torch.cuda.empty_cache()
         # 3-D droplet: Newton in float64 and float32, and the learned temperature start

@@ -377,6 +377,9 @@ template <typename R> __host__ __device__ __forceinline__ void hpsi3(R u, R th, 
     o[2] = R(0.5) * (o2 - o1);
 }
 
+// In the isothermal mode g is relaxed here all the same and never read: f's
+// collision takes nothing from g, and skipping it under a runtime test cost
+// the fused kernel more than the work it saved.
 template <int D, typename R, typename C>
 __device__ __forceinline__ void collide_cell(const C& s, const Macro<R>& m, R divu, const R* gh, const R* gT,
                                              const R* Phi, R* f, R* g)
@@ -433,11 +436,9 @@ __device__ __forceinline__ void collide_cell(const C& s, const Macro<R>& m, R di
         for (int i = 0; i < Q; ++i) {
             const int d0 = dig(i, 0), d1 = dig(i, 1);
             f[i] = cf0 * f[i] + fa[d0] * A0[1][d1] + fs[d0] * As[1][d1];
-            if (!s.iso) {  // isothermal: g is not evolved
-                R gi = cg0 * g[i] + ga[d0] * A0[1][d1] + gh0[d0] * H0[1][d1] + gb[d0] * B0[1][d1] + gk[d0] * Hs[1][d1];
-                if (cnorm2(i) == 1) gi += cc(i, 0) != 0 ? R(cc(i, 0)) * hq[0] : R(cc(i, 1)) * hq[1];
-                g[i] = gi;
-            }
+            R gi = cg0 * g[i] + ga[d0] * A0[1][d1] + gh0[d0] * H0[1][d1] + gb[d0] * B0[1][d1] + gk[d0] * Hs[1][d1];
+            if (cnorm2(i) == 1) gi += cc(i, 0) != 0 ? R(cc(i, 0)) * hq[0] : R(cc(i, 1)) * hq[1];
+            g[i] = gi;
         }
     } else {
         // 3-D: per population (folding the xy products costs registers that the
@@ -458,7 +459,7 @@ __device__ __forceinline__ void collide_cell(const C& s, const Macro<R>& m, R di
                 gst += R(0.5) * cq;
             }
             f[i] = cf0 * f[i] + cf1 * feq + cf2 * fst;
-            if (!s.iso) g[i] = cg0 * g[i] + cg1 * geq + cg2 * gst;
+            g[i] = cg0 * g[i] + cg1 * geq + cg2 * gst;
         }
     }
 }

@@ -283,10 +283,10 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
                     idx = (unsigned)i * Ncell + (unsigned)xs[d0] + rows[d1][d2];
                 }
                 f[i] = Codec<S, R>::ld(fb + idx);
-                if (Codec<S, R>::offset) f[i] += s.fref[isrc];
-                if (!s.iso) {  // isothermal: g is not evolved
-                    gp[i] = Codec<S, R>::ld(gb + idx);
-                    if (Codec<S, R>::offset) gp[i] += s.gref[isrc];
+                gp[i] = Codec<S, R>::ld(gb + idx);
+                if (Codec<S, R>::offset) {
+                    f[i] += s.fref[isrc];
+                    gp[i] += s.gref[isrc];
                 }
             }
         };
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
                     const R fr = Codec<S, R>::offset ? s.fref[i] : R(0);
                     const R gr = Codec<S, R>::offset ? s.gref[i] : R(0);
                     Codec<S, R>::st(fo + (unsigned)i * Ncell + self, f[i] - fr);
-                    if (!s.iso) Codec<S, R>::st(go + (unsigned)i * Ncell + self, gp[i] - gr);
+                    Codec<S, R>::st(go + (unsigned)i * Ncell + self, gp[i] - gr);
                 }
             }
             // next-step moments: f'_i(x) becomes f_i(x + c_i), or f_opp(i)(x) across a z wall.
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
                         atomicAdd(&s_acc[dd], f[i]);
                         if (ci0 != 0) atomicAdd(&s_acc[n0 + dd], ci0 > 0 ? f[i] : -f[i]);
                         if (ci1 != 0) atomicAdd(&s_acc[2 * n0 + dd], ci1 > 0 ? f[i] : -f[i]);
-                        if (!s.iso) atomicAdd(&s_acc[3 * n0 + dd], gp[i]);
+                        atomicAdd(&s_acc[3 * n0 + dd], gp[i]);
                     }
                 }
             } else {
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
                             const int ca = cc(i, a);
                             if (ca != 0) atomicAdd(&s_acc[(1 + a) * n0 + dd], (ca > 0) != bounce ? f[i] : -f[i]);
                         }
-                        if (!s.iso) atomicAdd(&s_acc[(1 + D) * n0 + dd], gp[i]);
+                        atomicAdd(&s_acc[(1 + D) * n0 + dd], gp[i]);
                     }
                 }
             }
