@@ -145,6 +145,14 @@ void lbm_destroy(lbm_handle h);
  * legacy default stream. */
 int lbm_set_stream(lbm_handle h, void *stream);
 
+/* Replace the body acceleration a (F_B = rho a, Eq. force_decomposition) of
+ * every simulation of h from the next step on, for forcing that varies in
+ * time (the pulsatile flows of Sec. III.A use a cos(omega t)).  accel: 3
+ * doubles (host); a 2-D lattice ignores accel[2].  The update is enqueued on
+ * h's stream ahead of later steps; captured step graphs read it too.
+ * Errors: LBM_E_INVALID (NULL, non-finite values), LBM_E_CUDA. */
+int lbm_set_force(lbm_handle h, const double *accel);
+
 /* Initial state (flowchart, first box): f = f^eq(rho, u, theta), g = g^eq with
  * theta = P(rho,T)/rho and e = e(rho,T).  rho > 0 and T > 0 everywhere.  For
  * 16-bit storage the per-direction offsets f^ref, g^ref are the rest

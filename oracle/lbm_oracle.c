@@ -678,6 +678,13 @@ static void one_step(orc_state *s)
     if (!p->isothermal) { t = s->g; s->g = s->gn; s->gn = t; }  /* isothermal: g is not evolved */
 }
 
+/* Replace the body acceleration (F_B = rho a, Eq. force_decomposition) from
+ * the next step on: forcing that varies in time. */
+void orc_set_accel(orc_state *s, const double *a)
+{
+    for (int k = 0; k < 3; ++k) s->p.accel[k] = a[k];
+}
+
 int orc_step(orc_state *s, int n)
 {
     for (int it = 0; it < n; ++it) one_step(s);

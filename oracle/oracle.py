@@ -79,6 +79,7 @@ def lib():
             "orc_get_threads": (i, []),
             "orc_init": (i, [vp, dp, dp, dp]),
             "orc_step": (i, [vp, i]),
+            "orc_set_accel": (None, [vp, dp]),
             "orc_moments": (i, [vp, dp, dp, dp]),
             "orc_invariants": (i, [vp, dp]),
             "orc_populations": (i, [vp, dp, dp]),
@@ -239,6 +240,12 @@ class Oracle:
         out = np.zeros(2 * self.dim + 3)
         lib().orc_invariants(self._h, _dp(out))
         return out
+
+    def set_accel(self, accel):
+        a = np.ascontiguousarray(np.asarray(accel, dtype=np.float64).reshape(-1)[:3])
+        if a.size < 3:
+            a = np.concatenate([a, np.zeros(3 - a.size)])
+        lib().orc_set_accel(self._h, _dp(a))
 
     def populations(self):
         f = np.zeros((self.Q, self.N))

@@ -617,6 +617,24 @@ int lbm_set_stream(lbm_handle h, void* stream)
     return LBM_OK;
 }
 
+int lbm_set_force(lbm_handle h, const double* accel)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (!accel) return fail(h, LBM_E_INVALID, "accel is NULL");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(accel[a])) return fail(h, LBM_E_INVALID, "accel must be finite");
+    for (SimDev& d : h->sims) {
+        d.acc[0] = accel[0];
+        d.acc[1] = accel[1];
+        d.acc[2] = h->dim == 3 ? accel[2] : 0.0;
+    }
+    // every kernel reads the constants from d_sims at run time (graphs included);
+    // the host copy stays alive, so the stream-ordered copy needs no staging
+    LBM_CUDA_CHECK(h, cudaMemcpyAsync(h->d_sims, h->sims.data(), h->sims.size() * sizeof(SimDev),
+                                      cudaMemcpyHostToDevice, h->stream));
+    return LBM_OK;
+}
+
 int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T, int on_device)
 {
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");

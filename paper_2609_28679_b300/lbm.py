@@ -64,6 +64,7 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "lbm_destroy": (None, [ctypes.c_void_p]),
     "lbm_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_set_force": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -176,6 +177,13 @@ def lbm_set_stream(h, stream) -> None:
 
 def lbm_init(h, rho, u, T, on_device: int) -> None:
     _check(_lib.lbm_init(h, _ptr(rho), _ptr(u), _ptr(T), int(on_device)), h)
+
+
+def lbm_set_force(h, accel) -> None:
+    a = np.ascontiguousarray(np.asarray(accel, dtype=np.float64).reshape(-1)[:3])
+    if a.size < 3:
+        a = np.concatenate([a, np.zeros(3 - a.size)])
+    _check(_lib.lbm_set_force(h, a.ctypes.data), h)
 
 
 def lbm_step(h, n: int) -> None:

@@ -104,5 +104,6 @@ def test_isothermal_with_heat_source_rejected_without_device(lib):
 
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_E_INVALID
+    assert lib.lbm_set_force(None, None) == lbm.LBM_E_INVALID
     assert lib.lbm_invariants(None, None) == lbm.LBM_E_INVALID
     lib.lbm_destroy(None)

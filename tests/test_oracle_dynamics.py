@@ -251,6 +251,40 @@ def test_isothermal_poiseuille():
     assert np.all(T == T0)
 
 
+def _womersley(xi, t, g, omega, Wo):
+    # Womersley's pulsatile channel flow driven by a cos(omega t) (Sec. III.A), xi = x / L in [0, 1]
+    si = np.sqrt(1j)
+    prof = 1.0 - np.cosh(si * Wo * (xi - 0.5)) / np.cosh(si * Wo / 2.0)
+    return np.real(g / (1j * omega) * prof * np.exp(1j * omega * t))
+
+
+def test_isothermal_womersley():
+    # Isothermal pulsatile flow between half-way bounce-back walls at z = -1/2 and nz - 1/2 (L = nz),
+    # body acceleration g cos(omega t) set before every step, started from the analytic profile
+    # at t = 0 and compared one period later with nu = tau theta.
+    nz, tau, T0, g, Wo = 32, 0.8, 0.3, 1e-6, 4.0
+    nu = tau * T0
+    omega = Wo * Wo * nu / (nz * nz)
+    period = int(round(2 * math.pi / omega))
+    omega = 2 * math.pi / period
+    Wo = nz * math.sqrt(omega / nu)
+    xi = (np.arange(nz) + 0.5) / nz
+    c = wl.Case(name="womersley", dim=3, nx=1, ny=1, nz=nz, zwalls=1, eos="ideal", R=1.0, cv=2.5,
+                k_over_mu=3.5 / 0.71, tau_f=tau, tau_g=tau, isothermal=1, init=dict(kind="uniform", rho0=1.0, T0=T0))
+    u0 = np.zeros((3, nz))
+    u0[0] = _womersley(xi, 0.0, g, omega, Wo)
+    o = orc.Oracle(oracle_params(c))
+    o.init(np.ones(nz), u0, np.full(nz, T0))
+    for n in range(period):
+        o.set_accel((g * math.cos(omega * n), 0.0, 0.0))
+        o.step(1)
+        if n + 1 in (period // 4, period // 2, period):
+            ux = o.moments()[1][0]
+            ref = _womersley(xi, n + 1, g, omega, Wo)
+            err = np.sqrt(np.sum((ux - ref) ** 2) / np.sum(ref ** 2))
+            assert err <= 0.01, (n + 1, err)
+
+
 def test_isothermal_sound_speed():
     # Without the energy equation a density wave travels at the isothermal sound speed
     # c_T = sqrt((dP/drho)_T) = sqrt(R T) of the ideal gas, not the adiabatic sqrt(gamma R T).
