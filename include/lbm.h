@@ -154,9 +154,17 @@ int lbm_set_stream(lbm_handle h, void *stream);
 int lbm_set_force(lbm_handle h, const double *accel);
 
 /* Initial state (flowchart, first box): f = f^eq(rho, u, theta), g = g^eq with
- * theta = P(rho,T)/rho and e = e(rho,T).  rho > 0 and T > 0 everywhere.  For
- * 16-bit storage the per-direction offsets f^ref, g^ref are the rest
- * equilibria at the mean rho and mean T of the first simulation of the call. */
+ * theta = P(rho,T)/rho and e = e(rho,T).  rho [N], u [dim][N] and T [N]
+ * float64, N the total cells of the handle (simulations concatenated, u per
+ * simulation as dim planes of its cells); on_device 0: host memory (pinned
+ * memory is copied by DMA, pageable memory through the driver's staging),
+ * 1: device memory.  The caller keeps ownership; the call synchronises, so
+ * the buffers may be reused on return.  For 16-bit storage the per-direction
+ * offsets f^ref, g^ref are the rest equilibria at the mean rho and mean T of
+ * each simulation.  Errors: LBM_E_INVALID for a NULL field or for rho <= 0,
+ * T <= 0 or NaN in any cell (checked on the device for 32- and 64-bit
+ * storage); after any error the handle must be initialised again before it
+ * steps (LBM_E_STATE); LBM_E_NOMEM, LBM_E_CUDA. */
 int lbm_init(lbm_handle h, const double *rho, const double *u, const double *T, int on_device);
 
 /* Advance every simulation of h by n >= 0 time steps (enqueue only). */

@@ -118,7 +118,7 @@ template <int D, typename R, typename S> struct Impl {
     static int init(lbm_ctx* h, const double* rho, const double* u, const double* T)
     {
         k_init<D, R, S><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, rho, u, T, (S*)h->pop[0],
-                                                                   (R*)h->W, h->Ntot);
+                                                                   (R*)h->W, h->Ntot, h->d_diag + kDiagInitBad);
         LBM_LAUNCH_CHECK(h, "k_init");
         h->cur = 0;
         h->moments_valid = false;
@@ -531,7 +531,7 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
     h->pop[1] = dev_alloc(h, (size_t)pops * h->sbytes);
     h->W = dev_alloc(h, (size_t)W_NF * cells * h->rbytes);
     h->M = dev_alloc(h, (size_t)2 * M_NF * cells * h->rbytes);
-    h->d_diag = (unsigned long long*)dev_alloc(h, 4 * sizeof(unsigned long long));
+    h->d_diag = (unsigned long long*)dev_alloc(h, kDiagSlots * sizeof(unsigned long long));
     h->d_partials = (double*)dev_alloc(h, h->table.size() * nv * sizeof(double));
     if (!h->d_sims || !h->d_table || !h->d_sim_block_start || !h->pop[0] || !h->pop[1] || !h->W || !h->M ||
         !h->d_diag || !h->d_partials) {
@@ -549,7 +549,7 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
                         h->stream), "table upload");
     chk(cudaMemcpyAsync(h->d_sim_block_start, h->sim_block_start.data(), h->sim_block_start.size() * sizeof(int),
                         cudaMemcpyHostToDevice, h->stream), "table upload");
-    chk(cudaMemsetAsync(h->d_diag, 0, 4 * sizeof(unsigned long long), h->stream), "diag reset");
+    chk(cudaMemsetAsync(h->d_diag, 0, kDiagSlots * sizeof(unsigned long long), h->stream), "diag reset");
     chk(cudaMemsetAsync(h->W, 0, (size_t)W_NF * cells * h->rbytes, h->stream), "work reset");
     if (rc == LBM_OK) rc = upload_sims(h);
     if (rc == LBM_OK) {
@@ -639,27 +639,28 @@ int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T, 
 {
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
     if (!rho || !u || !T) return fail(h, LBM_E_INVALID, "rho, u and T are required");
+    h->initialized = false;  // whatever follows, the old state is gone or suspect
     const long long N = h->Ntot;
     const size_t nb_s = (size_t)N * sizeof(double), nb_v = (size_t)N * h->dim * sizeof(double);
-    std::vector<double> hr, hu, hT;
-    const double *dr = rho, *du = u, *dT = T;
-    void* tmp = nullptr;
-    if (!on_device || h->storage == LBM_BF16 || h->storage == LBM_F16) {
-        // host copies (inputs, or the means for the 16-bit storage offsets)
-        hr.resize(N); hu.resize((size_t)N * h->dim); hT.resize(N);
-        cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-        LBM_CUDA_CHECK(h, cudaMemcpyAsync(hr.data(), rho, nb_s, kind, h->stream));
-        LBM_CUDA_CHECK(h, cudaMemcpyAsync(hu.data(), u, nb_v, kind, h->stream));
-        LBM_CUDA_CHECK(h, cudaMemcpyAsync(hT.data(), T, nb_s, kind, h->stream));
-        LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+    const bool offsets = h->storage == LBM_BF16 || h->storage == LBM_F16;
+    if (offsets) {
+        // the 16-bit storage offsets are the rest equilibria at the mean rho
+        // and T: those two fields are read on the host, and checked there
+        std::vector<double> hr, hT;
+        const double *pr = rho, *pT = T;
+        if (on_device) {
+            hr.resize(N); hT.resize(N);
+            LBM_CUDA_CHECK(h, cudaMemcpyAsync(hr.data(), rho, nb_s, cudaMemcpyDeviceToHost, h->stream));
+            LBM_CUDA_CHECK(h, cudaMemcpyAsync(hT.data(), T, nb_s, cudaMemcpyDeviceToHost, h->stream));
+            LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+            pr = hr.data(); pT = hT.data();
+        }
         for (long long k = 0; k < N; ++k)
-            if (!(hr[k] > 0) || !(hT[k] > 0)) return fail(h, LBM_E_INVALID, "rho and T must be > 0 everywhere");
-    }
-    if (h->storage == LBM_BF16 || h->storage == LBM_F16) {
+            if (!(pr[k] > 0) || !(pT[k] > 0)) return fail(h, LBM_E_INVALID, "rho and T must be > 0 everywhere");
         for (int s = 0; s < h->nsim; ++s) {
             SimDev& d = h->sims[s];
             double mr = 0, mT = 0;
-            for (long long k = 0; k < d.N; ++k) { mr += hr[d.cell_off + k]; mT += hT[d.cell_off + k]; }
+            for (long long k = 0; k < d.N; ++k) { mr += pr[d.cell_off + k]; mT += pT[d.cell_off + k]; }
             mr /= (double)d.N;
             mT /= (double)d.N;
             RhoPart<double> p = rho_part<double>(d, mr);
@@ -672,21 +673,37 @@ int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T, 
         int rc = upload_sims(h);
         if (rc) return rc;
     }
+    // Host inputs go straight to a device staging buffer (a DMA when the
+    // caller's memory is pinned); k_init counts the cells with rho <= 0 or
+    // T <= 0 (or NaN) into diagnostic slot kDiagInitBad, read back below.
+    const double *dr = rho, *du = u, *dT = T;
+    void* tmp = nullptr;
     if (!on_device) {
         tmp = dev_alloc(h, 2 * nb_s + nb_v);
         if (!tmp) return fail(h, LBM_E_NOMEM, "staging allocation failed");
         double* t = (double*)tmp;
-        LBM_CUDA_CHECK(h, cudaMemcpyAsync(t, hr.data(), nb_s, cudaMemcpyHostToDevice, h->stream));
-        LBM_CUDA_CHECK(h, cudaMemcpyAsync(t + N, hT.data(), nb_s, cudaMemcpyHostToDevice, h->stream));
-        LBM_CUDA_CHECK(h, cudaMemcpyAsync(t + 2 * N, hu.data(), nb_v, cudaMemcpyHostToDevice, h->stream));
+        cudaError_t e = cudaMemcpyAsync(t, rho, nb_s, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t + N, T, nb_s, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t + 2 * N, u, nb_v, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(h->stream);
+            lbm_glue_free(tmp);
+            return cuda_fail(h, e, "lbm_init upload");
+        }
         dr = t; dT = t + N; du = t + 2 * N;
     }
-    LBM_CUDA_CHECK(h, cudaMemsetAsync(h->d_diag, 0, 4 * sizeof(unsigned long long), h->stream));
-    int rc = h->ops.init(h, dr, du, dT);
+    unsigned long long bad = 0;
+    cudaError_t e = cudaMemsetAsync(h->d_diag, 0, kDiagSlots * sizeof(unsigned long long), h->stream);
+    int rc = e == cudaSuccess ? h->ops.init(h, dr, du, dT) : cuda_fail(h, e, "diag reset");
+    if (rc == LBM_OK) {
+        e = cudaMemcpyAsync(&bad, h->d_diag + kDiagInitBad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "lbm_init check");
+    }
     cudaError_t se = cudaStreamSynchronize(h->stream);
     lbm_glue_free(tmp);
     if (rc) return rc;
     if (se != cudaSuccess) return cuda_fail(h, se, "lbm_init");
+    if (bad) return fail(h, LBM_E_INVALID, "rho and T must be > 0 everywhere");
     h->initialized = true;
     return LBM_OK;
 }

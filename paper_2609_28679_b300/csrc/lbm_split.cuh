@@ -21,6 +21,12 @@ enum MField { M_RHO = 0, M_J = 1, M_G = 4, M_T = 5, M_NF = 6 };
 
 constexpr int kBlockCells = 256;
 
+// device diagnostic counters: slots 0-3 are the ones lbm_diagnostics reports
+// (non-finite state, theta <= 0, Newton cap, learned-T fallback); slot 4
+// counts the cells lbm_init rejected (rho <= 0 or T <= 0, or NaN)
+constexpr int kDiagInitBad = 4;
+constexpr int kDiagSlots = 8;
+
 struct BlockEntry {
     int sim;
     int start;
@@ -78,7 +84,8 @@ template <int D, typename R, typename S>
 __global__ void __launch_bounds__(kBlockCells) k_init(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
                                                       const double* __restrict__ rho_in, const double* __restrict__ u_in,
                                                       const double* __restrict__ T_in, S* __restrict__ pop,
-                                                      R* __restrict__ W, long long Ntot)
+                                                      R* __restrict__ W, long long Ntot,
+                                                      unsigned long long* __restrict__ bad)
 {
     constexpr int Q = Lat<D>::Q;
     __shared__ SimDev s;
@@ -89,7 +96,9 @@ __global__ void __launch_bounds__(kBlockCells) k_init(const SimDev* __restrict__
     int x, y, z;
     cell_xyz(s, k, x, y, z);
     const long long gk = s.cell_off + k;
-    R rho = (R)rho_in[gk], T = (R)T_in[gk], u[3] = {0, 0, 0};
+    const double rho_d = rho_in[gk], T_d = T_in[gk];
+    if (!(rho_d > 0.0) || !(T_d > 0.0)) atomicAdd(bad, 1ull);
+    R rho = (R)rho_d, T = (R)T_d, u[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < D; ++a) u[a] = (R)u_in[(long long)D * s.cell_off + (long long)a * s.N + k];
     RhoPart<R> p = rho_part<R>(s, rho);
