@@ -48,6 +48,29 @@
  *    both f and g.  For the macroscopic stencils, cells beyond a wall mirror
  *    the interior: scalars (rho, lap rho, T, h) even, velocity odd, so X_z is
  *    odd.
+ *  - zwalls = 2, the non-equilibrium-extrapolation walls of Sec. IV (thermal
+ *    Couette): the walls lie on the boundary cells z = 0 and z = nz - 1 (B),
+ *    whose neighbours N are z = 1 and z = nz - 2.  After phases A-C of a step
+ *    (all cells, from their current populations), every B cell is rebuilt:
+ *    u_B = u_W, T_B = T_W, f_B = f^eq(rho_B, u_W, theta_W) +
+ *    f_N - f^eq(rho_N, u_N, theta_N) and g_B alike, with theta_W = P(rho_B,
+ *    T_W)/rho_B and e_W = e(rho_B, T_W).  The text extrapolates rho_B =
+ *    rho_N (wall_rho = 1); where T_W differs from T_N that sets a pressure
+ *    step P_B - P_N across the wall link, mass leaks through the wall and the
+ *    thermal Couette profile misses the paper's analytic one by a margin that
+ *    does not shrink with resolution.  The default (wall_rho = 0) extrapolates
+ *    the pressure instead, rho_B solving P(rho_B, T_W) = P(rho_N, T_N) by
+ *    eight Newton steps from rho_N (rho_N again if that ends non-finite or
+ *    non-positive), which is the text's rho_B = rho_N wherever T_W = T_N and
+ *    converges to the analytic profile at second order.  Its phase-C fields become those of
+ *    the wall state and its force keeps the per-mass value of phase B
+ *    (F_B scaled by the new rho_B over the old).  Phases D-E then run on all
+ *    cells, B included.  A stencil reaching past a wall takes the value
+ *    extrapolated linearly through the boundary cell, v(z_B - m) =
+ *    2 v(z_B) - v(z_B + m) (mirrored for the upper wall), for every field.
+ *    Populations streaming out through a wall face return reversed (as with
+ *    zwalls = 1); B is rebuilt before they are used.  The moments reported
+ *    for a B cell are the rebuilt ones.  Not combined with isothermal = 1.
  *  - Peng-Robinson: the paper names the model only.  The textbook form with the
  *    Soave alpha(T) and a constant ideal-part c_v is used; e(rho,T) follows by
  *    integrating Eq. de_rho at constant T from rho = 0.  T(rho,e) is found by
@@ -70,7 +93,8 @@
 typedef struct {
     int dim;            /* 2 or 3 */
     int nx, ny, nz;     /* nz = 1 when dim = 2 */
-    int zwalls;         /* 0: periodic in z; 1: half-way bounce-back walls at both z faces */
+    int zwalls;         /* 0: periodic in z; 1: half-way bounce-back walls at both z faces;
+                           2: non-equilibrium-extrapolation walls on the cells z = 0 and z = nz - 1 */
     int eos;            /* ORC_IDEAL, ORC_VDW, ORC_PR */
     double R, cv;       /* gas constant; constant (ideal-part) specific heat */
     double a, b;        /* vdW / PR attraction and co-volume */
@@ -87,6 +111,9 @@ typedef struct {
                            0: constant tau_f, tau_g */
     int isothermal;     /* 1: the g equation is not solved (Sec. III.A, isothermal tests); every cell
                            keeps its initial temperature, e = e(rho, T) from the EoS */
+    double uw_lo[3], uw_hi[3]; /* zwalls = 2: velocities of the walls at z = 0 and z = nz - 1 */
+    double Tw_lo, Tw_hi;       /* zwalls = 2: their temperatures */
+    int wall_rho;              /* zwalls = 2: 0: rho_B from P(rho_B, T_W) = P_N; 1: rho_B = rho_N */
 } orc_params;
 
 typedef struct {
@@ -348,6 +375,8 @@ orc_state *orc_create(const orc_params *p)
 {
     if (!p || (p->dim != 2 && p->dim != 3) || p->nx < 1 || p->ny < 1 || p->nz < 1) return NULL;
     if (p->dim == 2 && (p->nz != 1 || p->zwalls)) return NULL;
+    if (p->zwalls < 0 || p->zwalls > 2) return NULL;
+    if (p->zwalls == 2 && (p->nz < 4 || p->isothermal || !(p->Tw_lo > 0) || !(p->Tw_hi > 0))) return NULL;
     orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
     s->p = *p;
     int cflat[81];
@@ -421,10 +450,21 @@ static long stencil_idx(const orc_state *s, int x, int y, int z, int *mirrored)
     return cidx(s, x, y, z);
 }
 
+/* Value past a non-equilibrium-extrapolation wall (zwalls = 2): linear
+ * extrapolation through the boundary cell, 2 v(z_B) - v(2 z_B - z). */
+static double nee_ghost(const orc_state *s, const double *fld, int x, int y, int z)
+{
+    int zb = z < 0 ? 0 : s->p.nz - 1;
+    x = wrap(x, s->p.nx);
+    y = wrap(y, s->p.ny);
+    return 2.0 * fld[cidx(s, x, y, zb)] - fld[cidx(s, x, y, 2 * zb - z)];
+}
+
 /* scalar field value at the neighbour (x+dx, y+dy, z+dz) (even mirror) */
 static inline double nb_scalar(const orc_state *s, const double *fld, int x, int y, int z, int dx, int dy, int dz)
 {
     int m;
+    if (s->p.zwalls == 2 && (z + dz < 0 || z + dz >= s->p.nz)) return nee_ghost(s, fld, x + dx, y + dy, z + dz);
     return fld[stencil_idx(s, x + dx, y + dy, z + dz, &m)];
 }
 
@@ -432,6 +472,8 @@ static inline double nb_scalar(const orc_state *s, const double *fld, int x, int
 static inline double nb_vector(const orc_state *s, const double *fld, int a, int x, int y, int z, int dx, int dy, int dz)
 {
     int m;
+    if (s->p.zwalls == 2 && (z + dz < 0 || z + dz >= s->p.nz))
+        return nee_ghost(s, fld + (long)a * s->N, x + dx, y + dy, z + dz);
     long k = stencil_idx(s, x + dx, y + dy, z + dz, &m);
     double v = fld[(long)a * s->N + k];
     return m ? -v : v;
@@ -572,6 +614,71 @@ static void macro_fields(orc_state *s)
 }
 
 /* ------------------------------------------------------------------------- */
+/* Non-equilibrium-extrapolation walls (zwalls = 2; Sec. IV, thermal Couette): */
+/* rebuild the boundary cells from the wall state and the non-equilibrium    */
+/* part of their neighbours, after phases A-C.  pops = 0 rebuilds only the    */
+/* macroscopic fields (for the reported moments).                             */
+/* ------------------------------------------------------------------------- */
+static void nee_walls(orc_state *s, int pops)
+{
+    const orc_params *p = &s->p;
+    if (p->zwalls != 2) return;
+    int D = p->dim, Q = s->Q;
+    long N = s->N;
+    for (int side = 0; side < 2; ++side) {
+        int zb = side ? p->nz - 1 : 0, zn = side ? p->nz - 2 : 1;
+        const double *uw = side ? p->uw_hi : p->uw_lo;
+        double Tw = side ? p->Tw_hi : p->Tw_lo;
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long kb = cidx(s, x, y, zb), kn = cidx(s, x, y, zn);
+                double rn = s->rho[kn], un[3], uW[3] = {0, 0, 0}, xi[3], zeta[3];
+                for (int a = 0; a < 3; ++a) un[a] = s->u[(long)a * N + kn];
+                for (int a = 0; a < D; ++a) uW[a] = uw[a];
+                /* wall state: rho_B (from rho_N or from P_N), u_W, T_W */
+                double rb = rn;
+                if (p->wall_rho == 0) {
+                    double PN = orc_eos_P(p, rn, s->T[kn]), r = rn;
+                    for (int it = 0; it < 8; ++it) r -= (orc_eos_P(p, r, Tw) - PN) / orc_eos_dPdrho(p, r, Tw);
+                    if (isfinite(r) && r > 0.0) rb = r;
+                }
+                double Pw = orc_eos_P(p, rb, Tw), thw = Pw / rb, ew = orc_eos_e(p, rb, Tw);
+                if (pops) {
+                    double feqB[27], geqB[27], feqN[27], geqN[27];
+                    for (int a = 0; a < D; ++a) { xi[a] = uW[a]; zeta[a] = thw + uW[a] * uW[a]; }
+                    orc_fprod(D, rb, xi, zeta, feqB);
+                    orc_geq(D, rb, uW, ew, thw, geqB);
+                    for (int a = 0; a < D; ++a) { xi[a] = un[a]; zeta[a] = s->theta[kn] + un[a] * un[a]; }
+                    orc_fprod(D, rn, xi, zeta, feqN);
+                    orc_geq(D, rn, un, s->e[kn], s->theta[kn], geqN);
+                    for (int i = 0; i < Q; ++i) {
+                        s->f[(long)i * N + kb] = feqB[i] + (s->f[(long)i * N + kn] - feqN[i]);
+                        s->g[(long)i * N + kb] = geqB[i] + (s->g[(long)i * N + kn] - geqN[i]);
+                    }
+                }
+                double scale = rb / s->rho[kb], u2 = 0;
+                for (int a = 0; a < 3; ++a) s->F[(long)a * N + kb] *= scale;
+                for (int a = 0; a < D; ++a) u2 += uW[a] * uW[a];
+                for (int a = 0; a < 3; ++a) s->u[(long)a * N + kb] = uW[a];
+                double cv = orc_eos_cv(p, rb, Tw), PT = orc_eos_dPdT(p, rb, Tw), Pr = orc_eos_dPdrho(p, rb, Tw);
+                double cs2 = Pr + Tw * PT * PT / (rb * rb * cv);
+                s->rho[kb] = rb;
+                s->T[kb] = Tw;
+                s->e[kb] = ew;
+                s->E[kb] = ew + 0.5 * u2;
+                s->P[kb] = Pw;
+                s->theta[kb] = thw;
+                s->h[kb] = ew + Pw / rb;
+                s->cvl[kb] = cv;
+                s->gam[kb] = 1.0 + PT / (rb * cv);
+                s->athe[kb] = ((double)(D + 2) / D - p->eta_over_mu) * thw - cs2;
+                for (int a = 0; a < 3; ++a)
+                    s->X[(long)a * N + kb] = (a < D) ? rb * uW[a] * uW[a] * uW[a] + 3.0 * rb * uW[a] * (thw - 1.0 / 3.0) : 0.0;
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* One time step                                                              */
 /* ------------------------------------------------------------------------- */
 static void one_step(orc_state *s)
@@ -584,6 +691,7 @@ static void one_step(orc_state *s)
     double beta_g = 1.0 / (2.0 * p->tau_g + 1.0);
 
     macro_fields(s);
+    nee_walls(s, 1);
 
 #pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < nz; ++z)
@@ -695,6 +803,7 @@ int orc_step(orc_state *s, int n)
 int orc_moments(orc_state *s, double *rho, double *u /* [dim][N] */, double *T)
 {
     macro_fields(s);
+    nee_walls(s, 0);
     long N = s->N;
     for (long k = 0; k < N; ++k) {
         if (rho) rho[k] = s->rho[k];
@@ -711,6 +820,7 @@ int orc_moments(orc_state *s, double *rho, double *u /* [dim][N] */, double *T)
 int orc_invariants(orc_state *s, double *out)
 {
     macro_fields(s);
+    nee_walls(s, 0);
     int D = s->p.dim;
     long N = s->N;
     double m = 0, M[3] = {0, 0, 0}, En = 0, Fs[3] = {0, 0, 0}, S = 0;

@@ -48,6 +48,9 @@ class OrcParams(ctypes.Structure):
         ("phi_central", ctypes.c_int),
         ("mu", ctypes.c_double),
         ("isothermal", ctypes.c_int),
+        ("uw_lo", ctypes.c_double * 3), ("uw_hi", ctypes.c_double * 3),
+        ("Tw_lo", ctypes.c_double), ("Tw_hi", ctypes.c_double),
+        ("wall_rho", ctypes.c_int),
     ]
 
 
@@ -101,9 +104,13 @@ def _dp(a: np.ndarray):
 def make_params(dim=2, nx=8, ny=8, nz=1, zwalls=0, eos="ideal", R=1.0, cv=2.5, a=0.0, b=0.0,
                 Tc=1.0, omega=0.0, Pc=None, kappa=0.0, eta_over_mu=0.0, k_over_mu=0.0,
                 tau_f=0.8, tau_g=0.8, accel=(0.0, 0.0, 0.0), q=0.0, zlo=0, zhi=0,
-                phi_central=0, mu=0.0, isothermal=0) -> OrcParams:
+                phi_central=0, mu=0.0, isothermal=0, uw_lo=(0.0, 0.0, 0.0), uw_hi=(0.0, 0.0, 0.0),
+                Tw_lo=0.0, Tw_hi=0.0, wall_rho=0) -> OrcParams:
     """Build the oracle's parameter struct.  For Peng-Robinson with ``Pc`` given
-    and ``a == 0``, a and b follow from (Tc, Pc) by the oracle's own helper."""
+    and ``a == 0``, a and b follow from (Tc, Pc) by the oracle's own helper.
+    zwalls = 2 selects the non-equilibrium-extrapolation walls with wall
+    velocities uw_lo, uw_hi and temperatures Tw_lo, Tw_hi; wall_rho picks the
+    boundary density (0: from the neighbour's pressure, 1: the neighbour's)."""
     kind = _EOS_NAMES[eos] if isinstance(eos, str) else int(eos)
     if kind == PR and a == 0.0 and Pc is not None:
         a, b = pr_from_critical(R, Tc, Pc)
@@ -118,6 +125,11 @@ def make_params(dim=2, nx=8, ny=8, nz=1, zwalls=0, eos="ideal", R=1.0, cv=2.5, a
     p.phi_central = int(phi_central)
     p.mu = float(mu)
     p.isothermal = int(isothermal)
+    for k in range(3):
+        p.uw_lo[k] = uw_lo[k] if k < len(uw_lo) else 0.0
+        p.uw_hi[k] = uw_hi[k] if k < len(uw_hi) else 0.0
+    p.Tw_lo, p.Tw_hi = float(Tw_lo), float(Tw_hi)
+    p.wall_rho = int(wall_rho)
     return p
 
 
@@ -278,4 +290,6 @@ def params_from_case(case) -> OrcParams:
                        kappa=case.kappa, eta_over_mu=case.eta_over_mu, k_over_mu=case.k_over_mu,
                        tau_f=case.tau_f, tau_g=case.tau_g, accel=case.accel, q=case.q,
                        zlo=case.zlo, zhi=case.zhi, phi_central=case.phi_central, mu=getattr(case, "mu", 0.0),
-                       isothermal=getattr(case, "isothermal", 0))
+                       isothermal=getattr(case, "isothermal", 0), uw_lo=getattr(case, "uw_lo", (0.0, 0.0, 0.0)),
+                       uw_hi=getattr(case, "uw_hi", (0.0, 0.0, 0.0)), Tw_lo=getattr(case, "Tw_lo", 0.0),
+                       Tw_hi=getattr(case, "Tw_hi", 0.0), wall_rho=getattr(case, "wall_rho", 0))

@@ -63,6 +63,11 @@ class Case:
     mu: float = 0.0               # > 0: tau = mu / P per cell (one tau for f and g); 0: tau_f, tau_g
     isothermal: int = 0           # 1: g not evolved, every cell keeps its initial T
     t_solver: int = 0             # Peng-Robinson T(rho, e): 0 Newton, 1 learned start + Newton
+    uw_lo: tuple = (0.0, 0.0, 0.0)  # zwalls = 2 (non-equilibrium-extrapolation walls on z = 0, nz - 1):
+    uw_hi: tuple = (0.0, 0.0, 0.0)  # wall velocities,
+    Tw_lo: float = 0.0              # wall temperatures,
+    Tw_hi: float = 0.0
+    wall_rho: int = 0               # and boundary density: 0 from the neighbour's pressure, 1 the neighbour's
     storage: str = "f64"          # f64 | f32 | bf16 | f16
     steps: int = 100
     init: dict = field(default_factory=dict)
@@ -120,13 +125,30 @@ def _droplet(c: Case):
     return rho, np.zeros((c.dim, c.ncell)), np.full(c.ncell, c.init["T0"])
 
 
+def _couette(c: Case):
+    """Linear u_x and T between the wall cells z = 0 and z = nz - 1 (their
+    wall values), rho = rho_ref T_ref / T (uniform rho T), plus seeded noise of
+    relative size amp on rho (default 0)."""
+    _, _, z = _coords(c)
+    s = z / (c.nz - 1)
+    T = c.Tw_lo + (c.Tw_hi - c.Tw_lo) * s
+    u = np.zeros((c.dim, c.ncell))
+    for a in range(c.dim):
+        u[a] = c.uw_lo[a] + (c.uw_hi[a] - c.uw_lo[a]) * s
+    rho = c.init.get("rho0", 1.0) * c.Tw_lo / T
+    amp = c.init.get("amp", 0.0)
+    if amp:
+        rho = rho * (1.0 + amp * uniform_pm1(c.init.get("seed", 1), c.ncell))
+    return rho, u, T
+
+
 def _uniform(c: Case):
     return (np.full(c.ncell, c.init.get("rho0", 1.0)), np.zeros((c.dim, c.ncell)),
             np.full(c.ncell, c.init.get("T0", 0.3)))
 
 
 _FIELDS = {"waves": _waves, "noisy_density": _noisy_density, "noisy_temperature": _noisy_temperature,
-           "droplet": _droplet, "uniform": _uniform}
+           "droplet": _droplet, "uniform": _uniform, "couette": _couette}
 
 # van der Waals fluid of the 2-D multiphase cases.  b = 2/21 (rho_c = 3.5) and
 # R/c_v = 0.4 as in the nitrogen table; a = 9/245 puts Tc = 4/35, i.e. the

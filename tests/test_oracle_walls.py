@@ -1,0 +1,110 @@
+"""Pins of the oracle's non-equilibrium-extrapolation walls (zwalls = 2; the
+wall treatment of Sec. IV): the thermal Couette flow against the paper's
+analytic temperature profile (Sec. IV, with the Prandtl and Eckert numbers of
+the text), its second-order convergence, the exact linear velocity, the rest
+state kept exactly, the pressure match of the boundary density, and the mass
+that the text's literal rho_B = rho_N lets through a wall with a temperature
+step."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2609_28679_b300 import workloads as wl
+from tests.util import run_oracle
+
+CV, RG = 2.5, 1.0
+CP = CV + RG  # ideal gas
+
+
+def _couette(nz, U, Pr, TC=0.33, dT=0.0, eos="ideal", wall_rho=0, **kw):
+    return wl.Case(name="couette", dim=3, nx=1, ny=1, nz=nz, zwalls=2, eos=eos, R=RG, cv=CV,
+                   k_over_mu=CP / Pr, tau_f=0.8, tau_g=0.8, phi_central=1, uw_hi=(U, 0.0, 0.0),
+                   Tw_lo=TC, Tw_hi=TC + dT, wall_rho=wall_rho, init=dict(kind="couette", rho0=3.0), **kw)
+
+
+def _analytic_T(c, xi):
+    # (T - T_C)/(T_H - T_C) = xi + (Pr Ec / 2) xi (1 - xi) with Pr Ec = mu U^2 / (k (T_H - T_C)):
+    # T = T_C + (T_H - T_C) xi + U^2 / (2 k/mu) xi (1 - xi)
+    U = c.uw_hi[0]
+    return c.Tw_lo + (c.Tw_hi - c.Tw_lo) * xi + U * U / (2.0 * c.k_over_mu) * xi * (1.0 - xi)
+
+
+def _steady(c, steps):
+    o = run_oracle(c, steps)
+    rho, u, T = o.moments()
+    return o, rho, u, T
+
+
+@pytest.mark.parametrize("Pr,dT", [(0.5, 0.0), (2.0, 0.0), (1.0, 0.02)])
+def test_thermal_couette_matches_analytic_profile(Pr, dT):
+    # Ec = U^2 / (c_p (T_H - T_C)) = 2 for dT = 0.02 (Ec infinite for equal wall temperatures)
+    c = _couette(17, 0.2, Pr, dT=dT)
+    o, rho, u, T = _steady(c, 4000)
+    xi = np.arange(c.nz) / (c.nz - 1)
+    bump = 0.2 ** 2 / (8.0 * c.k_over_mu)
+    assert np.max(np.abs(T - _analytic_T(c, xi))) <= 0.01 * bump
+    # a dropped viscous-heating term or wall temperature would miss by the whole bump
+    assert T[c.nz // 2] - (c.Tw_lo + 0.5 * dT) == pytest.approx(bump, rel=0.01)
+    # plane Couette: u_x linear between the walls, no wall-normal flow
+    assert np.max(np.abs(u[0] - 0.2 * xi)) <= 1e-12
+    assert np.max(np.abs(u[2])) <= 1e-12
+
+
+def test_thermal_couette_converges_at_second_order():
+    errs = []
+    for nz, steps in [(9, 1500), (17, 4000)]:
+        c = _couette(nz, 0.2, 2.0)
+        _, _, _, T = _steady(c, steps)
+        xi = np.arange(nz) / (nz - 1)
+        errs.append(np.max(np.abs(T - _analytic_T(c, xi))))
+    assert errs[0] / errs[1] == pytest.approx(4.0, rel=0.15)
+
+
+@pytest.mark.parametrize("wall_rho", [0, 1])
+def test_rest_state_at_wall_temperature_is_kept(wall_rho):
+    # uniform rho, u = 0 and T = T_W everywhere is a steady state of the walls: nothing moves
+    c = wl.Case(name="rest", dim=3, nx=3, ny=2, nz=6, zwalls=2, eos="vdw", R=1.0, cv=2.5, a=9 / 245,
+                b=2 / 21, k_over_mu=3.5, Tw_lo=0.4, Tw_hi=0.4, wall_rho=wall_rho,
+                init=dict(kind="uniform", rho0=1.3, T0=0.4))
+    o = run_oracle(c, 50)
+    rho, u, T = o.moments()
+    assert np.max(np.abs(rho - 1.3)) <= 1e-13
+    assert np.max(np.abs(u)) <= 1e-14
+    assert np.max(np.abs(T - 0.4)) <= 1e-13
+
+
+def test_boundary_density_matches_the_neighbour_pressure():
+    # wall_rho = 0: P(rho_B, T_W) = P(rho_N, T_N) on both walls, here for van der Waals with
+    # noisy density, a body force and different wall temperatures
+    c = wl.Case(name="walls", dim=3, nx=4, ny=3, nz=8, zwalls=2, eos="vdw", R=1.0, cv=2.5, a=9 / 245,
+                b=2 / 21, kappa=0.01, k_over_mu=3.5, accel=(1e-5, 0.0, -1e-5), phi_central=1,
+                uw_lo=(0.0, 0.01, 0.0), uw_hi=(0.02, 0.0, 0.0), Tw_lo=0.4, Tw_hi=0.43,
+                init=dict(kind="couette", rho0=1.5, amp=0.02, seed=5))
+    o = run_oracle(c, 30)
+    rho, u, T = o.moments()
+    p = o.p
+    N = c.nx * c.ny
+    for zb, zn, Tw, uw in [(0, 1, 0.4, c.uw_lo), (c.nz - 1, c.nz - 2, 0.43, c.uw_hi)]:
+        for k in range(N):
+            kb, kn = zb * N + k, zn * N + k
+            PB = orc.lib().orc_eos_P(p, rho[kb], T[kb])
+            PN = orc.lib().orc_eos_P(p, rho[kn], T[kn])
+            assert PB == pytest.approx(PN, rel=1e-13)
+            assert T[kb] == Tw
+            assert np.allclose(u.reshape(3, -1)[:, kb], uw, atol=0.0, rtol=0.0)
+
+
+def test_literal_neighbour_density_leaks_mass_through_a_heated_wall():
+    # wall_rho = 1 (rho_B = rho_N as the text states it): with T_W != T_N the wall link carries a
+    # pressure step, so the channel keeps losing mass and a wall-normal flow remains; the pressure
+    # match (wall_rho = 0) settles with no flow through the walls
+    lost = {}
+    for wall_rho in (0, 1):
+        c = _couette(17, 0.02, 1.0, dT=0.02, wall_rho=wall_rho)
+        o = run_oracle(c, 3000)
+        m0 = o.moments()[0].sum()
+        o.step(1000)
+        rho, u, T = o.moments()
+        lost[wall_rho] = (m0 - rho.sum()) / m0, np.max(np.abs(u[2]))
+    assert abs(lost[0][0]) <= 1e-12 and lost[0][1] <= 1e-12
+    assert lost[1][0] > 1e-5 and lost[1][1] > 1e-5
