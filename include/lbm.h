@@ -84,7 +84,9 @@ typedef struct lbm_ctx *lbm_handle;
 typedef struct {
     int dim;        /* 2 -> D2Q9, 3 -> D3Q27                                   */
     int nx, ny, nz; /* cells; nz = 1 when dim = 2                             */
-    int zwalls;     /* 0: periodic in z; 1: half-way bounce-back at both z faces (dim 3) */
+    int zwalls;     /* 0: periodic in z; 1: half-way bounce-back at both z faces (dim 3);
+                       2: non-equilibrium-extrapolation walls on the cells z = 0 and z = nz - 1
+                       (dim 3, nz >= 4; wall state from lbm_set_walls; split kernels) */
     int storage;    /* LBM_F64 | LBM_F32 | LBM_BF16 | LBM_F16                  */
     int phi_scheme; /* LBM_PHI_UPWIND | LBM_PHI_CENTRAL                        */
 } lbm_lattice;
@@ -152,6 +154,25 @@ int lbm_set_stream(lbm_handle h, void *stream);
  * h's stream ahead of later steps; captured step graphs read it too.
  * Errors: LBM_E_INVALID (NULL, non-finite values), LBM_E_CUDA. */
 int lbm_set_force(lbm_handle h, const double *accel);
+
+/* Wall state of the non-equilibrium-extrapolation walls (zwalls = 2), the
+ * wall treatment of the thermal Couette flow (Sec. IV), for every simulation
+ * of h that has them.  The walls lie on the boundary cells z = 0 (u_lo, T_lo)
+ * and z = nz - 1 (u_hi, T_hi).  Each step, after the macroscopic pass, a
+ * boundary cell B with neighbour N (z = 1, nz - 2) is rebuilt as
+ *   f_B = f^eq(rho_B, u_W, theta(rho_B, T_W)) + f_N - f^eq(rho_N, u_N, theta_N)
+ * and g_B alike, then collides like any cell.  rho_B: wall_rho 1 takes
+ * rho_N as the text states; wall_rho 0 (recommended) solves
+ * P(rho_B, T_W) = P(rho_N, T_N) by eight Newton steps from rho_N, which is
+ * rho_N wherever T_W = T_N and keeps mass from leaking through a wall whose
+ * temperature differs from its neighbour's.  Stencils past a wall use the
+ * linear extrapolation through the boundary cell, 2 v(z_B) - v(2 z_B - z).
+ * u_lo, u_hi: 3 doubles (host); T_lo, T_hi > 0.  Stepping a handle with such
+ * walls before this call fails with LBM_E_STATE; only the split kernels run
+ * them (lbm_set_kernel: LBM_E_UNSUPPORTED for the others).  Errors:
+ * LBM_E_INVALID (NULL, non-finite, T <= 0, wall_rho not 0/1), LBM_E_STATE
+ * (no such walls in h), LBM_E_CUDA. */
+int lbm_set_walls(lbm_handle h, const double *u_lo, double T_lo, const double *u_hi, double T_hi, int wall_rho);
 
 /* Initial state (flowchart, first box): f = f^eq(rho, u, theta), g = g^eq with
  * theta = P(rho,T)/rho and e = e(rho,T).  rho [N], u [dim][N] and T [N]

@@ -95,6 +95,14 @@ int cuda_fail(lbm_ctx* h, cudaError_t e, const char* where)
 
 void* dev_alloc(lbm_ctx* h, size_t n) { return lbm_glue_alloc(n, (void*)h->stream); }
 
+// some simulation of h has non-equilibrium-extrapolation walls (split kernels only)
+bool has_nee(const lbm_ctx* h)
+{
+    for (const SimDev& d : h->sims)
+        if (d.zwalls == 2) return true;
+    return false;
+}
+
 cudaError_t fused_dispatch(int storage, int dim, int eos, int mlp, int pc, int tx, int ty, int tz, const SimDev* sims,
                            const TileEntry* tiles, int ntiles, const void* src, void* dst, const void* Min, void* Mout,
                            long long Ntot, unsigned long long* diag, cudaStream_t stream);
@@ -132,6 +140,8 @@ template <int D, typename R, typename S> struct Impl {
         S* dst = (S*)h->pop[h->cur ^ 1];
         k_moments<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, src, (R*)h->W, h->Ntot);
         k_macro<D, R><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot, h->d_diag);
+        if (D == 3 && has_nee(h))
+            k_nee<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, src, (R*)h->W, h->Ntot, 1);
         k_collide<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, src, dst, (const R*)h->W, h->Ntot);
         LBM_LAUNCH_CHECK(h, "split step");
         h->cur ^= 1;
@@ -192,6 +202,8 @@ template <int D, typename R, typename S> struct Impl {
 
     static int step(lbm_ctx* h, int n)
     {
+        for (const SimDev& d : h->sims)
+            if (d.zwalls == 2 && !d.walls_set) return fail(h, LBM_E_STATE, "lbm_set_walls has not been called");
         for (int it = 0; it < n; ++it) {
             int rc = h->variant == LBM_KERNEL_FUSED ? fused_step(h)
                      : h->variant == LBM_KERNEL_ZMARCH ? zmarch_step(h) : split_step(h);
@@ -203,10 +215,15 @@ template <int D, typename R, typename S> struct Impl {
     // moments and macroscopic fields of the current state into W (no counters)
     static int macro(lbm_ctx* h)
     {
+        for (const SimDev& d : h->sims)
+            if (d.zwalls == 2 && !d.walls_set) return fail(h, LBM_E_STATE, "lbm_set_walls has not been called");
         const int nb = nblocks(h);
         k_moments<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (const S*)h->pop[h->cur],
                                                               (R*)h->W, h->Ntot);
         k_macro<D, R><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot, nullptr);
+        if (D == 3 && has_nee(h))
+            k_nee<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (S*)h->pop[h->cur], (R*)h->W,
+                                                              h->Ntot, 0);
         LBM_LAUNCH_CHECK(h, "macro");
         return LBM_OK;
     }
@@ -256,6 +273,7 @@ template <int D, typename R, typename S> struct Impl {
 
     static int fused_ok(lbm_ctx* h, int tx, int ty, int tz)
     {
+        if (has_nee(h)) return 0;  // non-equilibrium-extrapolation walls: split kernels only
         for (const SimDev& d : h->sims)
             if (d.eos != h->sims[0].eos) return 0;  // one equation of state per fused launch
         if (uses_mlp(h) && h->storage != LBM_F32) return 0;  // learned start built for float32 storage
@@ -373,7 +391,8 @@ int check_lattice(const lbm_lattice* L, std::string& why)
         why = "too many cells: Q * cells must stay below 2^32 per simulation";
         return LBM_E_INVALID;
     }
-    if (L->zwalls != 0 && L->zwalls != 1) { why = "zwalls must be 0 or 1"; return LBM_E_INVALID; }
+    if (L->zwalls < 0 || L->zwalls > 2) { why = "zwalls must be 0, 1 or 2"; return LBM_E_INVALID; }
+    if (L->zwalls == 2 && L->nz < 4) { why = "non-equilibrium-extrapolation walls need nz >= 4"; return LBM_E_INVALID; }
     if (L->storage < LBM_F64 || L->storage > LBM_F16) { why = "unknown storage"; return LBM_E_INVALID; }
     if (L->phi_scheme != LBM_PHI_UPWIND && L->phi_scheme != LBM_PHI_CENTRAL) { why = "unknown phi_scheme"; return LBM_E_INVALID; }
     return LBM_OK;
@@ -392,6 +411,7 @@ int fill_sim(SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, do
     if (E->isothermal != 0 && E->isothermal != 1) { why = "isothermal must be 0 or 1"; return LBM_E_INVALID; }
     if (E->isothermal && E->t_solver == LBM_T_MLP) { why = "isothermal runs invert no temperature"; return LBM_E_INVALID; }
     if (E->isothermal && H && H->q != 0.0) { why = "isothermal runs take no heat source"; return LBM_E_INVALID; }
+    if (E->isothermal && L->zwalls == 2) { why = "non-equilibrium-extrapolation walls set a temperature: not isothermal"; return LBM_E_INVALID; }
     s.nx = L->nx; s.ny = L->ny; s.nz = L->nz; s.zwalls = L->zwalls;
     s.N = (long long)L->nx * L->ny * L->nz;
     s.eos = E->kind;
@@ -558,7 +578,7 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
         fused_default_tile(h->dim, h->storage, dtx, dty, dtz);
         bool same_eos = true;
         for (const SimDev& d : h->sims) same_eos = same_eos && d.eos == h->sims[0].eos;
-        if (h->dim == 3 && same_eos && zmarch_shape(h->storage, 30, 14)) {
+        if (h->dim == 3 && same_eos && !has_nee(h) && zmarch_shape(h->storage, 30, 14)) {
             h->variant = LBM_KERNEL_ZMARCH;
             h->tx = 30; h->ty = 14; h->tz = 32;
             rc = build_tiles(h, 30, 14, 32);
@@ -630,6 +650,29 @@ int lbm_set_force(lbm_handle h, const double* accel)
     }
     // every kernel reads the constants from d_sims at run time (graphs included);
     // the host copy stays alive, so the stream-ordered copy needs no staging
+    LBM_CUDA_CHECK(h, cudaMemcpyAsync(h->d_sims, h->sims.data(), h->sims.size() * sizeof(SimDev),
+                                      cudaMemcpyHostToDevice, h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_walls(lbm_handle h, const double* u_lo, double T_lo, const double* u_hi, double T_hi, int wall_rho)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (!u_lo || !u_hi) return fail(h, LBM_E_INVALID, "wall velocities are NULL");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(u_lo[a]) || !std::isfinite(u_hi[a])) return fail(h, LBM_E_INVALID, "wall velocities must be finite");
+    if (!(T_lo > 0) || !(T_hi > 0) || !std::isfinite(T_lo) || !std::isfinite(T_hi))
+        return fail(h, LBM_E_INVALID, "wall temperatures must be finite and > 0");
+    if (wall_rho != 0 && wall_rho != 1) return fail(h, LBM_E_INVALID, "wall_rho must be 0 or 1");
+    if (!has_nee(h)) return fail(h, LBM_E_STATE, "no simulation of the handle has non-equilibrium-extrapolation walls");
+    for (SimDev& d : h->sims) {
+        if (d.zwalls != 2) continue;
+        for (int a = 0; a < 3; ++a) { d.uw[0][a] = u_lo[a]; d.uw[1][a] = u_hi[a]; }
+        d.Tw[0] = T_lo;
+        d.Tw[1] = T_hi;
+        d.wall_rho = wall_rho;
+        d.walls_set = 1;
+    }
     LBM_CUDA_CHECK(h, cudaMemcpyAsync(h->d_sims, h->sims.data(), h->sims.size() * sizeof(SimDev),
                                       cudaMemcpyHostToDevice, h->stream));
     return LBM_OK;
@@ -863,6 +906,8 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
         h->variant = LBM_KERNEL_SPLIT;
         return LBM_OK;
     }
+    if ((variant == LBM_KERNEL_ZMARCH || variant == LBM_KERNEL_FUSED) && has_nee(h))
+        return fail(h, LBM_E_UNSUPPORTED, "non-equilibrium-extrapolation walls run on the split kernels");
     if (variant == LBM_KERNEL_ZMARCH) {
         if (h->dim != 3) return fail(h, LBM_E_INVALID, "the z-march kernel runs D3Q27 lattices");
         if (tx <= 0 || ty <= 0) { tx = 30; ty = 14; }
@@ -938,7 +983,8 @@ int lbm_autotune(lbm_handle h, int trial_steps, int* variant, int* tx, int* ty, 
         bool same_eos = true;
         for (const SimDev& d : h->sims) same_eos = same_eos && d.eos == h->sims[0].eos;
         for (auto& t : zshapes)
-            if (same_eos && zmarch_shape(h->storage, t[0], t[1])) cands.push_back({LBM_KERNEL_ZMARCH, t[0], t[1], t[2]});
+            if (same_eos && !has_nee(h) && zmarch_shape(h->storage, t[0], t[1]))
+                cands.push_back({LBM_KERNEL_ZMARCH, t[0], t[1], t[2]});
     }
     h->graph_steps = 0;
     drop_graph(h);

@@ -48,6 +48,9 @@ struct SimDev {
     double mu;                    // > 0: tau = mu / P per cell (beta per cell); 0: beta_f, beta_g
     float fref[27], gref[27];     // storage offsets (16-bit storage only; zero otherwise)
     const float* mlp;             // learned T(rho, e) parameters (t_solver == LBM_T_MLP), or null
+    double uw[2][3], Tw[2];       // zwalls == 2: velocity and temperature of the walls at z = 0 and z = nz - 1
+    int wall_rho;                 // zwalls == 2: 0 rho_B from the neighbour's pressure, 1 rho_B = rho_N
+    int walls_set;                // zwalls == 2: lbm_set_walls has been called
 };
 
 // The same constants in the arithmetic type R (built once per tile on the

@@ -201,11 +201,25 @@ __device__ __forceinline__ int nb_coord(int v, int o, int n, bool mirror)
     return w;
 }
 
+// Value of field v at (x, y, z) between non-equilibrium-extrapolation walls
+// on the boundary cells z_B = 0 and nz - 1: v itself inside, the linear
+// extrapolation 2 v(z_B) - v(2 z_B - z) through the boundary cell past it
+// (x, y in the domain, z at most nz - 1 cells past a face).
+template <typename R, typename V>
+__device__ __forceinline__ R zval(const V& v, int x, int y, int z, int nz, int walls)
+{
+    if (z < 0 || z >= nz) {
+        const int zb = z < 0 ? 0 : nz - 1;
+        return R(2) * v(x, y, zb) - v(x, y, 2 * zb - z);
+    }
+    return v(x, y, z);
+}
+
 // lap rho at the in-domain cell (ix, iy, iz): (2D+1)-point stencil, with
-// neighbours beyond a z wall taken from their mirror images
+// neighbours past a z wall as zval gives them
 template <int D, typename R>
 __device__ __forceinline__ R lap_img(const R* __restrict__ rho, int ix, int iy, int iz, int nx, int ny, int nz,
-                                     bool walls)
+                                     int walls)
 {
     auto at = [&](int x, int y, int z) {
         return rho[(long long)x + (long long)nx * ((long long)y + (long long)ny * (long long)z)];
@@ -214,23 +228,34 @@ __device__ __forceinline__ R lap_img(const R* __restrict__ rho, int ix, int iy, 
     R L = 0;
     L += at(nb_coord(ix, 1, nx, false), iy, iz) - R(2) * c + at(nb_coord(ix, -1, nx, false), iy, iz);
     L += at(ix, nb_coord(iy, 1, ny, false), iz) - R(2) * c + at(ix, nb_coord(iy, -1, ny, false), iz);
-    if (D == 3) L += at(ix, iy, nb_coord(iz, 1, nz, walls)) - R(2) * c + at(ix, iy, nb_coord(iz, -1, nz, walls));
+    if (D == 3) {
+        if (walls == 2)
+            L += zval<R>(at, ix, iy, iz + 1, nz, 2) - R(2) * c + zval<R>(at, ix, iy, iz - 1, nz, 2);
+        else
+            L += at(ix, iy, nb_coord(iz, 1, nz, walls == 1)) - R(2) * c + at(ix, iy, nb_coord(iz, -1, nz, walls == 1));
+    }
     return L;
 }
 
 // Korteweg gradient of lap rho at (x, y, z) (central difference of lap rho
-// between the images of the two neighbours along each axis)
+// between the images of the two neighbours along each axis; past a
+// non-equilibrium-extrapolation wall lap rho is extrapolated like any field)
 template <int D, typename R>
 __device__ __forceinline__ void grad_lap(const R* __restrict__ rho, int x, int y, int z, int nx, int ny, int nz,
-                                         bool walls, R* gl)
+                                         int walls, R* gl)
 {
     gl[0] = R(0.5) * (lap_img<D, R>(rho, nb_coord(x, 1, nx, false), y, z, nx, ny, nz, walls) -
                       lap_img<D, R>(rho, nb_coord(x, -1, nx, false), y, z, nx, ny, nz, walls));
     gl[1] = R(0.5) * (lap_img<D, R>(rho, x, nb_coord(y, 1, ny, false), z, nx, ny, nz, walls) -
                       lap_img<D, R>(rho, x, nb_coord(y, -1, ny, false), z, nx, ny, nz, walls));
-    gl[2] = D == 3 ? R(0.5) * (lap_img<D, R>(rho, x, y, nb_coord(z, 1, nz, walls), nx, ny, nz, walls) -
-                               lap_img<D, R>(rho, x, y, nb_coord(z, -1, nz, walls), nx, ny, nz, walls))
-                   : R(0);
+    if (D == 3 && walls == 2) {
+        auto lap = [&](int xx, int yy, int zz) { return lap_img<D, R>(rho, xx, yy, zz, nx, ny, nz, 2); };
+        gl[2] = R(0.5) * (zval<R>(lap, x, y, z + 1, nz, 2) - zval<R>(lap, x, y, z - 1, nz, 2));
+    } else {
+        gl[2] = D == 3 ? R(0.5) * (lap_img<D, R>(rho, x, y, nb_coord(z, 1, nz, walls == 1), nx, ny, nz, walls) -
+                                   lap_img<D, R>(rho, x, y, nb_coord(z, -1, nz, walls == 1), nx, ny, nz, walls))
+                       : R(0);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -266,7 +291,7 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
             const R* rho = (FROM_M ? M + M_RHO * Ntot : W + W_RHO * Ntot) + s.cell_off;
             const R r = rho[k];
             R F[3] = {0, 0, 0}, j[3], gl[3];
-            grad_lap<D, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls != 0, gl);
+            grad_lap<D, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls, gl);
 #pragma unroll
             for (int a = 0; a < D; ++a) F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl[a];
 #pragma unroll
@@ -284,7 +309,7 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
         const R* rho = (FROM_M ? M + M_RHO * Ntot : W + W_RHO * Ntot) + s.cell_off;
         R r = rho[k];
         R F[3] = {0, 0, 0}, j[3], gl[3];
-        grad_lap<D, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls != 0, gl);
+        grad_lap<D, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls, gl);
 #pragma unroll
         for (int a = 0; a < D; ++a) F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl[a];  // Eqs. force_decomposition, korteweg_force
 #pragma unroll
@@ -314,6 +339,13 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
 template <typename R>
 __device__ __forceinline__ R wget(const SimDev& s, const R* __restrict__ fld, int x, int y, int z, bool odd)
 {
+    if (s.zwalls == 2 && (z < 0 || z >= s.nz)) {
+        // past a non-equilibrium-extrapolation wall: linear extrapolation through the boundary cell
+        const int zb = z < 0 ? 0 : s.nz - 1;
+        const long long xy = (long long)wrapi(x, s.nx) + (long long)s.nx * wrapi(y, s.ny);
+        const long long plane = (long long)s.nx * s.ny;
+        return R(2) * fld[xy + plane * zb] - fld[xy + plane * (2 * zb - z)];
+    }
     bool fl;
     long long kk = nb_index(s, x, y, z, fl);
     R v = fld[kk];
@@ -354,6 +386,103 @@ __device__ __forceinline__ void stencils(const SimDev& s, const R* __restrict__ 
         }
         Phi[a] = -dX / rho;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Non-equilibrium-extrapolation walls (zwalls == 2; the wall treatment of the
+// thermal Couette flow, Sec. IV), between the macroscopic pass and the
+// collision.  Each boundary cell z_B in {0, nz - 1} takes the wall velocity
+// and temperature, the density rho_N of its neighbour z_N in {1, nz - 2}
+// (wall_rho 1) or the density whose pressure at T_W is the neighbour's
+// (wall_rho 0: eight Newton steps from rho_N, rho_N again if they end
+// non-finite or non-positive), and the populations
+//   f_B = f^eq(rho_B, u_W, theta_W) + f_N - f^eq(rho_N, u_N, theta_N), g alike,
+// written to the storage slots its pull reads (no other cell reads those).
+// Its macroscopic fields become the wall state; its force keeps the
+// per-mass value of the macroscopic pass.  pops = 0 rebuilds the fields
+// only (for the reported moments and totals).
+// ---------------------------------------------------------------------------
+template <int D, typename R, typename S>
+__global__ void __launch_bounds__(kBlockCells) k_nee(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
+                                                     S* pop, R* __restrict__ W, long long Ntot, int pops)
+{
+    constexpr int Q = Lat<D>::Q;
+    __shared__ SimDev s;
+    const BlockEntry be = table[blockIdx.x];
+    load_sim(s, sims, be.sim);
+    const long long k = (long long)be.start + threadIdx.x;
+    if (D != 3 || s.zwalls != 2 || k >= s.N) return;
+    int x, y, z;
+    cell_xyz(s, k, x, y, z);
+    if (z != 0 && z != s.nz - 1) return;
+    const int side = z == 0 ? 0 : 1;
+    const long long plane = (long long)s.nx * s.ny;
+    const long long gb = s.cell_off + k, gn = s.cell_off + (side ? k - plane : k + plane);
+    const R rn = W[W_RHO * Ntot + gn];
+    const R Tw = (R)s.Tw[side];
+    R rb = rn;
+    if (s.wall_rho == 0) {
+        const R PN = W[W_P * Ntot + gn];  // P(rho_N, T_N)
+        R r = rn;
+#pragma unroll 1
+        for (int it = 0; it < 8; ++it) {
+            const Thermo<R> t = thermo<R>(s, rho_part<R>(s, r), Tw);
+            r -= (t.P - PN) / t.Pr;
+        }
+        if (isfinite(r) && r > R(0)) rb = r;
+    }
+    const RhoPart<R> pb = rho_part<R>(s, rb);
+    const Thermo<R> t = thermo<R>(s, pb, Tw);
+    const R ib = R(1) / rb;
+    const R thw = t.P * ib, ew = eos_e<R>(s, pb, Tw);
+    R uw[3], un[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        uw[a] = a < D ? (R)s.uw[side][a] : R(0);
+        un[a] = W[(W_U + a) * Ntot + gn];
+    }
+    if (pops) {
+        R feqB[Q], geqB[Q], feqN[Q], geqN[Q], fN[Q], gN[Q];
+        equilibria<D, R>(rb, uw, thw, ew, feqB, geqB);
+        equilibria<D, R>(rn, un, W[W_TH * Ntot + gn], W[W_E * Ntot + gn], feqN, geqN);
+        pull_cell<D, R, S>(s, pop, x, y, side ? z - 1 : z + 1, fN, gN);
+        S* fb = pop + s.pop_off;
+        S* gbuf = fb + (long long)Q * s.N;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            int j;
+            const long long idx = pull_index<D>(s, i, x, y, z, j);
+            const R fo = Codec<S, R>::offset ? (R)s.fref[j] : R(0);
+            const R go = Codec<S, R>::offset ? (R)s.gref[j] : R(0);
+            Codec<S, R>::st(fb + idx, feqB[i] + (fN[i] - feqN[i]) - fo);
+            Codec<S, R>::st(gbuf + idx, geqB[i] + (gN[i] - geqN[i]) - go);
+        }
+    }
+    const R scale = rb / W[W_RHO * Ntot + gb];
+    const R Qh = (R)heat_at(s, z);
+    R uF = 0, u2 = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const R Fa = W[(W_F + a) * Ntot + gb] * scale;
+        W[(W_F + a) * Ntot + gb] = Fa;
+        W[(W_U + a) * Ntot + gb] = uw[a];
+        W[(W_J + a) * Ntot + gb] = rb * uw[a] - R(0.5) * Fa;  // so that J + F/2 = rho_B u_W (Eq. def_u)
+        W[(W_X + a) * Ntot + gb] = a < D ? xflux<R>(rb, uw[a], thw) : R(0);
+        uF += uw[a] * Fa;
+        u2 += uw[a] * uw[a];
+    }
+    const R icv = s.eos == EOS_PR ? R(1) / t.cv : (R)s.inv_cv;
+    const R cs2 = t.Pr + Tw * t.PT * t.PT * ib * ib * icv;
+    W[W_RHO * Ntot + gb] = rb;
+    W[W_G * Ntot + gb] = rb * (ew + R(0.5) * u2) - R(0.5) * (uF + Qh);  // rho E at the wall state (Eq. def_E)
+    W[W_T * Ntot + gb] = Tw;
+    W[W_E * Ntot + gb] = ew;
+    W[W_P * Ntot + gb] = t.P;
+    W[W_TH * Ntot + gb] = thw;
+    W[W_H * Ntot + gb] = ew + thw;
+    W[W_CV * Ntot + gb] = t.cv;
+    W[W_GAM * Ntot + gb] = R(1) + t.PT * ib * icv;
+    W[W_ATHE * Ntot + gb] = (R)s.athe_c * thw - cs2;
 }
 
 // ---------------------------------------------------------------------------

@@ -65,6 +65,8 @@ _SIGS = {
     "lbm_destroy": (None, [ctypes.c_void_p]),
     "lbm_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_set_force": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_set_walls": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                     ctypes.c_double, ctypes.c_int]),
     "lbm_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -184,6 +186,14 @@ def lbm_set_force(h, accel) -> None:
     if a.size < 3:
         a = np.concatenate([a, np.zeros(3 - a.size)])
     _check(_lib.lbm_set_force(h, a.ctypes.data), h)
+
+
+def lbm_set_walls(h, u_lo, T_lo: float, u_hi, T_hi: float, wall_rho: int = 0) -> None:
+    lo = np.zeros(3)
+    hi = np.zeros(3)
+    lo[:len(u_lo)] = u_lo
+    hi[:len(u_hi)] = u_hi
+    _check(_lib.lbm_set_walls(h, lo.ctypes.data, float(T_lo), hi.ctypes.data, float(T_hi), int(wall_rho)), h)
 
 
 def lbm_step(h, n: int) -> None:
@@ -316,6 +326,9 @@ class Simulation:
                                       [c.tau_f for c in self.cases], [c.tau_g for c in self.cases],
                                       [p[2] for p in parts], [p[3] for p in parts])
         self.N = sum(c.ncell for c in self.cases)
+        c0 = self.cases[0]
+        if any(c.zwalls == 2 for c in self.cases):
+            lbm_set_walls(self.h, c0.uw_lo, c0.Tw_lo, c0.uw_hi, c0.Tw_hi, getattr(c0, "wall_rho", 0))
         if variant is not None:
             t = tile or (0, 0, 0)
             lbm_set_kernel(self.h, variant, *t)

@@ -83,6 +83,9 @@ def _create(lib, lat, eos, tau=0.8):
     ({}, dict(mu=float("nan")), 0.8, "mu nan"),
     ({}, dict(isothermal=2), 0.8, "isothermal flag"),
     ({}, dict(kind=lbm.LBM_PR, Tc=0.5, Pc=0.15, t_solver=lbm.LBM_T_MLP, isothermal=1), 0.8, "isothermal learned"),
+    (dict(dim=3, nz=8, zwalls=3), {}, 0.8, "zwalls value"),
+    (dict(dim=3, nz=3, zwalls=2), {}, 0.8, "extrapolation walls need nz >= 4"),
+    (dict(dim=3, nz=8, zwalls=2), dict(isothermal=1), 0.8, "extrapolation walls set T"),
 ])
 def test_invalid_arguments_rejected_without_device(lib, lat_kw, eos_kw, tau, why):
     lat = lbm.lbm_lattice(**{**dict(dim=2, nx=8, ny=8, nz=1, zwalls=0, storage=0, phi_scheme=0), **lat_kw})
@@ -105,5 +108,6 @@ def test_isothermal_with_heat_source_rejected_without_device(lib):
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_E_INVALID
     assert lib.lbm_set_force(None, None) == lbm.LBM_E_INVALID
+    assert lib.lbm_set_walls(None, None, 1.0, None, 1.0, 0) == lbm.LBM_E_INVALID
     assert lib.lbm_invariants(None, None) == lbm.LBM_E_INVALID
     lib.lbm_destroy(None)
