@@ -71,6 +71,32 @@
  *    Populations streaming out through a wall face return reversed (as with
  *    zwalls = 1); B is rebuilt before they are used.  The moments reported
  *    for a B cell are the rebuilt ones.  Not combined with isothermal = 1.
+ *  - Duct ends (Sec. III.A, Rayleigh and Fanno flows) reuse the boundary-cell
+ *    rebuild with other boundary states (face_kind): a subsonic inlet takes
+ *    the total pressure P0 and temperature T0 with the velocity of its
+ *    neighbour, T = T0 - |u|^2/(2 c_p), P = P0 (T/T0)^(c_p/R) (ideal gas with
+ *    constant c_v only); a supersonic inlet takes static P, T and u; a
+ *    subsonic outlet takes static P with u and T of the neighbour; a
+ *    supersonic outlet takes rho, u and T of the neighbour.  Where P and T are
+ *    given, rho_B solves P(rho_B, T) = P by the same eight Newton steps.
+ *    "Zero-order extrapolation" at the subsonic outlet is read as carrying
+ *    over the neighbour's mass flux, u_B = u_N rho_N / rho_B: carrying u_N
+ *    itself leaves a pressure step of ~15 % in the last cells and an energy
+ *    flux that misses the heat input (Rayleigh flow), while the mass flux
+ *    gives a smooth outlet and the Rayleigh and Fanno relations to 1e-4.
+ *    The boundary cell's force and heat keep their non-friction part per
+ *    unit mass; the friction force and its heat are evaluated again at the
+ *    rebuilt (rho_B, u_B).  The
+ *    text's 1-D duct runs as a 1 x 1 x nz column of D3Q27: with no x or y
+ *    variation its populations summed over c_x, c_y follow the 1-D product
+ *    form of the same model exactly, except that the normal viscous stress
+ *    is the 3-D one, (4/3 mu + eta) du/dz (both are regularisers of the
+ *    inviscid Rayleigh and Fanno solutions).
+ *  - Duct friction (Fanno flow): F_f = -k rho |u| u with k = f_D/(2 D_h) and
+ *    the compensating heat Q_f = -F_f.u, both added to F and Q of phase B.
+ *    u = (J + F/2)/rho then depends on F_f; the relation is solved exactly:
+ *    with w = (J + (F_B + F_K)/2)/rho, |u| (1 + k |u|/2) = |w|, so
+ *    u = 2 w / (1 + sqrt(1 + 2 k |w|)).
  *  - Peng-Robinson: the paper names the model only.  The textbook form with the
  *    Soave alpha(T) and a constant ideal-part c_v is used; e(rho,T) follows by
  *    integrating Eq. de_rho at constant T from rho = 0.  T(rho,e) is found by
@@ -114,7 +140,18 @@ typedef struct {
     double uw_lo[3], uw_hi[3]; /* zwalls = 2: velocities of the walls at z = 0 and z = nz - 1 */
     double Tw_lo, Tw_hi;       /* zwalls = 2: their temperatures */
     int wall_rho;              /* zwalls = 2: 0: rho_B from P(rho_B, T_W) = P_N; 1: rho_B = rho_N */
+    int face_kind[2];          /* zwalls = 2: ORC_FACE_* of the faces z = 0 and z = nz - 1; walls take
+                                  (uw, Tw) above, the open kinds take (uw, Tw, face_P) as their data */
+    double face_P[2];          /* static pressure (inlet static, outlet) or total pressure (inlet total) */
+    double friction;           /* duct friction k = f_D / (2 D_h): F = -k rho |u| u, with Q = -F.u */
 } orc_params;
+
+/* Boundary kinds of a z face with zwalls = 2 (Sec. IV walls; Sec. III.A duct ends) */
+#define ORC_FACE_WALL 0          /* wall: u_W, T_W; rho_B by wall_rho */
+#define ORC_FACE_INLET_TOTAL 1   /* subsonic inlet: total P0, T0 given, u from the neighbour (ideal gas) */
+#define ORC_FACE_INLET_STATIC 2  /* supersonic inlet: static P, T and u given */
+#define ORC_FACE_OUTLET_P 3      /* subsonic outlet: static P given, u and T from the neighbour */
+#define ORC_FACE_OUTLET_EXTRAP 4 /* supersonic outlet: rho, u, T from the neighbour */
 
 typedef struct {
     orc_params p;
@@ -377,6 +414,14 @@ orc_state *orc_create(const orc_params *p)
     if (p->dim == 2 && (p->nz != 1 || p->zwalls)) return NULL;
     if (p->zwalls < 0 || p->zwalls > 2) return NULL;
     if (p->zwalls == 2 && (p->nz < 4 || p->isothermal || !(p->Tw_lo > 0) || !(p->Tw_hi > 0))) return NULL;
+    for (int f = 0; f < 2; ++f) {
+        if (p->face_kind[f] < ORC_FACE_WALL || p->face_kind[f] > ORC_FACE_OUTLET_EXTRAP) return NULL;
+        if (p->face_kind[f] != ORC_FACE_WALL && p->zwalls != 2) return NULL;
+        if (p->face_kind[f] == ORC_FACE_INLET_TOTAL && p->eos != ORC_IDEAL) return NULL;
+        if ((p->face_kind[f] == ORC_FACE_INLET_TOTAL || p->face_kind[f] == ORC_FACE_INLET_STATIC ||
+             p->face_kind[f] == ORC_FACE_OUTLET_P) && !(p->face_P[f] > 0)) return NULL;
+    }
+    if (!(p->friction >= 0)) return NULL;
     orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
     s->p = *p;
     int cflat[81];
@@ -570,6 +615,25 @@ static void macro_fields(orc_state *s)
     for (long k = 0; k < N; ++k) {
         double r = s->rho[k];
         double uu[3] = {0, 0, 0}, uF = 0, u2 = 0;
+        if (p->friction > 0.0) {
+            /* duct friction F_f = -k rho |u| u at the u it produces, and Q_f = -F_f.u */
+            double w[3] = {0, 0, 0}, wn = 0, un = 0;
+            for (int a = 0; a < D; ++a) {
+                w[a] = (s->J[(long)a * N + k] + 0.5 * s->F[(long)a * N + k]) / r;
+                wn += w[a] * w[a];
+            }
+            wn = sqrt(wn);
+            double sc = 2.0 / (1.0 + sqrt(1.0 + 2.0 * p->friction * wn));
+            for (int a = 0; a < D; ++a) un += (sc * w[a]) * (sc * w[a]);
+            un = sqrt(un);
+            double Qf = 0;
+            for (int a = 0; a < D; ++a) {
+                double Ff = -p->friction * r * un * (sc * w[a]);
+                s->F[(long)a * N + k] += Ff;
+                Qf -= Ff * (sc * w[a]);
+            }
+            s->Qs[k] += Qf;
+        }
         for (int a = 0; a < D; ++a) {
             uu[a] = (s->J[(long)a * N + k] + 0.5 * s->F[(long)a * N + k]) / r;
             uF += uu[a] * s->F[(long)a * N + k];
@@ -628,20 +692,42 @@ static void nee_walls(orc_state *s, int pops)
     for (int side = 0; side < 2; ++side) {
         int zb = side ? p->nz - 1 : 0, zn = side ? p->nz - 2 : 1;
         const double *uw = side ? p->uw_hi : p->uw_lo;
-        double Tw = side ? p->Tw_hi : p->Tw_lo;
+        double Tw;
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
                 long kb = cidx(s, x, y, zb), kn = cidx(s, x, y, zn);
                 double rn = s->rho[kn], un[3], uW[3] = {0, 0, 0}, xi[3], zeta[3];
                 for (int a = 0; a < 3; ++a) un[a] = s->u[(long)a * N + kn];
                 for (int a = 0; a < D; ++a) uW[a] = uw[a];
-                /* wall state: rho_B (from rho_N or from P_N), u_W, T_W */
+                /* boundary state: rho_B, u_B (uW), T_B (Tw) of the face's kind */
+                int kind = p->face_kind[side];
+                double Pt = -1.0; /* pressure that rho_B must meet at Tw, if any */
+                Tw = side ? p->Tw_hi : p->Tw_lo;
+                if (kind == ORC_FACE_WALL) {
+                    if (p->wall_rho == 0) Pt = orc_eos_P(p, rn, s->T[kn]);
+                } else if (kind == ORC_FACE_INLET_TOTAL) {
+                    double cp = p->cv + p->R, n2 = 0;
+                    for (int a = 0; a < D; ++a) { uW[a] = un[a]; n2 += un[a] * un[a]; }
+                    double T0 = Tw;
+                    Tw = T0 - 0.5 * n2 / cp;
+                    Pt = p->face_P[side] * pow(Tw / T0, cp / p->R);
+                } else if (kind == ORC_FACE_INLET_STATIC) {
+                    Pt = p->face_P[side];
+                } else if (kind == ORC_FACE_OUTLET_P) {
+                    Tw = s->T[kn];
+                    Pt = p->face_P[side];
+                } else {
+                    for (int a = 0; a < D; ++a) uW[a] = un[a];
+                    Tw = s->T[kn];
+                }
                 double rb = rn;
-                if (p->wall_rho == 0) {
-                    double PN = orc_eos_P(p, rn, s->T[kn]), r = rn;
-                    for (int it = 0; it < 8; ++it) r -= (orc_eos_P(p, r, Tw) - PN) / orc_eos_dPdrho(p, r, Tw);
+                if (Pt > 0.0) {
+                    double r = rn;
+                    for (int it = 0; it < 8; ++it) r -= (orc_eos_P(p, r, Tw) - Pt) / orc_eos_dPdrho(p, r, Tw);
                     if (isfinite(r) && r > 0.0) rb = r;
                 }
+                if (kind == ORC_FACE_OUTLET_P) /* the neighbour's mass flux */
+                    for (int a = 0; a < D; ++a) uW[a] = un[a] * (rn / rb);
                 double Pw = orc_eos_P(p, rb, Tw), thw = Pw / rb, ew = orc_eos_e(p, rb, Tw);
                 if (pops) {
                     double feqB[27], geqB[27], feqN[27], geqN[27];
@@ -656,9 +742,16 @@ static void nee_walls(orc_state *s, int pops)
                         s->g[(long)i * N + kb] = geqB[i] + (s->g[(long)i * N + kn] - geqN[i]);
                     }
                 }
-                double scale = rb / s->rho[kb], u2 = 0;
-                for (int a = 0; a < 3; ++a) s->F[(long)a * N + kb] *= scale;
-                for (int a = 0; a < D; ++a) u2 += uW[a] * uW[a];
+                /* force and heat: non-friction part per unit mass kept, friction at (rho_B, u_B) */
+                double ro = s->rho[kb], uo2 = 0, u2 = 0;
+                for (int a = 0; a < D; ++a) { uo2 += s->u[(long)a * N + kb] * s->u[(long)a * N + kb]; u2 += uW[a] * uW[a]; }
+                double uon = sqrt(uo2), ubn = sqrt(u2);
+                for (int a = 0; a < 3; ++a) {
+                    double Ffo = a < D ? -p->friction * ro * uon * s->u[(long)a * N + kb] : 0.0;
+                    double Ffb = a < D ? -p->friction * rb * ubn * uW[a] : 0.0;
+                    s->F[(long)a * N + kb] = (s->F[(long)a * N + kb] - Ffo) * (rb / ro) + Ffb;
+                }
+                s->Qs[kb] += p->friction * (rb * ubn * u2 - ro * uon * uo2);
                 for (int a = 0; a < 3; ++a) s->u[(long)a * N + kb] = uW[a];
                 double cv = orc_eos_cv(p, rb, Tw), PT = orc_eos_dPdT(p, rb, Tw), Pr = orc_eos_dPdrho(p, rb, Tw);
                 double cs2 = Pr + Tw * PT * PT / (rb * rb * cv);

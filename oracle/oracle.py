@@ -51,6 +51,8 @@ class OrcParams(ctypes.Structure):
         ("uw_lo", ctypes.c_double * 3), ("uw_hi", ctypes.c_double * 3),
         ("Tw_lo", ctypes.c_double), ("Tw_hi", ctypes.c_double),
         ("wall_rho", ctypes.c_int),
+        ("face_kind", ctypes.c_int * 2), ("face_P", ctypes.c_double * 2),
+        ("friction", ctypes.c_double),
     ]
 
 
@@ -105,7 +107,7 @@ def make_params(dim=2, nx=8, ny=8, nz=1, zwalls=0, eos="ideal", R=1.0, cv=2.5, a
                 Tc=1.0, omega=0.0, Pc=None, kappa=0.0, eta_over_mu=0.0, k_over_mu=0.0,
                 tau_f=0.8, tau_g=0.8, accel=(0.0, 0.0, 0.0), q=0.0, zlo=0, zhi=0,
                 phi_central=0, mu=0.0, isothermal=0, uw_lo=(0.0, 0.0, 0.0), uw_hi=(0.0, 0.0, 0.0),
-                Tw_lo=0.0, Tw_hi=0.0, wall_rho=0) -> OrcParams:
+                Tw_lo=0.0, Tw_hi=0.0, wall_rho=0, face_kind=(0, 0), face_P=(0.0, 0.0), friction=0.0) -> OrcParams:
     """Build the oracle's parameter struct.  For Peng-Robinson with ``Pc`` given
     and ``a == 0``, a and b follow from (Tc, Pc) by the oracle's own helper.
     zwalls = 2 selects the non-equilibrium-extrapolation walls with wall
@@ -130,6 +132,10 @@ def make_params(dim=2, nx=8, ny=8, nz=1, zwalls=0, eos="ideal", R=1.0, cv=2.5, a
         p.uw_hi[k] = uw_hi[k] if k < len(uw_hi) else 0.0
     p.Tw_lo, p.Tw_hi = float(Tw_lo), float(Tw_hi)
     p.wall_rho = int(wall_rho)
+    for f in range(2):
+        p.face_kind[f] = int(face_kind[f])
+        p.face_P[f] = float(face_P[f])
+    p.friction = float(friction)
     return p
 
 
@@ -292,4 +298,6 @@ def params_from_case(case) -> OrcParams:
                        zlo=case.zlo, zhi=case.zhi, phi_central=case.phi_central, mu=getattr(case, "mu", 0.0),
                        isothermal=getattr(case, "isothermal", 0), uw_lo=getattr(case, "uw_lo", (0.0, 0.0, 0.0)),
                        uw_hi=getattr(case, "uw_hi", (0.0, 0.0, 0.0)), Tw_lo=getattr(case, "Tw_lo", 0.0),
-                       Tw_hi=getattr(case, "Tw_hi", 0.0), wall_rho=getattr(case, "wall_rho", 0))
+                       Tw_hi=getattr(case, "Tw_hi", 0.0), wall_rho=getattr(case, "wall_rho", 0),
+                       face_kind=getattr(case, "face_kind", (0, 0)), face_P=getattr(case, "face_P", (0.0, 0.0)),
+                       friction=getattr(case, "friction", 0.0))

@@ -68,6 +68,10 @@ class Case:
     Tw_lo: float = 0.0              # wall temperatures,
     Tw_hi: float = 0.0
     wall_rho: int = 0               # and boundary density: 0 from the neighbour's pressure, 1 the neighbour's
+    face_kind: tuple = (0, 0)       # zwalls = 2, per face: 0 wall, 1 inlet (total P0 = face_P, T0 = Tw),
+                                    # 2 inlet (static P = face_P, T = Tw, u = uw), 3 outlet (static P), 4 outlet
+    face_P: tuple = (0.0, 0.0)      # (extrapolated); see the open faces of the 1-D duct
+    friction: float = 0.0           # duct friction k = f_D / (2 D_h): F = -k rho |u| u, Q = -F.u
     storage: str = "f64"          # f64 | f32 | bf16 | f16
     steps: int = 100
     init: dict = field(default_factory=dict)
@@ -142,13 +146,20 @@ def _couette(c: Case):
     return rho, u, T
 
 
+def _duct(c: Case):
+    """Uniform rho0, T0 and velocity u0 along the last axis (the duct axis)."""
+    u = np.zeros((c.dim, c.ncell))
+    u[c.dim - 1] = c.init.get("u0", 0.0)
+    return (np.full(c.ncell, c.init.get("rho0", 1.0)), u, np.full(c.ncell, c.init.get("T0", 0.3)))
+
+
 def _uniform(c: Case):
     return (np.full(c.ncell, c.init.get("rho0", 1.0)), np.zeros((c.dim, c.ncell)),
             np.full(c.ncell, c.init.get("T0", 0.3)))
 
 
 _FIELDS = {"waves": _waves, "noisy_density": _noisy_density, "noisy_temperature": _noisy_temperature,
-           "droplet": _droplet, "uniform": _uniform, "couette": _couette}
+           "droplet": _droplet, "uniform": _uniform, "couette": _couette, "duct": _duct}
 
 # van der Waals fluid of the 2-D multiphase cases.  b = 2/21 (rho_c = 3.5) and
 # R/c_v = 0.4 as in the nitrogen table; a = 9/245 puts Tc = 4/35, i.e. the

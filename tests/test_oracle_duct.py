@@ -1,0 +1,117 @@
+"""Pins of the oracle's duct ends and duct friction (the 1-D duct flows of
+Sec. III.A: Rayleigh flow with a heat source, Fanno flow with friction and the
+compensating heat Q = -F.u), run as 1 x 1 x nz columns of D3Q27: the closed-form
+Rayleigh and Fanno relations T/T*, P/P* against the local Mach number, the
+total-enthalpy laws (H_in + Q z / mdot; H constant), a uniform mass flux, the
+exact uniform state kept by consistent inlet and outlet data, and the friction
+law with its exact energy budget."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2609_28679_b300 import workloads as wl
+from tests.util import run_oracle
+
+R_GAS, CV = 1.0, 2.5
+CP = R_GAS + CV
+GAM = CP / CV
+T_IN, P_IN, MA_IN = 0.1, 0.1, 0.3
+T0 = T_IN * (1.0 + 0.5 * (GAM - 1.0) * MA_IN ** 2)  # isentropic total state of the inlet
+P0 = P_IN * (T0 / T_IN) ** (CP / R_GAS)
+U_IN = MA_IN * math.sqrt(GAM * R_GAS * T_IN)
+
+
+def _duct(nz, q=0.0, friction=0.0, p_out=0.08, kinds=(1, 3), face_P=None, uw_lo=(0.0, 0.0, 0.0), T_lo=T0):
+    return wl.Case(name="duct", dim=3, nx=1, ny=1, nz=nz, zwalls=2, eos="ideal", R=R_GAS, cv=CV,
+                   k_over_mu=CP / 0.71, tau_f=0.8, tau_g=0.8, phi_central=1, q=q, zlo=0, zhi=0,
+                   friction=friction, face_kind=kinds, face_P=face_P or (P0, p_out), uw_lo=uw_lo,
+                   Tw_lo=T_lo, Tw_hi=T_lo,
+                   init=dict(kind="duct", rho0=P_IN / (R_GAS * T_IN), u0=U_IN, T0=T_IN))
+
+
+def _profiles(c, steps):
+    o = run_oracle(c, steps)
+    rho, u, T = o.moments()
+    uz = u.reshape(3, -1)[2]
+    P = rho * R_GAS * T
+    return rho, uz, T, P, uz / np.sqrt(GAM * R_GAS * T)
+
+
+def test_rayleigh_flow_relations():
+    # heat addition at subsonic speed: the flow accelerates and every cell lies on one Rayleigh line,
+    # T/T* = (1+g)^2 Ma^2/(1+g Ma^2)^2, P/P* = (1+g)/(1+g Ma^2), with one sonic state (T*, P*)
+    nz, q = 50, 4e-5
+    c = _duct(nz, q=q)
+    rho, uz, T, P, Ma = _profiles(c, 20000)
+    mdot = rho * uz
+    assert np.ptp(mdot[1:-1]) <= 1e-12 * mdot.mean()
+    assert Ma[-2] > Ma[1] + 0.01
+    Ts = T * (1 + GAM * Ma ** 2) ** 2 / ((1 + GAM) ** 2 * Ma ** 2)
+    Ps = P * (1 + GAM * Ma ** 2) / (1 + GAM)
+    assert np.ptp(Ts[1:-1]) <= 1e-3 * Ts.mean()
+    assert np.ptp(Ps[1:-1]) <= 1e-3 * Ps.mean()
+    # total enthalpy grows by the heat input: H(z) = H_1 + Q (z - 1) / mdot (to first order in dz)
+    H = CP * T + 0.5 * uz ** 2
+    z = np.arange(nz)
+    Hana = H[1] + q * (z - 1) / mdot.mean()
+    assert np.max(np.abs(H - Hana)[1:-1]) <= 0.03 * q * nz / mdot.mean()
+
+
+def test_rayleigh_relations_converge_with_resolution():
+    spreads = []
+    for nz in (25, 50):
+        c = _duct(nz, q=4e-5 * 50 / nz)
+        rho, uz, T, P, Ma = _profiles(c, 400 * nz)
+        Ts = T * (1 + GAM * Ma ** 2) ** 2 / ((1 + GAM) ** 2 * Ma ** 2)
+        spreads.append(np.ptp(Ts[1:-1]) / Ts.mean())
+    assert spreads[0] / spreads[1] == pytest.approx(2.0, rel=0.2)  # first order at fixed tau
+
+
+def test_fanno_flow_relations():
+    # friction at subsonic speed: T/T* = (1+g)/(2+(g-1)Ma^2), P/P* = sqrt((1+g)/(2+(g-1)Ma^2))/Ma,
+    # and the total enthalpy stays constant (the friction work returns as heat, Q = -F.u)
+    nz = 50
+    c = _duct(nz, friction=4e-3)
+    rho, uz, T, P, Ma = _profiles(c, 20000)
+    assert np.ptp((rho * uz)[1:-1]) <= 1e-12 * (rho * uz).mean()
+    assert Ma[-2] > Ma[1] + 0.02
+    Ts = T * (2 + (GAM - 1) * Ma ** 2) / (1 + GAM)
+    Ps = P * Ma / np.sqrt((GAM + 1) / (2 + (GAM - 1) * Ma ** 2))
+    assert np.ptp(Ts[1:-1]) <= 2e-4 * Ts.mean()
+    assert np.ptp(Ps[1:-1]) <= 2e-4 * Ps.mean()
+    H = CP * T + 0.5 * uz ** 2
+    assert np.ptp(H) <= 1e-3 * H.mean()
+
+
+@pytest.mark.parametrize("kinds", [(1, 3), (2, 4), (2, 3), (1, 4)])
+def test_uniform_flow_is_kept_by_consistent_duct_ends(kinds):
+    # inlet and outlet data that agree with a uniform subsonic flow leave it exactly uniform
+    nz = 12
+    face_P = (P0 if kinds[0] == 1 else P_IN, P_IN)
+    c = _duct(nz, kinds=kinds, face_P=face_P, uw_lo=(0.0, 0.0, U_IN), T_lo=T0 if kinds[0] == 1 else T_IN)
+    rho, uz, T, P, Ma = _profiles(c, 200)
+    assert np.max(np.abs(rho - P_IN / (R_GAS * T_IN))) <= 1e-12
+    assert np.max(np.abs(uz - U_IN)) <= 1e-12
+    assert np.max(np.abs(T - T_IN)) <= 1e-12
+
+
+def test_friction_law_and_energy_budget():
+    # uniform periodic flow: d(rho u)/dt = -k rho u^2 gives u(t) = u0 / (1 + k u0 t); the heat
+    # Q = -F.u returns the friction work, so total energy is conserved exactly and the momentum
+    # changes by the total force
+    k, u0, n = 0.05, 0.1, 400
+    c = wl.Case(name="fric", dim=3, nx=2, ny=2, nz=3, eos="ideal", R=R_GAS, cv=CV, k_over_mu=CP / 0.71,
+                friction=k, init=dict(kind="duct", rho0=1.0, u0=u0, T0=0.3))
+    o = run_oracle(c, 0)
+    prev = o.invariants()
+    for _ in range(n):
+        o.step(1)
+        cur = o.invariants()
+        assert abs(cur[4] - prev[4]) <= 1e-12 * abs(cur[4])          # rho E
+        assert abs(cur[-1]) <= 1e-14 * abs(cur[4])                   # sum (u.F + Q) = 0
+        assert cur[3] - prev[3] == pytest.approx(0.5 * (prev[7] + cur[7]), rel=1e-9)  # z momentum
+        prev = cur
+    uz = o.moments()[1].reshape(3, -1)[2]
+    assert np.allclose(uz, u0 / (1 + k * u0 * n), rtol=1e-3)
