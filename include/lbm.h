@@ -117,6 +117,10 @@ typedef struct {
 
 typedef struct {
     double accel[3]; /* body acceleration a: F_B = rho a (Eq. force_decomposition) */
+    double friction; /* duct friction k = f_D / (2 D_h) >= 0 (Fanno flow, Sec. III.A): F_f = -k rho |u| u
+                        joins F and its work returns as heat, Q_f = -F_f.u; u = (sum c f + F/2)/rho is
+                        solved with F_f exactly, u = 2 w / (1 + sqrt(1 + 2 k |w|)), w the velocity without
+                        F_f.  Split kernels only (0 for the others). */
 } lbm_force;
 
 typedef struct {
@@ -173,6 +177,30 @@ int lbm_set_force(lbm_handle h, const double *accel);
  * LBM_E_INVALID (NULL, non-finite, T <= 0, wall_rho not 0/1), LBM_E_STATE
  * (no such walls in h), LBM_E_CUDA. */
 int lbm_set_walls(lbm_handle h, const double *u_lo, double T_lo, const double *u_hi, double T_hi, int wall_rho);
+
+/* Boundary kinds of one z face with zwalls = 2 (the ends of the 1-D duct of
+ * Sec. III.A; the duct runs as a 1 x 1 x nz column of D3Q27, whose
+ * populations summed over c_x, c_y follow the 1-D product form exactly). */
+#define LBM_FACE_INLET_TOTAL 1   /* subsonic inlet: total pressure P and temperature T (ideal gas); u of the neighbour */
+#define LBM_FACE_INLET_STATIC 2  /* supersonic inlet: static P, T and the velocity u */
+#define LBM_FACE_OUTLET_P 3      /* subsonic outlet: static P; T and the mass flux rho u of the neighbour */
+#define LBM_FACE_OUTLET_EXTRAP 4 /* supersonic outlet: rho, u, T of the neighbour */
+
+/* Make face 0 (z = 0) or 1 (z = nz - 1) of every simulation of h that has
+ * zwalls = 2 an open duct end of the given kind.  The boundary cell is
+ * rebuilt each step as for lbm_set_walls: f_B = f^eq(rho_B, u_B, theta_B) +
+ * f_N - f^eq(N), g alike, with the boundary state (rho_B, u_B, T_B) of the
+ * kind: INLET_TOTAL T_B = T - |u_N|^2/(2 c_p), P_B = P (T_B/T)^(c_p/R),
+ * u_B = u_N; INLET_STATIC P, T and u as given; OUTLET_P P as given, T_N and
+ * u_B = u_N rho_N / rho_B; OUTLET_EXTRAP rho_N, u_N, T_N.  rho_B meets the
+ * pressure at T_B by eight Newton steps from rho_N.  u: 3 doubles (host;
+ * read for INLET_STATIC only, may be NULL otherwise); T > 0 for the inlets;
+ * P > 0 for all but OUTLET_EXTRAP.  A face set here replaces the wall that
+ * lbm_set_walls put there; each face must be set (here or by lbm_set_walls)
+ * before h steps.  Errors: LBM_E_INVALID (face, kind, values), LBM_E_STATE
+ * (no such walls in h), LBM_E_UNSUPPORTED (INLET_TOTAL with a non-ideal
+ * equation of state), LBM_E_CUDA. */
+int lbm_set_face(lbm_handle h, int face, int kind, const double *u, double T, double P);
 
 /* Initial state (flowchart, first box): f = f^eq(rho, u, theta), g = g^eq with
  * theta = P(rho,T)/rho and e = e(rho,T).  rho [N], u [dim][N] and T [N]

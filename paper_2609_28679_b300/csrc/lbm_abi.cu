@@ -95,12 +95,28 @@ int cuda_fail(lbm_ctx* h, cudaError_t e, const char* where)
 
 void* dev_alloc(lbm_ctx* h, size_t n) { return lbm_glue_alloc(n, (void*)h->stream); }
 
-// some simulation of h has non-equilibrium-extrapolation walls (split kernels only)
+// some simulation of h has non-equilibrium-extrapolation walls
 bool has_nee(const lbm_ctx* h)
 {
     for (const SimDev& d : h->sims)
         if (d.zwalls == 2) return true;
     return false;
+}
+
+// the handle needs the split kernels: extrapolated faces or duct friction
+bool split_only(const lbm_ctx* h)
+{
+    for (const SimDev& d : h->sims)
+        if (d.zwalls == 2 || d.friction > 0.0) return true;
+    return false;
+}
+
+// every face of a simulation with zwalls == 2 has its data
+bool faces_ready(const lbm_ctx* h)
+{
+    for (const SimDev& d : h->sims)
+        if (d.zwalls == 2 && !(d.face_set[0] && d.face_set[1])) return false;
+    return true;
 }
 
 cudaError_t fused_dispatch(int storage, int dim, int eos, int mlp, int pc, int tx, int ty, int tz, const SimDev* sims,
@@ -202,8 +218,7 @@ template <int D, typename R, typename S> struct Impl {
 
     static int step(lbm_ctx* h, int n)
     {
-        for (const SimDev& d : h->sims)
-            if (d.zwalls == 2 && !d.walls_set) return fail(h, LBM_E_STATE, "lbm_set_walls has not been called");
+        if (!faces_ready(h)) return fail(h, LBM_E_STATE, "lbm_set_walls / lbm_set_face has not set every face");
         for (int it = 0; it < n; ++it) {
             int rc = h->variant == LBM_KERNEL_FUSED ? fused_step(h)
                      : h->variant == LBM_KERNEL_ZMARCH ? zmarch_step(h) : split_step(h);
@@ -215,8 +230,7 @@ template <int D, typename R, typename S> struct Impl {
     // moments and macroscopic fields of the current state into W (no counters)
     static int macro(lbm_ctx* h)
     {
-        for (const SimDev& d : h->sims)
-            if (d.zwalls == 2 && !d.walls_set) return fail(h, LBM_E_STATE, "lbm_set_walls has not been called");
+        if (!faces_ready(h)) return fail(h, LBM_E_STATE, "lbm_set_walls / lbm_set_face has not set every face");
         const int nb = nblocks(h);
         k_moments<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (const S*)h->pop[h->cur],
                                                               (R*)h->W, h->Ntot);
@@ -273,7 +287,7 @@ template <int D, typename R, typename S> struct Impl {
 
     static int fused_ok(lbm_ctx* h, int tx, int ty, int tz)
     {
-        if (has_nee(h)) return 0;  // non-equilibrium-extrapolation walls: split kernels only
+        if (split_only(h)) return 0;  // extrapolated faces or duct friction: split kernels only
         for (const SimDev& d : h->sims)
             if (d.eos != h->sims[0].eos) return 0;  // one equation of state per fused launch
         if (uses_mlp(h) && h->storage != LBM_F32) return 0;  // learned start built for float32 storage
@@ -412,6 +426,8 @@ int fill_sim(SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, do
     if (E->isothermal && E->t_solver == LBM_T_MLP) { why = "isothermal runs invert no temperature"; return LBM_E_INVALID; }
     if (E->isothermal && H && H->q != 0.0) { why = "isothermal runs take no heat source"; return LBM_E_INVALID; }
     if (E->isothermal && L->zwalls == 2) { why = "non-equilibrium-extrapolation walls set a temperature: not isothermal"; return LBM_E_INVALID; }
+    if (F && (!(F->friction >= 0) || !std::isfinite(F->friction))) { why = "friction must be finite and >= 0"; return LBM_E_INVALID; }
+    if (F && F->friction > 0 && E->isothermal) { why = "friction heat needs the energy equation: not isothermal"; return LBM_E_INVALID; }
     s.nx = L->nx; s.ny = L->ny; s.nz = L->nz; s.zwalls = L->zwalls;
     s.N = (long long)L->nx * L->ny * L->nz;
     s.eos = E->kind;
@@ -435,6 +451,7 @@ int fill_sim(SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, do
     s.beta_f = 1.0 / (2.0 * tau_f + 1.0);
     s.beta_g = 1.0 / (2.0 * tau_g + 1.0);
     if (F) { s.acc[0] = F->accel[0]; s.acc[1] = F->accel[1]; s.acc[2] = L->dim == 3 ? F->accel[2] : 0.0; }
+    if (F) s.friction = F->friction;
     s.inv_cv = 1.0 / s.cv;
     s.inv_Tc = s.Tc > 0 ? 1.0 / s.Tc : 0.0;
     s.lam_c = s.b > 0 ? 1.0 / (2.0 * std::sqrt(2.0) * s.b) : 0.0;
@@ -578,7 +595,7 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
         fused_default_tile(h->dim, h->storage, dtx, dty, dtz);
         bool same_eos = true;
         for (const SimDev& d : h->sims) same_eos = same_eos && d.eos == h->sims[0].eos;
-        if (h->dim == 3 && same_eos && !has_nee(h) && zmarch_shape(h->storage, 30, 14)) {
+        if (h->dim == 3 && same_eos && !split_only(h) && zmarch_shape(h->storage, 30, 14)) {
             h->variant = LBM_KERNEL_ZMARCH;
             h->tx = 30; h->ty = 14; h->tz = 32;
             rc = build_tiles(h, 30, 14, 32);
@@ -671,7 +688,40 @@ int lbm_set_walls(lbm_handle h, const double* u_lo, double T_lo, const double* u
         d.Tw[0] = T_lo;
         d.Tw[1] = T_hi;
         d.wall_rho = wall_rho;
-        d.walls_set = 1;
+        d.face_kind[0] = d.face_kind[1] = 0;
+        d.face_set[0] = d.face_set[1] = 1;
+    }
+    LBM_CUDA_CHECK(h, cudaMemcpyAsync(h->d_sims, h->sims.data(), h->sims.size() * sizeof(SimDev),
+                                      cudaMemcpyHostToDevice, h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_face(lbm_handle h, int face, int kind, const double* u, double T, double P)
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (face != 0 && face != 1) return fail(h, LBM_E_INVALID, "face must be 0 (z = 0) or 1 (z = nz - 1)");
+    if (kind < LBM_FACE_INLET_TOTAL || kind > LBM_FACE_OUTLET_EXTRAP) return fail(h, LBM_E_INVALID, "unknown face kind");
+    const bool inlet = kind == LBM_FACE_INLET_TOTAL || kind == LBM_FACE_INLET_STATIC;
+    if (kind == LBM_FACE_INLET_STATIC) {
+        if (!u) return fail(h, LBM_E_INVALID, "a static inlet needs its velocity");
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(u[a])) return fail(h, LBM_E_INVALID, "velocity must be finite");
+    }
+    if (inlet && (!(T > 0) || !std::isfinite(T))) return fail(h, LBM_E_INVALID, "inlet temperature must be finite and > 0");
+    if (kind != LBM_FACE_OUTLET_EXTRAP && (!(P > 0) || !std::isfinite(P)))
+        return fail(h, LBM_E_INVALID, "face pressure must be finite and > 0");
+    if (!has_nee(h)) return fail(h, LBM_E_STATE, "no simulation of the handle has non-equilibrium-extrapolation walls");
+    for (const SimDev& d : h->sims)
+        if (d.zwalls == 2 && kind == LBM_FACE_INLET_TOTAL && d.eos != EOS_IDEAL)
+            return fail(h, LBM_E_UNSUPPORTED, "a total-state inlet needs the ideal gas");
+    for (SimDev& d : h->sims) {
+        if (d.zwalls != 2) continue;
+        for (int a = 0; a < 3; ++a) d.uw[face][a] = (kind == LBM_FACE_INLET_STATIC) ? u[a] : 0.0;
+        if (h->dim == 2) d.uw[face][2] = 0.0;
+        d.Tw[face] = inlet ? T : 1.0;
+        d.face_P[face] = P;
+        d.face_kind[face] = kind;
+        d.face_set[face] = 1;
     }
     LBM_CUDA_CHECK(h, cudaMemcpyAsync(h->d_sims, h->sims.data(), h->sims.size() * sizeof(SimDev),
                                       cudaMemcpyHostToDevice, h->stream));
@@ -906,8 +956,8 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
         h->variant = LBM_KERNEL_SPLIT;
         return LBM_OK;
     }
-    if ((variant == LBM_KERNEL_ZMARCH || variant == LBM_KERNEL_FUSED) && has_nee(h))
-        return fail(h, LBM_E_UNSUPPORTED, "non-equilibrium-extrapolation walls run on the split kernels");
+    if ((variant == LBM_KERNEL_ZMARCH || variant == LBM_KERNEL_FUSED) && split_only(h))
+        return fail(h, LBM_E_UNSUPPORTED, "extrapolated faces and duct friction run on the split kernels");
     if (variant == LBM_KERNEL_ZMARCH) {
         if (h->dim != 3) return fail(h, LBM_E_INVALID, "the z-march kernel runs D3Q27 lattices");
         if (tx <= 0 || ty <= 0) { tx = 30; ty = 14; }
@@ -983,7 +1033,7 @@ int lbm_autotune(lbm_handle h, int trial_steps, int* variant, int* tx, int* ty, 
         bool same_eos = true;
         for (const SimDev& d : h->sims) same_eos = same_eos && d.eos == h->sims[0].eos;
         for (auto& t : zshapes)
-            if (same_eos && !has_nee(h) && zmarch_shape(h->storage, t[0], t[1]))
+            if (same_eos && !split_only(h) && zmarch_shape(h->storage, t[0], t[1]))
                 cands.push_back({LBM_KERNEL_ZMARCH, t[0], t[1], t[2]});
     }
     h->graph_steps = 0;

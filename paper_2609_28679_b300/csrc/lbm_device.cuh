@@ -50,7 +50,10 @@ struct SimDev {
     const float* mlp;             // learned T(rho, e) parameters (t_solver == LBM_T_MLP), or null
     double uw[2][3], Tw[2];       // zwalls == 2: velocity and temperature of the walls at z = 0 and z = nz - 1
     int wall_rho;                 // zwalls == 2: 0 rho_B from the neighbour's pressure, 1 rho_B = rho_N
-    int walls_set;                // zwalls == 2: lbm_set_walls has been called
+    int face_kind[2];             // zwalls == 2: 0 wall, else LBM_FACE_* (open duct end)
+    int face_set[2];              // zwalls == 2: the face has its data (lbm_set_walls / lbm_set_face)
+    double face_P[2];             // pressure datum of an open face (total for INLET_TOTAL)
+    double friction;              // duct friction k: F_f = -k rho |u| u, Q_f = -F_f.u (split kernels)
 };
 
 // The same constants in the arithmetic type R (built once per tile on the

@@ -258,6 +258,47 @@ __device__ __forceinline__ void grad_lap(const R* __restrict__ rho, int x, int y
     }
 }
 
+// Duct friction (Fanno flow): F_f = -k rho |u| u joins F and Q gains
+// Q_f = -F_f.u, with u = (j + F/2)/rho solved exactly: for w the velocity
+// without F_f, |u| (1 + k |u|/2) = |w|, so u = 2 w / (1 + sqrt(1 + 2 k |w|)).
+template <int D, typename R>
+__device__ __forceinline__ void apply_friction(const SimDev& s, R r, const R* j, R* F, R& Q)
+{
+    if (!(s.friction > 0.0)) return;
+    const R k = (R)s.friction;
+    R w[3] = {0, 0, 0}, wn = 0, un = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        w[a] = (j[a] + R(0.5) * F[a]) / r;
+        wn += w[a] * w[a];
+    }
+    wn = sqrt(wn);
+    const R sc = R(2) / (R(1) + sqrt(R(1) + R(2) * k * wn));
+#pragma unroll
+    for (int a = 0; a < D; ++a) un += (sc * w[a]) * (sc * w[a]);
+    un = sqrt(un);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const R Ff = -k * r * un * (sc * w[a]);
+        F[a] += Ff;
+        Q -= Ff * (sc * w[a]);
+    }
+}
+
+// heat source of a cell including the friction heat k rho |u|^3 at its velocity
+template <int D, typename R>
+__device__ __forceinline__ R cell_heat(const SimDev& s, int z, R r, const R* u)
+{
+    R Q = (R)heat_at(s, z);
+    if (s.friction > 0.0) {
+        R u2 = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) u2 += u[a] * u[a];
+        Q += (R)s.friction * r * sqrt(u2) * u2;
+    }
+    return Q;
+}
+
 // ---------------------------------------------------------------------------
 // Pass 2: force, velocity, energy, temperature and closure scalars per cell.
 // ---------------------------------------------------------------------------
@@ -296,9 +337,10 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
             for (int a = 0; a < D; ++a) F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl[a];
 #pragma unroll
             for (int a = 0; a < 3; ++a) j[a] = FROM_M ? M[(M_J + a) * Ntot + gk] : W[(W_J + a) * Ntot + gk];
+            R Qc = (R)heat_at(s, z);
+            apply_friction<D, R>(s, r, j, F, Qc);
             rr = (float)r;
-            ee = (float)macro_energy<D, R>(r, j, FROM_M ? M[M_G * Ntot + gk] : W[W_G * Ntot + gk], F,
-                                            (R)heat_at(s, z));
+            ee = (float)macro_energy<D, R>(r, j, FROM_M ? M[M_G * Ntot + gk] : W[W_G * Ntot + gk], F, Qc);
         }
         Tml = (R)mlp_T_warp(mlp_s, rr, ee);
     }
@@ -315,6 +357,7 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
 #pragma unroll
         for (int a = 0; a < 3; ++a) j[a] = FROM_M ? M[(M_J + a) * Ntot + gk] : W[(W_J + a) * Ntot + gk];
         R Q = (R)heat_at(s, z);
+        apply_friction<D, R>(s, r, j, F, Q);
         Macro<R> m = macro_cell<D, R>(s, r, j, FROM_M ? M[M_G * Ntot + gk] : W[W_G * Ntot + gk], F, Q,
                                       use_mlp ? Tml : W[W_T * Ntot + gk], flags);
         if (FROM_M) W[W_RHO * Ntot + gk] = r;
@@ -395,7 +438,9 @@ __device__ __forceinline__ void stencils(const SimDev& s, const R* __restrict__ 
 // and temperature, the density rho_N of its neighbour z_N in {1, nz - 2}
 // (wall_rho 1) or the density whose pressure at T_W is the neighbour's
 // (wall_rho 0: eight Newton steps from rho_N, rho_N again if they end
-// non-finite or non-positive), and the populations
+// non-finite or non-positive); an open face (the duct ends of Sec. III.A)
+// takes the boundary state of its kind instead (LBM_FACE_* in lbm.h).  The
+// populations are
 //   f_B = f^eq(rho_B, u_W, theta_W) + f_N - f^eq(rho_N, u_N, theta_N), g alike,
 // written to the storage slots its pull reads (no other cell reads those).
 // Its macroscopic fields become the wall state; its force keeps the
@@ -419,28 +464,53 @@ __global__ void __launch_bounds__(kBlockCells) k_nee(const SimDev* __restrict__ 
     const long long plane = (long long)s.nx * s.ny;
     const long long gb = s.cell_off + k, gn = s.cell_off + (side ? k - plane : k + plane);
     const R rn = W[W_RHO * Ntot + gn];
-    const R Tw = (R)s.Tw[side];
-    R rb = rn;
-    if (s.wall_rho == 0) {
-        const R PN = W[W_P * Ntot + gn];  // P(rho_N, T_N)
-        R r = rn;
-#pragma unroll 1
-        for (int it = 0; it < 8; ++it) {
-            const Thermo<R> t = thermo<R>(s, rho_part<R>(s, r), Tw);
-            r -= (t.P - PN) / t.Pr;
-        }
-        if (isfinite(r) && r > R(0)) rb = r;
-    }
-    const RhoPart<R> pb = rho_part<R>(s, rb);
-    const Thermo<R> t = thermo<R>(s, pb, Tw);
-    const R ib = R(1) / rb;
-    const R thw = t.P * ib, ew = eos_e<R>(s, pb, Tw);
+    const int kind = s.face_kind[side];
     R uw[3], un[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         uw[a] = a < D ? (R)s.uw[side][a] : R(0);
         un[a] = W[(W_U + a) * Ntot + gn];
     }
+    // boundary state (rho_B, u_B = uw, T_B = Tw) of the face's kind; Pt: the pressure rho_B must meet at Tw
+    R Tw = (R)s.Tw[side], Pt = R(-1);
+    if (kind == 0) {
+        if (s.wall_rho == 0) Pt = W[W_P * Ntot + gn];  // P(rho_N, T_N)
+    } else if (kind == 1) {  // subsonic inlet from the total state (ideal gas)
+        const R cp = (R)s.cv + (R)s.R;
+        R n2 = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) { uw[a] = un[a]; n2 += un[a] * un[a]; }
+        const R T0 = Tw;
+        Tw = T0 - R(0.5) * n2 / cp;
+        Pt = (R)s.face_P[side] * pow(Tw / T0, cp / (R)s.R);
+    } else if (kind == 2) {  // static inlet
+        Pt = (R)s.face_P[side];
+    } else if (kind == 3) {  // pressure outlet
+        Tw = W[W_T * Ntot + gn];
+        Pt = (R)s.face_P[side];
+    } else {  // extrapolated outlet
+#pragma unroll
+        for (int a = 0; a < D; ++a) uw[a] = un[a];
+        Tw = W[W_T * Ntot + gn];
+    }
+    R rb = rn;
+    if (Pt > R(0)) {
+        R r = rn;
+#pragma unroll 1
+        for (int it = 0; it < 8; ++it) {
+            const Thermo<R> t = thermo<R>(s, rho_part<R>(s, r), Tw);
+            r -= (t.P - Pt) / t.Pr;
+        }
+        if (isfinite(r) && r > R(0)) rb = r;
+    }
+    if (kind == 3) {  // the neighbour's mass flux
+#pragma unroll
+        for (int a = 0; a < D; ++a) uw[a] = un[a] * (rn / rb);
+    }
+    const RhoPart<R> pb = rho_part<R>(s, rb);
+    const Thermo<R> t = thermo<R>(s, pb, Tw);
+    const R ib = R(1) / rb;
+    const R thw = t.P * ib, ew = eos_e<R>(s, pb, Tw);
     if (pops) {
         R feqB[Q], geqB[Q], feqN[Q], geqN[Q], fN[Q], gN[Q];
         equilibria<D, R>(rb, uw, thw, ew, feqB, geqB);
@@ -458,18 +528,27 @@ __global__ void __launch_bounds__(kBlockCells) k_nee(const SimDev* __restrict__ 
             Codec<S, R>::st(gbuf + idx, geqB[i] + (gN[i] - geqN[i]) - go);
         }
     }
-    const R scale = rb / W[W_RHO * Ntot + gb];
-    const R Qh = (R)heat_at(s, z);
-    R uF = 0, u2 = 0;
+    // force and heat: the non-friction part per unit mass kept, friction at (rho_B, u_B)
+    const R ro = W[W_RHO * Ntot + gb], kf = (R)s.friction;
+    R uo[3], uo2 = 0, u2 = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const R Fa = W[(W_F + a) * Ntot + gb] * scale;
+        uo[a] = W[(W_U + a) * Ntot + gb];
+        if (a < D) { uo2 += uo[a] * uo[a]; u2 += uw[a] * uw[a]; }
+    }
+    const R uon = sqrt(uo2), ubn = sqrt(u2);
+    const R Qh = cell_heat<D, R>(s, z, rb, uw);
+    R uF = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const R Ffo = a < D ? -kf * ro * uon * uo[a] : R(0);
+        const R Ffb = a < D ? -kf * rb * ubn * uw[a] : R(0);
+        const R Fa = (W[(W_F + a) * Ntot + gb] - Ffo) * (rb / ro) + Ffb;
         W[(W_F + a) * Ntot + gb] = Fa;
         W[(W_U + a) * Ntot + gb] = uw[a];
-        W[(W_J + a) * Ntot + gb] = rb * uw[a] - R(0.5) * Fa;  // so that J + F/2 = rho_B u_W (Eq. def_u)
+        W[(W_J + a) * Ntot + gb] = rb * uw[a] - R(0.5) * Fa;  // so that J + F/2 = rho_B u_B (Eq. def_u)
         W[(W_X + a) * Ntot + gb] = a < D ? xflux<R>(rb, uw[a], thw) : R(0);
         uF += uw[a] * Fa;
-        u2 += uw[a] * uw[a];
     }
     const R icv = s.eos == EOS_PR ? R(1) / t.cv : (R)s.inv_cv;
     const R cs2 = t.Pr + Tw * t.PT * t.PT * ib * ib * icv;
@@ -509,7 +588,7 @@ __global__ void __launch_bounds__(kBlockCells) k_collide(const SimDev* __restric
         m.u[a] = W[(W_U + a) * Ntot + gk];
         m.F[a] = W[(W_F + a) * Ntot + gk];
     }
-    m.Q = (R)heat_at(s, z);
+    m.Q = cell_heat<D, R>(s, z, m.rho, m.u);
     m.T = W[W_T * Ntot + gk];
     m.P = W[W_P * Ntot + gk];
     m.theta = W[W_TH * Ntot + gk];
@@ -567,7 +646,8 @@ __global__ void __launch_bounds__(kBlockCells) k_invariants(const SimDev* __rest
             v[D + 2 + a] = Fa;
             uF += ua * Fa;
         }
-        double Q = heat_at(s, z);
+        R ur[3] = {W[(W_U + 0) * Ntot + gk], W[(W_U + 1) * Ntot + gk], W[(W_U + 2) * Ntot + gk]};
+        double Q = (double)cell_heat<D, R>(s, z, W[W_RHO * Ntot + gk], ur);
         v[D + 1] = (double)W[W_G * Ntot + gk] + 0.5 * (uF + Q);  // Eq. def_E
         v[2 * D + 2] = uF + Q;
     }

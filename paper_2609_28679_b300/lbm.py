@@ -22,6 +22,7 @@ LBM_IDEAL, LBM_VDW, LBM_PR = 0, 1, 2
 LBM_T_NEWTON, LBM_T_MLP = 0, 1
 LBM_PHI_UPWIND, LBM_PHI_CENTRAL = 0, 1
 LBM_KERNEL_AUTO, LBM_KERNEL_SPLIT, LBM_KERNEL_FUSED, LBM_KERNEL_ZMARCH = 0, 1, 2, 3
+LBM_FACE_INLET_TOTAL, LBM_FACE_INLET_STATIC, LBM_FACE_OUTLET_P, LBM_FACE_OUTLET_EXTRAP = 1, 2, 3, 4
 
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "bf16": LBM_BF16, "f16": LBM_F16}
 EOS = {"ideal": LBM_IDEAL, "vdw": LBM_VDW, "pr": LBM_PR}
@@ -45,7 +46,7 @@ class lbm_eos(ctypes.Structure):
 
 
 class lbm_force(ctypes.Structure):
-    _fields_ = [("accel", ctypes.c_double * 3)]
+    _fields_ = [("accel", ctypes.c_double * 3), ("friction", ctypes.c_double)]
 
 
 class lbm_heat(ctypes.Structure):
@@ -67,6 +68,8 @@ _SIGS = {
     "lbm_set_force": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_set_walls": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                                      ctypes.c_double, ctypes.c_int]),
+    "lbm_set_face": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
+                                    ctypes.c_double]),
     "lbm_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -196,6 +199,13 @@ def lbm_set_walls(h, u_lo, T_lo: float, u_hi, T_hi: float, wall_rho: int = 0) ->
     _check(_lib.lbm_set_walls(h, lo.ctypes.data, float(T_lo), hi.ctypes.data, float(T_hi), int(wall_rho)), h)
 
 
+def lbm_set_face(h, face: int, kind: int, u=None, T: float = 0.0, P: float = 0.0) -> None:
+    uu = np.zeros(3)
+    if u is not None:
+        uu[:len(u)] = u
+    _check(_lib.lbm_set_face(h, int(face), int(kind), uu.ctypes.data, float(T), float(P)), h)
+
+
 def lbm_step(h, n: int) -> None:
     _check(_lib.lbm_step(h, int(n)), h)
 
@@ -305,7 +315,7 @@ def structs_from_case(case):
     eos = lbm_eos(EOS[case.eos], case.R, case.cv, case.a, case.b, case.Tc, case.Pc, case.omega, case.kappa,
                   case.eta_over_mu, case.k_over_mu, getattr(case, "t_solver", LBM_T_NEWTON), getattr(case, "mu", 0.0),
                   getattr(case, "isothermal", 0))
-    force = lbm_force((ctypes.c_double * 3)(*case.accel))
+    force = lbm_force((ctypes.c_double * 3)(*case.accel), getattr(case, "friction", 0.0))
     heat = lbm_heat(case.q, case.zlo, case.zhi)
     return lat, eos, force, heat
 
@@ -329,6 +339,10 @@ class Simulation:
         c0 = self.cases[0]
         if any(c.zwalls == 2 for c in self.cases):
             lbm_set_walls(self.h, c0.uw_lo, c0.Tw_lo, c0.uw_hi, c0.Tw_hi, getattr(c0, "wall_rho", 0))
+            for face, kind in enumerate(getattr(c0, "face_kind", (0, 0))):
+                if kind:
+                    lbm_set_face(self.h, face, kind, c0.uw_lo if face == 0 else c0.uw_hi,
+                                 c0.Tw_lo if face == 0 else c0.Tw_hi, c0.face_P[face])
         if variant is not None:
             t = tile or (0, 0, 0)
             lbm_set_kernel(self.h, variant, *t)

@@ -109,5 +109,16 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_E_INVALID
     assert lib.lbm_set_force(None, None) == lbm.LBM_E_INVALID
     assert lib.lbm_set_walls(None, None, 1.0, None, 1.0, 0) == lbm.LBM_E_INVALID
+    assert lib.lbm_set_face(None, 0, lbm.LBM_FACE_OUTLET_P, None, 1.0, 1.0) == lbm.LBM_E_INVALID
+
+
+@pytest.mark.parametrize("friction", [-1e-3, float("nan")])
+def test_invalid_friction_rejected_without_device(lib, friction):
+    lat = lbm.lbm_lattice(dim=3, nx=1, ny=1, nz=8, zwalls=0, storage=0, phi_scheme=0)
+    eos = lbm.lbm_eos(kind=0, R=1.0, cv=2.5)
+    force = lbm.lbm_force((ctypes.c_double * 3)(0.0, 0.0, 0.0), friction)
+    h = ctypes.c_void_p()
+    rc = lib.lbm_create(ctypes.byref(lat), ctypes.byref(eos), 0.8, 0.8, ctypes.byref(force), None, ctypes.byref(h))
+    assert rc == lbm.LBM_E_INVALID and not h.value
     assert lib.lbm_invariants(None, None) == lbm.LBM_E_INVALID
     lib.lbm_destroy(None)

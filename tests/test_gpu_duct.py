@@ -1,0 +1,158 @@
+"""Duct ends and duct friction (the 1-D duct flows of Sec. III.A, run as
+columns of D3Q27) on the GPU split kernels, through the C ABI, against the
+FP64 CPU oracle on the same seeded inputs: populations and moments element by
+element for every face kind and for friction (also in 2-D), the conservation
+totals, the steady Rayleigh relations, and the API rules.
+
+Tolerances as in the other parity tests: float64 1e-12 relative (u to 1e-12 of
+max(max|u_ref|, 1e-3)), float32 1e-5 (u to 1e-5 of the lattice speed)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2609_28679_b300 import lbm
+from paper_2609_28679_b300 import workloads as wl
+from tests.util import oracle_params, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+R_GAS, CV = 1.0, 2.5
+CP, GAM = R_GAS + CV, (R_GAS + CV) / CV
+T_IN, P_IN, MA_IN = 0.1, 0.1, 0.3
+T0 = T_IN * (1.0 + 0.5 * (GAM - 1.0) * MA_IN ** 2)
+P0 = P_IN * (T0 / T_IN) ** (CP / R_GAS)
+U_IN = MA_IN * math.sqrt(GAM * R_GAS * T_IN)
+
+
+def _duct(nz=40, nx=1, ny=1, q=0.0, friction=0.0, kinds=(1, 3), face_P=(P0, 0.08), uw_lo=(0.0, 0.0, 0.0),
+          T_lo=T0, storage="f64", amp=0.0):
+    init = dict(kind="duct", rho0=P_IN / (R_GAS * T_IN), u0=U_IN, T0=T_IN)
+    c = wl.Case(name="duct", dim=3, nx=nx, ny=ny, nz=nz, zwalls=2, eos="ideal", R=R_GAS, cv=CV,
+                k_over_mu=CP / 0.71, tau_f=0.8, tau_g=0.8, phi_central=1, q=q, zlo=0, zhi=0, friction=friction,
+                face_kind=kinds, face_P=face_P, uw_lo=uw_lo, Tw_lo=T_lo, Tw_hi=T_lo, storage=storage, init=init)
+    return c
+
+
+def _noisy_fields(c, amp, seed):
+    rho, u, T = c.fields()
+    rho = rho * (1.0 + amp * wl.uniform_pm1(seed, c.ncell))
+    T = T * (1.0 + amp * wl.uniform_pm1(seed + 1, c.ncell))
+    return rho, u, T
+
+
+def _pair(c, steps, fields):
+    sim = lbm.Simulation(c)
+    assert sim.kernel()[0] == lbm.LBM_KERNEL_SPLIT
+    sim.init(fields)
+    sim.step(steps)
+    o = orc.Oracle(oracle_params(c))
+    o.init(*fields)
+    o.step(steps)
+    return sim, o
+
+
+def _compare(sim, o, tol, f32=False):
+    f, g = sim.populations()
+    fr, gr = o.populations()
+    assert rel_linf(f, fr.ravel()) <= tol
+    assert rel_linf(g, gr.ravel()) <= tol
+    rho, u, T = sim.moments()
+    rr, ur, Tr = o.moments()
+    assert rel_linf(rho, rr) <= tol
+    assert rel_linf(T, Tr) <= tol
+    tol_u = tol if f32 else tol * max(float(np.max(np.abs(ur))), 1e-3)
+    assert float(np.max(np.abs(u - ur.ravel()))) <= tol_u
+
+
+@pytest.mark.parametrize("kinds,face_P,uw_lo,T_lo", [
+    ((1, 3), (P0, 0.08), (0.0, 0.0, 0.0), T0),          # subsonic: total inlet, pressure outlet
+    ((2, 4), (P_IN, 0.0), (0.0, 0.0, U_IN), T_IN),      # static inlet, extrapolated outlet
+    ((2, 3), (P_IN, 0.09), (0.0, 0.0, U_IN), T_IN),
+])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 2)])
+def test_f64_duct_ends_match_oracle(kinds, face_P, uw_lo, T_lo, nx, ny):
+    c = _duct(nz=40, nx=nx, ny=ny, q=4e-5, kinds=kinds, face_P=face_P, uw_lo=uw_lo, T_lo=T_lo)
+    sim, o = _pair(c, 120, _noisy_fields(c, 0.01, 31))
+    _compare(sim, o, 1e-12)
+
+
+def test_f64_fanno_friction_matches_oracle():
+    c = _duct(nz=40, friction=4e-3)
+    sim, o = _pair(c, 150, _noisy_fields(c, 0.01, 32))
+    _compare(sim, o, 1e-12)
+
+
+def test_f64_friction_2d_periodic_matches_oracle_and_conserves_energy():
+    # friction in a periodic 2-D van der Waals flow: parity, and Q = -F.u keeps total energy exact
+    # (friction the only force, so that sum (u.F + Q) vanishes)
+    c = wl.vdw_spinodal(n=24, storage="f64")
+    c.friction, c.accel, c.kappa = 0.05, (0.0, 0.0, 0.0), 0.0
+    c.init = dict(kind="waves", rho0=wl.VDW_RHO_MID_090, amp_rho=0.01, amp_u=0.05, T0=0.1)
+    fields = c.fields()
+    fields[1][0] += 0.04  # mean flow along x
+    sim, o = _pair(c, 30, fields)
+    _compare(sim, o, 1e-12)
+    gi = sim.invariants()[0]
+    oi = o.invariants()
+    assert np.all(np.abs(gi - oi) <= 1e-12 * np.maximum(np.abs(oi), np.abs(oi[0])))
+    assert abs(gi[-1]) <= 1e-12 * abs(gi[3])  # sum (u.F + Q) = 0
+
+
+def test_f32_duct_matches_oracle():
+    c = _duct(nz=40, q=4e-5, friction=2e-3, storage="f32")
+    sim, o = _pair(c, 120, _noisy_fields(c, 0.01, 33))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+def test_rayleigh_relations_on_the_gpu():
+    nz, q = 50, 4e-5
+    c = _duct(nz=nz, q=q)
+    sim = lbm.Simulation(c)
+    sim.init()
+    sim.step(20000)
+    rho, u, T = sim.moments()
+    uz = u.reshape(3, -1)[2]
+    P = rho * R_GAS * T
+    Ma = uz / np.sqrt(GAM * R_GAS * T)
+    assert np.ptp((rho * uz)[1:-1]) <= 1e-10 * (rho * uz).mean()
+    Ts = T * (1 + GAM * Ma ** 2) ** 2 / ((1 + GAM) ** 2 * Ma ** 2)
+    Ps = P * (1 + GAM * Ma ** 2) / (1 + GAM)
+    assert np.ptp(Ts[1:-1]) <= 1e-3 * Ts.mean()
+    assert np.ptp(Ps[1:-1]) <= 1e-3 * Ps.mean()
+
+
+def test_duct_api_rules():
+    c = _duct(nz=12, friction=1e-3)
+    lat, eos, force, heat = lbm.structs_from_case(c)
+    h = lbm.lbm_create(lat, eos, c.tau_f, c.tau_g, force, heat)
+    try:
+        assert lbm.lbm_get_kernel(h)[0] == lbm.LBM_KERNEL_SPLIT
+        rho, u, T = c.fields()
+        lbm.lbm_init(h, rho, u.ravel(), T, 0)
+        lbm.lbm_set_face(h, 0, lbm.LBM_FACE_INLET_TOTAL, None, T0, P0)
+        with pytest.raises(lbm.LbmError, match="every face"):
+            lbm.lbm_step(h, 1)  # face 1 not set yet
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_set_face(h, 1, lbm.LBM_FACE_OUTLET_P, None, 0.0, -1.0)
+        lbm.lbm_set_face(h, 1, lbm.LBM_FACE_OUTLET_P, None, 0.0, 0.08)
+        lbm.lbm_step(h, 2)
+        with pytest.raises(lbm.LbmError, match="split"):
+            lbm.lbm_set_kernel(h, lbm.LBM_KERNEL_FUSED)
+    finally:
+        lbm.lbm_destroy(h)
+    # friction alone (periodic) also keeps the split kernels
+    p = wl.vdw_spinodal(n=16, storage="f64")
+    p.friction = 1e-3
+    sim = lbm.Simulation(p)
+    assert sim.kernel()[0] == lbm.LBM_KERNEL_SPLIT
+    sim.close()
+    # a total-state inlet needs the ideal gas
+    v = _duct(nz=12)
+    v.eos, v.a, v.b = "vdw", wl.VDW_A, wl.VDW_B
+    v.face_kind = (0, 0)
+    sim = lbm.Simulation(v)
+    with pytest.raises(lbm.LbmError, match="ideal"):
+        lbm.lbm_set_face(sim.h, 0, lbm.LBM_FACE_INLET_TOTAL, None, 0.1, 0.1)
+    sim.close()
