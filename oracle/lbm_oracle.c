@@ -92,11 +92,15 @@
  *    form of the same model exactly, except that the normal viscous stress
  *    is the 3-D one, (4/3 mu + eta) du/dz (both are regularisers of the
  *    inviscid Rayleigh and Fanno solutions).
- *  - Duct friction (Fanno flow): F_f = -k rho |u| u with k = f_D/(2 D_h) and
- *    the compensating heat Q_f = -F_f.u, both added to F and Q of phase B.
- *    u = (J + F/2)/rho then depends on F_f; the relation is solved exactly:
- *    with w = (J + (F_B + F_K)/2)/rho, |u| (1 + k |u|/2) = |w|, so
- *    u = 2 w / (1 + sqrt(1 + 2 k |w|)).
+ *  - Duct resistance: the friction of Fanno flow F_f = -k rho |u| u (k =
+ *    f_D/(2 D_h)) and the Darcy throttle of the throttling process F_t =
+ *    -K phi(z) rho u (phi a Gaussian of width sigma at the middle of the
+ *    duct), with the compensating heat Q_r = -F_r.u, added to F and Q of
+ *    phase B.  u = (J + F/2)/rho then depends on F_r; the relation is solved
+ *    exactly: with w = (J + (F_B + F_K)/2)/rho and a = 1 + K phi/2,
+ *    |u| (a + k |u|/2) = |w|, so u = 2 w / (a + sqrt(a^2 + 2 k |w|)).
+ *    The throttling inlet (face kind 5) holds static P and T with the
+ *    neighbour's velocity.
  *  - Peng-Robinson: the paper names the model only.  The textbook form with the
  *    Soave alpha(T) and a constant ideal-part c_v is used; e(rho,T) follows by
  *    integrating Eq. de_rho at constant T from rho = 0.  T(rho,e) is found by
@@ -144,6 +148,8 @@ typedef struct {
                                   (uw, Tw) above, the open kinds take (uw, Tw, face_P) as their data */
     double face_P[2];          /* static pressure (inlet static, outlet) or total pressure (inlet total) */
     double friction;           /* duct friction k = f_D / (2 D_h): F = -k rho |u| u, with Q = -F.u */
+    double throttle_K;         /* throttle (Sec. III.B, throttling): F = -K phi(z) rho u, with Q = -F.u, */
+    double throttle_sigma;     /* phi(z) = exp(-((z - (nz - 1)/2) / sigma)^2)  (dim 3) */
 } orc_params;
 
 /* Boundary kinds of a z face with zwalls = 2 (Sec. IV walls; Sec. III.A duct ends) */
@@ -152,6 +158,7 @@ typedef struct {
 #define ORC_FACE_INLET_STATIC 2  /* supersonic inlet: static P, T and u given */
 #define ORC_FACE_OUTLET_P 3      /* subsonic outlet: static P given, u and T from the neighbour */
 #define ORC_FACE_OUTLET_EXTRAP 4 /* supersonic outlet: rho, u, T from the neighbour */
+#define ORC_FACE_INLET_PT 5      /* inlet with static P and T given, u from the neighbour (throttling) */
 
 typedef struct {
     orc_params p;
@@ -415,13 +422,15 @@ orc_state *orc_create(const orc_params *p)
     if (p->zwalls < 0 || p->zwalls > 2) return NULL;
     if (p->zwalls == 2 && (p->nz < 4 || p->isothermal || !(p->Tw_lo > 0) || !(p->Tw_hi > 0))) return NULL;
     for (int f = 0; f < 2; ++f) {
-        if (p->face_kind[f] < ORC_FACE_WALL || p->face_kind[f] > ORC_FACE_OUTLET_EXTRAP) return NULL;
+        if (p->face_kind[f] < ORC_FACE_WALL || p->face_kind[f] > ORC_FACE_INLET_PT) return NULL;
         if (p->face_kind[f] != ORC_FACE_WALL && p->zwalls != 2) return NULL;
         if (p->face_kind[f] == ORC_FACE_INLET_TOTAL && p->eos != ORC_IDEAL) return NULL;
         if ((p->face_kind[f] == ORC_FACE_INLET_TOTAL || p->face_kind[f] == ORC_FACE_INLET_STATIC ||
-             p->face_kind[f] == ORC_FACE_OUTLET_P) && !(p->face_P[f] > 0)) return NULL;
+             p->face_kind[f] == ORC_FACE_OUTLET_P || p->face_kind[f] == ORC_FACE_INLET_PT) && !(p->face_P[f] > 0))
+            return NULL;
     }
-    if (!(p->friction >= 0)) return NULL;
+    if (!(p->friction >= 0) || !(p->throttle_K >= 0)) return NULL;
+    if (p->throttle_K > 0 && (p->dim != 3 || !(p->throttle_sigma > 0))) return NULL;
     orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
     s->p = *p;
     int cflat[81];
@@ -546,6 +555,14 @@ int orc_init(orc_state *s, const double *rho, const double *u /* [dim][N] */, co
     return 0;
 }
 
+/* K phi(z) of the throttle at layer z (0 without one) */
+static double throttle_phi(const orc_params *p, long z)
+{
+    if (!(p->throttle_K > 0.0) || p->dim != 3) return 0.0;
+    double d = ((double)z - 0.5 * (double)(p->nz - 1)) / p->throttle_sigma;
+    return p->throttle_K * exp(-d * d);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Phases A-C: macroscopic fields of the current populations                 */
 /* ------------------------------------------------------------------------- */
@@ -615,20 +632,22 @@ static void macro_fields(orc_state *s)
     for (long k = 0; k < N; ++k) {
         double r = s->rho[k];
         double uu[3] = {0, 0, 0}, uF = 0, u2 = 0;
-        if (p->friction > 0.0) {
-            /* duct friction F_f = -k rho |u| u at the u it produces, and Q_f = -F_f.u */
+        double Kphi = throttle_phi(p, k / ((long)p->nx * p->ny));
+        if (p->friction > 0.0 || Kphi > 0.0) {
+            /* duct resistance F_r = -rho (K phi + k |u|) u at the u it produces, and Q_r = -F_r.u */
             double w[3] = {0, 0, 0}, wn = 0, un = 0;
             for (int a = 0; a < D; ++a) {
                 w[a] = (s->J[(long)a * N + k] + 0.5 * s->F[(long)a * N + k]) / r;
                 wn += w[a] * w[a];
             }
             wn = sqrt(wn);
-            double sc = 2.0 / (1.0 + sqrt(1.0 + 2.0 * p->friction * wn));
+            double a0 = 1.0 + 0.5 * Kphi;
+            double sc = 2.0 / (a0 + sqrt(a0 * a0 + 2.0 * p->friction * wn));
             for (int a = 0; a < D; ++a) un += (sc * w[a]) * (sc * w[a]);
             un = sqrt(un);
             double Qf = 0;
             for (int a = 0; a < D; ++a) {
-                double Ff = -p->friction * r * un * (sc * w[a]);
+                double Ff = -r * (Kphi + p->friction * un) * (sc * w[a]);
                 s->F[(long)a * N + k] += Ff;
                 Qf -= Ff * (sc * w[a]);
             }
@@ -716,6 +735,9 @@ static void nee_walls(orc_state *s, int pops)
                 } else if (kind == ORC_FACE_OUTLET_P) {
                     Tw = s->T[kn];
                     Pt = p->face_P[side];
+                } else if (kind == ORC_FACE_INLET_PT) {
+                    for (int a = 0; a < D; ++a) uW[a] = un[a];
+                    Pt = p->face_P[side];
                 } else {
                     for (int a = 0; a < D; ++a) uW[a] = un[a];
                     Tw = s->T[kn];
@@ -746,12 +768,13 @@ static void nee_walls(orc_state *s, int pops)
                 double ro = s->rho[kb], uo2 = 0, u2 = 0;
                 for (int a = 0; a < D; ++a) { uo2 += s->u[(long)a * N + kb] * s->u[(long)a * N + kb]; u2 += uW[a] * uW[a]; }
                 double uon = sqrt(uo2), ubn = sqrt(u2);
+                double Kphi = throttle_phi(p, zb);
                 for (int a = 0; a < 3; ++a) {
-                    double Ffo = a < D ? -p->friction * ro * uon * s->u[(long)a * N + kb] : 0.0;
-                    double Ffb = a < D ? -p->friction * rb * ubn * uW[a] : 0.0;
+                    double Ffo = a < D ? -ro * (Kphi + p->friction * uon) * s->u[(long)a * N + kb] : 0.0;
+                    double Ffb = a < D ? -rb * (Kphi + p->friction * ubn) * uW[a] : 0.0;
                     s->F[(long)a * N + kb] = (s->F[(long)a * N + kb] - Ffo) * (rb / ro) + Ffb;
                 }
-                s->Qs[kb] += p->friction * (rb * ubn * u2 - ro * uon * uo2);
+                s->Qs[kb] += rb * (Kphi + p->friction * ubn) * u2 - ro * (Kphi + p->friction * uon) * uo2;
                 for (int a = 0; a < 3; ++a) s->u[(long)a * N + kb] = uW[a];
                 double cv = orc_eos_cv(p, rb, Tw), PT = orc_eos_dPdT(p, rb, Tw), Pr = orc_eos_dPdrho(p, rb, Tw);
                 double cs2 = Pr + Tw * PT * PT / (rb * rb * cv);

@@ -53,6 +53,7 @@ class OrcParams(ctypes.Structure):
         ("wall_rho", ctypes.c_int),
         ("face_kind", ctypes.c_int * 2), ("face_P", ctypes.c_double * 2),
         ("friction", ctypes.c_double),
+        ("throttle_K", ctypes.c_double), ("throttle_sigma", ctypes.c_double),
     ]
 
 
@@ -107,7 +108,8 @@ def make_params(dim=2, nx=8, ny=8, nz=1, zwalls=0, eos="ideal", R=1.0, cv=2.5, a
                 Tc=1.0, omega=0.0, Pc=None, kappa=0.0, eta_over_mu=0.0, k_over_mu=0.0,
                 tau_f=0.8, tau_g=0.8, accel=(0.0, 0.0, 0.0), q=0.0, zlo=0, zhi=0,
                 phi_central=0, mu=0.0, isothermal=0, uw_lo=(0.0, 0.0, 0.0), uw_hi=(0.0, 0.0, 0.0),
-                Tw_lo=0.0, Tw_hi=0.0, wall_rho=0, face_kind=(0, 0), face_P=(0.0, 0.0), friction=0.0) -> OrcParams:
+                Tw_lo=0.0, Tw_hi=0.0, wall_rho=0, face_kind=(0, 0), face_P=(0.0, 0.0), friction=0.0, throttle_K=0.0,
+                throttle_sigma=0.0) -> OrcParams:
     """Build the oracle's parameter struct.  For Peng-Robinson with ``Pc`` given
     and ``a == 0``, a and b follow from (Tc, Pc) by the oracle's own helper.
     zwalls = 2 selects the non-equilibrium-extrapolation walls with wall
@@ -136,6 +138,7 @@ def make_params(dim=2, nx=8, ny=8, nz=1, zwalls=0, eos="ideal", R=1.0, cv=2.5, a
         p.face_kind[f] = int(face_kind[f])
         p.face_P[f] = float(face_P[f])
     p.friction = float(friction)
+    p.throttle_K, p.throttle_sigma = float(throttle_K), float(throttle_sigma)
     return p
 
 
@@ -300,4 +303,5 @@ def params_from_case(case) -> OrcParams:
                        uw_hi=getattr(case, "uw_hi", (0.0, 0.0, 0.0)), Tw_lo=getattr(case, "Tw_lo", 0.0),
                        Tw_hi=getattr(case, "Tw_hi", 0.0), wall_rho=getattr(case, "wall_rho", 0),
                        face_kind=getattr(case, "face_kind", (0, 0)), face_P=getattr(case, "face_P", (0.0, 0.0)),
-                       friction=getattr(case, "friction", 0.0))
+                       friction=getattr(case, "friction", 0.0), throttle_K=getattr(case, "throttle_K", 0.0),
+                       throttle_sigma=getattr(case, "throttle_sigma", 0.0))

@@ -70,8 +70,11 @@ class Case:
     wall_rho: int = 0               # and boundary density: 0 from the neighbour's pressure, 1 the neighbour's
     face_kind: tuple = (0, 0)       # zwalls = 2, per face: 0 wall, 1 inlet (total P0 = face_P, T0 = Tw),
                                     # 2 inlet (static P = face_P, T = Tw, u = uw), 3 outlet (static P), 4 outlet
-    face_P: tuple = (0.0, 0.0)      # (extrapolated); see the open faces of the 1-D duct
+                                    # (extrapolated), 5 inlet (static P = face_P, T = Tw, u of the neighbour)
+    face_P: tuple = (0.0, 0.0)      # pressure datum of each open face
     friction: float = 0.0           # duct friction k = f_D / (2 D_h): F = -k rho |u| u, Q = -F.u
+    throttle_K: float = 0.0         # throttle: F = -K phi(z) rho u, Q = -F.u, phi a Gaussian of width
+    throttle_sigma: float = 0.0     # throttle_sigma at the middle of the duct (dim 3)
     storage: str = "f64"          # f64 | f32 | bf16 | f16
     steps: int = 100
     init: dict = field(default_factory=dict)

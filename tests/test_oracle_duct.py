@@ -115,3 +115,53 @@ def test_friction_law_and_energy_budget():
         prev = cur
     uz = o.moments()[1].reshape(3, -1)[2]
     assert np.allclose(uz, u0 / (1 + k * u0 * n), rtol=1e-3)
+
+
+def _vdw_state(p, P, h, guess):
+    # (rho, T) with pressure P and specific enthalpy h = e + P/rho
+    from scipy import optimize
+    L = orc.lib()
+
+    def res(x):
+        rho, T = x
+        Pc = L.orc_eos_P(p, rho, T)
+        return [Pc / P - 1.0, (L.orc_eos_e(p, rho, T) + Pc / rho) / h - 1.0]
+
+    return optimize.fsolve(res, guess, xtol=1e-13)
+
+
+@pytest.mark.parametrize("Pr,hr", [(15.0, 5.0), (3.0, 11.25)])
+def test_throttling_reproduces_the_joule_thomson_coefficient(Pr, hr):
+    # Throttling (Sec. III.B): a Darcy throttle F = -K phi rho u with Q = -F.u between an inlet at fixed
+    # (P_in, T_in) and an outlet at 0.98 P_in keeps h uniform, and Delta T / Delta P is the Joule-Thomson
+    # coefficient mu_JT = -(1/c_P) [1/rho - T P_T / (rho^2 P_rho)] of van der Waals (both signs: the
+    # states lie on either side of the inversion line).  Reduced fluid b = 2/21, Tc, Pc scaled down so
+    # that the dense states' sound speed stays near 0.3 lattice speeds; low conduction (k/mu = 0.35).
+    a, b, cv = wl.VDW_A * 0.05, wl.VDW_B, 2.5
+    Tc, Pc = 8 * a / (27 * b), a / (27 * b * b)
+    p = orc.make_params(dim=3, nx=1, ny=1, nz=40, eos="vdw", R=1.0, cv=cv, a=a, b=b)
+    P_in = Pr * Pc
+    rho_in, T_in = _vdw_state(p, P_in, hr * Tc, [2.0 / (3.0 * b), 1.5 * Tc])
+    c = wl.Case(name="throttle", dim=3, nx=1, ny=1, nz=40, zwalls=2, eos="vdw", R=1.0, cv=cv, a=a, b=b,
+                k_over_mu=0.35, eta_over_mu=3.0, tau_f=2.0, tau_g=2.0, phi_central=1, face_kind=(5, 3),
+                face_P=(P_in, 0.98 * P_in), Tw_lo=T_in, Tw_hi=T_in, throttle_K=0.02, throttle_sigma=3.0,
+                init=dict(kind="duct", rho0=rho_in, u0=0.0, T0=T_in))
+    threads = orc.get_threads()
+    orc.set_threads(1)
+    try:
+        o = run_oracle(c, 25000)
+    finally:
+        orc.set_threads(threads)
+    rho, u, T = o.moments()
+    uz = u.reshape(3, -1)[2]
+    L = orc.lib()
+    P = np.array([L.orc_eos_P(o.p, r, t) for r, t in zip(rho, T)])
+    h = np.array([L.orc_eos_e(o.p, r, t) for r, t in zip(rho, T)]) + P / rho
+    assert np.ptp((rho * uz)[1:-1]) <= 1e-6 * (rho * uz).mean()
+    assert np.ptp(h + 0.5 * uz ** 2) <= 2e-3 * abs(h.mean())
+    r_m, T_m = 0.5 * (rho[1] + rho[-2]), 0.5 * (T[1] + T[-2])
+    P_rho, P_T = L.orc_eos_dPdrho(o.p, r_m, T_m), L.orc_eos_dPdT(o.p, r_m, T_m)
+    c_P = L.orc_eos_cv(o.p, r_m, T_m) + T_m * P_T ** 2 / (r_m ** 2 * P_rho)
+    mu_jt = -(1.0 / r_m - T_m * P_T / (r_m ** 2 * P_rho)) / c_P
+    dTdP = (T[-2] - T[1]) / (P[-2] - P[1])
+    assert dTdP == pytest.approx(mu_jt, rel=0.02)
