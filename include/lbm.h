@@ -121,6 +121,10 @@ typedef struct {
                         joins F and its work returns as heat, Q_f = -F_f.u; u = (sum c f + F/2)/rho is
                         solved with F_f exactly, u = 2 w / (1 + sqrt(1 + 2 k |w|)), w the velocity without
                         F_f.  Split kernels only (0 for the others). */
+    double throttle_K;     /* Darcy throttle (throttling process, Sec. III.B): F_t = -K phi(z) rho u with */
+    double throttle_sigma; /* phi = exp(-((z - (nz-1)/2)/sigma)^2), dim 3, and its heat Q_t = -F_t.u; solved
+                              with F_f: u = 2 w / (a + sqrt(a^2 + 2 k |w|)), a = 1 + K phi/2.  Split
+                              kernels only; K >= 0, sigma > 0 when K > 0. */
 } lbm_force;
 
 typedef struct {
@@ -185,6 +189,7 @@ int lbm_set_walls(lbm_handle h, const double *u_lo, double T_lo, const double *u
 #define LBM_FACE_INLET_STATIC 2  /* supersonic inlet: static P, T and the velocity u */
 #define LBM_FACE_OUTLET_P 3      /* subsonic outlet: static P; T and the mass flux rho u of the neighbour */
 #define LBM_FACE_OUTLET_EXTRAP 4 /* supersonic outlet: rho, u, T of the neighbour */
+#define LBM_FACE_INLET_PT 5      /* inlet at fixed static P and T (throttling); u of the neighbour */
 
 /* Make face 0 (z = 0) or 1 (z = nz - 1) of every simulation of h that has
  * zwalls = 2 an open duct end of the given kind.  The boundary cell is
@@ -192,7 +197,8 @@ int lbm_set_walls(lbm_handle h, const double *u_lo, double T_lo, const double *u
  * f_N - f^eq(N), g alike, with the boundary state (rho_B, u_B, T_B) of the
  * kind: INLET_TOTAL T_B = T - |u_N|^2/(2 c_p), P_B = P (T_B/T)^(c_p/R),
  * u_B = u_N; INLET_STATIC P, T and u as given; OUTLET_P P as given, T_N and
- * u_B = u_N rho_N / rho_B; OUTLET_EXTRAP rho_N, u_N, T_N.  rho_B meets the
+ * u_B = u_N rho_N / rho_B; OUTLET_EXTRAP rho_N, u_N, T_N; INLET_PT P and T as
+ * given, u_N.  rho_B meets the
  * pressure at T_B by eight Newton steps from rho_N.  u: 3 doubles (host;
  * read for INLET_STATIC only, may be NULL otherwise); T > 0 for the inlets;
  * P > 0 for all but OUTLET_EXTRAP.  A face set here replaces the wall that

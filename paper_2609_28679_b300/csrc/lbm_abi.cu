@@ -107,7 +107,7 @@ bool has_nee(const lbm_ctx* h)
 bool split_only(const lbm_ctx* h)
 {
     for (const SimDev& d : h->sims)
-        if (d.zwalls == 2 || d.friction > 0.0) return true;
+        if (d.zwalls == 2 || d.friction > 0.0 || d.throttle_K > 0.0) return true;
     return false;
 }
 
@@ -428,6 +428,11 @@ int fill_sim(SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, do
     if (E->isothermal && L->zwalls == 2) { why = "non-equilibrium-extrapolation walls set a temperature: not isothermal"; return LBM_E_INVALID; }
     if (F && (!(F->friction >= 0) || !std::isfinite(F->friction))) { why = "friction must be finite and >= 0"; return LBM_E_INVALID; }
     if (F && F->friction > 0 && E->isothermal) { why = "friction heat needs the energy equation: not isothermal"; return LBM_E_INVALID; }
+    if (F && (!(F->throttle_K >= 0) || !std::isfinite(F->throttle_K))) { why = "throttle_K must be finite and >= 0"; return LBM_E_INVALID; }
+    if (F && F->throttle_K > 0 && (L->dim != 3 || !(F->throttle_sigma > 0) || !std::isfinite(F->throttle_sigma) || E->isothermal)) {
+        why = "a throttle needs dim 3, throttle_sigma > 0 and the energy equation";
+        return LBM_E_INVALID;
+    }
     s.nx = L->nx; s.ny = L->ny; s.nz = L->nz; s.zwalls = L->zwalls;
     s.N = (long long)L->nx * L->ny * L->nz;
     s.eos = E->kind;
@@ -451,7 +456,7 @@ int fill_sim(SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, do
     s.beta_f = 1.0 / (2.0 * tau_f + 1.0);
     s.beta_g = 1.0 / (2.0 * tau_g + 1.0);
     if (F) { s.acc[0] = F->accel[0]; s.acc[1] = F->accel[1]; s.acc[2] = L->dim == 3 ? F->accel[2] : 0.0; }
-    if (F) s.friction = F->friction;
+    if (F) { s.friction = F->friction; s.throttle_K = F->throttle_K; s.throttle_sigma = F->throttle_sigma; }
     s.inv_cv = 1.0 / s.cv;
     s.inv_Tc = s.Tc > 0 ? 1.0 / s.Tc : 0.0;
     s.lam_c = s.b > 0 ? 1.0 / (2.0 * std::sqrt(2.0) * s.b) : 0.0;
@@ -700,8 +705,8 @@ int lbm_set_face(lbm_handle h, int face, int kind, const double* u, double T, do
 {
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
     if (face != 0 && face != 1) return fail(h, LBM_E_INVALID, "face must be 0 (z = 0) or 1 (z = nz - 1)");
-    if (kind < LBM_FACE_INLET_TOTAL || kind > LBM_FACE_OUTLET_EXTRAP) return fail(h, LBM_E_INVALID, "unknown face kind");
-    const bool inlet = kind == LBM_FACE_INLET_TOTAL || kind == LBM_FACE_INLET_STATIC;
+    if (kind < LBM_FACE_INLET_TOTAL || kind > LBM_FACE_INLET_PT) return fail(h, LBM_E_INVALID, "unknown face kind");
+    const bool inlet = kind == LBM_FACE_INLET_TOTAL || kind == LBM_FACE_INLET_STATIC || kind == LBM_FACE_INLET_PT;
     if (kind == LBM_FACE_INLET_STATIC) {
         if (!u) return fail(h, LBM_E_INVALID, "a static inlet needs its velocity");
         for (int a = 0; a < 3; ++a)

@@ -54,6 +54,7 @@ struct SimDev {
     int face_set[2];              // zwalls == 2: the face has its data (lbm_set_walls / lbm_set_face)
     double face_P[2];             // pressure datum of an open face (total for INLET_TOTAL)
     double friction;              // duct friction k: F_f = -k rho |u| u, Q_f = -F_f.u (split kernels)
+    double throttle_K, throttle_sigma;  // Darcy throttle F_t = -K phi(z) rho u, Q_t = -F_t.u (split kernels)
 };
 
 // The same constants in the arithmetic type R (built once per tile on the

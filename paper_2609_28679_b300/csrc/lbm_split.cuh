@@ -258,13 +258,23 @@ __device__ __forceinline__ void grad_lap(const R* __restrict__ rho, int x, int y
     }
 }
 
-// Duct friction (Fanno flow): F_f = -k rho |u| u joins F and Q gains
-// Q_f = -F_f.u, with u = (j + F/2)/rho solved exactly: for w the velocity
-// without F_f, |u| (1 + k |u|/2) = |w|, so u = 2 w / (1 + sqrt(1 + 2 k |w|)).
-template <int D, typename R>
-__device__ __forceinline__ void apply_friction(const SimDev& s, R r, const R* j, R* F, R& Q)
+// K phi(z) of the Darcy throttle at layer z (0 without one)
+__device__ __forceinline__ double throttle_phi(const SimDev& s, int z)
 {
-    if (!(s.friction > 0.0)) return;
+    if (!(s.throttle_K > 0.0)) return 0.0;
+    const double d = ((double)z - 0.5 * (double)(s.nz - 1)) / s.throttle_sigma;
+    return s.throttle_K * exp(-d * d);
+}
+
+// Duct resistance: friction (Fanno flow) and throttle (throttling process),
+// F_r = -rho (K phi + k |u|) u joins F and Q gains Q_r = -F_r.u, with
+// u = (j + F/2)/rho solved exactly: for w the velocity without F_r and
+// a = 1 + K phi/2, |u| (a + k |u|/2) = |w|, so u = 2 w / (a + sqrt(a^2 + 2 k |w|)).
+template <int D, typename R>
+__device__ __forceinline__ void apply_friction(const SimDev& s, int z, R r, const R* j, R* F, R& Q)
+{
+    const R Kphi = (R)throttle_phi(s, z);
+    if (!(s.friction > 0.0) && !(Kphi > R(0))) return;
     const R k = (R)s.friction;
     R w[3] = {0, 0, 0}, wn = 0, un = 0;
 #pragma unroll
@@ -273,28 +283,30 @@ __device__ __forceinline__ void apply_friction(const SimDev& s, R r, const R* j,
         wn += w[a] * w[a];
     }
     wn = sqrt(wn);
-    const R sc = R(2) / (R(1) + sqrt(R(1) + R(2) * k * wn));
+    const R a0 = R(1) + R(0.5) * Kphi;
+    const R sc = R(2) / (a0 + sqrt(a0 * a0 + R(2) * k * wn));
 #pragma unroll
     for (int a = 0; a < D; ++a) un += (sc * w[a]) * (sc * w[a]);
     un = sqrt(un);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const R Ff = -k * r * un * (sc * w[a]);
+        const R Ff = -r * (Kphi + k * un) * (sc * w[a]);
         F[a] += Ff;
         Q -= Ff * (sc * w[a]);
     }
 }
 
-// heat source of a cell including the friction heat k rho |u|^3 at its velocity
+// heat source of a cell including the resistance heat rho (K phi + k |u|) |u|^2 at its velocity
 template <int D, typename R>
 __device__ __forceinline__ R cell_heat(const SimDev& s, int z, R r, const R* u)
 {
     R Q = (R)heat_at(s, z);
-    if (s.friction > 0.0) {
+    const R Kphi = (R)throttle_phi(s, z);
+    if (s.friction > 0.0 || Kphi > R(0)) {
         R u2 = 0;
 #pragma unroll
         for (int a = 0; a < D; ++a) u2 += u[a] * u[a];
-        Q += (R)s.friction * r * sqrt(u2) * u2;
+        Q += r * (Kphi + (R)s.friction * sqrt(u2)) * u2;
     }
     return Q;
 }
@@ -338,7 +350,7 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
 #pragma unroll
             for (int a = 0; a < 3; ++a) j[a] = FROM_M ? M[(M_J + a) * Ntot + gk] : W[(W_J + a) * Ntot + gk];
             R Qc = (R)heat_at(s, z);
-            apply_friction<D, R>(s, r, j, F, Qc);
+            apply_friction<D, R>(s, z, r, j, F, Qc);
             rr = (float)r;
             ee = (float)macro_energy<D, R>(r, j, FROM_M ? M[M_G * Ntot + gk] : W[W_G * Ntot + gk], F, Qc);
         }
@@ -357,7 +369,7 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
 #pragma unroll
         for (int a = 0; a < 3; ++a) j[a] = FROM_M ? M[(M_J + a) * Ntot + gk] : W[(W_J + a) * Ntot + gk];
         R Q = (R)heat_at(s, z);
-        apply_friction<D, R>(s, r, j, F, Q);
+        apply_friction<D, R>(s, z, r, j, F, Q);
         Macro<R> m = macro_cell<D, R>(s, r, j, FROM_M ? M[M_G * Ntot + gk] : W[W_G * Ntot + gk], F, Q,
                                       use_mlp ? Tml : W[W_T * Ntot + gk], flags);
         if (FROM_M) W[W_RHO * Ntot + gk] = r;
@@ -488,6 +500,10 @@ __global__ void __launch_bounds__(kBlockCells) k_nee(const SimDev* __restrict__ 
     } else if (kind == 3) {  // pressure outlet
         Tw = W[W_T * Ntot + gn];
         Pt = (R)s.face_P[side];
+    } else if (kind == 5) {  // inlet at fixed static P and T
+#pragma unroll
+        for (int a = 0; a < D; ++a) uw[a] = un[a];
+        Pt = (R)s.face_P[side];
     } else {  // extrapolated outlet
 #pragma unroll
         for (int a = 0; a < D; ++a) uw[a] = un[a];
@@ -529,7 +545,7 @@ __global__ void __launch_bounds__(kBlockCells) k_nee(const SimDev* __restrict__ 
         }
     }
     // force and heat: the non-friction part per unit mass kept, friction at (rho_B, u_B)
-    const R ro = W[W_RHO * Ntot + gb], kf = (R)s.friction;
+    const R ro = W[W_RHO * Ntot + gb], kf = (R)s.friction, Kphi = (R)throttle_phi(s, z);
     R uo[3], uo2 = 0, u2 = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -541,8 +557,8 @@ __global__ void __launch_bounds__(kBlockCells) k_nee(const SimDev* __restrict__ 
     R uF = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const R Ffo = a < D ? -kf * ro * uon * uo[a] : R(0);
-        const R Ffb = a < D ? -kf * rb * ubn * uw[a] : R(0);
+        const R Ffo = a < D ? -ro * (Kphi + kf * uon) * uo[a] : R(0);
+        const R Ffb = a < D ? -rb * (Kphi + kf * ubn) * uw[a] : R(0);
         const R Fa = (W[(W_F + a) * Ntot + gb] - Ffo) * (rb / ro) + Ffb;
         W[(W_F + a) * Ntot + gb] = Fa;
         W[(W_U + a) * Ntot + gb] = uw[a];

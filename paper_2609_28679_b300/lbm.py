@@ -22,7 +22,7 @@ LBM_IDEAL, LBM_VDW, LBM_PR = 0, 1, 2
 LBM_T_NEWTON, LBM_T_MLP = 0, 1
 LBM_PHI_UPWIND, LBM_PHI_CENTRAL = 0, 1
 LBM_KERNEL_AUTO, LBM_KERNEL_SPLIT, LBM_KERNEL_FUSED, LBM_KERNEL_ZMARCH = 0, 1, 2, 3
-LBM_FACE_INLET_TOTAL, LBM_FACE_INLET_STATIC, LBM_FACE_OUTLET_P, LBM_FACE_OUTLET_EXTRAP = 1, 2, 3, 4
+LBM_FACE_INLET_TOTAL, LBM_FACE_INLET_STATIC, LBM_FACE_OUTLET_P, LBM_FACE_OUTLET_EXTRAP, LBM_FACE_INLET_PT = 1, 2, 3, 4, 5
 
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "bf16": LBM_BF16, "f16": LBM_F16}
 EOS = {"ideal": LBM_IDEAL, "vdw": LBM_VDW, "pr": LBM_PR}
@@ -46,7 +46,8 @@ class lbm_eos(ctypes.Structure):
 
 
 class lbm_force(ctypes.Structure):
-    _fields_ = [("accel", ctypes.c_double * 3), ("friction", ctypes.c_double)]
+    _fields_ = [("accel", ctypes.c_double * 3), ("friction", ctypes.c_double), ("throttle_K", ctypes.c_double),
+                ("throttle_sigma", ctypes.c_double)]
 
 
 class lbm_heat(ctypes.Structure):
@@ -315,7 +316,8 @@ def structs_from_case(case):
     eos = lbm_eos(EOS[case.eos], case.R, case.cv, case.a, case.b, case.Tc, case.Pc, case.omega, case.kappa,
                   case.eta_over_mu, case.k_over_mu, getattr(case, "t_solver", LBM_T_NEWTON), getattr(case, "mu", 0.0),
                   getattr(case, "isothermal", 0))
-    force = lbm_force((ctypes.c_double * 3)(*case.accel), getattr(case, "friction", 0.0))
+    force = lbm_force((ctypes.c_double * 3)(*case.accel), getattr(case, "friction", 0.0),
+                      getattr(case, "throttle_K", 0.0), getattr(case, "throttle_sigma", 0.0))
     heat = lbm_heat(case.q, case.zlo, case.zhi)
     return lat, eos, force, heat
 

@@ -156,3 +156,50 @@ def test_duct_api_rules():
     with pytest.raises(lbm.LbmError, match="ideal"):
         lbm.lbm_set_face(sim.h, 0, lbm.LBM_FACE_INLET_TOTAL, None, 0.1, 0.1)
     sim.close()
+
+
+def _throttle_case(storage="f64", Pr=15.0, hr=5.0):
+    from scipy import optimize
+
+    a, b, cv = wl.VDW_A * 0.05, wl.VDW_B, 2.5
+    Tc, Pc = 8 * a / (27 * b), a / (27 * b * b)
+    p = orc.make_params(dim=3, nx=1, ny=1, nz=40, eos="vdw", R=1.0, cv=cv, a=a, b=b)
+    L = orc.lib()
+    P_in, h_in = Pr * Pc, hr * Tc
+
+    def res(x):
+        P = L.orc_eos_P(p, x[0], x[1])
+        return [P / P_in - 1.0, (L.orc_eos_e(p, x[0], x[1]) + P / x[0]) / h_in - 1.0]
+
+    rho_in, T_in = optimize.fsolve(res, [2.0 / (3.0 * b), 1.5 * Tc], xtol=1e-13)
+    return wl.Case(name="throttle", dim=3, nx=1, ny=1, nz=40, zwalls=2, eos="vdw", R=1.0, cv=cv, a=a, b=b,
+                   k_over_mu=0.35, eta_over_mu=3.0, tau_f=2.0, tau_g=2.0, phi_central=1, face_kind=(5, 3),
+                   face_P=(P_in, 0.98 * P_in), Tw_lo=T_in, Tw_hi=T_in, throttle_K=0.02, throttle_sigma=3.0,
+                   storage=storage, init=dict(kind="duct", rho0=rho_in, u0=0.0, T0=T_in))
+
+
+@pytest.mark.parametrize("storage,tol,steps", [("f64", 1e-12, 300), ("f32", 1e-5, 60)])
+def test_throttle_matches_oracle(storage, tol, steps):
+    # float32 over fewer steps: in this dense, cold fluid (theta ~ 0.016, b rho ~ 0.66) the pressure and
+    # the boundary Newton steps lose digits to cancellation, and the weakly damped sound waves carry the
+    # rounding along: float32 drifts to 2e-5 of the float64 oracle by 300 steps
+    c = _throttle_case(storage)
+    sim, o = _pair(c, steps, _noisy_fields(c, 0.002, 34))
+    _compare(sim, o, tol, f32=storage == "f32")
+
+
+def test_throttle_joule_thomson_on_the_gpu():
+    # steady throttling: Delta T / Delta P equals the van der Waals Joule-Thomson coefficient
+    c = _throttle_case("f64")
+    sim = lbm.Simulation(c)
+    sim.init()
+    sim.step(25000)
+    rho, u, T = sim.moments()
+    o = orc.Oracle(oracle_params(c))
+    L = orc.lib()
+    P = np.array([L.orc_eos_P(o.p, r, t) for r, t in zip(rho, T)])
+    r_m, T_m = 0.5 * (rho[1] + rho[-2]), 0.5 * (T[1] + T[-2])
+    P_rho, P_T = L.orc_eos_dPdrho(o.p, r_m, T_m), L.orc_eos_dPdT(o.p, r_m, T_m)
+    c_P = L.orc_eos_cv(o.p, r_m, T_m) + T_m * P_T ** 2 / (r_m ** 2 * P_rho)
+    mu_jt = -(1.0 / r_m - T_m * P_T / (r_m ** 2 * P_rho)) / c_P
+    assert (T[-2] - T[1]) / (P[-2] - P[1]) == pytest.approx(mu_jt, rel=0.02)
