@@ -103,12 +103,34 @@ bool has_nee(const lbm_ctx* h)
     return false;
 }
 
-// the handle needs the split kernels: extrapolated faces or duct friction
+// the fused kernels run none of: extrapolated faces, duct friction, throttle
 bool split_only(const lbm_ctx* h)
 {
     for (const SimDev& d : h->sims)
         if (d.zwalls == 2 || d.friction > 0.0 || d.throttle_K > 0.0) return true;
     return false;
+}
+
+// duct friction or a throttle: split kernels only
+bool has_resistance(const lbm_ctx* h)
+{
+    for (const SimDev& d : h->sims)
+        if (d.friction > 0.0 || d.throttle_K > 0.0) return true;
+    return false;
+}
+
+bool zmarch_shape(int storage, int tx, int ty);
+
+// the z-march kernel can run h with this xy tile (extrapolated faces: tiles
+// 30 x 14 and 30 x 6 with 32- or 64-bit storage)
+bool zmarch_ok(const lbm_ctx* h, int tx, int ty)
+{
+    if (h->dim != 3 || has_resistance(h)) return false;
+    for (const SimDev& d : h->sims)
+        if (d.eos != h->sims[0].eos) return false;
+    if (has_nee(h))
+        return (h->storage == LBM_F32 || h->storage == LBM_F64) && tx == 30 && (ty == 14 || ty == 6);
+    return zmarch_shape(h->storage, tx, ty);
 }
 
 // every face of a simulation with zwalls == 2 has its data
@@ -127,6 +149,9 @@ cudaError_t zmarch_dispatch(int storage, int eos, int tx, int ty, int zl, const 
                             int ntiles, const void* src, void* dst, const void* W, void* Mout, long long Ntot,
                             cudaStream_t stream);
 bool zmarch_shape(int storage, int tx, int ty);
+cudaError_t zmarch_nee_dispatch(int storage, int eos, int tx, int ty, int zl, const SimDev* sims,
+                                const TileEntry* tiles, int ntiles, const void* src, void* dst, const void* W,
+                                void* Mout, long long Ntot, cudaStream_t stream);
 cudaError_t zmacro_dispatch(int storage, int eos, int mlp, const SimDev* sims, const BlockEntry* table, int nblocks,
                             const void* M, void* W, long long Ntot, unsigned long long* diag, cudaStream_t stream);
 
@@ -208,9 +233,15 @@ template <int D, typename R, typename S> struct Impl {
                                             nblocks(h), mbuf(h, h->cur), h->W, h->Ntot, h->d_diag, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "z-march macroscopic pass");
         }
-        cudaError_t e = zmarch_dispatch(h->storage, h->sims[0].eos, h->tx, h->ty, h->tz, h->d_sims, h->d_tiles,
-                                        (int)h->tiles.size(), h->pop[h->cur], h->pop[h->cur ^ 1], h->W,
-                                        mbuf(h, h->cur ^ 1), h->Ntot, h->stream);
+        const bool nee = has_nee(h);
+        if (nee) {  // rebuild the boundary cells (slots of their pulls, fields) before the collide-stream pass
+            k_nee<D, R, S><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (S*)h->pop[h->cur],
+                                                                      (R*)h->W, h->Ntot, 1);
+            LBM_LAUNCH_CHECK(h, "boundary cells");
+        }
+        cudaError_t e = (nee ? zmarch_nee_dispatch : zmarch_dispatch)(
+            h->storage, h->sims[0].eos, h->tx, h->ty, h->tz, h->d_sims, h->d_tiles, (int)h->tiles.size(),
+            h->pop[h->cur], h->pop[h->cur ^ 1], h->W, mbuf(h, h->cur ^ 1), h->Ntot, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "z-march step");
         h->cur ^= 1;
         return LBM_OK;
@@ -342,6 +373,17 @@ cudaError_t zmacro_dispatch(int storage, int eos, int mlp, const SimDev* sims, c
     case LBM_F32: return zmacro_dispatch_f32(eos, mlp, sims, table, nblocks, M, W, Ntot, diag, stream);
     case LBM_BF16: return zmacro_dispatch_bf16(eos, mlp, sims, table, nblocks, M, W, Ntot, diag, stream);
     case LBM_F16: return zmacro_dispatch_f16(eos, mlp, sims, table, nblocks, M, W, Ntot, diag, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t zmarch_nee_dispatch(int storage, int eos, int tx, int ty, int zl, const SimDev* sims,
+                                const TileEntry* tiles, int ntiles, const void* src, void* dst, const void* W,
+                                void* Mout, long long Ntot, cudaStream_t stream)
+{
+    switch (storage) {
+    case LBM_F64: return zmarch_nee_dispatch_f64(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    case LBM_F32: return zmarch_nee_dispatch_f32(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
     }
     return cudaErrorInvalidValue;
 }
@@ -600,7 +642,7 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
         fused_default_tile(h->dim, h->storage, dtx, dty, dtz);
         bool same_eos = true;
         for (const SimDev& d : h->sims) same_eos = same_eos && d.eos == h->sims[0].eos;
-        if (h->dim == 3 && same_eos && !split_only(h) && zmarch_shape(h->storage, 30, 14)) {
+        if (h->dim == 3 && same_eos && zmarch_ok(h, 30, 14)) {
             h->variant = LBM_KERNEL_ZMARCH;
             h->tx = 30; h->ty = 14; h->tz = 32;
             rc = build_tiles(h, 30, 14, 32);
@@ -961,8 +1003,10 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
         h->variant = LBM_KERNEL_SPLIT;
         return LBM_OK;
     }
-    if ((variant == LBM_KERNEL_ZMARCH || variant == LBM_KERNEL_FUSED) && split_only(h))
-        return fail(h, LBM_E_UNSUPPORTED, "extrapolated faces and duct friction run on the split kernels");
+    if (variant == LBM_KERNEL_FUSED && split_only(h))
+        return fail(h, LBM_E_UNSUPPORTED, "extrapolated faces, duct friction and throttles run on the split or z-march kernels");
+    if (variant == LBM_KERNEL_ZMARCH && has_resistance(h))
+        return fail(h, LBM_E_UNSUPPORTED, "duct friction and throttles run on the split kernels");
     if (variant == LBM_KERNEL_ZMARCH) {
         if (h->dim != 3) return fail(h, LBM_E_INVALID, "the z-march kernel runs D3Q27 lattices");
         if (tx <= 0 || ty <= 0) { tx = 30; ty = 14; }
@@ -970,6 +1014,8 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
         for (const SimDev& d : h->sims)
             if (d.eos != h->sims[0].eos) return fail(h, LBM_E_INVALID, "one equation of state per z-march launch");
         if (!zmarch_shape(h->storage, tx, ty)) return fail(h, LBM_E_INVALID, "z-march tile not built");
+        if (!zmarch_ok(h, tx, ty))
+            return fail(h, LBM_E_UNSUPPORTED, "extrapolated faces on the z-march: tiles 30x14 or 30x6, 32- or 64-bit storage");
         LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
         int rc = build_tiles(h, tx, ty, tz);
         if (rc) return rc;
@@ -1038,7 +1084,7 @@ int lbm_autotune(lbm_handle h, int trial_steps, int* variant, int* tx, int* ty, 
         bool same_eos = true;
         for (const SimDev& d : h->sims) same_eos = same_eos && d.eos == h->sims[0].eos;
         for (auto& t : zshapes)
-            if (same_eos && !split_only(h) && zmarch_shape(h->storage, t[0], t[1]))
+            if (same_eos && zmarch_ok(h, t[0], t[1]))
                 cands.push_back({LBM_KERNEL_ZMARCH, t[0], t[1], t[2]});
     }
     h->graph_steps = 0;

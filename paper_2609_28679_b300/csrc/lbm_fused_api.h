@@ -28,6 +28,14 @@ struct BlockEntry;
 
 LBM_FUSED_DECL(f64)
 LBM_FUSED_DECL(f32)
+
+// z-march with extrapolated z faces (tiles 30 x 14 and 30 x 6; 32- and 64-bit storage)
+cudaError_t zmarch_nee_dispatch_f64(int eos, int tx, int ty, int zl, const SimDev* sims, const TileEntry* tiles,
+                                    int ntiles, const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                                    cudaStream_t stream);
+cudaError_t zmarch_nee_dispatch_f32(int eos, int tx, int ty, int zl, const SimDev* sims, const TileEntry* tiles,
+                                    int ntiles, const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                                    cudaStream_t stream);
 LBM_FUSED_DECL(bf16)
 LBM_FUSED_DECL(f16)
 #undef LBM_FUSED_DECL

@@ -82,6 +82,30 @@ cudaError_t zgo(int tx, int ty, int zl, const SimDev* sims, const TileEntry* til
 }
 }  // namespace
 
+// z-march with extrapolated z faces (walls and duct ends), on the default and the narrow tile
+namespace {
+template <int EK>
+cudaError_t zgo_nee(int tx, int ty, int zl, const SimDev* sims, const TileEntry* tiles, int ntiles, const void* src,
+                    void* dst, const void* W, void* Mout, long long Ntot, cudaStream_t stream)
+{
+    if (tx == 30 && ty == 14)
+        return zmarch_launch_shape<float, float, EK, 30, 14, true>(sims, tiles, ntiles, zl, src, dst, W, Mout, Ntot, stream);
+    if (tx == 30 && ty == 6)
+        return zmarch_launch_shape<float, float, EK, 30, 6, true>(sims, tiles, ntiles, zl, src, dst, W, Mout, Ntot, stream);
+    return cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t zmarch_nee_dispatch_f32(int eos, int tx, int ty, int zl, const SimDev* sims, const TileEntry* tiles,
+                                    int ntiles, const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                                    cudaStream_t stream)
+{
+    if (eos == EOS_IDEAL) return zgo_nee<EOS_IDEAL>(tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    if (eos == EOS_VDW) return zgo_nee<EOS_VDW>(tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    if (eos == EOS_PR) return zgo_nee<EOS_PR>(tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t zmarch_dispatch_f32(int eos, int tx, int ty, int zl, const SimDev* sims, const TileEntry* tiles,
                                 int ntiles, const void* src, void* dst, const void* W, void* Mout, long long Ntot,
                                 cudaStream_t stream)

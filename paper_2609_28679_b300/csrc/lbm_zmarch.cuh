@@ -24,7 +24,11 @@ namespace lbm {
 
 constexpr int kZThreads = 256;
 
-template <typename R, typename S, int EK, int TX, int TY>
+// NEE: z faces with non-equilibrium-extrapolation walls or duct ends
+// (zwalls == 2): stencils past a face take the linear extrapolation through
+// the boundary cell, 2 v(z_B) - v(2 z_B - z), instead of mirror images; the
+// boundary cells themselves were rebuilt by k_nee before this pass.
+template <typename R, typename S, int EK, int TX, int TY, bool NEE = false>
 __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
     k_zmarch(const SimDev* __restrict__ sims, const TileEntry* __restrict__ tiles, int ntiles, int ZL,
              const S* __restrict__ src, S* __restrict__ dst, const R* __restrict__ W, R* __restrict__ Mout,
@@ -70,13 +74,22 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
                 const int z = wrapc(zc, nz);
                 // z neighbours of the stencils: periodic, or mirrored beyond walls (flip: odd fields change sign)
                 int zn[5];
-                bool zf[5];
+                bool zf[5], zx[5];
 #pragma unroll
                 for (int o = -2; o <= 2; ++o) {
-                    if (walls) zn[o + 2] = mirror_z(zc + o, nz, zf[o + 2]);
-                    else {
-                        zn[o + 2] = wrapc(zc + o, nz);
+                    if constexpr (NEE) {
+                        // past a face: the image 2 z_B - z (zx marks the extrapolated neighbours)
+                        const int zz = zc + o;
+                        zx[o + 2] = zz < 0 || zz >= nz;
+                        zn[o + 2] = zz < 0 ? -zz : (zz >= nz ? 2 * (nz - 1) - zz : zz);
                         zf[o + 2] = false;
+                    } else {
+                        zx[o + 2] = false;
+                        if (walls) zn[o + 2] = mirror_z(zc + o, nz, zf[o + 2]);
+                        else {
+                            zn[o + 2] = wrapc(zc + o, nz);
+                            zf[o + 2] = false;
+                        }
                     }
                 }
                 for (int k = tid; k < N1; k += kZThreads) {
@@ -112,7 +125,50 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
 
                     // stencils: div u, grad h, grad T (central) and Phi (Eq. correction)
                     R divu, gh[3], gT[3], Phi[3];
-                    {
+                    if constexpr (NEE) {
+                        // the same stencils with extrapolated z neighbours past a face
+                        auto Wz = [&](int f, int o) -> R {
+                            const unsigned ci = cell(x, y, zn[o + 2]);
+                            if (zx[o + 2]) return R(2) * Wf(f, cell(x, y, zc + o < 0 ? 0 : nz - 1)) - Wf(f, ci);
+                            return Wf(f, ci);
+                        };
+                        const unsigned cxm = cell(xm1, y, z), cxp = cell(xp1, y, z);
+                        const unsigned cym = cell(x, ym1, z), cyp = cell(x, yp1, z);
+                        divu = R(0.5) * ((Wf(W_U, cxp) - Wf(W_U, cxm)) + (Wf(W_U + 1, cyp) - Wf(W_U + 1, cym)) +
+                                         (Wz(W_U + 2, 1) - Wz(W_U + 2, -1)));
+                        gh[0] = R(0.5) * (Wf(W_H, cxp) - Wf(W_H, cxm));
+                        gh[1] = R(0.5) * (Wf(W_H, cyp) - Wf(W_H, cym));
+                        gh[2] = R(0.5) * (Wz(W_H, 1) - Wz(W_H, -1));
+                        gT[0] = R(0.5) * (Wf(W_T, cxp) - Wf(W_T, cxm));
+                        gT[1] = R(0.5) * (Wf(W_T, cyp) - Wf(W_T, cym));
+                        gT[2] = R(0.5) * (Wz(W_T, 1) - Wz(W_T, -1));
+                        R dX[3];
+                        if (s.phi_central) {
+                            dX[0] = R(0.5) * (Wf(W_X, cxp) - Wf(W_X, cxm));
+                            dX[1] = R(0.5) * (Wf(W_X + 1, cyp) - Wf(W_X + 1, cym));
+                            dX[2] = R(0.5) * (Wz(W_X + 2, 1) - Wz(W_X + 2, -1));
+                        } else {
+                            const R X0x = Wf(W_X, gk), X0y = Wf(W_X + 1, gk), X0z = Wf(W_X + 2, gk);
+                            if (m.u[0] >= R(0))
+                                dX[0] = R(0.5) * (R(3) * X0x - R(4) * Wf(W_X, cxm) +
+                                                  Wf(W_X, cell(wrapc(x - 2, nx), y, z)));
+                            else
+                                dX[0] = -R(0.5) * (R(3) * X0x - R(4) * Wf(W_X, cxp) +
+                                                   Wf(W_X, cell(wrapc(x + 2, nx), y, z)));
+                            if (m.u[1] >= R(0))
+                                dX[1] = R(0.5) * (R(3) * X0y - R(4) * Wf(W_X + 1, cym) +
+                                                  Wf(W_X + 1, cell(x, wrapc(y - 2, ny), z)));
+                            else
+                                dX[1] = -R(0.5) * (R(3) * X0y - R(4) * Wf(W_X + 1, cyp) +
+                                                   Wf(W_X + 1, cell(x, wrapc(y + 2, ny), z)));
+                            if (m.u[2] >= R(0))
+                                dX[2] = R(0.5) * (R(3) * X0z - R(4) * Wz(W_X + 2, -1) + Wz(W_X + 2, -2));
+                            else
+                                dX[2] = -R(0.5) * (R(3) * X0z - R(4) * Wz(W_X + 2, 1) + Wz(W_X + 2, 2));
+                        }
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) Phi[a] = -dX[a] * m.ir;
+                    } else {
                         const unsigned cxm = cell(xm1, y, z), cxp = cell(xp1, y, z);
                         const unsigned cym = cell(x, ym1, z), cyp = cell(x, yp1, z);
                         const unsigned czm = cell(x, y, zn[1]), czp = cell(x, y, zn[3]);
@@ -296,7 +352,7 @@ __global__ void __launch_bounds__(kBlockCells) k_zmacro(const SimDev* __restrict
         const R* rho = M + M_RHO * Ntot + s.cell_off;
         r = rho[k];
         R gl[3];
-        grad_lap<3, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls != 0, gl);
+        grad_lap<3, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls, gl);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             F[a] = r * s.acc[a] + s.kappa * r * gl[a];  // Eqs. force_decomposition, korteweg_force
@@ -361,18 +417,18 @@ cudaError_t zmacro_dispatch_t(int eos, int mlp, const SimDev* sims, const BlockE
     return cudaErrorInvalidValue;
 }
 
-template <typename R, typename S, int EK, int TX, int TY>
+template <typename R, typename S, int EK, int TX, int TY, bool NEE = false>
 cudaError_t zmarch_launch_shape(const SimDev* sims, const TileEntry* tiles, int ntiles, int ZL, const void* src,
                                 void* dst, const void* W, void* Mout, long long Ntot, cudaStream_t stream)
 {
     constexpr size_t smem = (size_t)15 * TX * TY * sizeof(R);
     static int grid_cap = 0;
     if (grid_cap == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_zmarch<R, S, EK, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_zmarch<R, S, EK, TX, TY, NEE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, dev = 0, nsm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_zmarch<R, S, EK, TX, TY>, kZThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_zmarch<R, S, EK, TX, TY, NEE>, kZThreads, smem);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -380,7 +436,7 @@ cudaError_t zmarch_launch_shape(const SimDev* sims, const TileEntry* tiles, int 
         grid_cap = per_sm * nsm;
     }
     const int grid = ntiles < grid_cap ? ntiles : grid_cap;
-    k_zmarch<R, S, EK, TX, TY><<<grid, kZThreads, smem, stream>>>(sims, tiles, ntiles, ZL, (const S*)src, (S*)dst,
+    k_zmarch<R, S, EK, TX, TY, NEE><<<grid, kZThreads, smem, stream>>>(sims, tiles, ntiles, ZL, (const S*)src, (S*)dst,
                                                                   (const R*)W, (R*)Mout, Ntot);
     return cudaGetLastError();
 }

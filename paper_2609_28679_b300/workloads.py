@@ -226,6 +226,29 @@ def pr_droplet(n: int = 384, steps: int = 3000, storage: str = "f32", radius: fl
                           T0=0.9 * PR_TC * s, seed=5, amp=0.01, shell=4.0))
 
 
+def thermal_couette(n: int = 256, nz: int = 128, steps: int = 2000, storage: str = "f32") -> Case:
+    """3-D thermal Couette flow (Sec. IV) between non-equilibrium-extrapolation
+    walls on z = 0 (at rest, T_C) and z = nz - 1 (moving in x, T_H), ideal gas,
+    Pr = 2; linear initial profiles with seeded density noise."""
+    return Case(name=f"thermal_couette_{n}x{n}x{nz}", dim=3, nx=n, ny=n, nz=nz, zwalls=2, eos="ideal", R=1.0,
+                cv=2.5, k_over_mu=1.75, phi_central=1, uw_hi=(0.1, 0.0, 0.0), Tw_lo=0.33, Tw_hi=0.35,
+                storage=storage, steps=steps, init=dict(kind="couette", rho0=3.0, amp=1e-3, seed=12))
+
+
+def fanno_duct(n: int = 128, nz: int = 256, steps: int = 2000, storage: str = "f32") -> Case:
+    """A bundle of n x n periodic-in-xy ducts along z (Sec. III.A, Fanno flow):
+    total-state inlet at z = 0, pressure outlet at nz - 1, duct friction,
+    ideal gas starting at Ma 0.3 with seeded density noise."""
+    T_in, P_in, ma = 0.1, 0.1, 0.3
+    gam = 3.5 / 2.5
+    T0 = T_in * (1.0 + 0.5 * (gam - 1.0) * ma * ma)
+    P0 = P_in * (T0 / T_in) ** 3.5
+    return Case(name=f"fanno_duct_{n}x{n}x{nz}", dim=3, nx=n, ny=n, nz=nz, zwalls=2, eos="ideal", R=1.0, cv=2.5,
+                k_over_mu=3.5 / 0.71, phi_central=1, friction=4e-3 * 40.0 / nz, face_kind=(1, 3),
+                face_P=(P0, 0.08), Tw_lo=T0, Tw_hi=T0, storage=storage, steps=steps,
+                init=dict(kind="duct", rho0=P_in / T_in, u0=ma * math.sqrt(gam * T_in), T0=T_in))
+
+
 def vdw_batch(nsim: int = 64, steps: int = 2000, seed: int = 4, lmin: int = 64, lmax: int = 1024,
               storage: str = "f32") -> list[Case]:
     """Independent 2-D van der Waals quenches: side lengths log-uniform over

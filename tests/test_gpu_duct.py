@@ -42,9 +42,16 @@ def _noisy_fields(c, amp, seed):
     return rho, u, T
 
 
-def _pair(c, steps, fields):
+SPLIT, ZMARCH = lbm.LBM_KERNEL_SPLIT, lbm.LBM_KERNEL_ZMARCH
+
+
+def _pair(c, steps, fields, variant=SPLIT):
     sim = lbm.Simulation(c)
-    assert sim.kernel()[0] == lbm.LBM_KERNEL_SPLIT
+    tile = (0, 0, 0)
+    if isinstance(variant, tuple):
+        variant, tile = variant
+    lbm.lbm_set_kernel(sim.h, variant, *tile)
+    assert sim.kernel()[0] == variant
     sim.init(fields)
     sim.step(steps)
     o = orc.Oracle(oracle_params(c))
@@ -72,9 +79,10 @@ def _compare(sim, o, tol, f32=False):
     ((2, 3), (P_IN, 0.09), (0.0, 0.0, U_IN), T_IN),
 ])
 @pytest.mark.parametrize("nx,ny", [(1, 1), (3, 2)])
-def test_f64_duct_ends_match_oracle(kinds, face_P, uw_lo, T_lo, nx, ny):
+@pytest.mark.parametrize("variant", [SPLIT, (ZMARCH, (30, 6, 4))])
+def test_f64_duct_ends_match_oracle(kinds, face_P, uw_lo, T_lo, nx, ny, variant):
     c = _duct(nz=40, nx=nx, ny=ny, q=4e-5, kinds=kinds, face_P=face_P, uw_lo=uw_lo, T_lo=T_lo)
-    sim, o = _pair(c, 120, _noisy_fields(c, 0.01, 31))
+    sim, o = _pair(c, 120, _noisy_fields(c, 0.01, 31), variant)
     _compare(sim, o, 1e-12)
 
 
@@ -128,7 +136,9 @@ def test_duct_api_rules():
     lat, eos, force, heat = lbm.structs_from_case(c)
     h = lbm.lbm_create(lat, eos, c.tau_f, c.tau_g, force, heat)
     try:
-        assert lbm.lbm_get_kernel(h)[0] == lbm.LBM_KERNEL_SPLIT
+        assert lbm.lbm_get_kernel(h)[0] == lbm.LBM_KERNEL_SPLIT  # friction: split kernels
+        with pytest.raises(lbm.LbmError, match="split"):
+            lbm.lbm_set_kernel(h, lbm.LBM_KERNEL_ZMARCH)
         rho, u, T = c.fields()
         lbm.lbm_init(h, rho, u.ravel(), T, 0)
         lbm.lbm_set_face(h, 0, lbm.LBM_FACE_INLET_TOTAL, None, T0, P0)

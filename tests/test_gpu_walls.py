@@ -36,10 +36,19 @@ def _wall_case(eos="vdw", nx=5, ny=4, nz=12, storage="f64", wall_rho=0, phi_cent
     return wl.Case(**base)
 
 
-def _pair(c, steps, fields=None):
+SPLIT, ZMARCH = lbm.LBM_KERNEL_SPLIT, lbm.LBM_KERNEL_ZMARCH
+# split kernels, and the z-march with the default range and with 4-plane ranges (several per column)
+VARIANTS = [SPLIT, (ZMARCH, (30, 14, 32)), (ZMARCH, (30, 6, 4))]
+
+
+def _pair(c, steps, fields=None, variant=SPLIT):
     fields = fields if fields is not None else c.fields()
     sim = lbm.Simulation(c)
-    assert sim.kernel()[0] == lbm.LBM_KERNEL_SPLIT
+    tile = (0, 0, 0)
+    if isinstance(variant, tuple):
+        variant, tile = variant
+    lbm.lbm_set_kernel(sim.h, variant, *tile)
+    assert sim.kernel()[0] == variant
     sim.init(fields)
     sim.step(steps)
     o = orc.Oracle(oracle_params(c))
@@ -61,18 +70,20 @@ def _compare(sim, o, tol, f32=False):
     assert float(np.max(np.abs(u - ur.ravel()))) <= tol_u
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("wall_rho", [0, 1])
 @pytest.mark.parametrize("eos", ["ideal", "vdw", "pr"])
-def test_f64_walls_match_oracle(eos, wall_rho):
+def test_f64_walls_match_oracle(eos, wall_rho, variant):
     c = _wall_case(eos, wall_rho=wall_rho)
-    sim, o = _pair(c, 25)
+    sim, o = _pair(c, 25, variant=variant)
     _compare(sim, o, 1e-12)
 
 
-def test_f64_walls_central_phi_ragged_plane():
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_f64_walls_central_phi_ragged_plane(variant):
     # 7 x 3 planes (one block holds cells of several z layers), central Phi
     c = _wall_case("vdw", nx=7, ny=3, nz=9, phi_central=1)
-    sim, o = _pair(c, 30)
+    sim, o = _pair(c, 30, variant=variant)
     _compare(sim, o, 1e-12)
 
 
@@ -104,11 +115,20 @@ def test_f64_walls_batch_of_uneven_simulations():
         off += n
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("eos", ["ideal", "vdw"])
-def test_f32_walls_match_oracle(eos):
+def test_f32_walls_match_oracle(eos, variant):
     c = _wall_case(eos, storage="f32", phi_central=1)
-    sim, o = _pair(c, 25)
+    sim, o = _pair(c, 25, variant=variant)
     _compare(sim, o, 1e-5, f32=True)
+
+
+def test_default_kernels_for_walls():
+    # 32- and 64-bit storage: the z-march; 16-bit storage: the split kernels
+    for storage, want in (("f64", ZMARCH), ("f32", ZMARCH), ("bf16", SPLIT)):
+        sim = lbm.Simulation(_wall_case("ideal", storage=storage))
+        assert sim.kernel()[0] == want, storage
+        sim.close()
 
 
 def test_bf16_walls_error_bound():
@@ -148,9 +168,10 @@ def test_walls_must_be_set_and_run_split_only():
         lbm.lbm_init(h, rho, u.ravel(), T, 0)
         with pytest.raises(lbm.LbmError, match="lbm_set_walls"):
             lbm.lbm_step(h, 1)
-        for variant in (lbm.LBM_KERNEL_FUSED, lbm.LBM_KERNEL_ZMARCH):
-            with pytest.raises(lbm.LbmError, match="split"):
-                lbm.lbm_set_kernel(h, variant)
+        with pytest.raises(lbm.LbmError, match="split"):
+            lbm.lbm_set_kernel(h, lbm.LBM_KERNEL_FUSED)
+        with pytest.raises(lbm.LbmError, match="30x14"):
+            lbm.lbm_set_kernel(h, lbm.LBM_KERNEL_ZMARCH, 62, 14, 32)
         lbm.lbm_set_kernel(h, lbm.LBM_KERNEL_AUTO)
         assert lbm.lbm_get_kernel(h)[0] == lbm.LBM_KERNEL_SPLIT
         with pytest.raises(lbm.LbmError):
