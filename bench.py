@@ -309,10 +309,10 @@ def _measure_forms(lbm, wl, torch, steps):
         res["f32_pr_slab_256_isothermal"] = ri
         del fs64
         torch.cuda.empty_cache()
-        # the split kernels behind the extrapolation walls and the duct ends (thermal Couette, Fanno duct)
-        res["f32_thermal_couette_256x256x128_split"], _ = _form(lbm, torch, wl.thermal_couette(256, 128),
+        # extrapolation walls (z-march) and a friction duct (split kernels): thermal Couette, Fanno duct
+        res["f32_thermal_couette_256x256x128"], _ = _form(lbm, torch, wl.thermal_couette(256, 128),
                                                                steps, 4, tune=False, warm=2)
-        res["f32_fanno_duct_128x128x256_split"], _ = _form(lbm, torch, wl.fanno_duct(128, 256), steps, 4,
+        res["f32_fanno_duct_128x128x256"], _ = _form(lbm, torch, wl.fanno_duct(128, 256), steps, 4,
                                                           tune=False, warm=2)
         torch.cuda.empty_cache()
         # 3-D droplet: Newton in float64 and float32, and the learned temperature start
