@@ -125,7 +125,7 @@ bool zmarch_shape(int storage, int tx, int ty);
 // 30 x 14 and 30 x 6 with 32- or 64-bit storage)
 bool zmarch_ok(const lbm_ctx* h, int tx, int ty)
 {
-    if (h->dim != 3 || has_resistance(h)) return false;
+    if (h->dim != 3 || (has_resistance(h) && !has_nee(h))) return false;  // resistance: extrapolated variant only
     for (const SimDev& d : h->sims)
         if (d.eos != h->sims[0].eos) return false;
     if (has_nee(h))
@@ -1005,8 +1005,8 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
     }
     if (variant == LBM_KERNEL_FUSED && split_only(h))
         return fail(h, LBM_E_UNSUPPORTED, "extrapolated faces, duct friction and throttles run on the split or z-march kernels");
-    if (variant == LBM_KERNEL_ZMARCH && has_resistance(h))
-        return fail(h, LBM_E_UNSUPPORTED, "duct friction and throttles run on the split kernels");
+    if (variant == LBM_KERNEL_ZMARCH && has_resistance(h) && !has_nee(h))
+        return fail(h, LBM_E_UNSUPPORTED, "duct friction and throttles run on the split kernels without extrapolated faces");
     if (variant == LBM_KERNEL_ZMARCH) {
         if (h->dim != 3) return fail(h, LBM_E_INVALID, "the z-march kernel runs D3Q27 lattices");
         if (tx <= 0 || ty <= 0) { tx = 30; ty = 14; }

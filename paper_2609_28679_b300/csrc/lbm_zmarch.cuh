@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
     R* acc = reinterpret_cast<R*>(smem_raw);  // [3 planes][5: rho, j (3), G][N0]
     __shared__ SimK<R, EK> s;
     __shared__ int cur_sim;
+    __shared__ double s_res[3];  // NEE: duct friction k, throttle K and sigma
     const int tid = threadIdx.x;
     if (tid == 0) cur_sim = -1;
     __syncthreads();
@@ -51,6 +52,11 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
             if (tid == 0) {
                 simc_from<R>(static_cast<SimC<R>&>(s), sims[te.sim]);
                 cur_sim = te.sim;
+                if constexpr (NEE) {
+                    s_res[0] = sims[te.sim].friction;
+                    s_res[1] = sims[te.sim].throttle_K;
+                    s_res[2] = sims[te.sim].throttle_sigma;
+                }
             }
             __syncthreads();
         }
@@ -113,6 +119,18 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
                         m.F[a] = Wf(W_F + a, gk);
                     }
                     m.Q = heat_q<R>(s, z);
+                    if constexpr (NEE) {
+                        // heat of the duct resistance, rho (K phi + k |u|) |u|^2 (Q = -F.u of the first pass)
+                        if (s_res[0] > 0.0 || s_res[1] > 0.0) {
+                            R Kphi = R(0);
+                            if (s_res[1] > 0.0) {
+                                const double d = ((double)z - 0.5 * (double)(nz - 1)) / s_res[2];
+                                Kphi = (R)(s_res[1] * exp(-d * d));
+                            }
+                            const R u2 = m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2];
+                            m.Q += m.rho * (Kphi + (R)s_res[0] * sqrt(u2)) * u2;
+                        }
+                    }
                     m.T = Wf(W_T, gk);
                     m.P = Wf(W_P, gk);
                     m.theta = Wf(W_TH, gk);
@@ -361,6 +379,7 @@ __global__ void __launch_bounds__(kBlockCells) k_zmacro(const SimDev* __restrict
         Gm = M[M_G * Ntot + gk];
         Tg = W[W_T * Ntot + gk];
         Qh = heat_q<R>(s, z);
+        apply_friction<3, R>(s_dev, z, r, j, F, Qh);  // duct friction and throttle (zero otherwise)
     }
     if constexpr (ML) {
         if (s.mlp != nullptr) {  // block-uniform: whole warps evaluate the network

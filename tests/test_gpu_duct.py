@@ -86,9 +86,10 @@ def test_f64_duct_ends_match_oracle(kinds, face_P, uw_lo, T_lo, nx, ny, variant)
     _compare(sim, o, 1e-12)
 
 
-def test_f64_fanno_friction_matches_oracle():
+@pytest.mark.parametrize("variant", [SPLIT, (ZMARCH, (30, 14, 32)), (ZMARCH, (30, 6, 4))])
+def test_f64_fanno_friction_matches_oracle(variant):
     c = _duct(nz=40, friction=4e-3)
-    sim, o = _pair(c, 150, _noisy_fields(c, 0.01, 32))
+    sim, o = _pair(c, 150, _noisy_fields(c, 0.01, 32), variant)
     _compare(sim, o, 1e-12)
 
 
@@ -108,9 +109,10 @@ def test_f64_friction_2d_periodic_matches_oracle_and_conserves_energy():
     assert abs(gi[-1]) <= 1e-12 * abs(gi[3])  # sum (u.F + Q) = 0
 
 
-def test_f32_duct_matches_oracle():
+@pytest.mark.parametrize("variant", [SPLIT, (ZMARCH, (30, 6, 4))])
+def test_f32_duct_matches_oracle(variant):
     c = _duct(nz=40, q=4e-5, friction=2e-3, storage="f32")
-    sim, o = _pair(c, 120, _noisy_fields(c, 0.01, 33))
+    sim, o = _pair(c, 120, _noisy_fields(c, 0.01, 33), variant)
     _compare(sim, o, 1e-5, f32=True)
 
 
@@ -136,9 +138,7 @@ def test_duct_api_rules():
     lat, eos, force, heat = lbm.structs_from_case(c)
     h = lbm.lbm_create(lat, eos, c.tau_f, c.tau_g, force, heat)
     try:
-        assert lbm.lbm_get_kernel(h)[0] == lbm.LBM_KERNEL_SPLIT  # friction: split kernels
-        with pytest.raises(lbm.LbmError, match="split"):
-            lbm.lbm_set_kernel(h, lbm.LBM_KERNEL_ZMARCH)
+        assert lbm.lbm_get_kernel(h)[0] == lbm.LBM_KERNEL_ZMARCH  # extrapolated faces: the z-march
         rho, u, T = c.fields()
         lbm.lbm_init(h, rho, u.ravel(), T, 0)
         lbm.lbm_set_face(h, 0, lbm.LBM_FACE_INLET_TOTAL, None, T0, P0)
@@ -152,11 +152,18 @@ def test_duct_api_rules():
             lbm.lbm_set_kernel(h, lbm.LBM_KERNEL_FUSED)
     finally:
         lbm.lbm_destroy(h)
-    # friction alone (periodic) also keeps the split kernels
+    # friction without extrapolated faces runs on the split kernels only (2-D, and 3-D periodic)
     p = wl.vdw_spinodal(n=16, storage="f64")
     p.friction = 1e-3
     sim = lbm.Simulation(p)
     assert sim.kernel()[0] == lbm.LBM_KERNEL_SPLIT
+    sim.close()
+    p3 = wl.pr_heated_slab(n=8, nz=6, storage="f64")
+    p3.friction = 1e-3
+    sim = lbm.Simulation(p3)
+    assert sim.kernel()[0] == lbm.LBM_KERNEL_SPLIT
+    with pytest.raises(lbm.LbmError, match="split"):
+        lbm.lbm_set_kernel(sim.h, lbm.LBM_KERNEL_ZMARCH)
     sim.close()
     # a total-state inlet needs the ideal gas
     v = _duct(nz=12)
@@ -188,13 +195,14 @@ def _throttle_case(storage="f64", Pr=15.0, hr=5.0):
                    storage=storage, init=dict(kind="duct", rho0=rho_in, u0=0.0, T0=T_in))
 
 
+@pytest.mark.parametrize("variant", [SPLIT, (ZMARCH, (30, 6, 4))])
 @pytest.mark.parametrize("storage,tol,steps", [("f64", 1e-12, 300), ("f32", 1e-5, 60)])
-def test_throttle_matches_oracle(storage, tol, steps):
+def test_throttle_matches_oracle(storage, tol, steps, variant):
     # float32 over fewer steps: in this dense, cold fluid (theta ~ 0.016, b rho ~ 0.66) the pressure and
     # the boundary Newton steps lose digits to cancellation, and the weakly damped sound waves carry the
     # rounding along: float32 drifts to 2e-5 of the float64 oracle by 300 steps
     c = _throttle_case(storage)
-    sim, o = _pair(c, steps, _noisy_fields(c, 0.002, 34))
+    sim, o = _pair(c, steps, _noisy_fields(c, 0.002, 34), variant)
     _compare(sim, o, tol, f32=storage == "f32")
 
 
