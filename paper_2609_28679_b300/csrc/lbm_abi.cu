@@ -43,6 +43,8 @@ struct lbm_ctx {
     SimDev* d_sims = nullptr;
     std::vector<BlockEntry> table;
     BlockEntry* d_table = nullptr;
+    std::vector<BlockEntry> face_table;  // blocks of boundary cells of extrapolated faces (k_nee)
+    BlockEntry* d_face_table = nullptr;
     std::vector<int> sim_block_start;
     int* d_sim_block_start = nullptr;
     std::vector<TileEntry> tiles;
@@ -182,7 +184,8 @@ template <int D, typename R, typename S> struct Impl {
         k_moments<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, src, (R*)h->W, h->Ntot);
         k_macro<D, R><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot, h->d_diag);
         if (D == 3 && has_nee(h))
-            k_nee<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, src, (R*)h->W, h->Ntot, 1);
+            k_nee<D, R, S><<<(int)h->face_table.size(), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_face_table, src,
+                                                                                     (R*)h->W, h->Ntot, 1);
         k_collide<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, src, dst, (const R*)h->W, h->Ntot);
         LBM_LAUNCH_CHECK(h, "split step");
         h->cur ^= 1;
@@ -235,8 +238,8 @@ template <int D, typename R, typename S> struct Impl {
         }
         const bool nee = has_nee(h);
         if (nee) {  // rebuild the boundary cells (slots of their pulls, fields) before the collide-stream pass
-            k_nee<D, R, S><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (S*)h->pop[h->cur],
-                                                                      (R*)h->W, h->Ntot, 1);
+            k_nee<D, R, S><<<(int)h->face_table.size(), kBlockCells, 0, h->stream>>>(
+                h->d_sims, h->d_face_table, (S*)h->pop[h->cur], (R*)h->W, h->Ntot, 1);
             LBM_LAUNCH_CHECK(h, "boundary cells");
         }
         cudaError_t e = (nee ? zmarch_nee_dispatch : zmarch_dispatch)(
@@ -267,8 +270,8 @@ template <int D, typename R, typename S> struct Impl {
                                                               (R*)h->W, h->Ntot);
         k_macro<D, R><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot, nullptr);
         if (D == 3 && has_nee(h))
-            k_nee<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (S*)h->pop[h->cur], (R*)h->W,
-                                                              h->Ntot, 0);
+            k_nee<D, R, S><<<(int)h->face_table.size(), kBlockCells, 0, h->stream>>>(
+                h->d_sims, h->d_face_table, (S*)h->pop[h->cur], (R*)h->W, h->Ntot, 0);
         LBM_LAUNCH_CHECK(h, "macro");
         return LBM_OK;
     }
@@ -519,8 +522,9 @@ void free_all(lbm_ctx* h)
 {
     drop_graph(h);
     void* ptrs[] = {h->d_sims, h->d_table, h->d_sim_block_start, h->d_tiles, h->pop[0], h->pop[1],
-                    h->W, h->M, h->d_diag, h->d_partials, h->d_mlp};
+                    h->W, h->M, h->d_diag, h->d_partials, h->d_mlp, h->d_face_table};
     for (void* p : ptrs) lbm_glue_free(p);
+    h->d_face_table = nullptr;
     h->d_sims = nullptr; h->d_table = nullptr; h->d_sim_block_start = nullptr; h->d_tiles = nullptr;
     h->pop[0] = h->pop[1] = nullptr; h->W = nullptr; h->M = nullptr; h->d_diag = nullptr; h->d_partials = nullptr;
     h->d_mlp = nullptr;
@@ -606,6 +610,12 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
         for (long long k = 0; k < h->sims[s].N; k += kBlockCells) h->table.push_back(BlockEntry{s, (int)k});
     }
     h->sim_block_start.push_back((int)h->table.size());
+    // the boundary cells of extrapolated faces: the layers z = 0 and z = nz - 1 of each such simulation
+    for (int s = 0; s < nsim; ++s) {
+        if (h->sims[s].zwalls != 2) continue;
+        const long long faces = 2LL * h->sims[s].nx * h->sims[s].ny;
+        for (long long k = 0; k < faces; k += kBlockCells) h->face_table.push_back(BlockEntry{s, (int)k});
+    }
     const int nv = 2 * h->dim + 3;
 
     h->d_sims = (SimDev*)dev_alloc(h, nsim * sizeof(SimDev));
@@ -617,8 +627,9 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
     h->M = dev_alloc(h, (size_t)2 * M_NF * cells * h->rbytes);
     h->d_diag = (unsigned long long*)dev_alloc(h, kDiagSlots * sizeof(unsigned long long));
     h->d_partials = (double*)dev_alloc(h, h->table.size() * nv * sizeof(double));
+    if (!h->face_table.empty()) h->d_face_table = (BlockEntry*)dev_alloc(h, h->face_table.size() * sizeof(BlockEntry));
     if (!h->d_sims || !h->d_table || !h->d_sim_block_start || !h->pop[0] || !h->pop[1] || !h->W || !h->M ||
-        !h->d_diag || !h->d_partials) {
+        !h->d_diag || !h->d_partials || (!h->face_table.empty() && !h->d_face_table)) {
         free_all(h);
         delete h;
         return fail(nullptr, LBM_E_NOMEM,
@@ -633,6 +644,9 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
                         h->stream), "table upload");
     chk(cudaMemcpyAsync(h->d_sim_block_start, h->sim_block_start.data(), h->sim_block_start.size() * sizeof(int),
                         cudaMemcpyHostToDevice, h->stream), "table upload");
+    if (!h->face_table.empty())
+        chk(cudaMemcpyAsync(h->d_face_table, h->face_table.data(), h->face_table.size() * sizeof(BlockEntry),
+                            cudaMemcpyHostToDevice, h->stream), "face table upload");
     chk(cudaMemsetAsync(h->d_diag, 0, kDiagSlots * sizeof(unsigned long long), h->stream), "diag reset");
     chk(cudaMemsetAsync(h->W, 0, (size_t)W_NF * cells * h->rbytes, h->stream), "work reset");
     if (rc == LBM_OK) rc = upload_sims(h);

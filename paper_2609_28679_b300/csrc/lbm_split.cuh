@@ -459,21 +459,24 @@ __device__ __forceinline__ void stencils(const SimDev& s, const R* __restrict__ 
 // per-mass value of the macroscopic pass.  pops = 0 rebuilds the fields
 // only (for the reported moments and totals).
 // ---------------------------------------------------------------------------
+// face_table: blocks of (simulation, first face cell), the face cells of a
+// simulation numbered z = 0 layer first, then z = nz - 1.
 template <int D, typename R, typename S>
-__global__ void __launch_bounds__(kBlockCells) k_nee(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
-                                                     S* pop, R* __restrict__ W, long long Ntot, int pops)
+__global__ void __launch_bounds__(kBlockCells) k_nee(const SimDev* __restrict__ sims,
+                                                     const BlockEntry* __restrict__ face_table, S* pop,
+                                                     R* __restrict__ W, long long Ntot, int pops)
 {
     constexpr int Q = Lat<D>::Q;
     __shared__ SimDev s;
-    const BlockEntry be = table[blockIdx.x];
+    const BlockEntry be = face_table[blockIdx.x];
     load_sim(s, sims, be.sim);
-    const long long k = (long long)be.start + threadIdx.x;
-    if (D != 3 || s.zwalls != 2 || k >= s.N) return;
+    const long long plane = (long long)s.nx * s.ny;
+    const long long idx = (long long)be.start + threadIdx.x;
+    if (D != 3 || s.zwalls != 2 || idx >= 2 * plane) return;
+    const int side = idx >= plane ? 1 : 0;
+    const long long k = side ? (long long)(s.nz - 1) * plane + (idx - plane) : idx;
     int x, y, z;
     cell_xyz(s, k, x, y, z);
-    if (z != 0 && z != s.nz - 1) return;
-    const int side = z == 0 ? 0 : 1;
-    const long long plane = (long long)s.nx * s.ny;
     const long long gb = s.cell_off + k, gn = s.cell_off + (side ? k - plane : k + plane);
     const R rn = W[W_RHO * Ntot + gn];
     const int kind = s.face_kind[side];

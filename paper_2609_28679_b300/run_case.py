@@ -5,7 +5,7 @@ time per step: the command line that profilers wrap.
     python -m paper_2609_28679_b300.run_case pr_heated_slab 128 f32 zmarch:30x14x32 --steps 4
 
 Workloads: acoustic_shear, vdw_spinodal, pr_heated_slab, pr_droplet (size =
-cells per side).  Kernel: auto (autotuner), split, fused[:TXxTY[xTZ]] or
+cells per side), thermal_couette (n x n x n/2), fanno_duct (n x n x 2n).  Kernel: auto (autotuner), split, fused[:TXxTY[xTZ]] or
 zmarch[:TXxTYxZL].
 """
 from __future__ import annotations
@@ -22,6 +22,8 @@ _CASES = {
     "vdw_spinodal": lambda n, st: wl.vdw_spinodal(n, storage=st),
     "pr_heated_slab": lambda n, st: wl.pr_heated_slab(n, storage=st),
     "pr_droplet": lambda n, st: wl.pr_droplet(n, storage=st, radius=n / 8.0),
+    "thermal_couette": lambda n, st: wl.thermal_couette(n, n // 2, storage=st),
+    "fanno_duct": lambda n, st: wl.fanno_duct(n, 2 * n, storage=st),
 }
 _VARIANTS = {"split": lbm.LBM_KERNEL_SPLIT, "fused": lbm.LBM_KERNEL_FUSED, "zmarch": lbm.LBM_KERNEL_ZMARCH}
 
