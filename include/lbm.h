@@ -86,7 +86,8 @@ typedef struct {
     int nx, ny, nz; /* cells; nz = 1 when dim = 2                             */
     int zwalls;     /* 0: periodic in z; 1: half-way bounce-back at both z faces (dim 3);
                        2: non-equilibrium-extrapolation walls on the cells z = 0 and z = nz - 1
-                       (dim 3, nz >= 4; wall state from lbm_set_walls; split kernels) */
+                       (dim 3, nz >= 4; wall state from lbm_set_walls / lbm_set_face; split kernels,
+                       and the z-march with 32- or 64-bit storage on tiles 30x14 and 30x6) */
     int storage;    /* LBM_F64 | LBM_F32 | LBM_BF16 | LBM_F16                  */
     int phi_scheme; /* LBM_PHI_UPWIND | LBM_PHI_CENTRAL                        */
 } lbm_lattice;
@@ -120,11 +121,11 @@ typedef struct {
     double friction; /* duct friction k = f_D / (2 D_h) >= 0 (Fanno flow, Sec. III.A): F_f = -k rho |u| u
                         joins F and its work returns as heat, Q_f = -F_f.u; u = (sum c f + F/2)/rho is
                         solved with F_f exactly, u = 2 w / (1 + sqrt(1 + 2 k |w|)), w the velocity without
-                        F_f.  Split kernels only (0 for the others). */
+                        F_f.  Split kernels, and the z-march when the lattice has zwalls = 2. */
     double throttle_K;     /* Darcy throttle (throttling process, Sec. III.B): F_t = -K phi(z) rho u with */
     double throttle_sigma; /* phi = exp(-((z - (nz-1)/2)/sigma)^2), dim 3, and its heat Q_t = -F_t.u; solved
-                              with F_f: u = 2 w / (a + sqrt(a^2 + 2 k |w|)), a = 1 + K phi/2.  Split
-                              kernels only; K >= 0, sigma > 0 when K > 0. */
+                              with F_f: u = 2 w / (a + sqrt(a^2 + 2 k |w|)), a = 1 + K phi/2.  Kernels
+                              as for friction; K >= 0, sigma > 0 when K > 0. */
 } lbm_force;
 
 typedef struct {
@@ -176,8 +177,10 @@ int lbm_set_force(lbm_handle h, const double *accel);
  * temperature differs from its neighbour's.  Stencils past a wall use the
  * linear extrapolation through the boundary cell, 2 v(z_B) - v(2 z_B - z).
  * u_lo, u_hi: 3 doubles (host); T_lo, T_hi > 0.  Stepping a handle with such
- * walls before this call fails with LBM_E_STATE; only the split kernels run
- * them (lbm_set_kernel: LBM_E_UNSUPPORTED for the others).  Errors:
+ * walls before this call fails with LBM_E_STATE.  The split kernels run
+ * them, and the z-march with 32- or 64-bit storage on its 30x14 and 30x6
+ * tiles (the default then); lbm_set_kernel answers LBM_E_UNSUPPORTED for
+ * the fused kernels and other z-march tiles.  Errors:
  * LBM_E_INVALID (NULL, non-finite, T <= 0, wall_rho not 0/1), LBM_E_STATE
  * (no such walls in h), LBM_E_CUDA. */
 int lbm_set_walls(lbm_handle h, const double *u_lo, double T_lo, const double *u_hi, double T_hi, int wall_rho);
@@ -264,8 +267,8 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz);
 int lbm_set_graph(lbm_handle h, int steps_per_graph);
 
 /* Autotuner: time trial_steps steps (after 2 warm-up steps) of the split path
- * and of every built fused tile for this lattice, storage and equation of
- * state, select the fastest, and restore the state as it was (populations,
+ * and of every built fused and z-march tile that runs this lattice, storage,
+ * equation of state and boundary set, select the fastest, and restore the state as it was (populations,
  * Newton guess and diagnostic counters; the step count does not advance).
  * Outputs (any may be NULL): the chosen variant and tile, its ms per step.
  * Synchronises; allocates one snapshot of the populations for the duration
