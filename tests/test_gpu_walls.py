@@ -186,3 +186,23 @@ def test_walls_must_be_set_and_run_split_only():
     with pytest.raises(lbm.LbmError, match="no simulation"):
         lbm.lbm_set_walls(sim.h, (0, 0, 0), 0.3, (0, 0, 0), 0.3)
     sim.close()
+
+
+def test_autotune_with_walls_restores_the_state():
+    # the trial steps rewrite the boundary slots of the current populations; the snapshot restores them
+    c = _wall_case("vdw", nx=40, ny=20, nz=24, storage="f32", phi_central=1)
+    sim = lbm.Simulation(c)
+    sim.init()
+    sim.step(3)
+    f0, g0 = sim.populations()
+    (variant, tx, ty, tz), ms = sim.autotune(3)
+    assert variant in (SPLIT, ZMARCH) and ms > 0
+    if variant == ZMARCH:
+        assert (tx, ty) in ((30, 14), (30, 6))
+    f1, g1 = sim.populations()
+    assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    sim.step(4)
+    o = orc.Oracle(oracle_params(c))
+    o.init(*c.fields())
+    o.step(7)
+    assert rel_linf(sim.moments()[0], o.moments()[0]) <= 1e-5
