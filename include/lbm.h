@@ -126,12 +126,19 @@ typedef struct {
     double throttle_sigma; /* phi = exp(-((z - (nz-1)/2)/sigma)^2), dim 3, and its heat Q_t = -F_t.u; solved
                               with F_f: u = 2 w / (a + sqrt(a^2 + 2 k |w|)), a = 1 + K phi/2.  Kernels
                               as for friction; K >= 0, sigma > 0 when K > 0. */
+    const double *field;   /* optional per-cell body force F_B(x) added to rho a (Eq. force_decomposition):
+                              device memory, float64 [dim][N] over this simulation's N cells, x fastest;
+                              owned by the caller, read at every step (it may change between steps) and
+                              kept alive while the handle steps; NULL for none.  Split kernels. */
 } lbm_force;
 
 typedef struct {
     double q;         /* volumetric heat source Q                                 */
     int zmask_lo;     /* Q acts on cells with zmask_lo <= z < zmask_hi ...        */
     int zmask_hi;     /* ... and everywhere when zmask_hi <= 0                    */
+    const double *field; /* optional per-cell heat source Q(x) added to the above: device memory,
+                            float64 [N] of this simulation, owned by the caller, read at every step;
+                            NULL for none.  Split kernels. */
 } lbm_heat;
 
 /* Create one simulation.  tau_f, tau_g are the paper's relaxation time tau of

@@ -171,6 +171,7 @@ typedef struct {
     double *lap, *F, *Qs;            /* phase B */
     double *u, *T, *P, *theta, *h, *cvl, *gam, *athe, *E, *e; /* phase C */
     double *X;                       /* phase D helper: X_alpha = rho u_alpha^3 + 3 rho u_alpha (theta - 1/3) */
+    double *Ffield, *Qfield;         /* optional per-cell body force F_B [3][N] and heat source [N] (or NULL) */
     long newton_cap_hits;
     long theta_nonpos;
 } orc_state;
@@ -455,6 +456,8 @@ void orc_destroy(orc_state *s)
     double *arr[] = {s->f, s->g, s->fn, s->gn, s->rho, s->J, s->G, s->lap, s->F, s->Qs, s->u, s->T,
                      s->P, s->theta, s->h, s->cvl, s->gam, s->athe, s->E, s->e, s->X};
     for (size_t k = 0; k < sizeof(arr) / sizeof(arr[0]); ++k) free(arr[k]);
+    free(s->Ffield);
+    free(s->Qfield);
     free(s);
 }
 
@@ -619,11 +622,12 @@ static void macro_fields(orc_state *s)
                         double gL = 0.5 * (nb_scalar(s, s->lap, x, y, z, e[0], e[1], e[2]) -
                                            nb_scalar(s, s->lap, x, y, z, -e[0], -e[1], -e[2]));
                         Fa = r * p->accel[a] + p->kappa * r * gL;
+                        if (s->Ffield) Fa += s->Ffield[(long)a * N + k];
                     }
                     s->F[(long)a * N + k] = Fa;
                 }
                 int in_mask = (p->zhi <= 0) || (z >= p->zlo && z < p->zhi);
-                s->Qs[k] = in_mask ? p->q : 0.0;
+                s->Qs[k] = (in_mask ? p->q : 0.0) + (s->Qfield ? s->Qfield[k] : 0.0);
             }
 
     /* C: Eqs. def_u, def_E, T(rho,e), P, and the closure scalars */
@@ -904,6 +908,26 @@ static void one_step(orc_state *s)
 
 /* Replace the body acceleration (F_B = rho a, Eq. force_decomposition) from
  * the next step on: forcing that varies in time. */
+/* Per-cell body force F_B(x) [dim][N] (added to rho a + F_K, Eq. force_decomposition)
+ * and heat source Q(x) [N] (added to the uniform or masked Q), copied; NULL
+ * removes them. */
+void orc_set_fields(orc_state *s, const double *F, const double *Q)
+{
+    int D = s->p.dim;
+    long N = s->N;
+    free(s->Ffield);
+    free(s->Qfield);
+    s->Ffield = s->Qfield = NULL;
+    if (F) {
+        s->Ffield = zalloc(3 * N);
+        for (int a = 0; a < D; ++a) memcpy(s->Ffield + (long)a * N, F + (long)a * N, (size_t)N * sizeof(double));
+    }
+    if (Q) {
+        s->Qfield = zalloc(N);
+        memcpy(s->Qfield, Q, (size_t)N * sizeof(double));
+    }
+}
+
 void orc_set_accel(orc_state *s, const double *a)
 {
     for (int k = 0; k < 3; ++k) s->p.accel[k] = a[k];

@@ -86,6 +86,7 @@ def lib():
             "orc_init": (i, [vp, dp, dp, dp]),
             "orc_step": (i, [vp, i]),
             "orc_set_accel": (None, [vp, dp]),
+            "orc_set_fields": (None, [vp, dp, dp]),
             "orc_moments": (i, [vp, dp, dp, dp]),
             "orc_invariants": (i, [vp, dp]),
             "orc_populations": (i, [vp, dp, dp]),
@@ -261,6 +262,17 @@ class Oracle:
         out = np.zeros(2 * self.dim + 3)
         lib().orc_invariants(self._h, _dp(out))
         return out
+
+    def set_fields(self, F=None, Q=None):
+        """Per-cell body force F_B [dim][N] and heat source Q [N] (None: none)."""
+        Fp = Qp = None
+        if F is not None:
+            F = np.ascontiguousarray(F, dtype=np.float64).reshape(self.dim, self.N)
+            Fp = _dp(F)
+        if Q is not None:
+            Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(self.N)
+            Qp = _dp(Q)
+        lib().orc_set_fields(self._h, Fp, Qp)
 
     def set_accel(self, accel):
         a = np.ascontiguousarray(np.asarray(accel, dtype=np.float64).reshape(-1)[:3])

@@ -105,11 +105,19 @@ bool has_nee(const lbm_ctx* h)
     return false;
 }
 
-// the fused kernels run none of: extrapolated faces, duct friction, throttle
+// the fused kernels run none of: extrapolated faces, duct friction, throttle, per-cell force or heat
 bool split_only(const lbm_ctx* h)
 {
     for (const SimDev& d : h->sims)
-        if (d.zwalls == 2 || d.friction > 0.0 || d.throttle_K > 0.0) return true;
+        if (d.zwalls == 2 || d.friction > 0.0 || d.throttle_K > 0.0 || d.ffield || d.qfield) return true;
+    return false;
+}
+
+// per-cell force or heat fields: split kernels only
+bool has_fields(const lbm_ctx* h)
+{
+    for (const SimDev& d : h->sims)
+        if (d.ffield || d.qfield) return true;
     return false;
 }
 
@@ -127,7 +135,7 @@ bool zmarch_shape(int storage, int tx, int ty);
 // 30 x 14 and 30 x 6 with 32- or 64-bit storage)
 bool zmarch_ok(const lbm_ctx* h, int tx, int ty)
 {
-    if (h->dim != 3 || (has_resistance(h) && !has_nee(h))) return false;  // resistance: extrapolated variant only
+    if (h->dim != 3 || has_fields(h) || (has_resistance(h) && !has_nee(h))) return false;  // resistance: extrapolated variant only
     for (const SimDev& d : h->sims)
         if (d.eos != h->sims[0].eos) return false;
     if (has_nee(h))
@@ -502,6 +510,9 @@ int fill_sim(SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, do
     s.beta_g = 1.0 / (2.0 * tau_g + 1.0);
     if (F) { s.acc[0] = F->accel[0]; s.acc[1] = F->accel[1]; s.acc[2] = L->dim == 3 ? F->accel[2] : 0.0; }
     if (F) { s.friction = F->friction; s.throttle_K = F->throttle_K; s.throttle_sigma = F->throttle_sigma; }
+    if (F) s.ffield = F->field;
+    if (H) s.qfield = H->field;
+    if (s.qfield && E->isothermal) { why = "a heat field needs the energy equation: not isothermal"; return LBM_E_INVALID; }
     s.inv_cv = 1.0 / s.cv;
     s.inv_Tc = s.Tc > 0 ? 1.0 / s.Tc : 0.0;
     s.lam_c = s.b > 0 ? 1.0 / (2.0 * std::sqrt(2.0) * s.b) : 0.0;
@@ -1021,6 +1032,8 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
         return fail(h, LBM_E_UNSUPPORTED, "extrapolated faces, duct friction and throttles run on the split or z-march kernels");
     if (variant == LBM_KERNEL_ZMARCH && has_resistance(h) && !has_nee(h))
         return fail(h, LBM_E_UNSUPPORTED, "duct friction and throttles run on the split kernels without extrapolated faces");
+    if (variant == LBM_KERNEL_ZMARCH && has_fields(h))
+        return fail(h, LBM_E_UNSUPPORTED, "per-cell force and heat fields run on the split kernels");
     if (variant == LBM_KERNEL_ZMARCH) {
         if (h->dim != 3) return fail(h, LBM_E_INVALID, "the z-march kernel runs D3Q27 lattices");
         if (tx <= 0 || ty <= 0) { tx = 30; ty = 14; }

@@ -55,6 +55,8 @@ struct SimDev {
     double face_P[2];             // pressure datum of an open face (total for INLET_TOTAL)
     double friction;              // duct friction k: F_f = -k rho |u| u, Q_f = -F_f.u (split kernels)
     double throttle_K, throttle_sigma;  // Darcy throttle F_t = -K phi(z) rho u, Q_t = -F_t.u (split kernels)
+    const double* ffield;         // optional per-cell body force [D][N] (device, caller's), split kernels
+    const double* qfield;         // optional per-cell heat source [N] (device, caller's), split kernels
 };
 
 // The same constants in the arithmetic type R (built once per tile on the

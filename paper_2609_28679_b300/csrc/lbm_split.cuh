@@ -296,11 +296,12 @@ __device__ __forceinline__ void apply_friction(const SimDev& s, int z, R r, cons
     }
 }
 
-// heat source of a cell including the resistance heat rho (K phi + k |u|) |u|^2 at its velocity
+// heat source of cell k (layer z): the uniform or masked Q, the caller's per-cell Q, and the resistance
+// heat rho (K phi + k |u|) |u|^2 at its velocity
 template <int D, typename R>
-__device__ __forceinline__ R cell_heat(const SimDev& s, int z, R r, const R* u)
+__device__ __forceinline__ R cell_heat(const SimDev& s, int z, long long k, R r, const R* u)
 {
-    R Q = (R)heat_at(s, z);
+    R Q = (R)(heat_at(s, z) + (s.qfield ? s.qfield[k] : 0.0));
     const R Kphi = (R)throttle_phi(s, z);
     if (s.friction > 0.0 || Kphi > R(0)) {
         R u2 = 0;
@@ -346,10 +347,11 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
             R F[3] = {0, 0, 0}, j[3], gl[3];
             grad_lap<D, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls, gl);
 #pragma unroll
-            for (int a = 0; a < D; ++a) F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl[a];
+            for (int a = 0; a < D; ++a)
+                F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl[a] + (s.ffield ? (R)s.ffield[(long long)a * s.N + k] : R(0));
 #pragma unroll
             for (int a = 0; a < 3; ++a) j[a] = FROM_M ? M[(M_J + a) * Ntot + gk] : W[(W_J + a) * Ntot + gk];
-            R Qc = (R)heat_at(s, z);
+            R Qc = (R)(heat_at(s, z) + (s.qfield ? s.qfield[k] : 0.0));
             apply_friction<D, R>(s, z, r, j, F, Qc);
             rr = (float)r;
             ee = (float)macro_energy<D, R>(r, j, FROM_M ? M[M_G * Ntot + gk] : W[W_G * Ntot + gk], F, Qc);
@@ -365,10 +367,11 @@ __global__ void __launch_bounds__(kBlockCells) k_macro(const SimDev* __restrict_
         R F[3] = {0, 0, 0}, j[3], gl[3];
         grad_lap<D, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls, gl);
 #pragma unroll
-        for (int a = 0; a < D; ++a) F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl[a];  // Eqs. force_decomposition, korteweg_force
+        for (int a = 0; a < D; ++a)  // Eqs. force_decomposition, korteweg_force; the caller's F_B(x)
+            F[a] = r * (R)s.acc[a] + (R)s.kappa * r * gl[a] + (s.ffield ? (R)s.ffield[(long long)a * s.N + k] : R(0));
 #pragma unroll
         for (int a = 0; a < 3; ++a) j[a] = FROM_M ? M[(M_J + a) * Ntot + gk] : W[(W_J + a) * Ntot + gk];
-        R Q = (R)heat_at(s, z);
+        R Q = (R)(heat_at(s, z) + (s.qfield ? s.qfield[k] : 0.0));
         apply_friction<D, R>(s, z, r, j, F, Q);
         Macro<R> m = macro_cell<D, R>(s, r, j, FROM_M ? M[M_G * Ntot + gk] : W[W_G * Ntot + gk], F, Q,
                                       use_mlp ? Tml : W[W_T * Ntot + gk], flags);
@@ -556,7 +559,7 @@ __global__ void __launch_bounds__(kBlockCells) k_nee(const SimDev* __restrict__ 
         if (a < D) { uo2 += uo[a] * uo[a]; u2 += uw[a] * uw[a]; }
     }
     const R uon = sqrt(uo2), ubn = sqrt(u2);
-    const R Qh = cell_heat<D, R>(s, z, rb, uw);
+    const R Qh = cell_heat<D, R>(s, z, k, rb, uw);
     R uF = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(kBlockCells) k_collide(const SimDev* __restric
         m.u[a] = W[(W_U + a) * Ntot + gk];
         m.F[a] = W[(W_F + a) * Ntot + gk];
     }
-    m.Q = cell_heat<D, R>(s, z, m.rho, m.u);
+    m.Q = cell_heat<D, R>(s, z, k, m.rho, m.u);
     m.T = W[W_T * Ntot + gk];
     m.P = W[W_P * Ntot + gk];
     m.theta = W[W_TH * Ntot + gk];
@@ -666,7 +669,7 @@ __global__ void __launch_bounds__(kBlockCells) k_invariants(const SimDev* __rest
             uF += ua * Fa;
         }
         R ur[3] = {W[(W_U + 0) * Ntot + gk], W[(W_U + 1) * Ntot + gk], W[(W_U + 2) * Ntot + gk]};
-        double Q = (double)cell_heat<D, R>(s, z, W[W_RHO * Ntot + gk], ur);
+        double Q = (double)cell_heat<D, R>(s, z, k, W[W_RHO * Ntot + gk], ur);
         v[D + 1] = (double)W[W_G * Ntot + gk] + 0.5 * (uF + Q);  // Eq. def_E
         v[2 * D + 2] = uF + Q;
     }

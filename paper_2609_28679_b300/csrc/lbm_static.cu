@@ -171,8 +171,9 @@ int lbm_step_static(const lbm_lattice* lattice, const lbm_eos* eos, double tau_f
         return fail(LBM_E_INVALID, "bad lattice sizes");
     if (L.storage != LBM_F64) return fail(LBM_E_UNSUPPORTED, "lbm_step_static works on float64 populations only");
     if (L.zwalls == 2) return fail(LBM_E_UNSUPPORTED, "non-equilibrium-extrapolation walls need a handle (lbm_set_walls)");
-    if (force && (force->friction != 0.0 || force->throttle_K != 0.0))
-        return fail(LBM_E_UNSUPPORTED, "duct friction and throttles run on the split kernels of a handle");
+    if (force && (force->friction != 0.0 || force->throttle_K != 0.0 || force->field))
+        return fail(LBM_E_UNSUPPORTED, "duct friction, throttles and force fields run on the split kernels of a handle");
+    if (heat && heat->field) return fail(LBM_E_UNSUPPORTED, "heat fields run on the split kernels of a handle");
     if (L.zwalls != 0 && L.zwalls != 1) return fail(LBM_E_INVALID, "zwalls must be 0, 1 or 2");
     if (L.phi_scheme != LBM_PHI_UPWIND && L.phi_scheme != LBM_PHI_CENTRAL) return fail(LBM_E_INVALID, "unknown phi_scheme");
     const long long N = (long long)L.nx * L.ny * L.nz;

@@ -47,11 +47,12 @@ class lbm_eos(ctypes.Structure):
 
 class lbm_force(ctypes.Structure):
     _fields_ = [("accel", ctypes.c_double * 3), ("friction", ctypes.c_double), ("throttle_K", ctypes.c_double),
-                ("throttle_sigma", ctypes.c_double)]
+                ("throttle_sigma", ctypes.c_double), ("field", ctypes.c_void_p)]
 
 
 class lbm_heat(ctypes.Structure):
-    _fields_ = [("q", ctypes.c_double), ("zmask_lo", ctypes.c_int), ("zmask_hi", ctypes.c_int)]
+    _fields_ = [("q", ctypes.c_double), ("zmask_lo", ctypes.c_int), ("zmask_hi", ctypes.c_int),
+                ("field", ctypes.c_void_p)]
 
 
 _lib = None

@@ -351,3 +351,39 @@ def test_vdw_coexistence_densities():
     assert rho[nx // 2] == pytest.approx(rl_T, rel=0.02)
     assert rho[0] == pytest.approx(rv_T, rel=0.02)
     assert np.max(np.abs(u)) < 1e-3
+
+
+def test_per_cell_heat_field_equals_the_uniform_source():
+    # Q(x) given per cell (Eq. force_decomposition's generic source) adds to the uniform Q: a field equal
+    # to q everywhere reproduces q bit for bit
+    c = wl.acoustic_shear(n=12, storage="f64")
+    a = run_oracle(c, 0)
+    q = c.q
+    c0 = wl.acoustic_shear(n=12, storage="f64")
+    c0.q = 0.0
+    b = run_oracle(c0, 0)
+    b.set_fields(None, np.full(c0.ncell, q))
+    a.step(15)
+    b.step(15)
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+def test_per_cell_force_field_follows_the_momentum_budget():
+    # F_B(x) per cell: total momentum changes by the total force each step (half-force moments, Eq. def_u)
+    c = wl.vdw_spinodal(n=10, storage="f64")
+    c.accel = (0.0, 0.0, 0.0)
+    o = run_oracle(c, 0)
+    rng = np.random.default_rng(3)
+    F = 1e-5 * rng.standard_normal((2, c.ncell))
+    o.set_fields(F, None)
+    prev = o.invariants()
+    for _ in range(10):
+        o.step(1)
+        cur = o.invariants()
+        for a in range(2):
+            assert cur[1 + a] - prev[1 + a] == pytest.approx(0.5 * (prev[4 + a] + cur[4 + a]), rel=1e-9, abs=1e-15)
+        prev = cur
+    # the Korteweg force sums to zero on a periodic grid; what is left is the field's total
+    assert cur[4] == pytest.approx(F[0].sum(), rel=1e-9, abs=1e-14)
