@@ -101,13 +101,15 @@ def test_fields_3d_walls_match_oracle():
 
 def test_field_changed_between_steps():
     # the kernels read the caller's field at every step: a new field takes effect from the next step
+    import torch
+
     c = wl.acoustic_shear(n=24, storage="f64")
     F, Q = _fields(c, 7)
     F2, Q2 = _fields(c, 8)
     r = _Run(c, F, Q)
     r.step(10)
-    r.F.copy_(__import__("torch").from_numpy(F2))
-    r.Q.copy_(__import__("torch").from_numpy(Q2))
+    r.F.copy_(torch.from_numpy(F2))
+    r.Q.copy_(torch.from_numpy(Q2))
     r.step(10)
     o = _oracle(c, F, Q)
     o.step(10)
