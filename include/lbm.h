@@ -178,17 +178,19 @@ int lbm_set_force(lbm_handle h, const double *accel);
  * boundary cell B with neighbour N (z = 1, nz - 2) is rebuilt as
  *   f_B = f^eq(rho_B, u_W, theta(rho_B, T_W)) + f_N - f^eq(rho_N, u_N, theta_N)
  * and g_B alike, then collides like any cell.  rho_B: wall_rho 1 takes
- * rho_N as the text states; wall_rho 0 (recommended) solves
- * P(rho_B, T_W) = P(rho_N, T_N) by eight Newton steps from rho_N, which is
- * rho_N wherever T_W = T_N and keeps mass from leaking through a wall whose
- * temperature differs from its neighbour's.  Stencils past a wall use the
+ * rho_N as the text states; wall_rho 0 solves P(rho_B, T_W) = P(rho_N, T_N)
+ * by eight Newton steps from rho_N, which is rho_N wherever T_W = T_N and
+ * keeps mass from leaking through a wall whose temperature differs from its
+ * neighbour's; wall_rho 2 solves P(rho_B, T_W) = 2 P_N - P_NN (NN two cells
+ * inside), the same where the pressure is uniform, and also tight under a
+ * force normal to the wall (a hydrostatic pressure gradient).  Stencils past a wall use the
  * linear extrapolation through the boundary cell, 2 v(z_B) - v(2 z_B - z).
  * u_lo, u_hi: 3 doubles (host); T_lo, T_hi > 0.  Stepping a handle with such
  * walls before this call fails with LBM_E_STATE.  The split kernels run
  * them, and the z-march with 32- or 64-bit storage on its 30x14 and 30x6
  * tiles (the default then); lbm_set_kernel answers LBM_E_UNSUPPORTED for
  * the fused kernels and other z-march tiles.  Errors:
- * LBM_E_INVALID (NULL, non-finite, T <= 0, wall_rho not 0/1), LBM_E_STATE
+ * LBM_E_INVALID (NULL, non-finite, T <= 0, wall_rho not 0, 1 or 2), LBM_E_STATE
  * (no such walls in h), LBM_E_CUDA. */
 int lbm_set_walls(lbm_handle h, const double *u_lo, double T_lo, const double *u_hi, double T_hi, int wall_rho);
 

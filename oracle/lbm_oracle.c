@@ -62,7 +62,13 @@
  *    the pressure instead, rho_B solving P(rho_B, T_W) = P(rho_N, T_N) by
  *    eight Newton steps from rho_N (rho_N again if that ends non-finite or
  *    non-positive), which is the text's rho_B = rho_N wherever T_W = T_N and
- *    converges to the analytic profile at second order.  Its phase-C fields become those of
+ *    converges to the analytic profile at second order.  With a force normal
+ *    to the wall (the cross-flow Poiseuille flow of Sec. III.A) the pressure
+ *    is not uniform at rest, P_B = P_N sets a pressure step against it and the
+ *    channel again leaks; wall_rho = 2 extrapolates the pressure linearly from
+ *    the two cells inside, P_B = 2 P_N - P_NN, which is P_N where the pressure
+ *    is uniform and keeps the wall tight under any smooth pressure gradient.
+ *    Its phase-C fields become those of
  *    the wall state and its force keeps the per-mass value of phase B
  *    (F_B scaled by the new rho_B over the old).  Phases D-E then run on all
  *    cells, B included.  A stencil reaching past a wall takes the value
@@ -143,7 +149,8 @@ typedef struct {
                            keeps its initial temperature, e = e(rho, T) from the EoS */
     double uw_lo[3], uw_hi[3]; /* zwalls = 2: velocities of the walls at z = 0 and z = nz - 1 */
     double Tw_lo, Tw_hi;       /* zwalls = 2: their temperatures */
-    int wall_rho;              /* zwalls = 2: 0: rho_B from P(rho_B, T_W) = P_N; 1: rho_B = rho_N */
+    int wall_rho;              /* zwalls = 2: 0: rho_B from P(rho_B, T_W) = P_N; 1: rho_B = rho_N;
+                                  2: rho_B from P(rho_B, T_W) = 2 P_N - P_NN (NN: two cells in) */
     int face_kind[2];          /* zwalls = 2: ORC_FACE_* of the faces z = 0 and z = nz - 1; walls take
                                   (uw, Tw) above, the open kinds take (uw, Tw, face_P) as their data */
     double face_P[2];          /* static pressure (inlet static, outlet) or total pressure (inlet total) */
@@ -422,6 +429,7 @@ orc_state *orc_create(const orc_params *p)
     if (p->dim == 2 && (p->nz != 1 || p->zwalls)) return NULL;
     if (p->zwalls < 0 || p->zwalls > 2) return NULL;
     if (p->zwalls == 2 && (p->nz < 4 || p->isothermal || !(p->Tw_lo > 0) || !(p->Tw_hi > 0))) return NULL;
+    if (p->wall_rho < 0 || p->wall_rho > 2) return NULL;
     for (int f = 0; f < 2; ++f) {
         if (p->face_kind[f] < ORC_FACE_WALL || p->face_kind[f] > ORC_FACE_INLET_PT) return NULL;
         if (p->face_kind[f] != ORC_FACE_WALL && p->zwalls != 2) return NULL;
@@ -728,6 +736,10 @@ static void nee_walls(orc_state *s, int pops)
                 Tw = side ? p->Tw_hi : p->Tw_lo;
                 if (kind == ORC_FACE_WALL) {
                     if (p->wall_rho == 0) Pt = orc_eos_P(p, rn, s->T[kn]);
+                    if (p->wall_rho == 2) { /* pressure extrapolated linearly from the two cells inside */
+                        long knn = cidx(s, x, y, side ? p->nz - 3 : 2);
+                        Pt = 2.0 * s->P[kn] - s->P[knn];
+                    }
                 } else if (kind == ORC_FACE_INLET_TOTAL) {
                     double cp = p->cv + p->R, n2 = 0;
                     for (int a = 0; a < D; ++a) { uW[a] = un[a]; n2 += un[a] * un[a]; }

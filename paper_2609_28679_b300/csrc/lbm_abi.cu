@@ -752,7 +752,7 @@ int lbm_set_walls(lbm_handle h, const double* u_lo, double T_lo, const double* u
         if (!std::isfinite(u_lo[a]) || !std::isfinite(u_hi[a])) return fail(h, LBM_E_INVALID, "wall velocities must be finite");
     if (!(T_lo > 0) || !(T_hi > 0) || !std::isfinite(T_lo) || !std::isfinite(T_hi))
         return fail(h, LBM_E_INVALID, "wall temperatures must be finite and > 0");
-    if (wall_rho != 0 && wall_rho != 1) return fail(h, LBM_E_INVALID, "wall_rho must be 0 or 1");
+    if (wall_rho < 0 || wall_rho > 2) return fail(h, LBM_E_INVALID, "wall_rho must be 0, 1 or 2");
     if (!has_nee(h)) return fail(h, LBM_E_STATE, "no simulation of the handle has non-equilibrium-extrapolation walls");
     for (SimDev& d : h->sims) {
         if (d.zwalls != 2) continue;

@@ -452,8 +452,9 @@ __device__ __forceinline__ void stencils(const SimDev& s, const R* __restrict__ 
 // collision.  Each boundary cell z_B in {0, nz - 1} takes the wall velocity
 // and temperature, the density rho_N of its neighbour z_N in {1, nz - 2}
 // (wall_rho 1) or the density whose pressure at T_W is the neighbour's
-// (wall_rho 0: eight Newton steps from rho_N, rho_N again if they end
-// non-finite or non-positive); an open face (the duct ends of Sec. III.A)
+// (wall_rho 0) or the linear extrapolation 2 P_N - P_NN from two cells
+// inside (wall_rho 2) (eight Newton steps from rho_N, rho_N again if they
+// end non-finite or non-positive); an open face (the duct ends of Sec. III.A)
 // takes the boundary state of its kind instead (LBM_FACE_* in lbm.h).  The
 // populations are
 //   f_B = f^eq(rho_B, u_W, theta_W) + f_N - f^eq(rho_N, u_N, theta_N), g alike,
@@ -493,6 +494,10 @@ __global__ void __launch_bounds__(kBlockCells) k_nee(const SimDev* __restrict__ 
     R Tw = (R)s.Tw[side], Pt = R(-1);
     if (kind == 0) {
         if (s.wall_rho == 0) Pt = W[W_P * Ntot + gn];  // P(rho_N, T_N)
+        if (s.wall_rho == 2) {                        // 2 P_N - P_NN, NN two cells inside (nz >= 4)
+            const long long gnn = s.cell_off + (side ? k - 2 * plane : k + 2 * plane);
+            Pt = R(2) * W[W_P * Ntot + gn] - W[W_P * Ntot + gnn];
+        }
     } else if (kind == 1) {  // subsonic inlet from the total state (ideal gas)
         const R cp = (R)s.cv + (R)s.R;
         R n2 = 0;

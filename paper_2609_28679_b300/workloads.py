@@ -67,7 +67,8 @@ class Case:
     uw_hi: tuple = (0.0, 0.0, 0.0)  # wall velocities,
     Tw_lo: float = 0.0              # wall temperatures,
     Tw_hi: float = 0.0
-    wall_rho: int = 0               # and boundary density: 0 from the neighbour's pressure, 1 the neighbour's
+    wall_rho: int = 0               # and boundary density: 0 from the neighbour's pressure, 1 the neighbour's,
+                                    # 2 from the pressure extrapolated linearly from two cells inside
     face_kind: tuple = (0, 0)       # zwalls = 2, per face: 0 wall, 1 inlet (total P0 = face_P, T0 = Tw),
                                     # 2 inlet (static P = face_P, T = Tw, u = uw), 3 outlet (static P), 4 outlet
                                     # (extrapolated), 5 inlet (static P = face_P, T = Tw, u of the neighbour)

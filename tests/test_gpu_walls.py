@@ -71,7 +71,7 @@ def _compare(sim, o, tol, f32=False):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
-@pytest.mark.parametrize("wall_rho", [0, 1])
+@pytest.mark.parametrize("wall_rho", [0, 1, 2])
 @pytest.mark.parametrize("eos", ["ideal", "vdw", "pr"])
 def test_f64_walls_match_oracle(eos, wall_rho, variant):
     c = _wall_case(eos, wall_rho=wall_rho)

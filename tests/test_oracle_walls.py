@@ -2,9 +2,11 @@
 wall treatment of Sec. IV): the thermal Couette flow against the paper's
 analytic temperature profile (Sec. IV, with the Prandtl and Eckert numbers of
 the text), its second-order convergence, the exact linear velocity, the rest
-state kept exactly, the pressure match of the boundary density, and the mass
+state kept exactly, the pressure match of the boundary density, the mass
 that the text's literal rho_B = rho_N lets through a wall with a temperature
-step."""
+step, and the compressible Poiseuille flow with cross-flow acceleration
+(Sec. III.A) against an independent boundary-value solution of the
+Navier-Stokes-Fourier equations."""
 import numpy as np
 import pytest
 
@@ -60,7 +62,7 @@ def test_thermal_couette_converges_at_second_order():
     assert errs[0] / errs[1] == pytest.approx(4.0, rel=0.15)
 
 
-@pytest.mark.parametrize("wall_rho", [0, 1])
+@pytest.mark.parametrize("wall_rho", [0, 1, 2])
 def test_rest_state_at_wall_temperature_is_kept(wall_rho):
     # uniform rho, u = 0 and T = T_W everywhere is a steady state of the walls: nothing moves
     c = wl.Case(name="rest", dim=3, nx=3, ny=2, nz=6, zwalls=2, eos="vdw", R=1.0, cv=2.5, a=9 / 245,
@@ -108,3 +110,63 @@ def test_literal_neighbour_density_leaks_mass_through_a_heated_wall():
         lost[wall_rho] = (m0 - rho.sum()) / m0, np.max(np.abs(u[2]))
     assert abs(lost[0][0]) <= 1e-12 and lost[0][1] <= 1e-12
     assert lost[1][0] > 1e-5 and lost[1][1] > 1e-5
+
+
+def _steady_nsf_poiseuille(L, tau, kmu, TC, TH, gx, gz, mass):
+    # Steady compressible Poiseuille flow between isothermal walls at z = 0 and L (Sec. III.A, cross-flow
+    # acceleration), from the Navier-Stokes-Fourier equations with mu = tau P and k = (k/mu) mu, ideal gas
+    # (R = 1): (mu u')' = -rho g_x, (k T')' + mu u'^2 = 0, P' = rho g_z, u_z = 0, u = 0 and T given at the
+    # walls, total mass given.  Solved as a boundary-value problem, independently of the lattice.
+    from scipy.integrate import solve_bvp
+
+    def rhs(z, y):
+        u, S, T, H, P, m = y
+        return np.vstack([S / (tau * P), -(P / T) * gx, H / (kmu * tau * P), -S * S / (tau * P), P * gz / T, P / T])
+
+    def bc(ya, yb):
+        return np.array([ya[0], yb[0], ya[2] - TC, yb[2] - TH, ya[5], yb[5] - mass])
+
+    z = np.linspace(0.0, L, 200)
+    P0 = mass / L * TC
+    y0 = np.vstack([np.zeros_like(z), np.zeros_like(z), TC + (TH - TC) * z / L, np.zeros_like(z),
+                    np.full_like(z, P0), P0 / TC * z])
+    sol = solve_bvp(rhs, bc, z, y0, tol=1e-10, max_nodes=100000)
+    assert sol.status == 0
+    return sol.sol
+
+
+@pytest.mark.parametrize("ratio", [50.0, -50.0])
+def test_cross_flow_poiseuille_matches_the_steady_nsf_solution(ratio):
+    # streamwise g_x with the paper's wall-normal g_z = +-50 g_x between walls at T_C and T_H: u_x, T and
+    # rho against the boundary-value solution of the same equations with the simulated mass.  wall_rho = 2
+    # keeps the walls tight against the hydrostatic pressure gradient (density from 1.9 to 3.1 across the
+    # channel); wall_rho = 0 sets P_B = P_N against it and the channel drains
+    nz, tau, kmu, TC, TH, gx = 33, 0.8, 1.75, 0.33, 0.35, 1e-4
+    out = {}
+    for wall_rho in (2, 0):
+        c = wl.Case(name="pois", dim=3, nx=1, ny=1, nz=nz, zwalls=2, eos="ideal", R=1.0, cv=2.5, k_over_mu=kmu,
+                    tau_f=tau, tau_g=tau, phi_central=1, accel=(gx, 0.0, ratio * gx), Tw_lo=TC, Tw_hi=TH,
+                    wall_rho=wall_rho, init=dict(kind="couette", rho0=3.0))
+        threads = orc.get_threads()
+        orc.set_threads(1)
+        try:
+            o = run_oracle(c, 25000)
+        finally:
+            orc.set_threads(threads)
+        rho, u, T = o.moments()
+        out[wall_rho] = rho, u.reshape(3, -1), T
+    rho, u, T = out[2]
+    z = np.arange(nz, dtype=float)
+    mass = np.trapezoid(rho, z)
+    ref = _steady_nsf_poiseuille(nz - 1, tau, kmu, TC, TH, gx, ratio * gx, mass)(z)
+    Umax = ref[0].max()
+    assert np.max(np.abs(u[2])) <= 5e-3 * Umax
+    assert np.max(np.abs(u[0] - ref[0])) <= 1e-2 * Umax
+    assert np.max(np.abs(T - ref[2])) <= 4e-2 * np.ptp(ref[2])
+    assert np.max(np.abs(rho - ref[4] / ref[2])) <= 3e-3 * rho.mean()
+    # the cross-flow acceleration matters: without it the density profile is far off
+    ref0 = _steady_nsf_poiseuille(nz - 1, tau, kmu, TC, TH, gx, 0.0, mass)(z)
+    assert np.max(np.abs(rho - ref0[4] / ref0[2])) > 0.1 * rho.mean()
+    # with P_B = P_N a wall-normal flow of ~10 % of U remains and mass leaves the channel
+    assert np.max(np.abs(out[0][1][2])) > 5e-2 * Umax
+    assert out[0][0].mean() < 0.5 * rho.mean()
