@@ -24,7 +24,7 @@
  * paper's D3Q27 set (Eq. D3Q27c); D = 2 uses its tensor-product restriction
  * D2Q9 (the paper names no 2-D set).
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - beta = 1/(2 tau + 1) with a constant tau per distribution (Eq. beta); the
  *    shear viscosity mu = tau P then follows the local pressure.  eta and k
  *    enter only through the ratios eta/mu and k/mu.  With mu > 0 the paper's
