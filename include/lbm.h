@@ -172,7 +172,7 @@ int lbm_set_stream(lbm_handle h, void *stream);
 int lbm_set_force(lbm_handle h, const double *accel);
 
 /* Wall state of the non-equilibrium-extrapolation walls (zwalls = 2), the
- * wall treatment of the thermal Couette flow (Sec. IV), for every simulation
+ * wall treatment of the thermal Couette flow (App. B), for every simulation
  * of h that has them.  The walls lie on the boundary cells z = 0 (u_lo, T_lo)
  * and z = nz - 1 (u_hi, T_hi).  Each step, after the macroscopic pass, a
  * boundary cell B with neighbour N (z = 1, nz - 2) is rebuilt as

@@ -48,7 +48,7 @@
  *    both f and g.  For the macroscopic stencils, cells beyond a wall mirror
  *    the interior: scalars (rho, lap rho, T, h) even, velocity odd, so X_z is
  *    odd.
- *  - zwalls = 2, the non-equilibrium-extrapolation walls of Sec. IV (thermal
+ *  - zwalls = 2, the non-equilibrium-extrapolation walls of App. B (thermal
  *    Couette): the walls lie on the boundary cells z = 0 and z = nz - 1 (B),
  *    whose neighbours N are z = 1 and z = nz - 2.  After phases A-C of a step
  *    (all cells, from their current populations), every B cell is rebuilt:
@@ -159,7 +159,7 @@ typedef struct {
     double throttle_sigma;     /* phi(z) = exp(-((z - (nz - 1)/2) / sigma)^2)  (dim 3) */
 } orc_params;
 
-/* Boundary kinds of a z face with zwalls = 2 (Sec. IV walls; Sec. III.A duct ends) */
+/* Boundary kinds of a z face with zwalls = 2 (App. B walls; Sec. III.A duct ends) */
 #define ORC_FACE_WALL 0          /* wall: u_W, T_W; rho_B by wall_rho */
 #define ORC_FACE_INLET_TOTAL 1   /* subsonic inlet: total P0, T0 given, u from the neighbour (ideal gas) */
 #define ORC_FACE_INLET_STATIC 2  /* supersonic inlet: static P, T and u given */
@@ -709,7 +709,7 @@ static void macro_fields(orc_state *s)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Non-equilibrium-extrapolation walls (zwalls = 2; Sec. IV, thermal Couette): */
+/* Non-equilibrium-extrapolation walls (zwalls = 2; App. B, thermal Couette): */
 /* rebuild the boundary cells from the wall state and the non-equilibrium    */
 /* part of their neighbours, after phases A-C.  pops = 0 rebuilds only the    */
 /* macroscopic fields (for the reported moments).                             */

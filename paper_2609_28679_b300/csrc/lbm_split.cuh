@@ -448,7 +448,7 @@ __device__ __forceinline__ void stencils(const SimDev& s, const R* __restrict__ 
 
 // ---------------------------------------------------------------------------
 // Non-equilibrium-extrapolation walls (zwalls == 2; the wall treatment of the
-// thermal Couette flow, Sec. IV), between the macroscopic pass and the
+// thermal Couette flow, App. B), between the macroscopic pass and the
 // collision.  Each boundary cell z_B in {0, nz - 1} takes the wall velocity
 // and temperature, the density rho_N of its neighbour z_N in {1, nz - 2}
 // (wall_rho 1) or the density whose pressure at T_W is the neighbour's

@@ -228,7 +228,7 @@ def pr_droplet(n: int = 384, steps: int = 3000, storage: str = "f32", radius: fl
 
 
 def thermal_couette(n: int = 256, nz: int = 128, steps: int = 2000, storage: str = "f32") -> Case:
-    """3-D thermal Couette flow (Sec. IV) between non-equilibrium-extrapolation
+    """3-D thermal Couette flow (App. B) between non-equilibrium-extrapolation
     walls on z = 0 (at rest, T_C) and z = nz - 1 (moving in x, T_H), ideal gas,
     Pr = 2; linear initial profiles with seeded density noise."""
     return Case(name=f"thermal_couette_{n}x{n}x{nz}", dim=3, nx=n, ny=n, nz=nz, zwalls=2, eos="ideal", R=1.0,

@@ -1,5 +1,5 @@
 """Non-equilibrium-extrapolation walls (zwalls = 2, the wall treatment of the
-thermal Couette flow, Sec. IV) on the GPU split kernels, through the C ABI,
+thermal Couette flow, App. B) on the GPU split kernels, through the C ABI,
 against the FP64 CPU oracle on the same seeded inputs: populations and
 moments element by element, the conservation totals, a batch of uneven
 simulations, the steady Couette profile, and the API rules (walls set before
@@ -143,7 +143,7 @@ def test_bf16_walls_error_bound():
 
 @pytest.mark.parametrize("storage,tol", [("f64", 0.01), ("f32", 0.02)])
 def test_thermal_couette_steady_profile(storage, tol):
-    # the paper's analytic profile (Sec. IV): T = T_C + (T_H - T_C) xi + U^2 / (2 k/mu) xi (1 - xi)
+    # the paper's analytic profile (App. B): T = T_C + (T_H - T_C) xi + U^2 / (2 k/mu) xi (1 - xi)
     nz, U, kmu = 17, 0.2, 1.75
     c = wl.Case(name="couette", dim=3, nx=2, ny=2, nz=nz, zwalls=2, eos="ideal", R=1.0, cv=2.5, k_over_mu=kmu,
                  phi_central=1, uw_hi=(U, 0.0, 0.0), Tw_lo=0.33, Tw_hi=0.35, storage=storage,

@@ -1,6 +1,6 @@
 """Pins of the oracle's non-equilibrium-extrapolation walls (zwalls = 2; the
-wall treatment of Sec. IV): the thermal Couette flow against the paper's
-analytic temperature profile (Sec. IV, with the Prandtl and Eckert numbers of
+wall treatment of App. B): the thermal Couette flow against the paper's
+analytic temperature profile (App. B, with the Prandtl and Eckert numbers of
 the text), its second-order convergence, the exact linear velocity, the rest
 state kept exactly, the pressure match of the boundary density, the mass
 that the text's literal rho_B = rho_N lets through a wall with a temperature
