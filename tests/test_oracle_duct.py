@@ -165,3 +165,21 @@ def test_throttling_reproduces_the_joule_thomson_coefficient(Pr, hr):
     mu_jt = -(1.0 / r_m - T_m * P_T / (r_m ** 2 * P_rho)) / c_P
     dTdP = (T[-2] - T[1]) / (P[-2] - P[1])
     assert dTdP == pytest.approx(mu_jt, rel=0.02)
+
+
+def test_bench_recipes_of_the_wall_and_duct_forms_are_sound():
+    # the thermal Couette and Fanno duct workloads the benchmark times, at reduced size: finite fields,
+    # the wall temperatures held, a uniform mass flux along the ducts after the inlet transient
+    tc = wl.thermal_couette(6, 12)
+    o = run_oracle(tc, 300)
+    rho, u, T = o.moments()
+    plane = tc.nx * tc.ny
+    assert np.all(np.isfinite(rho)) and np.all(rho > 0)
+    assert np.all(T[:plane] == tc.Tw_lo) and np.all(T[-plane:] == tc.Tw_hi)
+    fd = wl.fanno_duct(2, 40)
+    o = run_oracle(fd, 4000)
+    rho, u, T = o.moments()
+    uz = u.reshape(3, -1)[2].reshape(fd.nz, -1)
+    m = (rho.reshape(fd.nz, -1) * uz).mean(axis=1)
+    assert np.all(np.isfinite(m)) and m.min() > 0
+    assert np.ptp(m[1:-1]) <= 1e-3 * m.mean()
