@@ -78,6 +78,8 @@ extern "C" {
 #define LBM_KERNEL_SPLIT 1 /* moments, macroscopic, collide-stream: three passes         */
 #define LBM_KERNEL_FUSED 2 /* one pass per step, shared-memory halo tiles                */
 #define LBM_KERNEL_ZMARCH 3 /* D3Q27: macroscopic pass + z-marching collide-stream pass   */
+#define LBM_KERNEL_ZGATHER 4 /* D3Q27: macroscopic pass + column-march collide-stream pass with
+                                staged pulls and gathered moments (32-/16-bit storage)      */
 
 typedef struct lbm_ctx *lbm_handle;
 
@@ -261,10 +263,12 @@ int lbm_invariants(lbm_handle h, double *out);
  * Host pointer; synchronises. */
 int lbm_diagnostics(lbm_handle h, long long out[4]);
 
-/* Kernel selection: variant LBM_KERNEL_AUTO / SPLIT / FUSED / ZMARCH; tx, ty,
- * tz the tile of the fused variant, or for ZMARCH (3-D only) the xy tile and
- * the number of z planes each CTA marches through (0: default).  Errors:
- * LBM_E_INVALID for a tile the variant cannot run. */
+/* Kernel selection: variant LBM_KERNEL_AUTO / SPLIT / FUSED / ZMARCH /
+ * ZGATHER; tx, ty, tz the tile of the fused variant, or for ZMARCH (3-D only)
+ * the xy tile and the number of z planes each CTA marches through (0:
+ * default); ZGATHER has the xy tile 30 x 14 (tx, ty 0 or 30, 14) and takes
+ * tz as its number of planes.  Errors: LBM_E_INVALID for a tile the variant
+ * cannot run, LBM_E_UNSUPPORTED for a lattice or boundary set it does not run. */
 int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz);
 
 /* Replay lbm_step's time steps as CUDA graphs of `steps_per_graph` steps (an
@@ -290,28 +294,35 @@ int lbm_get_kernel(lbm_handle h, int *variant, int *tx, int *ty, int *tz);
 /* One time step of float64 populations owned by the caller, allocating
  * nothing.  The paper has no counterpart: this is a variant of the library's
  * three-pass step for callers that cannot allocate device memory when they
- * step -- code running inside a CUDA graph capture managed by someone else,
- * hosts that give the library a fixed memory budget, callers outside
- * PyTorch's allocator.  Its work arrays live in one fixed-size static device
- * array (room for 65536 cells, about 11.5 MB, held on every GPU that loads the
- * library until the process exits).
+ * step.  The handle path takes its memory from PyTorch's caching allocator at
+ * lbm_create; hosts that give each library a fixed device-memory budget up
+ * front, programs that link this library without PyTorch, and time-critical
+ * loops that must not call cudaMalloc or cudaFree (which waits for the whole
+ * device) cannot use it.  This call keeps its work arrays in one fixed-size
+ * static device array (room for 65536 cells, about 11.5 MB, held on every GPU
+ * that loads the library until the process exits) and passes the simulation
+ * constants to the device as a kernel argument: no allocation, no copy from
+ * host memory.
  *
  * f_in, g_in: pre-collision populations [Q][N] (device, float64, the layout
  * of lbm_populations); f_out, g_out: the pre-collision populations of the
- * next step (device, must not alias the inputs).  lattice->storage must be
- * LBM_F64.  Peng-Robinson's Newton iteration starts from e/c_v (no guess is
- * carried between calls).  Work is enqueued on `stream` (NULL: the legacy
- * default stream); the call does not synchronise.
+ * next step (device, must not overlap the inputs).  lattice->storage must be
+ * LBM_F64.  Peng-Robinson's Newton iteration starts from the critical
+ * temperature Tc in every cell (no temperature is carried between calls).
+ * Work is enqueued on `stream` (NULL: the legacy default stream); the call
+ * does not synchronise.
  *
  * The first call on a device looks up the static array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array: calls whose kernels overlap on the GPU (other
  * streams, other threads) race and corrupt each other -- serialise them.
  * Nothing carries over between calls: each one rewrites what it reads.
- * Errors: LBM_E_INVALID (NULL pointers, bad sizes, more than 65536 cells,
- * aliasing), LBM_E_UNSUPPORTED (storage other than float64, the isothermal
- * mode, which needs the temperature a handle carries), LBM_E_CUDA;
- * lbm_last_error(NULL) describes the failure. */
+ * Errors: LBM_E_INVALID (NULL pointers, what lbm_create rejects, more than
+ * 65536 cells, overlapping inputs and outputs), LBM_E_UNSUPPORTED (storage
+ * other than float64, extrapolated walls, friction, throttles, force or heat
+ * fields, t_solver other than LBM_T_NEWTON, the isothermal mode, which needs
+ * the temperature a handle carries), LBM_E_CUDA; lbm_last_error(NULL)
+ * describes the failure. */
 int lbm_step_static(const lbm_lattice *lattice, const lbm_eos *eos, double tau_f, double tau_g,
                     const lbm_force *force, const lbm_heat *heat, const double *f_in, const double *g_in,
                     double *f_out, double *g_out, void *stream);

@@ -143,6 +143,18 @@ bool zmarch_ok(const lbm_ctx* h, int tx, int ty)
     return zmarch_shape(h->storage, tx, ty);
 }
 
+// the column-march kernel (staged pulls, gathered moments) can run h: D3Q27,
+// 32- or 16-bit storage, one equation of state, no extrapolated faces,
+// resistance or per-cell fields, nx a multiple of the elements per 16-byte copy
+bool zgather_ok(const lbm_ctx* h)
+{
+    if (h->dim != 3 || h->storage == LBM_F64 || has_fields(h) || has_resistance(h) || has_nee(h)) return false;
+    const int chunk = h->storage == LBM_F32 ? 4 : 8;
+    for (const SimDev& d : h->sims)
+        if (d.eos != h->sims[0].eos || d.nx % chunk != 0) return false;
+    return true;
+}
+
 // every face of a simulation with zwalls == 2 has its data
 bool faces_ready(const lbm_ctx* h)
 {
@@ -164,6 +176,9 @@ cudaError_t zmarch_nee_dispatch(int storage, int eos, int tx, int ty, int zl, co
                                 void* Mout, long long Ntot, cudaStream_t stream);
 cudaError_t zmacro_dispatch(int storage, int eos, int mlp, const SimDev* sims, const BlockEntry* table, int nblocks,
                             const void* M, void* W, long long Ntot, unsigned long long* diag, cudaStream_t stream);
+cudaError_t zgather_dispatch(int storage, int eos, int zl, const SimDev* sims, const TileEntry* tiles, int ntiles,
+                             const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                             cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Typed implementation of every operation for one (D, arithmetic, storage).
@@ -250,9 +265,14 @@ template <int D, typename R, typename S> struct Impl {
                 h->d_sims, h->d_face_table, (S*)h->pop[h->cur], (R*)h->W, h->Ntot, 1);
             LBM_LAUNCH_CHECK(h, "boundary cells");
         }
-        cudaError_t e = (nee ? zmarch_nee_dispatch : zmarch_dispatch)(
-            h->storage, h->sims[0].eos, h->tx, h->ty, h->tz, h->d_sims, h->d_tiles, (int)h->tiles.size(),
-            h->pop[h->cur], h->pop[h->cur ^ 1], h->W, mbuf(h, h->cur ^ 1), h->Ntot, h->stream);
+        cudaError_t e;
+        if (h->variant == LBM_KERNEL_ZGATHER)
+            e = zgather_dispatch(h->storage, h->sims[0].eos, h->tz, h->d_sims, h->d_tiles, (int)h->tiles.size(),
+                                 h->pop[h->cur], h->pop[h->cur ^ 1], h->W, mbuf(h, h->cur ^ 1), h->Ntot, h->stream);
+        else
+            e = (nee ? zmarch_nee_dispatch : zmarch_dispatch)(
+                h->storage, h->sims[0].eos, h->tx, h->ty, h->tz, h->d_sims, h->d_tiles, (int)h->tiles.size(),
+                h->pop[h->cur], h->pop[h->cur ^ 1], h->W, mbuf(h, h->cur ^ 1), h->Ntot, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "z-march step");
         h->cur ^= 1;
         return LBM_OK;
@@ -263,7 +283,8 @@ template <int D, typename R, typename S> struct Impl {
         if (!faces_ready(h)) return fail(h, LBM_E_STATE, "lbm_set_walls / lbm_set_face has not set every face");
         for (int it = 0; it < n; ++it) {
             int rc = h->variant == LBM_KERNEL_FUSED ? fused_step(h)
-                     : h->variant == LBM_KERNEL_ZMARCH ? zmarch_step(h) : split_step(h);
+                     : (h->variant == LBM_KERNEL_ZMARCH || h->variant == LBM_KERNEL_ZGATHER) ? zmarch_step(h)
+                                                                                              : split_step(h);
             if (rc) return rc;
         }
         return LBM_OK;
@@ -395,6 +416,18 @@ cudaError_t zmarch_nee_dispatch(int storage, int eos, int tx, int ty, int zl, co
     switch (storage) {
     case LBM_F64: return zmarch_nee_dispatch_f64(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
     case LBM_F32: return zmarch_nee_dispatch_f32(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t zgather_dispatch(int storage, int eos, int zl, const SimDev* sims, const TileEntry* tiles, int ntiles,
+                             const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                             cudaStream_t stream)
+{
+    switch (storage) {
+    case LBM_F32: return zgather_dispatch_f32(eos, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    case LBM_BF16: return zgather_dispatch_bf16(eos, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    case LBM_F16: return zgather_dispatch_f16(eos, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
     }
     return cudaErrorInvalidValue;
 }
@@ -667,7 +700,11 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
         fused_default_tile(h->dim, h->storage, dtx, dty, dtz);
         bool same_eos = true;
         for (const SimDev& d : h->sims) same_eos = same_eos && d.eos == h->sims[0].eos;
-        if (h->dim == 3 && same_eos && zmarch_ok(h, 30, 14)) {
+        if (zgather_ok(h)) {
+            h->variant = LBM_KERNEL_ZGATHER;
+            h->tx = 30; h->ty = 14; h->tz = 32;
+            rc = build_tiles(h, 30, 14, 32);
+        } else if (h->dim == 3 && same_eos && zmarch_ok(h, 30, 14)) {
             h->variant = LBM_KERNEL_ZMARCH;
             h->tx = 30; h->ty = 14; h->tz = 32;
             rc = build_tiles(h, 30, 14, 32);
@@ -693,6 +730,15 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
 
 // message of a failing call that has no handle (lbm_create*, lbm_step_static)
 void lbm_set_global_error(const std::string& msg) { g_create_error = msg; }
+
+// the lattice and constant checks of lbm_create, for entry points without a handle
+int lbm_check_and_fill_sim(SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, double tau_g,
+                           const lbm_force* F, const lbm_heat* H, std::string& why)
+{
+    int rc = check_lattice(L, why);
+    if (rc) return rc;
+    return fill_sim(s, L, E, tau_f, tau_g, F, H, why);
+}
 
 extern "C" {
 
@@ -1034,6 +1080,22 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
         return fail(h, LBM_E_UNSUPPORTED, "duct friction and throttles run on the split kernels without extrapolated faces");
     if (variant == LBM_KERNEL_ZMARCH && has_fields(h))
         return fail(h, LBM_E_UNSUPPORTED, "per-cell force and heat fields run on the split kernels");
+    if (variant == LBM_KERNEL_ZGATHER) {
+        if (h->dim != 3) return fail(h, LBM_E_INVALID, "the z-march kernels run D3Q27 lattices");
+        if (!zgather_ok(h))
+            return fail(h, LBM_E_UNSUPPORTED,
+                        "the gathering z-march needs 32- or 16-bit storage, nx a multiple of 4 (float32) or 8 (16-bit), "
+                        "one equation of state and no extrapolated faces, resistance or per-cell fields");
+        if ((tx > 0 && tx != 30) || (ty > 0 && ty != 14))
+            return fail(h, LBM_E_INVALID, "the gathering z-march has the fixed xy tile 30 x 14");
+        if (tz <= 0) tz = 32;
+        LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+        int rc = build_tiles(h, 30, 14, tz);
+        if (rc) return rc;
+        h->variant = LBM_KERNEL_ZGATHER;
+        h->tx = 30; h->ty = 14; h->tz = tz;
+        return LBM_OK;
+    }
     if (variant == LBM_KERNEL_ZMARCH) {
         if (h->dim != 3) return fail(h, LBM_E_INVALID, "the z-march kernel runs D3Q27 lattices");
         if (tx <= 0 || ty <= 0) { tx = 30; ty = 14; }
@@ -1113,6 +1175,8 @@ int lbm_autotune(lbm_handle h, int trial_steps, int* variant, int* tx, int* ty, 
         for (auto& t : zshapes)
             if (same_eos && zmarch_ok(h, t[0], t[1]))
                 cands.push_back({LBM_KERNEL_ZMARCH, t[0], t[1], t[2]});
+        if (zgather_ok(h))
+            for (int zl : {16, 32, 64}) cands.push_back({LBM_KERNEL_ZGATHER, 30, 14, zl});
     }
     h->graph_steps = 0;
     drop_graph(h);

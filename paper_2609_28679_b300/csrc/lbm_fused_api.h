@@ -40,4 +40,15 @@ LBM_FUSED_DECL(bf16)
 LBM_FUSED_DECL(f16)
 #undef LBM_FUSED_DECL
 
+// column-march collide-stream pass (staged pulls, gathered moments): 32- and 16-bit storage
+cudaError_t zgather_dispatch_f32(int eos, int zl, const SimDev* sims, const TileEntry* tiles, int ntiles,
+                                 const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                                 cudaStream_t stream);
+cudaError_t zgather_dispatch_bf16(int eos, int zl, const SimDev* sims, const TileEntry* tiles, int ntiles,
+                                  const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                                  cudaStream_t stream);
+cudaError_t zgather_dispatch_f16(int eos, int zl, const SimDev* sims, const TileEntry* tiles, int ntiles,
+                                 const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                                 cudaStream_t stream);
+
 }  // namespace lbm

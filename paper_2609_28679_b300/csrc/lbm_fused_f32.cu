@@ -2,6 +2,7 @@
 // for D2Q9 and D3Q27 and each equation of state.
 #include "lbm_fused.cuh"
 #include "lbm_fused_api.h"
+#include "lbm_zgather.cuh"
 #include "lbm_zmarch.cuh"
 
 namespace lbm {
@@ -128,6 +129,13 @@ bool zmarch_shape_f32(int tx, int ty)
     ZTILES(ZHAS)
 #undef ZHAS
     return false;
+}
+
+cudaError_t zgather_dispatch_f32(int eos, int zl, const SimDev* sims, const TileEntry* tiles, int ntiles,
+                                 const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                                 cudaStream_t stream)
+{
+    return zgather_dispatch_t<float>(eos, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
 }
 
 }  // namespace lbm

@@ -1,15 +1,22 @@
 // lbm_step_static: one float64 time step on caller-owned populations that
 // allocates nothing.
 //
-// Some callers cannot allocate device memory at the point where they step a
-// simulation: code running while a framework captures a CUDA graph (where an
-// allocation would be recorded into, or break, the capture), embedded or
-// plugin hosts that hand out a fixed device-memory budget and forbid further
-// allocation, and callers whose allocator is not PyTorch's.  For them the
-// work arrays of the three-pass step (moments, macroscopic fields, the
-// simulation constants and the block table) live in one file-scope
-// __device__ array of fixed size, so the call needs no cudaMalloc, no
-// cudaFree and no allocating library routine.
+// The handle-based entry points take their device memory (populations,
+// moments, macroscopic fields, tables) from PyTorch's caching allocator when
+// a simulation is created.  Some callers cannot allocate device memory at
+// all, or not at the point where they step:
+//   - host programs that hand every library a fixed device-memory budget up
+//     front and refuse later requests (plugin hosts, embedded solvers that
+//     pre-plan their memory);
+//   - C or C++ programs that link liblbm.so without PyTorch, so there is no
+//     caching allocator behind the handle path;
+//   - time-critical loops that must not call cudaFree, which waits for the
+//     whole device, or cudaMalloc, whose latency is unbounded.
+// For them the work arrays of the three-pass step (the simulation constants,
+// the block table and the macroscopic fields) live in one file-scope
+// __device__ array of fixed size: the call makes no cudaMalloc, no cudaFree
+// and no allocating library call, and copies nothing from host memory (the
+// constants reach the device as a kernel argument).
 //
 // The array holds room for kStaticMaxCells cells.  Every process that loads
 // the library keeps it on every GPU it uses until exit.  All calls share it:
@@ -25,6 +32,8 @@
 #include "lbm_split.cuh"
 
 void lbm_set_global_error(const std::string& msg);  // lbm_abi.cu
+int lbm_check_and_fill_sim(lbm::SimDev& s, const lbm_lattice* L, const lbm_eos* E, double tau_f, double tau_g,
+                           const lbm_force* F, const lbm_heat* H, std::string& why);  // lbm_abi.cu
 
 namespace {
 
@@ -50,8 +59,19 @@ int fail(int code, const std::string& msg)
     return code;
 }
 
+// The constants of this call (a kernel argument, copied by the launch) and
+// the block table {0, b * kBlockCells} written into the scratch's head.
+__global__ void __launch_bounds__(kBlockCells) k_static_setup(SimDev s, SimDev* __restrict__ d_sim,
+                                                              BlockEntry* __restrict__ d_table, int nb)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_sim = s;
+    for (int b = blockIdx.x * kBlockCells + threadIdx.x; b < nb; b += gridDim.x * kBlockCells)
+        d_table[b] = BlockEntry{0, b * kBlockCells};
+}
+
 // moments of pre-collision populations held at their own cell: rho, j, G;
-// the Newton guess slot is cleared (Newton then starts from e / c_v)
+// the Newton guess slot is cleared (Newton then starts from the critical
+// temperature, as on a handle's first step)
 template <int D>
 __global__ void __launch_bounds__(kBlockCells) k_static_moments(const SimDev* __restrict__ sims,
                                                                 const double* __restrict__ f,
@@ -166,66 +186,41 @@ int lbm_step_static(const lbm_lattice* lattice, const lbm_eos* eos, double tau_f
 {
     if (!lattice || !eos || !f_in || !g_in || !f_out || !g_out) return fail(LBM_E_INVALID, "NULL argument");
     const lbm_lattice& L = *lattice;
-    if (L.dim != 2 && L.dim != 3) return fail(LBM_E_INVALID, "dim must be 2 or 3");
-    if (L.nx < 1 || L.ny < 1 || L.nz < 1 || (L.dim == 2 && (L.nz != 1 || L.zwalls)))
-        return fail(LBM_E_INVALID, "bad lattice sizes");
+    // what this entry point leaves to the handle path
     if (L.storage != LBM_F64) return fail(LBM_E_UNSUPPORTED, "lbm_step_static works on float64 populations only");
     if (L.zwalls == 2) return fail(LBM_E_UNSUPPORTED, "non-equilibrium-extrapolation walls need a handle (lbm_set_walls)");
     if (force && (force->friction != 0.0 || force->throttle_K != 0.0 || force->field))
         return fail(LBM_E_UNSUPPORTED, "duct friction, throttles and force fields run on the split kernels of a handle");
     if (heat && heat->field) return fail(LBM_E_UNSUPPORTED, "heat fields run on the split kernels of a handle");
-    if (L.zwalls != 0 && L.zwalls != 1) return fail(LBM_E_INVALID, "zwalls must be 0, 1 or 2");
-    if (L.phi_scheme != LBM_PHI_UPWIND && L.phi_scheme != LBM_PHI_CENTRAL) return fail(LBM_E_INVALID, "unknown phi_scheme");
-    const long long N = (long long)L.nx * L.ny * L.nz;
+    if (eos->t_solver != LBM_T_NEWTON)
+        return fail(LBM_E_UNSUPPORTED, "lbm_step_static inverts the temperature by Newton only (t_solver = LBM_T_NEWTON)");
+    if (eos->isothermal) return fail(LBM_E_UNSUPPORTED, "the isothermal mode needs the temperature a handle carries");
+    // the checks of lbm_create
+    SimDev s;
+    std::string why;
+    int rc = lbm_check_and_fill_sim(s, lattice, eos, tau_f, tau_g, force, heat, why);
+    if (rc) return fail(rc, "lbm_step_static: " + why);
+    const long long N = s.N;
     if (N > kStaticMaxCells)
         return fail(LBM_E_INVALID, "lbm_step_static: " + std::to_string(N) + " cells exceed the static maximum of " +
                                        std::to_string(kStaticMaxCells));
-    if (f_in == f_out || g_in == g_out) return fail(LBM_E_INVALID, "input and output populations must not alias");
-    if (eos->kind < LBM_IDEAL || eos->kind > LBM_PR || !(eos->R > 0) || !(eos->cv > 0) || !(tau_f > 0) || !(tau_g > 0))
-        return fail(LBM_E_INVALID, "bad equation of state or relaxation time");
-    if (eos->kind == LBM_PR && !(eos->Tc > 0)) return fail(LBM_E_INVALID, "Peng-Robinson needs Tc > 0");
-
-    SimDev s;
-    std::memset(&s, 0, sizeof(s));
-    s.nx = L.nx; s.ny = L.ny; s.nz = L.nz; s.zwalls = L.zwalls;
-    s.N = N;
-    s.eos = eos->kind;
-    s.phi_central = L.phi_scheme == LBM_PHI_CENTRAL;
-    s.R = eos->R; s.cv = eos->cv; s.a = eos->a; s.b = eos->b; s.Tc = eos->Tc;
-    if (eos->kind == LBM_PR) {
-        if (eos->a == 0.0) {
-            if (!(eos->Pc > 0)) return fail(LBM_E_INVALID, "Peng-Robinson needs a, b or Pc > 0");
-            s.a = 0.45724 * eos->R * eos->R * eos->Tc * eos->Tc / eos->Pc;
-            s.b = 0.07780 * eos->R * eos->Tc / eos->Pc;
-        }
-        s.kw = 0.37464 + 1.54226 * eos->omega - 0.26992 * eos->omega * eos->omega;
-    }
-    if (!(eos->mu >= 0) || !std::isfinite(eos->mu)) return fail(LBM_E_INVALID, "mu must be finite and >= 0");
-    if (eos->isothermal) return fail(LBM_E_UNSUPPORTED, "the isothermal mode needs the temperature a handle carries");
-    s.kappa = eos->kappa; s.eta_mu = eos->eta_over_mu; s.k_mu = eos->k_over_mu;
-    s.mu = eos->mu;
-    s.beta_f = 1.0 / (2.0 * tau_f + 1.0);
-    s.beta_g = 1.0 / (2.0 * tau_g + 1.0);
-    if (force) { s.acc[0] = force->accel[0]; s.acc[1] = force->accel[1]; s.acc[2] = L.dim == 3 ? force->accel[2] : 0.0; }
-    if (heat) { s.q = heat->q; s.zlo = heat->zmask_lo; s.zhi = heat->zmask_hi; }
-    s.inv_cv = 1.0 / s.cv;
-    s.inv_Tc = s.Tc > 0 ? 1.0 / s.Tc : 0.0;
-    s.lam_c = s.b > 0 ? 1.0 / (2.0 * 1.4142135623730951 * s.b) : 0.0;
-    s.athe_c = (double)(L.dim + 2) / (double)L.dim - s.eta_mu;
+    const int Q = L.dim == 2 ? 9 : 27;
+    const double* in_lo[2] = {f_in, g_in};
+    const double* out_lo[2] = {f_out, g_out};
+    for (int a = 0; a < 2; ++a)  // [Q][N] ranges of the inputs and outputs must not overlap
+        for (int b = 0; b < 2; ++b)
+            if (in_lo[a] < out_lo[b] + (size_t)Q * N && out_lo[b] < in_lo[a] + (size_t)Q * N)
+                return fail(LBM_E_INVALID, "input and output populations must not alias");
 
     void* base = nullptr;
-    int rc = scratch_address(&base);
+    rc = scratch_address(&base);
     if (rc) return rc;
     SimDev* d_sim = reinterpret_cast<SimDev*>(base);
     BlockEntry* d_table = reinterpret_cast<BlockEntry*>(static_cast<unsigned char*>(base) + kSimBytes);
     double* W = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + kSimBytes + kTableBytes);
     const int nb = (int)((N + kBlockCells - 1) / kBlockCells);
-    BlockEntry table[kStaticBlocks];
-    for (int b = 0; b < nb; ++b) table[b] = BlockEntry{0, b * kBlockCells};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemcpyAsync(d_sim, &s, sizeof(SimDev), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_table, table, nb * sizeof(BlockEntry), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return fail(LBM_E_CUDA, std::string("lbm_step_static upload: ") + cudaGetErrorString(e));
+    k_static_setup<<<1, kBlockCells, 0, st>>>(s, d_sim, d_table, nb);
     // the work arrays are laid out as [W_NF][N] for this call
     if (L.dim == 2) {
         k_static_moments<2><<<nb, kBlockCells, 0, st>>>(d_sim, f_in, g_in, W, N);
@@ -236,10 +231,8 @@ int lbm_step_static(const lbm_lattice* lattice, const lbm_eos* eos, double tau_f
         k_macro<3, double><<<nb, kBlockCells, 0, st>>>(d_sim, d_table, W, N, nullptr);
         k_static_collide<3><<<nb, kBlockCells, 0, st>>>(d_sim, f_in, g_in, f_out, g_out, W, N);
     }
-    e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LBM_E_CUDA, std::string("lbm_step_static launch: ") + cudaGetErrorString(e));
-    // the host copies of s and table above must not be released before the
-    // stream consumed them (pageable source: the copy is staged before return)
     return LBM_OK;
 }
 

@@ -1,0 +1,394 @@
+// Column-march collide-stream pass for D3Q27 (second pass of the 3-D step,
+// after k_zmacro): the pulled populations are staged in shared memory by
+// asynchronous copies and the next-step moments are gathered, not scattered.
+//
+// A CTA of 512 threads owns an xy tile of 30 x 14 cells and a range of ZL
+// planes; thread (cx, cy) = (lane, warp) keeps the same column of the
+// collided 32 x 16 region (the tile plus a one-cell rim) for every plane, so
+// the three moment planes it is summing (z - 1, z, z + 1) stay in its
+// registers.  One plane is processed as six layers (f then g, one value of
+// c_z at a time, nine populations each):
+//   1. the layer's nine pulled source boxes (16 rows x 34 cells, shifted by
+//      -c_y and -c_z; x rounded out to 16-byte chunks) were copied into a
+//      ring buffer by cp.async several layers earlier -- the copies are in
+//      flight without holding registers;
+//   2. each thread relaxes its cell's nine populations (Eqs. LBM_f, LBM_g),
+//      stores those of owned cells, and writes all nine to a gather buffer;
+//   3. after one barrier each owned thread reads, for the plane z + c_z, the
+//      nine values that stream into its own cell (from (cx - c_x, cy - c_y)):
+//      rho, j and G of the next step accumulate in registers, no atomics.
+//      Populations leaving through a z wall return into the cell they left,
+//      reversed (half-way bounce-back).
+// The plane below the current one is then complete and its moments are
+// written.  Rim collisions are the repeated work, as in the scatter march:
+// (32 x 16)/(30 x 14) in xy and (ZL + 2)/ZL in z.
+//
+// Requirements (checked by the host before selecting it): 32- or 16-bit
+// storage, nx a multiple of the elements per 16-byte chunk, no
+// extrapolated faces, no per-cell force or heat fields, one equation of
+// state per launch.
+#pragma once
+
+#include "lbm_device.cuh"
+#include "lbm_fused.cuh"
+#include "lbm_split.cuh"
+
+#include <type_traits>
+
+namespace lbm {
+
+constexpr int kZgThreads = 512;        // one thread per column of the collided region
+constexpr int kZgCX = 32, kZgCY = 16;  // collided region: the owned tile plus a one-cell rim
+constexpr int kZgTX = kZgCX - 2, kZgTY = kZgCY - 2;
+
+template <typename S> struct ZgStage {
+    static constexpr int C = 16 / (int)sizeof(S);                  // elements per 16-byte copy
+    static constexpr int NCH = (kZgCX + 2 + 2 * (C - 1)) / C;       // copies per row: 34 cells + alignment
+    static constexpr int NCOL = NCH * C;                            // staged elements per row
+    static constexpr int SLOT = kZgCY * NCOL;                       // one population's box
+    static constexpr int LAYER = 9 * SLOT;                          // the nine populations of a c_z layer
+    static constexpr int CHUNKS = 9 * kZgCY * NCH;                  // 16-byte copies per layer
+    static constexpr int RING = sizeof(S) == 4 ? 4 : 6;             // layers in the ring (in flight: RING - 1)
+    static constexpr size_t stage_bytes = (size_t)RING * LAYER * sizeof(S);
+    static constexpr size_t gather_bytes = (size_t)9 * kZgCY * kZgCX * sizeof(float);
+    static constexpr size_t smem_bytes = stage_bytes + gather_bytes;
+};
+
+__device__ __forceinline__ void cp_async16(const void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename S> __device__ __forceinline__ float stored_to_f(S v);
+template <> __device__ __forceinline__ float stored_to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float stored_to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float stored_to_f<__half>(__half v) { return __half2float(v); }
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Macroscopic state of a cell and its stencils (div u, grad h, grad T, Phi;
+// Eq. correction) from the first pass's fields: periodic x, y; z periodic or
+// mirrored beyond half-way bounce-back walls (velocity and X_z odd).
+template <typename R, int EK>
+__device__ __forceinline__ void zg_state(const SimK<R, EK>& s, const R* __restrict__ Wc, long long Ntot, int x, int y,
+                                         int z, Macro<R>& m, R& divu, R* gh, R* gT, R* Phi)
+{
+    const int nx = s.nx, ny = s.ny, nz = s.nz;
+    const bool walls = s.zwalls != 0;
+    auto cell = [&](int xx, int yy, int zz) { return (unsigned)xx + (unsigned)nx * ((unsigned)yy + (unsigned)ny * (unsigned)zz); };
+    auto Wf = [&](int f, unsigned c) { return Wc[(size_t)f * Ntot + c]; };
+    int zn[5];
+    bool zf[5];
+#pragma unroll
+    for (int o = -2; o <= 2; ++o) {
+        if (walls) zn[o + 2] = mirror_z(z + o, nz, zf[o + 2]);
+        else {
+            zn[o + 2] = wrapc(z + o, nz);
+            zf[o + 2] = false;
+        }
+    }
+    const int xm1 = x == 0 ? nx - 1 : x - 1, xp1 = x == nx - 1 ? 0 : x + 1;
+    const int ym1 = y == 0 ? ny - 1 : y - 1, yp1 = y == ny - 1 ? 0 : y + 1;
+    const unsigned gk = cell(x, y, z);
+    m.rho = Wf(W_RHO, gk);
+    m.ir = R(1) / m.rho;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        m.u[a] = Wf(W_U + a, gk);
+        m.F[a] = Wf(W_F + a, gk);
+    }
+    m.Q = heat_q<R>(s, z);
+    m.T = Wf(W_T, gk);
+    m.P = Wf(W_P, gk);
+    m.theta = Wf(W_TH, gk);
+    m.h = Wf(W_H, gk);
+    m.cv = Wf(W_CV, gk);
+    m.icv = EK == EOS_PR ? R(1) / m.cv : s.inv_cv;
+    m.gam = Wf(W_GAM, gk);
+    m.athe = Wf(W_ATHE, gk);
+    m.e = Wf(W_E, gk);
+    const unsigned cxm = cell(xm1, y, z), cxp = cell(xp1, y, z);
+    const unsigned cym = cell(x, ym1, z), cyp = cell(x, yp1, z);
+    const unsigned czm = cell(x, y, zn[1]), czp = cell(x, y, zn[3]);
+    const R szm = zf[1] ? R(-1) : R(1), szp = zf[3] ? R(-1) : R(1);
+    divu = R(0.5) * ((Wf(W_U, cxp) - Wf(W_U, cxm)) + (Wf(W_U + 1, cyp) - Wf(W_U + 1, cym)) +
+                     (szp * Wf(W_U + 2, czp) - szm * Wf(W_U + 2, czm)));
+    gh[0] = R(0.5) * (Wf(W_H, cxp) - Wf(W_H, cxm));
+    gh[1] = R(0.5) * (Wf(W_H, cyp) - Wf(W_H, cym));
+    gh[2] = R(0.5) * (Wf(W_H, czp) - Wf(W_H, czm));
+    gT[0] = R(0.5) * (Wf(W_T, cxp) - Wf(W_T, cxm));
+    gT[1] = R(0.5) * (Wf(W_T, cyp) - Wf(W_T, cym));
+    gT[2] = R(0.5) * (Wf(W_T, czp) - Wf(W_T, czm));
+    R dX[3];
+    if (s.phi_central) {
+        dX[0] = R(0.5) * (Wf(W_X, cxp) - Wf(W_X, cxm));
+        dX[1] = R(0.5) * (Wf(W_X + 1, cyp) - Wf(W_X + 1, cym));
+        dX[2] = R(0.5) * (szp * Wf(W_X + 2, czp) - szm * Wf(W_X + 2, czm));
+    } else {
+        // second-order one-sided by the sign of u_alpha (u >= 0: backward)
+        const R X0x = Wf(W_X, gk), X0y = Wf(W_X + 1, gk), X0z = Wf(W_X + 2, gk);
+        if (m.u[0] >= R(0))
+            dX[0] = R(0.5) * (R(3) * X0x - R(4) * Wf(W_X, cxm) + Wf(W_X, cell(wrapc(x - 2, nx), y, z)));
+        else
+            dX[0] = -R(0.5) * (R(3) * X0x - R(4) * Wf(W_X, cxp) + Wf(W_X, cell(wrapc(x + 2, nx), y, z)));
+        if (m.u[1] >= R(0))
+            dX[1] = R(0.5) * (R(3) * X0y - R(4) * Wf(W_X + 1, cym) + Wf(W_X + 1, cell(x, wrapc(y - 2, ny), z)));
+        else
+            dX[1] = -R(0.5) * (R(3) * X0y - R(4) * Wf(W_X + 1, cyp) + Wf(W_X + 1, cell(x, wrapc(y + 2, ny), z)));
+        if (m.u[2] >= R(0)) {
+            const R s2 = zf[0] ? R(-1) : R(1);
+            dX[2] = R(0.5) * (R(3) * X0z - R(4) * szm * Wf(W_X + 2, czm) + s2 * Wf(W_X + 2, cell(x, y, zn[0])));
+        } else {
+            const R s2 = zf[4] ? R(-1) : R(1);
+            dX[2] = -R(0.5) * (R(3) * X0z - R(4) * szp * Wf(W_X + 2, czp) + s2 * Wf(W_X + 2, cell(x, y, zn[4])));
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Phi[a] = -dX[a] * m.ir;
+}
+
+template <typename S, int EK>
+__global__ void __launch_bounds__(kZgThreads, 1)
+    k_zgather(const SimDev* __restrict__ sims, const TileEntry* __restrict__ tiles, int ntiles, int ZL,
+              const S* __restrict__ src, S* __restrict__ dst, const float* __restrict__ W, float* __restrict__ Mout,
+              long long Ntot)
+{
+    using R = float;
+    using G = ZgStage<S>;
+    constexpr int C = G::C, NCH = G::NCH, NCOL = G::NCOL, K = G::RING;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* stage = reinterpret_cast<S*>(smem_raw);                      // [K][9][kZgCY][NCOL]
+    R* gbuf = reinterpret_cast<R*>(smem_raw + G::stage_bytes);     // [9][kZgCY][kZgCX]
+    __shared__ SimK<R, EK> s;
+    __shared__ int cur_sim;
+    const int tid = threadIdx.x, cx = tid & 31, cy = tid >> 5;
+    if (tid == 0) cur_sim = -1;
+    __syncthreads();
+
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileEntry te = tiles[t];
+        if (te.sim != cur_sim) {
+            __syncthreads();
+            if (tid == 0) {
+                simc_from<R>(static_cast<SimC<R>&>(s), sims[te.sim]);
+                cur_sim = te.sim;
+            }
+            __syncthreads();
+        }
+        const int nx = s.nx, ny = s.ny, nz = s.nz;
+        const bool walls = s.zwalls != 0;
+        const unsigned Ncell = (unsigned)s.N;
+        const unsigned plane_cells = (unsigned)nx * (unsigned)ny;
+        const R* Wc = W + s.cell_off;
+        const S* fb = src + s.pop_off;
+        const S* gb = fb + (size_t)27 * s.N;
+        S* fo = dst + s.pop_off;
+        S* go = fo + (size_t)27 * s.N;
+        R* Mo = Mout + s.cell_off;
+        const int zend = min(te.z0 + ZL, nz);
+        // collided planes: the owned range plus one rim plane each side (none beyond a wall)
+        const int pfirst = (walls && te.z0 == 0) ? 0 : te.z0 - 1;
+        const int plast = (walls && zend == nz) ? nz - 1 : zend;
+        const int LPP = s.iso ? 3 : 6;  // isothermal: g is not evolved
+        const int nstages = (plast - pfirst + 1) * LPP;
+        const int vx = min(kZgTX, nx - te.x0), vy = min(kZgTY, ny - te.y0);
+        const bool own_xy = cx >= 1 && cx <= vx && cy >= 1 && cy <= vy;
+        const int xa = floor_div(te.x0 - 2, C) * C;  // first staged x (unwrapped, chunk-aligned)
+        const int x = wrapc(te.x0 - 1 + cx, nx), y = wrapc(te.y0 - 1 + cy, ny);
+        const int base_col = te.x0 - 1 + cx - xa;  // staged column of this thread's own x
+
+        // stage st: plane pfirst + st / LPP, layer st % LPP (0-2: f with c_z = 0, +1, -1; 3-5: g)
+        auto issue = [&](int st) {
+            if (st < nstages) {
+                const int pi = st / LPP, l = st - pi * LPP;
+                const int zc = pfirst + pi;
+                const int d2 = l % 3;
+                int zs = zc - cval(d2);
+                const bool bounce = walls && (zs < 0 || zs >= nz);  // pulled across a wall: opp(i) of the cell itself
+                zs = bounce ? zc : wrapc(zs, nz);
+                const S* base = (l < 3 ? fb : gb) + (size_t)zs * plane_cells;
+                S* sb = stage + (size_t)(st % K) * G::LAYER;
+                for (int c = tid; c < G::CHUNKS; c += kZgThreads) {
+                    const int j = c / (kZgCY * NCH), r = (c / NCH) % kZgCY, q = c % NCH;
+                    const int i = 9 * d2 + j;
+                    const int ip = bounce ? opp(i) : i;
+                    const int sy = bounce ? 0 : cval(j / 3);
+                    const int yg = wrapc(te.y0 - 1 + r - sy, ny);
+                    const int xg = wrapc(xa + q * C, nx);
+                    cp_async16(sb + (j * kZgCY + r) * NCOL + q * C, base + (size_t)ip * Ncell + (unsigned)yg * (unsigned)nx + (unsigned)xg);
+                }
+            }
+            cp_async_commit();  // one group per stage, empty past the end
+        };
+#pragma unroll 1
+        for (int st = 0; st < K - 1; ++st) issue(st);
+
+        // next-step moments of the planes z - 1, z, z + 1 (rho, j, G)
+        R acc[3][5];
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) acc[p][q] = R(0);
+
+        int sidx = 0;
+#pragma unroll 1
+        for (int zc = pfirst; zc <= plast; ++zc) {
+            const int z = wrapc(zc, nz);
+            Macro<R> m;
+            R divu, gh[3], gT[3], Phi[3];
+            zg_state<R, EK>(s, Wc, Ntot, x, y, z, m, divu, gh, gT, Phi);
+            Coll<3, R> cl = Coll<3, R>::make(s, m, divu, gh, gT, Phi);
+            const bool own = own_xy && zc >= te.z0 && zc < zend;
+            const unsigned gk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+
+            // one layer: relax the nine populations with c_z digit D2 of f (G_ == false) or g
+            auto layer = [&](auto D2c, auto Gc) {
+                constexpr int d2 = decltype(D2c)::value;
+                constexpr bool isg = decltype(Gc)::value;
+                constexpr int cz = cval(d2);
+                cp_async_wait<K - 2>();
+                __syncthreads();  // stage sidx landed for every thread; last layer's gathers are done
+                const S* sb = stage + (size_t)(sidx % K) * G::LAYER;
+                const bool bin = walls && (zc - cz < 0 || zc - cz >= nz);    // pulled across a wall
+                const bool bout = walls && (zc + cz < 0 || zc + cz >= nz);   // streams across a wall
+                R v[9];
+                static_for<0, 9>([&](auto J) {
+                    constexpr int j = decltype(J)::value;
+                    constexpr int i = 9 * d2 + j;
+                    constexpr int cxj = cc(i, 0);
+                    const int col = bin ? base_col : base_col - cxj;
+                    const R* ref = isg ? s.gref : s.fref;
+                    R p = stored_to_f<S>(sb[(j * kZgCY + cy) * NCOL + col]);
+                    if constexpr (Codec<S, R>::offset) p += bin ? ref[opp(i)] : ref[i];
+                    R w;
+                    if constexpr (isg) w = cl.template g<i>(p);
+                    else w = cl.template f<i>(p);
+                    v[j] = w;
+                    if (own) {
+                        S* o = isg ? go : fo;
+                        Codec<S, R>::st(o + (unsigned)i * Ncell + gk, w - (Codec<S, R>::offset ? ref[i] : R(0)));
+                    }
+                    gbuf[(j * kZgCY + cy) * kZgCX + cx] = w;
+                });
+                issue(sidx + K - 1);  // into the buffer read one layer ago
+                ++sidx;
+                __syncthreads();  // gather buffer complete
+                if (own_xy) {
+                    if (bout) {
+                        // half-way bounce-back: f'_i returns to this cell as opp(i)
+                        R sr = 0, sx = 0, sy = 0;
+                        static_for<0, 9>([&](auto J) {
+                            constexpr int j = decltype(J)::value;
+                            sr += v[j];
+                            if (cc(9 * d2 + j, 0) != 0) sx -= R(cc(9 * d2 + j, 0)) * v[j];
+                            if (cc(9 * d2 + j, 1) != 0) sy -= R(cc(9 * d2 + j, 1)) * v[j];
+                        });
+                        if constexpr (isg) acc[1][4] += sr;
+                        else {
+                            acc[1][0] += sr;
+                            acc[1][1] += sx;
+                            acc[1][2] += sy;
+                            acc[1][3] -= R(cz) * sr;
+                        }
+                    } else {
+                        // the nine values that stream into this cell of plane zc + c_z
+                        R sr = 0, sx = 0, sy = 0;
+                        static_for<0, 9>([&](auto J) {
+                            constexpr int j = decltype(J)::value;
+                            constexpr int cxj = cc(9 * d2 + j, 0), cyj = cc(9 * d2 + j, 1);
+                            const R w = gbuf[(j * kZgCY + cy - cyj) * kZgCX + cx - cxj];
+                            sr += w;
+                            if (cxj != 0) sx += R(cxj) * w;
+                            if (cyj != 0) sy += R(cyj) * w;
+                        });
+                        if constexpr (isg) acc[cz + 1][4] += sr;
+                        else {
+                            acc[cz + 1][0] += sr;
+                            acc[cz + 1][1] += sx;
+                            acc[cz + 1][2] += sy;
+                            acc[cz + 1][3] += R(cz) * sr;
+                        }
+                    }
+                }
+            };
+            using IsF = std::false_type;
+            using IsG = std::true_type;
+            layer(std::integral_constant<int, 0>{}, IsF{});
+            layer(std::integral_constant<int, 1>{}, IsF{});
+            layer(std::integral_constant<int, 2>{}, IsF{});
+            if (!s.iso) {
+                cl.prepare_g();
+                layer(std::integral_constant<int, 0>{}, IsG{});
+                layer(std::integral_constant<int, 1>{}, IsG{});
+                layer(std::integral_constant<int, 2>{}, IsG{});
+            }
+            // plane zc - 1 has all its contributions
+            const int zf = zc - 1;
+            if (own_xy && zf >= te.z0 && zf < zend) {
+                const unsigned kk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)zf);
+                Mo[M_RHO * Ntot + kk] = acc[0][0];
+                Mo[(M_J + 0) * Ntot + kk] = acc[0][1];
+                Mo[(M_J + 1) * Ntot + kk] = acc[0][2];
+                Mo[(M_J + 2) * Ntot + kk] = acc[0][3];
+                Mo[M_G * Ntot + kk] = acc[0][4];
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                acc[0][q] = acc[1][q];
+                acc[1][q] = acc[2][q];
+                acc[2][q] = R(0);
+            }
+        }
+        // the top plane when a wall ends the march there (no rim plane above it)
+        if (own_xy && plast >= te.z0 && plast < zend) {
+            const unsigned kk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)plast);
+            Mo[M_RHO * Ntot + kk] = acc[0][0];
+            Mo[(M_J + 0) * Ntot + kk] = acc[0][1];
+            Mo[(M_J + 1) * Ntot + kk] = acc[0][2];
+            Mo[(M_J + 2) * Ntot + kk] = acc[0][3];
+            Mo[M_G * Ntot + kk] = acc[0][4];
+        }
+        cp_async_wait<0>();
+        __syncthreads();  // the ring is reused by the next tile
+    }
+}
+
+template <typename S, int EK>
+cudaError_t zgather_launch(const SimDev* sims, const TileEntry* tiles, int ntiles, int ZL, const void* src, void* dst,
+                           const void* W, void* Mout, long long Ntot, cudaStream_t stream)
+{
+    constexpr size_t smem = ZgStage<S>::smem_bytes;
+    static_assert(smem <= 227u * 1024u, "z-gather buffers do not fit in shared memory");
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_zgather<S, EK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, dev = 0, nsm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_zgather<S, EK>, kZgThreads, smem);
+        if (e != cudaSuccess) return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        grid_cap = per_sm * nsm;
+    }
+    const int grid = ntiles < grid_cap ? ntiles : grid_cap;
+    k_zgather<S, EK><<<grid, kZgThreads, smem, stream>>>(sims, tiles, ntiles, ZL, (const S*)src, (S*)dst,
+                                                         (const float*)W, (float*)Mout, Ntot);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t zgather_dispatch_t(int eos, int zl, const SimDev* sims, const TileEntry* tiles, int ntiles,
+                               const void* src, void* dst, const void* W, void* Mout, long long Ntot,
+                               cudaStream_t stream)
+{
+    if (eos == EOS_IDEAL) return zgather_launch<S, EOS_IDEAL>(sims, tiles, ntiles, zl, src, dst, W, Mout, Ntot, stream);
+    if (eos == EOS_VDW) return zgather_launch<S, EOS_VDW>(sims, tiles, ntiles, zl, src, dst, W, Mout, Ntot, stream);
+    if (eos == EOS_PR) return zgather_launch<S, EOS_PR>(sims, tiles, ntiles, zl, src, dst, W, Mout, Ntot, stream);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

@@ -6,7 +6,7 @@ time per step: the command line that profilers wrap.
 
 Workloads: acoustic_shear, vdw_spinodal, pr_heated_slab, pr_droplet (size =
 cells per side), thermal_couette (n x n x n/2), fanno_duct (n x n x 2n).  Kernel: auto (autotuner), split, fused[:TXxTY[xTZ]] or
-zmarch[:TXxTYxZL].
+zmarch[:TXxTYxZL] or zgather[:30x14xZL].
 """
 from __future__ import annotations
 
@@ -25,7 +25,8 @@ _CASES = {
     "thermal_couette": lambda n, st: wl.thermal_couette(n, n // 2, storage=st),
     "fanno_duct": lambda n, st: wl.fanno_duct(n, 2 * n, storage=st),
 }
-_VARIANTS = {"split": lbm.LBM_KERNEL_SPLIT, "fused": lbm.LBM_KERNEL_FUSED, "zmarch": lbm.LBM_KERNEL_ZMARCH}
+_VARIANTS = {"split": lbm.LBM_KERNEL_SPLIT, "fused": lbm.LBM_KERNEL_FUSED, "zmarch": lbm.LBM_KERNEL_ZMARCH,
+             "zgather": lbm.LBM_KERNEL_ZGATHER}
 
 
 def main(argv=None) -> int:

@@ -20,6 +20,7 @@ from tests.util import oracle_params, rel_linf
 pytestmark = pytest.mark.gpu
 
 SPLIT, FUSED, ZMARCH = lbm.LBM_KERNEL_SPLIT, lbm.LBM_KERNEL_FUSED, lbm.LBM_KERNEL_ZMARCH
+ZGATHER = lbm.LBM_KERNEL_ZGATHER
 
 
 def _variants():
@@ -29,6 +30,11 @@ def _variants():
 def _variants3():
     # z-march with the default range and with 4-plane ranges (several ranges per column)
     return [SPLIT, FUSED, (ZMARCH, (30, 14, 32)), (ZMARCH, (30, 6, 4))]
+
+
+def _variants3_f32():
+    # 32- and 16-bit storage add the gathering z-march: default range and 4-plane ranges
+    return _variants3() + [(ZGATHER, (30, 14, 32)), (ZGATHER, (30, 14, 4))]
 
 
 def _run_pair(case, steps, variant, fields=None):
@@ -287,7 +293,7 @@ def test_f32_ideal_2d(variant):
     _compare(sim, o, 1e-5, f32=True)
 
 
-@pytest.mark.parametrize("variant", _variants3())
+@pytest.mark.parametrize("variant", _variants3_f32())
 def test_f32_pr_3d_walls(variant):
     c = wl.pr_heated_slab(n=12, nz=10, storage="f32")
     c.zhi = 3
@@ -296,14 +302,86 @@ def test_f32_pr_3d_walls(variant):
 
 
 # ---------------------------------------------------------------------------
+# The gathering z-march (staged pulls, moments gathered per column): several
+# tiles in x and y with ragged far edges, several plane ranges, walls and
+# periodic z, lattices narrower than the tile, and every other variant's
+# workloads at float32 (1e-5).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("zl", [32, 4, 5])
+def test_f32_zgather_ragged_periodic_vdw(zl):
+    c = wl.Case(name="vdw3rag", dim=3, nx=68, ny=31, nz=11, eos="vdw", R=1.0, cv=2.5, a=wl.VDW_A, b=wl.VDW_B,
+                kappa=wl.VDW_KAPPA, eta_over_mu=wl.VDW_ETA, k_over_mu=3.5, accel=(2e-4, -1e-4, 3e-4), q=1e-6,
+                phi_central=1, storage="f32",
+                init=dict(kind="noisy_density", rho0=2.0, amp=0.01, T0=1.1 * wl.VDW_TC, seed=31))
+    sim, o = _run_pair(c, 10, (ZGATHER, (30, 14, zl)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+@pytest.mark.parametrize("zl", [32, 3])
+def test_f32_zgather_walls_heat_gravity(zl):
+    c = wl.pr_heated_slab(n=36, nz=13, storage="f32")
+    c.ny = 17
+    c.zhi = 4
+    c.phi_central = 1
+    sim, o = _run_pair(c, 10, (ZGATHER, (30, 14, zl)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+def test_f32_zgather_droplet_periodic():
+    c = wl.pr_droplet(n=20, radius=5.0, storage="f32")
+    sim, o = _run_pair(c, 8, (ZGATHER, (30, 14, 8)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_f32_zgather_lattice_narrower_than_tile(n):
+    # nx, ny below the 30 x 14 tile: the collided region wraps around the lattice several times
+    c = wl.Case(name="tiny", dim=3, nx=n, ny=6, nz=5, eos="ideal", R=1.0, cv=2.5, k_over_mu=3.5,
+                accel=(1e-4, 2e-4, -1e-4), q=1e-6, storage="f32", phi_central=1,
+                init=dict(kind="noisy_density", rho0=1.0, amp=0.02, T0=0.3, seed=32))
+    sim, o = _run_pair(c, 6, (ZGATHER, (30, 14, 2)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+@pytest.mark.parametrize("zwalls", [0, 1])
+def test_f32_zgather_isothermal(zwalls):
+    c = wl.Case(name="vdw3iso", dim=3, nx=36, ny=17, nz=12, zwalls=zwalls, eos="vdw", R=1.0, cv=2.5, a=wl.VDW_A,
+                b=wl.VDW_B, kappa=wl.VDW_KAPPA, eta_over_mu=wl.VDW_ETA, k_over_mu=3.5, accel=(2e-4, -1e-4, 3e-4),
+                isothermal=1, phi_central=1, storage="f32",
+                init=dict(kind="noisy_density", rho0=2.0, amp=0.01, T0=1.1 * wl.VDW_TC, seed=22))
+    sim, o = _run_pair(c, 10, (ZGATHER, (30, 14, 4)))
+    _compare_isothermal(sim, o, 1e-5, f32=True)
+
+
+def test_f32_zgather_constant_mu_walls():
+    c = wl.pr_heated_slab(n=32, nz=13, storage="f32")
+    c.ny = 9
+    c.zhi = 4
+    c.phi_central = 1
+    _with_mu(c, c.init["rho0"], c.init["T0"])
+    sim, o = _run_pair(c, 10, (ZGATHER, (30, 14, 5)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+def test_zgather_refuses_what_it_does_not_run():
+    # float64 storage, and nx not a multiple of the 16-byte copy width
+    for c in (wl.pr_heated_slab(n=12, nz=6, storage="f64"), wl.pr_heated_slab(n=10, nz=6, storage="f32")):
+        sim = lbm.Simulation(c)
+        with pytest.raises(lbm.LbmError, match="gathering z-march"):
+            lbm.lbm_set_kernel(sim.h, ZGATHER, 30, 14, 8)
+        sim.close()
+
+
+# ---------------------------------------------------------------------------
 # 16-bit storage of f - f^ref, float32 arithmetic.  One rounding of the stored
 # deviation per step: |delta f| <= 2^-9 |f - f^ref| (bf16) or 2^-12 (f16) per
 # step; bounded here over a short horizon relative to the population scale.
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("storage,tol", [("bf16", 2e-3), ("f16", 3e-4)])
-@pytest.mark.parametrize("variant", [SPLIT, (ZMARCH, (30, 6, 4))])
+@pytest.mark.parametrize("variant", [SPLIT, (ZMARCH, (30, 6, 4)), (ZGATHER, (30, 14, 4))])
 def test_16bit_storage_error_bound(storage, tol, variant):
-    c = wl.pr_heated_slab(n=10, nz=8, storage=storage)
+    c = wl.pr_heated_slab(n=16, nz=8, storage=storage)  # nx a multiple of 8 (16-byte copies of 16-bit values)
+    c.ny = 10
     sim, o = _run_pair(c, 10, variant)
     f, g = sim.populations()
     fr, gr = o.populations()
