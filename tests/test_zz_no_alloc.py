@@ -1,13 +1,14 @@
 """The allocation-free step (lbm_step_static) against the handle-based path.
 
 lbm_step_static serves callers that cannot allocate device memory when they
-step a simulation (inside someone else's CUDA graph capture, under a fixed
-memory budget, outside PyTorch's allocator): its work arrays sit in a fixed
-static device array.  Two calls in a row must reproduce two steps of the
-regular entry point (lbm_create/lbm_init/lbm_step, read back with
-lbm_populations) to the float64 parity tolerance of the suite, 1e-12
-relative.  This file is collected last so that a run stopping at the first
-failure has run every other test before it.
+step a simulation: hosts that hand the library a fixed device-memory budget,
+programs linking the library without PyTorch's allocator, loops that must
+not call cudaMalloc or cudaFree.  Its work arrays sit in a fixed static
+device array.  Two calls in a row must reproduce two steps of the regular
+entry point (lbm_create/lbm_init/lbm_step, read back with lbm_populations)
+to the float64 parity tolerance of the suite, 1e-12 relative.  This file is
+collected last so that a run stopping at the first failure has run every
+other test before it.
 """
 import numpy as np
 import pytest
@@ -64,3 +65,29 @@ def test_static_step_rejects_oversized_lattice():
     buf = torch.zeros(9 * 8, dtype=torch.float64, device="cuda")
     with pytest.raises(lbm.LbmError, match="exceed the static maximum"):
         lbm.lbm_step_static(lat, eos, 0.8, 0.8, force, heat, buf, buf.clone(), buf.clone(), buf.clone())
+
+
+def test_static_step_rejects_what_it_does_not_run():
+    import torch
+
+    buf = torch.zeros(27 * 64, dtype=torch.float64, device="cuda")
+    # the checks lbm_create makes: Peng-Robinson with b = 0, van der Waals with a < 0
+    pr = wl.pr_heated_slab(n=4, nz=4, storage="f64")
+    lat, eos, force, heat = lbm.structs_from_case(pr)
+    eos.a, eos.b = 0.5, 0.0
+    with pytest.raises(lbm.LbmError, match="b > 0"):
+        lbm.lbm_step_static(lat, eos, 0.8, 0.8, force, heat, buf, buf.clone(), buf.clone(), buf.clone())
+    vdw = wl.vdw_spinodal(n=8, storage="f64")
+    lat, eos, force, heat = lbm.structs_from_case(vdw)
+    eos.a = -1.0
+    with pytest.raises(lbm.LbmError, match="a, b >= 0"):
+        lbm.lbm_step_static(lat, eos, 0.8, 0.8, force, heat, buf, buf.clone(), buf.clone(), buf.clone())
+    # the learned temperature start needs a handle's parameters
+    lat, eos, force, heat = lbm.structs_from_case(pr)
+    eos.t_solver = lbm.LBM_T_MLP
+    with pytest.raises(lbm.LbmError, match="Newton only"):
+        lbm.lbm_step_static(lat, eos, 0.8, 0.8, force, heat, buf, buf.clone(), buf.clone(), buf.clone())
+    # outputs overlapping the inputs
+    lat, eos, force, heat = lbm.structs_from_case(vdw)
+    with pytest.raises(lbm.LbmError, match="alias"):
+        lbm.lbm_step_static(lat, eos, 0.8, 0.8, force, heat, buf, buf.clone(), buf[8:], buf.clone())
