@@ -49,10 +49,22 @@ template <typename S> struct ZgStage {
     static constexpr int LAYER = 9 * SLOT;                          // the nine populations of a c_z layer
     static constexpr int CHUNKS = 9 * kZgCY * NCH;                  // 16-byte copies per layer
     static constexpr int RING = sizeof(S) == 4 ? 4 : 6;             // layers in the ring (in flight: RING - 1)
+    static constexpr int PER_THREAD = (CHUNKS + kZgThreads - 1) / kZgThreads;  // copies per thread per layer
     static constexpr size_t stage_bytes = (size_t)RING * LAYER * sizeof(S);
     static constexpr size_t gather_bytes = (size_t)9 * kZgCY * kZgCX * sizeof(float);
-    static constexpr size_t smem_bytes = stage_bytes + gather_bytes;
+    static constexpr size_t desc_bytes = (size_t)PER_THREAD * kZgThreads * sizeof(uint4);
+    static constexpr size_t smem_bytes = stage_bytes + gather_bytes + desc_bytes;
 };
+
+// opp(j) within one c_z layer of nine directions (j = d0 + 3 d1; digits 0, 1, 2
+// mean c = 0, +1, -1): 4 bits per entry
+constexpr unsigned long long kOpp9 = 0x453786120ULL;
+__device__ __forceinline__ int opp9(int j) { return (int)((kOpp9 >> (4 * j)) & 15u); }
+constexpr bool opp9_table_ok(int j = 0)
+{
+    return j == 9 || ((int)((kOpp9 >> (4 * j)) & 15u) == opp(j) && opp9_table_ok(j + 1));
+}
+static_assert(opp9_table_ok(), "kOpp9 must list opp(j) for j = 0..8");
 
 __device__ __forceinline__ void cp_async16(const void* smem, const void* gmem)
 {
@@ -162,6 +174,9 @@ __global__ void __launch_bounds__(kZgThreads, 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* stage = reinterpret_cast<S*>(smem_raw);                      // [K][9][kZgCY][NCOL]
     R* gbuf = reinterpret_cast<R*>(smem_raw + G::stage_bytes);     // [9][kZgCY][kZgCX]
+    // per thread and copy: (staged element offset | slot << 16, source offset in a
+    // plane for a shifted pull, the same without the shift for a pull across a wall)
+    uint4* desc = reinterpret_cast<uint4*>(smem_raw + G::stage_bytes + G::gather_bytes);  // [PER_THREAD][threads]
     __shared__ SimK<R, EK> s;
     __shared__ int cur_sim;
     const int tid = threadIdx.x, cx = tid & 31, cy = tid >> 5;
@@ -200,31 +215,50 @@ __global__ void __launch_bounds__(kZgThreads, 1)
         const int x = wrapc(te.x0 - 1 + cx, nx), y = wrapc(te.y0 - 1 + cy, ny);
         const int base_col = te.x0 - 1 + cx - xa;  // staged column of this thread's own x
 
-        // stage st: plane pfirst + st / LPP, layer st % LPP (0-2: f with c_z = 0, +1, -1; 3-5: g)
-        auto issue = [&](int st) {
-            if (st < nstages) {
-                const int pi = st / LPP, l = st - pi * LPP;
-                const int zc = pfirst + pi;
-                const int d2 = l % 3;
+        // this thread's copies of a layer: fixed per tile except for the plane and population
+#pragma unroll
+        for (int k = 0; k < G::PER_THREAD; ++k) {
+            const int c = tid + k * kZgThreads;
+            uint4 d = make_uint4(0xffffffffu, 0u, 0u, 0u);
+            if (c < G::CHUNKS) {
+                const int j = c / (kZgCY * NCH), r = (c / NCH) % kZgCY, q = c % NCH;
+                const unsigned xg = (unsigned)wrapc(xa + q * C, nx);
+                const unsigned yn = (unsigned)wrapc(te.y0 - 1 + r - cval(j / 3), ny);
+                const unsigned yb = (unsigned)wrapc(te.y0 - 1 + r, ny);
+                d = make_uint4((unsigned)((j * kZgCY + r) * NCOL + q * C) | ((unsigned)j << 16),
+                               yn * (unsigned)nx + xg, yb * (unsigned)nx + xg, 0u);
+            }
+            desc[k * kZgThreads + tid] = d;
+        }
+        // stages in issue order: plane index ipl, layer il (0-2: f with c_z = 0, +1, -1; 3-5: g), ring slot ib
+        int ipl = 0, il = 0, ib = 0, issued = 0;
+        auto issue = [&]() {
+            if (issued < nstages) {
+                const int zc = pfirst + ipl;
+                const int d2 = il < 3 ? il : il - 3;
                 int zs = zc - cval(d2);
                 const bool bounce = walls && (zs < 0 || zs >= nz);  // pulled across a wall: opp(i) of the cell itself
                 zs = bounce ? zc : wrapc(zs, nz);
-                const S* base = (l < 3 ? fb : gb) + (size_t)zs * plane_cells;
-                S* sb = stage + (size_t)(st % K) * G::LAYER;
-                for (int c = tid; c < G::CHUNKS; c += kZgThreads) {
-                    const int j = c / (kZgCY * NCH), r = (c / NCH) % kZgCY, q = c % NCH;
-                    const int i = 9 * d2 + j;
-                    const int ip = bounce ? opp(i) : i;
-                    const int sy = bounce ? 0 : cval(j / 3);
-                    const int yg = wrapc(te.y0 - 1 + r - sy, ny);
-                    const int xg = wrapc(xa + q * C, nx);
-                    cp_async16(sb + (j * kZgCY + r) * NCOL + q * C, base + (size_t)ip * Ncell + (unsigned)yg * (unsigned)nx + (unsigned)xg);
+                const S* base = (il < 3 ? fb : gb) + (size_t)zs * plane_cells;
+                S* sb = stage + (size_t)ib * G::LAYER;
+                const int po = bounce ? 9 * odig(d2) : 9 * d2;
+#pragma unroll
+                for (int k = 0; k < G::PER_THREAD; ++k) {
+                    const uint4 d = desc[k * kZgThreads + tid];
+                    if (k + 1 < G::PER_THREAD || d.x != 0xffffffffu) {
+                        const int j = (int)(d.x >> 16);
+                        const unsigned ip = (unsigned)(po + (bounce ? opp9(j) : j));
+                        cp_async16(sb + (d.x & 0xffffu), base + (ip * Ncell + (bounce ? d.z : d.y)));
+                    }
                 }
             }
             cp_async_commit();  // one group per stage, empty past the end
+            ++issued;
+            if (++il == LPP) { il = 0; ++ipl; }
+            if (++ib == K) ib = 0;
         };
 #pragma unroll 1
-        for (int st = 0; st < K - 1; ++st) issue(st);
+        for (int st = 0; st < K - 1; ++st) issue();
 
         // next-step moments of the planes z - 1, z, z + 1 (rho, j, G)
         R acc[3][5];
@@ -233,7 +267,7 @@ __global__ void __launch_bounds__(kZgThreads, 1)
 #pragma unroll
             for (int q = 0; q < 5; ++q) acc[p][q] = R(0);
 
-        int sidx = 0;
+        int rb = 0;  // ring slot of the layer being relaxed
 #pragma unroll 1
         for (int zc = pfirst; zc <= plast; ++zc) {
             const int z = wrapc(zc, nz);
@@ -250,18 +284,21 @@ __global__ void __launch_bounds__(kZgThreads, 1)
                 constexpr bool isg = decltype(Gc)::value;
                 constexpr int cz = cval(d2);
                 cp_async_wait<K - 2>();
-                __syncthreads();  // stage sidx landed for every thread; last layer's gathers are done
-                const S* sb = stage + (size_t)(sidx % K) * G::LAYER;
+                __syncthreads();  // this layer's copies landed for every thread; last layer's gathers are done
                 const bool bin = walls && (zc - cz < 0 || zc - cz >= nz);    // pulled across a wall
                 const bool bout = walls && (zc + cz < 0 || zc + cz >= nz);   // streams across a wall
+                // this thread's staged row: pulls from x - c_x (c_x = 0, +1, -1), no shift across a wall
+                const S* r0 = stage + (size_t)rb * G::LAYER + cy * NCOL + base_col;
+                const S* rm = bin ? r0 : r0 - 1;
+                const S* rp = bin ? r0 : r0 + 1;
                 R v[9];
                 static_for<0, 9>([&](auto J) {
                     constexpr int j = decltype(J)::value;
                     constexpr int i = 9 * d2 + j;
                     constexpr int cxj = cc(i, 0);
-                    const int col = bin ? base_col : base_col - cxj;
+                    const S* rowp = cxj == 0 ? r0 : (cxj > 0 ? rm : rp);
                     const R* ref = isg ? s.gref : s.fref;
-                    R p = stored_to_f<S>(sb[(j * kZgCY + cy) * NCOL + col]);
+                    R p = stored_to_f<S>(rowp[j * G::SLOT]);
                     if constexpr (Codec<S, R>::offset) p += bin ? ref[opp(i)] : ref[i];
                     R w;
                     if constexpr (isg) w = cl.template g<i>(p);
@@ -273,8 +310,8 @@ __global__ void __launch_bounds__(kZgThreads, 1)
                     }
                     gbuf[(j * kZgCY + cy) * kZgCX + cx] = w;
                 });
-                issue(sidx + K - 1);  // into the buffer read one layer ago
-                ++sidx;
+                issue();  // into the buffer read one layer ago
+                if (++rb == K) rb = 0;
                 __syncthreads();  // gather buffer complete
                 if (own_xy) {
                     if (bout) {

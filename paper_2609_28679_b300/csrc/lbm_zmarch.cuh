@@ -336,6 +336,39 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
     }
 }
 
+// grad lap rho at (x, y, z) for periodic z or half-way bounce-back walls
+// (mirror images beyond them), from the 25 distinct densities the six
+// neighbouring Laplacians use, with 32-bit indices: the same stencil as
+// grad_lap (lap rho at the images of the two neighbours along each axis).
+template <typename R>
+__device__ __forceinline__ void grad_lap_zm(const R* __restrict__ rho, int x, int y, int z, int nx, int ny, int nz,
+                                            bool mirror, R* gl)
+{
+    auto at = [&](int xx, int yy, int zz) {
+        return rho[(unsigned)xx + (unsigned)nx * ((unsigned)yy + (unsigned)ny * (unsigned)zz)];
+    };
+    const int xp = nb_coord(x, 1, nx, false), xm = nb_coord(x, -1, nx, false);
+    const int yp = nb_coord(y, 1, ny, false), ym = nb_coord(y, -1, ny, false);
+    const int zp = nb_coord(z, 1, nz, mirror), zm = nb_coord(z, -1, nz, mirror);
+    // Laplacian at an in-domain cell whose axis neighbours are given
+    auto lap = [&](int cx, int cy, int cz, int cxp, int cxm, int cyp, int cym, int czp, int czm) {
+        const R c = at(cx, cy, cz);
+        R L = at(cxp, cy, cz) - R(2) * c + at(cxm, cy, cz);
+        L += at(cx, cyp, cz) - R(2) * c + at(cx, cym, cz);
+        L += at(cx, cy, czp) - R(2) * c + at(cx, cy, czm);
+        return L;
+    };
+    const R Lxp = lap(xp, y, z, nb_coord(xp, 1, nx, false), x, yp, ym, zp, zm);
+    const R Lxm = lap(xm, y, z, x, nb_coord(xm, -1, nx, false), yp, ym, zp, zm);
+    const R Lyp = lap(x, yp, z, xp, xm, nb_coord(yp, 1, ny, false), y, zp, zm);
+    const R Lym = lap(x, ym, z, xp, xm, y, nb_coord(ym, -1, ny, false), zp, zm);
+    const R Lzp = lap(x, y, zp, xp, xm, yp, ym, nb_coord(zp, 1, nz, mirror), nb_coord(zp, -1, nz, mirror));
+    const R Lzm = lap(x, y, zm, xp, xm, yp, ym, nb_coord(zm, 1, nz, mirror), nb_coord(zm, -1, nz, mirror));
+    gl[0] = R(0.5) * (Lxp - Lxm);
+    gl[1] = R(0.5) * (Lyp - Lym);
+    gl[2] = R(0.5) * (Lzp - Lzm);
+}
+
 // First pass of the z-march step: the macroscopic state of every cell
 // (Eqs. def_u, def_E, the EoS and its closure scalars, the flux X of
 // Eq. correction) from the carried moments rho, j, G, with last step's T as
@@ -366,11 +399,17 @@ __global__ void __launch_bounds__(kBlockCells) k_zmacro(const SimDev* __restrict
     int x = 0, y = 0, z = 0;
     R r = R(1), F[3] = {0, 0, 0}, j[3] = {0, 0, 0}, Gm = R(0), Tg = R(0), Qh = R(0);
     if (valid) {
-        cell_xyz(s, k, x, y, z);
+        {  // Q N < 2^32 per simulation: 32-bit coordinates
+            const unsigned ku = (unsigned)k, rr = ku / (unsigned)s.nx;
+            x = (int)(ku - rr * (unsigned)s.nx);
+            z = (int)(rr / (unsigned)s.ny);
+            y = (int)(rr - (unsigned)z * (unsigned)s.ny);
+        }
         const R* rho = M + M_RHO * Ntot + s.cell_off;
         r = rho[k];
         R gl[3];
-        grad_lap<3, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls, gl);
+        if (s.zwalls == 2) grad_lap<3, R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls, gl);
+        else grad_lap_zm<R>(rho, x, y, z, s.nx, s.ny, s.nz, s.zwalls == 1, gl);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             F[a] = r * s.acc[a] + s.kappa * r * gl[a];  // Eqs. force_decomposition, korteweg_force
