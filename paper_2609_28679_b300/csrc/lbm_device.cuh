@@ -483,7 +483,13 @@ template <int D, typename R> struct Coll {
     R A0[3][3], As[3][3], B0[3][3], H0[3][3], Hs[3][3];
     R cf0, cf1, cf2, cg0, cg1, cg2;
 
-    template <typename C>
+    // ES_FROM_CV: e(rho, T*) from e(rho, T) and the local c_v instead of the
+    // equation of state.  e is linear in T for the ideal and van der Waals
+    // gases; for Peng-Robinson e(T) = cv0 T - A(rho) (1 + k - k sqrt(T/Tc))
+    // and c_v(T) = cv0 + A k / (2 sqrt(T Tc)) give
+    //   e(T*) = e(T) + cv0 (T* - T) + 2 (c_v(T) - cv0)(sqrt(T T*) - T)
+    // exactly (one square root; no logarithm or division).
+    template <bool ES_FROM_CV = false, typename C>
     __device__ __forceinline__ static Coll make(const C& s, const Macro<R>& m, R divu, const R* gh, const R* gT,
                                                 const R* Phi)
     {
@@ -501,8 +507,13 @@ template <int D, typename R> struct Coll {
         }
         c.ths = m.theta + m.athe * divu + (m.gam - R(1)) * m.Q * m.ir;
         const R Ts = m.T + (m.Q * m.ir - R(0.5) * FF * m.ir * m.ir) * m.icv;
-        const RhoPart<R> p = rho_part<R>(s, m.rho);
-        c.es = eos_e<R>(s, p, Ts);
+        if constexpr (ES_FROM_CV) {
+            c.es = m.e + (R)s.cv * (Ts - m.T);
+            if (s.eos == EOS_PR) c.es += R(2) * (m.cv - (R)s.cv) * (sqrt(m.T * Ts) - m.T);
+        } else {
+            const RhoPart<R> p = rho_part<R>(s, m.rho);
+            c.es = eos_e<R>(s, p, Ts);
+        }
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             psi3<R>(m.u[a], m.theta + m.u[a] * m.u[a], c.A0[a]);

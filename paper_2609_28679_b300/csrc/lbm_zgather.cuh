@@ -51,7 +51,7 @@ template <typename S> struct ZgStage {
     static constexpr int RING = sizeof(S) == 4 ? 4 : 6;             // layers in the ring (in flight: RING - 1)
     static constexpr int PER_THREAD = (CHUNKS + kZgThreads - 1) / kZgThreads;  // copies per thread per layer
     static constexpr size_t stage_bytes = (size_t)RING * LAYER * sizeof(S);
-    static constexpr size_t gather_bytes = (size_t)9 * kZgCY * kZgCX * sizeof(float);
+    static constexpr size_t gather_bytes = (size_t)2 * 9 * kZgCY * kZgCX * sizeof(float);  // two layers
     static constexpr size_t desc_bytes = (size_t)PER_THREAD * kZgThreads * sizeof(uint4);
     static constexpr size_t smem_bytes = stage_bytes + gather_bytes + desc_bytes;
 };
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kZgThreads, 1)
     constexpr int C = G::C, NCH = G::NCH, NCOL = G::NCOL, K = G::RING;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* stage = reinterpret_cast<S*>(smem_raw);                      // [K][9][kZgCY][NCOL]
-    R* gbuf = reinterpret_cast<R*>(smem_raw + G::stage_bytes);     // [9][kZgCY][kZgCX]
+    R* gbuf = reinterpret_cast<R*>(smem_raw + G::stage_bytes);     // [2][9][kZgCY][kZgCX]
     // per thread and copy: (staged element offset | slot << 16, source offset in a
     // plane for a shifted pull, the same without the shift for a pull across a wall)
     uint4* desc = reinterpret_cast<uint4*>(smem_raw + G::stage_bytes + G::gather_bytes);  // [PER_THREAD][threads]
@@ -230,12 +230,13 @@ __global__ void __launch_bounds__(kZgThreads, 1)
             }
             desc[k * kZgThreads + tid] = d;
         }
-        // stages in issue order: plane index ipl, layer il (0-2: f with c_z = 0, +1, -1; 3-5: g), ring slot ib
+        // stages in issue order: plane index ipl, layer il (0-2: f with c_z = -1, 0, +1; 3-5: g), ring slot ib
         int ipl = 0, il = 0, ib = 0, issued = 0;
         auto issue = [&]() {
             if (issued < nstages) {
                 const int zc = pfirst + ipl;
-                const int d2 = il < 3 ? il : il - 3;
+                const int l3 = il < 3 ? il : il - 3;
+                const int d2 = l3 == 0 ? 2 : l3 - 1;  // c_z = -1, 0, +1
                 int zs = zc - cval(d2);
                 const bool bounce = walls && (zs < 0 || zs >= nz);  // pulled across a wall: opp(i) of the cell itself
                 zs = bounce ? zc : wrapc(zs, nz);
@@ -260,12 +261,54 @@ __global__ void __launch_bounds__(kZgThreads, 1)
 #pragma unroll 1
         for (int st = 0; st < K - 1; ++st) issue();
 
-        // next-step moments of the planes z - 1, z, z + 1 (rho, j, G)
+        // next-step moments (rho, j, G) of the planes zc - 1, zc, zc + 1 around the current plane zc
         R acc[3][5];
 #pragma unroll
         for (int p = 0; p < 3; ++p)
 #pragma unroll
             for (int q = 0; q < 5; ++q) acc[p][q] = R(0);
+        auto finalize = [&](int slot, int zf) {  // the moments of plane zf are complete
+            if (own_xy && zf >= te.z0 && zf < zend) {
+                const unsigned kk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)zf);
+                Mo[M_RHO * Ntot + kk] = acc[slot][0];
+                Mo[(M_J + 0) * Ntot + kk] = acc[slot][1];
+                Mo[(M_J + 1) * Ntot + kk] = acc[slot][2];
+                Mo[(M_J + 2) * Ntot + kk] = acc[slot][3];
+                Mo[M_G * Ntot + kk] = acc[slot][4];
+            }
+        };
+        // add (rho, j, G) contributions to the accumulator of plane zc + idx - 1
+        auto add = [&](int idx, bool isg, R sr, R sx, R sy, R sz) {
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                if (p != idx) continue;
+                if (isg) acc[p][4] += sr;
+                else {
+                    acc[p][0] += sr;
+                    acc[p][1] += sx;
+                    acc[p][2] += sy;
+                    acc[p][3] += sz;
+                }
+            }
+        };
+        // The gather of a layer runs after the next layer's barrier (one barrier per
+        // layer, two gather buffers): pending layer's buffer, c_z, distribution, plane.
+        bool pend = false, pend_g = false;
+        int pend_slot = 0, pend_cz = 0, pend_zc = 0, wslot = 0;
+        auto gather_pending = [&](int zc) {
+            if (!pend || !own_xy) return;
+            const R* g0 = gbuf + pend_slot * (9 * kZgCY * kZgCX) + cy * kZgCX + cx;
+            R sr = 0, sx = 0, sy = 0;
+            static_for<0, 9>([&](auto J) {
+                constexpr int j = decltype(J)::value;
+                constexpr int cxj = cval(j % 3), cyj = cval(j / 3);
+                const R w = g0[j * kZgCY * kZgCX - cyj * kZgCX - cxj];  // from (cx - c_x, cy - c_y)
+                sr += w;
+                if (cxj != 0) sx += R(cxj) * w;
+                if (cyj != 0) sy += R(cyj) * w;
+            });
+            add(pend_zc + pend_cz - zc + 1, pend_g, sr, sx, sy, R(pend_cz) * sr);
+        };
 
         int rb = 0;  // ring slot of the layer being relaxed
 #pragma unroll 1
@@ -274,103 +317,114 @@ __global__ void __launch_bounds__(kZgThreads, 1)
             Macro<R> m;
             R divu, gh[3], gT[3], Phi[3];
             zg_state<R, EK>(s, Wc, Ntot, x, y, z, m, divu, gh, gT, Phi);
-            Coll<3, R> cl = Coll<3, R>::make(s, m, divu, gh, gT, Phi);
+            Coll<3, R> cl = Coll<3, R>::template make<true>(s, m, divu, gh, gT, Phi);
             const bool own = own_xy && zc >= te.z0 && zc < zend;
             const unsigned gk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
 
-            // one layer: relax the nine populations with c_z digit D2 of f (G_ == false) or g
-            auto layer = [&](auto D2c, auto Gc) {
+            // The relaxation folded per axis (Eqs. LBM_f, LBM_g with the equilibria in
+            // product form): rho and the weights of f^eq, f*, g^eq, g* ride on the x factors.
+            R fx1[3], fx2[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                fx1[d] = cl.cf1 * cl.rho * cl.A0[0][d];
+                fx2[d] = cl.cf2 * cl.rho * cl.As[0][d];
+            }
+            R gx1[3] = {}, gx2[3] = {}, gx3[3] = {}, gx4[3] = {}, hq[3] = {};  // g factors, set before the g layers
+
+            // one layer: relax the nine populations with c_z digit d2 of f (isg false) or g
+            auto layer = [&](auto D2c, auto Gc, auto POSc) {
                 constexpr int d2 = decltype(D2c)::value;
                 constexpr bool isg = decltype(Gc)::value;
+                constexpr int pos = decltype(POSc)::value;
                 constexpr int cz = cval(d2);
                 cp_async_wait<K - 2>();
-                __syncthreads();  // this layer's copies landed for every thread; last layer's gathers are done
+                __syncthreads();  // this layer's copies landed everywhere; the previous layer's gather buffer is complete
+                gather_pending(zc);
+                pend = false;
+                // after the gather of the last c_z = -1 layer of plane zc, plane zc - 1 is complete
+                if (pos == (s.iso ? 1 : 4)) finalize(0, zc - 1);
                 const bool bin = walls && (zc - cz < 0 || zc - cz >= nz);    // pulled across a wall
                 const bool bout = walls && (zc + cz < 0 || zc + cz >= nz);   // streams across a wall
                 // this thread's staged row: pulls from x - c_x (c_x = 0, +1, -1), no shift across a wall
                 const S* r0 = stage + (size_t)rb * G::LAYER + cy * NCOL + base_col;
                 const S* rm = bin ? r0 : r0 - 1;
                 const S* rp = bin ? r0 : r0 + 1;
-                R v[9];
+                R* gw = gbuf + wslot * (9 * kZgCY * kZgCX) + cy * kZgCX + cx;
                 static_for<0, 9>([&](auto J) {
                     constexpr int j = decltype(J)::value;
                     constexpr int i = 9 * d2 + j;
-                    constexpr int cxj = cc(i, 0);
+                    constexpr int d0 = dig(i, 0), d1 = dig(i, 1);
+                    constexpr int cxj = cc(i, 0), cyj = cc(i, 1);
                     const S* rowp = cxj == 0 ? r0 : (cxj > 0 ? rm : rp);
                     const R* ref = isg ? s.gref : s.fref;
                     R p = stored_to_f<S>(rowp[j * G::SLOT]);
                     if constexpr (Codec<S, R>::offset) p += bin ? ref[opp(i)] : ref[i];
                     R w;
-                    if constexpr (isg) w = cl.template g<i>(p);
-                    else w = cl.template f<i>(p);
-                    v[j] = w;
+                    if constexpr (isg) {
+                        w = cl.cg0 * p;
+                        w = fma(fma(gx1[d0], cl.A0[1][d1], gx2[d0] * cl.H0[1][d1]), cl.A0[2][d2], w);
+                        w = fma(gx2[d0] * cl.A0[1][d1], cl.H0[2][d2], w);
+                        w = fma(fma(gx3[d0], cl.B0[1][d1], gx4[d0] * cl.Hs[1][d1]), cl.B0[2][d2], w);
+                        w = fma(gx4[d0] * cl.B0[1][d1], cl.Hs[2][d2], w);
+                        if constexpr (cnorm2(i) == 1) w += cxj != 0 ? R(cxj) * hq[0] : (cyj != 0 ? R(cyj) * hq[1] : R(cz) * hq[2]);
+                    } else {
+                        w = cl.cf0 * p;
+                        w = fma(fx1[d0] * cl.A0[1][d1], cl.A0[2][d2], w);
+                        w = fma(fx2[d0] * cl.As[1][d1], cl.As[2][d2], w);
+                    }
                     if (own) {
                         S* o = isg ? go : fo;
                         Codec<S, R>::st(o + (unsigned)i * Ncell + gk, w - (Codec<S, R>::offset ? ref[i] : R(0)));
                     }
-                    gbuf[(j * kZgCY + cy) * kZgCX + cx] = w;
+                    gw[j * kZgCY * kZgCX] = w;
                 });
                 issue();  // into the buffer read one layer ago
                 if (++rb == K) rb = 0;
-                __syncthreads();  // gather buffer complete
-                if (own_xy) {
-                    if (bout) {
-                        // half-way bounce-back: f'_i returns to this cell as opp(i)
+                if (bout) {
+                    // half-way bounce-back: f'_i returns to this cell as opp(i) (own values, reversed c)
+                    if (own_xy) {
                         R sr = 0, sx = 0, sy = 0;
                         static_for<0, 9>([&](auto J) {
                             constexpr int j = decltype(J)::value;
-                            sr += v[j];
-                            if (cc(9 * d2 + j, 0) != 0) sx -= R(cc(9 * d2 + j, 0)) * v[j];
-                            if (cc(9 * d2 + j, 1) != 0) sy -= R(cc(9 * d2 + j, 1)) * v[j];
-                        });
-                        if constexpr (isg) acc[1][4] += sr;
-                        else {
-                            acc[1][0] += sr;
-                            acc[1][1] += sx;
-                            acc[1][2] += sy;
-                            acc[1][3] -= R(cz) * sr;
-                        }
-                    } else {
-                        // the nine values that stream into this cell of plane zc + c_z
-                        R sr = 0, sx = 0, sy = 0;
-                        static_for<0, 9>([&](auto J) {
-                            constexpr int j = decltype(J)::value;
-                            constexpr int cxj = cc(9 * d2 + j, 0), cyj = cc(9 * d2 + j, 1);
-                            const R w = gbuf[(j * kZgCY + cy - cyj) * kZgCX + cx - cxj];
+                            constexpr int cxj = cval(j % 3), cyj = cval(j / 3);
+                            const R w = gw[j * kZgCY * kZgCX];
                             sr += w;
-                            if (cxj != 0) sx += R(cxj) * w;
-                            if (cyj != 0) sy += R(cyj) * w;
+                            if (cxj != 0) sx -= R(cxj) * w;
+                            if (cyj != 0) sy -= R(cyj) * w;
                         });
-                        if constexpr (isg) acc[cz + 1][4] += sr;
-                        else {
-                            acc[cz + 1][0] += sr;
-                            acc[cz + 1][1] += sx;
-                            acc[cz + 1][2] += sy;
-                            acc[cz + 1][3] += R(cz) * sr;
-                        }
+                        add(1, isg, sr, sx, sy, -R(cz) * sr);
                     }
+                } else {
+                    pend = true;
+                    pend_g = isg;
+                    pend_slot = wslot;
+                    pend_cz = cz;
+                    pend_zc = zc;
+                    wslot ^= 1;
                 }
             };
             using IsF = std::false_type;
             using IsG = std::true_type;
-            layer(std::integral_constant<int, 0>{}, IsF{});
-            layer(std::integral_constant<int, 1>{}, IsF{});
-            layer(std::integral_constant<int, 2>{}, IsF{});
+            using I0 = std::integral_constant<int, 0>;
+            using I1 = std::integral_constant<int, 1>;
+            using I2 = std::integral_constant<int, 2>;
+            // c_z = -1, 0, +1 (digits 2, 0, 1) for f, then for g
+            layer(I2{}, IsF{}, std::integral_constant<int, 0>{});
+            layer(I0{}, IsF{}, std::integral_constant<int, 1>{});
+            layer(I1{}, IsF{}, std::integral_constant<int, 2>{});
             if (!s.iso) {
                 cl.prepare_g();
-                layer(std::integral_constant<int, 0>{}, IsG{});
-                layer(std::integral_constant<int, 1>{}, IsG{});
-                layer(std::integral_constant<int, 2>{}, IsG{});
-            }
-            // plane zc - 1 has all its contributions
-            const int zf = zc - 1;
-            if (own_xy && zf >= te.z0 && zf < zend) {
-                const unsigned kk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)zf);
-                Mo[M_RHO * Ntot + kk] = acc[0][0];
-                Mo[(M_J + 0) * Ntot + kk] = acc[0][1];
-                Mo[(M_J + 1) * Ntot + kk] = acc[0][2];
-                Mo[(M_J + 2) * Ntot + kk] = acc[0][3];
-                Mo[M_G * Ntot + kk] = acc[0][4];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    gx1[d] = cl.cg1 * cl.rho * (cl.e * cl.A0[0][d] + cl.H0[0][d]);
+                    gx2[d] = cl.cg1 * cl.rho * cl.A0[0][d];
+                    gx3[d] = cl.cg2 * cl.rho * (cl.es * cl.B0[0][d] + cl.Hs[0][d]);
+                    gx4[d] = cl.cg2 * cl.rho * cl.B0[0][d];
+                    hq[d] = cl.cg2 * R(0.5) * cl.qc[d];
+                }
+                layer(I2{}, IsG{}, std::integral_constant<int, 3>{});
+                layer(I0{}, IsG{}, std::integral_constant<int, 4>{});
+                layer(I1{}, IsG{}, std::integral_constant<int, 5>{});
             }
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
@@ -379,15 +433,8 @@ __global__ void __launch_bounds__(kZgThreads, 1)
                 acc[2][q] = R(0);
             }
         }
-        // the top plane when a wall ends the march there (no rim plane above it)
-        if (own_xy && plast >= te.z0 && plast < zend) {
-            const unsigned kk = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)plast);
-            Mo[M_RHO * Ntot + kk] = acc[0][0];
-            Mo[(M_J + 0) * Ntot + kk] = acc[0][1];
-            Mo[(M_J + 1) * Ntot + kk] = acc[0][2];
-            Mo[(M_J + 2) * Ntot + kk] = acc[0][3];
-            Mo[M_G * Ntot + kk] = acc[0][4];
-        }
+        // the top plane when a wall ends the march there (its last layers bounce back: nothing pending)
+        finalize(0, plast);
         cp_async_wait<0>();
         __syncthreads();  // the ring is reused by the next tile
     }
