@@ -271,6 +271,25 @@ int lbm_diagnostics(lbm_handle h, long long out[4]);
  * cannot run, LBM_E_UNSUPPORTED for a lattice or boundary set it does not run. */
 int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz);
 
+/* n eager time steps (no graphs) with CUDA events recorded on h's stream
+ * between the passes of every step; on return (synchronised) ms_per_pass
+ * holds the mean device time per step of pass 1, 2, 3 and of the whole step:
+ *   z-march variants: macroscopic pass, boundary-cell rebuild (0 without
+ *                     extrapolated faces), collide-stream pass;
+ *   fused:            0, 0, the one-pass step;
+ *   split:            moments, macroscopic pass (and boundary cells), collide-stream.
+ * A step that prepares the carried moments first (after lbm_init or a
+ * kernel change) runs before the recorded ones.  Errors as lbm_step. */
+int lbm_step_timed(lbm_handle h, int n, double ms_per_pass[4]);
+
+/* The float64 fused multiply-add rate of the current device (TFLOP/s, 2
+ * FLOP per FMA): eight independent chains per thread, four full waves of
+ * CTAs, best of three timed launches after a warm-up (ms: that launch's
+ * duration, may be NULL).  Measurement infrastructure for the arithmetic
+ * bound of the float64 forms; allocates nothing; synchronises `stream`
+ * (NULL: the legacy default stream).  Errors: LBM_E_INVALID, LBM_E_CUDA. */
+int lbm_fp64_peak(double *tflops, double *ms, void *stream);
+
 /* Replay lbm_step's time steps as CUDA graphs of `steps_per_graph` steps (an
  * even number >= 2; 0 turns graphs off).  lbm_step(h, n) then runs one eager
  * step, n-1 steps as whole graphs and the remainder eagerly.  The graph is

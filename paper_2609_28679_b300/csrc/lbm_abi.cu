@@ -65,6 +65,8 @@ struct lbm_ctx {
     int graph_steps = 0;               // steps per captured CUDA graph (0: launch eagerly)
     float* d_mlp = nullptr;            // learned temperature parameters (lbm_mlp_load)
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};  // per starting buffer parity
+    std::vector<cudaEvent_t> pass_ev;  // lbm_step_timed: 4 events per step (start, after passes 1, 2, 3)
+    int pass_step = -1;                // step of lbm_step_timed being recorded (-1: none)
     std::string err;
     Ops ops{};
 };
@@ -96,6 +98,12 @@ int cuda_fail(lbm_ctx* h, cudaError_t e, const char* where)
     } while (0)
 
 void* dev_alloc(lbm_ctx* h, size_t n) { return lbm_glue_alloc(n, (void*)h->stream); }
+
+// lbm_step_timed: mark the boundary k (0 start, 1-3 after each pass) of the step being recorded
+void pass_mark(lbm_ctx* h, int k)
+{
+    if (h->pass_step >= 0) cudaEventRecord(h->pass_ev[4 * (size_t)h->pass_step + k], h->stream);
+}
 
 // some simulation of h has non-equilibrium-extrapolation walls
 bool has_nee(const lbm_ctx* h)
@@ -204,12 +212,16 @@ template <int D, typename R, typename S> struct Impl {
         const int nb = nblocks(h);
         S* src = (S*)h->pop[h->cur];
         S* dst = (S*)h->pop[h->cur ^ 1];
+        pass_mark(h, 0);
         k_moments<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, src, (R*)h->W, h->Ntot);
+        pass_mark(h, 1);
         k_macro<D, R><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot, h->d_diag);
         if (D == 3 && has_nee(h))
             k_nee<D, R, S><<<(int)h->face_table.size(), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_face_table, src,
                                                                                      (R*)h->W, h->Ntot, 1);
+        pass_mark(h, 2);
         k_collide<D, R, S><<<nb, kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, src, dst, (const R*)h->W, h->Ntot);
+        pass_mark(h, 3);
         LBM_LAUNCH_CHECK(h, "split step");
         h->cur ^= 1;
         h->moments_valid = false;
@@ -232,12 +244,16 @@ template <int D, typename R, typename S> struct Impl {
             int rc = fused_prepare(h);
             if (rc) return rc;
         }
+        pass_mark(h, 0);
+        pass_mark(h, 1);
+        pass_mark(h, 2);
         cudaError_t e = fused_dispatch(h->storage, D, h->sims[0].eos, uses_mlp(h), all_central(h), h->tx, h->ty, h->tz,
                                        h->d_sims,
                                        h->d_tiles,
                                        (int)h->tiles.size(), h->pop[h->cur], h->pop[h->cur ^ 1], mbuf(h, h->cur),
                                        mbuf(h, h->cur ^ 1), h->Ntot, h->d_diag, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "fused step");
+        pass_mark(h, 3);
         h->cur ^= 1;
         return LBM_OK;
     }
@@ -250,6 +266,7 @@ template <int D, typename R, typename S> struct Impl {
             int rc = fused_prepare(h);
             if (rc) return rc;
         }
+        pass_mark(h, 0);
         if (uses_mlp(h) && h->storage != LBM_F32) {  // learned start with 16-bit or float64 storage: generic pass
             k_macro<D, R, true><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot,
                                                                            h->d_diag, mbuf(h, h->cur));
@@ -259,12 +276,14 @@ template <int D, typename R, typename S> struct Impl {
                                             nblocks(h), mbuf(h, h->cur), h->W, h->Ntot, h->d_diag, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "z-march macroscopic pass");
         }
+        pass_mark(h, 1);
         const bool nee = has_nee(h);
         if (nee) {  // rebuild the boundary cells (slots of their pulls, fields) before the collide-stream pass
             k_nee<D, R, S><<<(int)h->face_table.size(), kBlockCells, 0, h->stream>>>(
                 h->d_sims, h->d_face_table, (S*)h->pop[h->cur], (R*)h->W, h->Ntot, 1);
             LBM_LAUNCH_CHECK(h, "boundary cells");
         }
+        pass_mark(h, 2);
         cudaError_t e;
         if (h->variant == LBM_KERNEL_ZGATHER)
             e = zgather_dispatch(h->storage, h->sims[0].eos, h->tz, h->d_sims, h->d_tiles, (int)h->tiles.size(),
@@ -274,6 +293,7 @@ template <int D, typename R, typename S> struct Impl {
                 h->storage, h->sims[0].eos, h->tx, h->ty, h->tz, h->d_sims, h->d_tiles, (int)h->tiles.size(),
                 h->pop[h->cur], h->pop[h->cur ^ 1], h->W, mbuf(h, h->cur ^ 1), h->Ntot, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "z-march step");
+        pass_mark(h, 3);
         h->cur ^= 1;
         return LBM_OK;
     }
@@ -565,6 +585,8 @@ void drop_graph(lbm_ctx* h)
 void free_all(lbm_ctx* h)
 {
     drop_graph(h);
+    for (cudaEvent_t ev : h->pass_ev) cudaEventDestroy(ev);
+    h->pass_ev.clear();
     void* ptrs[] = {h->d_sims, h->d_table, h->d_sim_block_start, h->d_tiles, h->pop[0], h->pop[1],
                     h->W, h->M, h->d_diag, h->d_partials, h->d_mlp, h->d_face_table};
     for (void* p : ptrs) lbm_glue_free(p);
@@ -963,6 +985,46 @@ int lbm_step(lbm_handle h, int n)
         LBM_CUDA_CHECK(h, cudaGraphLaunch(h->graph_exec[h->cur], h->stream));
     }
     return left ? h->ops.step(h, left) : LBM_OK;
+}
+
+int lbm_step_timed(lbm_handle h, int n, double ms_per_pass[4])
+{
+    if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
+    if (n < 1 || !ms_per_pass) return fail(h, LBM_E_INVALID, "n must be >= 1 and ms_per_pass non-NULL");
+    if (!h->initialized) return fail(h, LBM_E_STATE, "lbm_init has not been called");
+    // the first step prepares the carried moments outside the recorded passes
+    if ((h->variant == LBM_KERNEL_FUSED || h->variant == LBM_KERNEL_ZMARCH || h->variant == LBM_KERNEL_ZGATHER) &&
+        !h->moments_valid) {
+        int rc = h->ops.step(h, 1);
+        if (rc) return rc;
+    }
+    const size_t need = 4 * (size_t)n;
+    while (h->pass_ev.size() < need) {
+        cudaEvent_t ev;
+        LBM_CUDA_CHECK(h, cudaEventCreate(&ev));
+        h->pass_ev.push_back(ev);
+    }
+    int rc = LBM_OK;
+    for (int k = 0; k < n && rc == LBM_OK; ++k) {
+        h->pass_step = k;
+        rc = h->ops.step(h, 1);
+    }
+    h->pass_step = -1;
+    if (rc) return rc;
+    LBM_CUDA_CHECK(h, cudaEventSynchronize(h->pass_ev[need - 1]));
+    double acc[4] = {0, 0, 0, 0};
+    for (int k = 0; k < n; ++k) {
+        for (int p = 0; p < 3; ++p) {
+            float ms = 0.f;
+            LBM_CUDA_CHECK(h, cudaEventElapsedTime(&ms, h->pass_ev[4 * (size_t)k + p], h->pass_ev[4 * (size_t)k + p + 1]));
+            acc[p] += ms;
+        }
+        float tot = 0.f;
+        LBM_CUDA_CHECK(h, cudaEventElapsedTime(&tot, h->pass_ev[4 * (size_t)k], h->pass_ev[4 * (size_t)k + 3]));
+        acc[3] += tot;
+    }
+    for (int p = 0; p < 4; ++p) ms_per_pass[p] = acc[p] / n;
+    return LBM_OK;
 }
 
 int lbm_set_graph(lbm_handle h, int steps_per_graph)

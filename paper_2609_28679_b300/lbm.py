@@ -78,6 +78,8 @@ _SIGS = {
     "lbm_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_invariants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_step_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "lbm_fp64_peak": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_set_kernel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_get_kernel": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4),
     "lbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -228,6 +230,21 @@ def lbm_diagnostics(h) -> np.ndarray:
     out = np.zeros(4, dtype=np.int64)
     _check(_lib.lbm_diagnostics(h, out.ctypes.data_as(ctypes.c_void_p)), h)
     return out
+
+
+def lbm_step_timed(h, n: int) -> np.ndarray:
+    """Mean device ms per step of passes 1, 2, 3 and of the whole step over n steps."""
+    out = np.zeros(4, dtype=np.float64)
+    _check(_lib.lbm_step_timed(h, int(n), out.ctypes.data_as(ctypes.c_void_p)), h)
+    return out
+
+
+def lbm_fp64_peak(stream=None) -> tuple:
+    """(TFLOP/s, ms of the timed launch) of the float64 FMA probe."""
+    lib = _lib_gpu()
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib.lbm_fp64_peak(ctypes.byref(tf), ctypes.byref(ms), ctypes.c_void_p(stream or 0)), None)
+    return tf.value, ms.value
 
 
 def lbm_set_kernel(h, variant: int, tx: int = 0, ty: int = 0, tz: int = 0) -> None:

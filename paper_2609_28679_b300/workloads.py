@@ -262,3 +262,21 @@ def vdw_batch(nsim: int = 64, steps: int = 2000, seed: int = 4, lmin: int = 64, 
         c = vdw_spinodal(n=L, steps=steps, storage=storage, Tr=Tr, rho0=VDW_RHOC, seed=1000 + s)
         cases.append(replace(c, name=f"vdw_batch_{s}_{L}"))
     return cases
+
+
+def window(case: Case, center, half: int, full_z: bool = False):
+    """Sub-case over the periodic window [c - half, c + half) of `case` around
+    `center` (the full z extent when full_z, e.g. between walls) and its
+    initial fields sliced from the case's: a bounded sample of a large
+    workload (the window is closed periodically at its faces)."""
+    rho, u, T = case.fields()
+    shape = (case.nz, case.ny, case.nx)
+    ix = (center[0] + np.arange(-half, half)) % case.nx
+    iy = (center[1] + np.arange(-half, half)) % case.ny
+    iz = np.arange(case.nz) if full_z else (center[2] + np.arange(-half, half)) % case.nz
+    sel = np.ix_(iz, iy, ix)
+    rw = rho.reshape(shape)[sel].ravel()
+    Tw = T.reshape(shape)[sel].ravel()
+    uw = np.stack([u[a].reshape(shape)[sel].ravel() for a in range(case.dim)])
+    sub = replace(case, name=case.name + "_window", nx=len(ix), ny=len(iy), nz=len(iz))
+    return sub, (rw, uw, Tw), sel
