@@ -321,24 +321,31 @@ def _vs_f64(ref, ref_fields, r, fields):
     r["rel_dev_vs_f64_gpu"] = {"rho": _rel_dev(fields[0], ref_fields[0]), "T": _rel_dev(fields[1], ref_fields[1])}
 
 
-def _fp64_bound(r, fp64_peak, flops_per_cell):
-    """The float64 form against the float64 arithmetic bound (FMA probe)."""
-    if fp64_peak and flops_per_cell:
-        achieved = flops_per_cell * r["mlups"] * 1e6 / 1e12
-        r["fp64_alu"] = {"flops_per_cell": flops_per_cell, "achieved_tflops": achieved, "peak_tflops": fp64_peak,
-                         "frac": achieved / fp64_peak, "peak_source": "lbm_fp64_peak probe, same run"}
+def _fp64_bound(r, fp64_peak, work):
+    """The float64 form against the float64 arithmetic bound: the FMA probe's
+    rate in FLOP/s and, since DADD and DMUL take a float64 pipe slot like DFMA,
+    in float64 instructions per second (probe TFLOP/s / 2)."""
+    if fp64_peak and work:
+        flops, instr = work
+        cells_s = r["mlups"] * 1e6
+        r["fp64_alu"] = {"bound": "alu", "flops_per_cell": flops, "achieved_tflops": flops * cells_s / 1e12,
+                         "peak_tflops": fp64_peak, "frac_flops": flops * cells_s / 1e12 / fp64_peak,
+                         "fp64_instr_per_cell": instr, "achieved_ginstr_s": instr * cells_s / 1e9,
+                         "peak_ginstr_s": fp64_peak / 2 * 1e3, "frac_pipe": instr * cells_s / 1e9 / (fp64_peak / 2 * 1e3),
+                         "peak_source": "lbm_fp64_peak probe, same run"}
 
 
 def _fp64_flops_per_cell(workload: str):
-    """float64 FLOP per cell update of a workload's step (ncu op counts, profiles/fp64_flops.txt)."""
+    """(float64 FLOP, float64 instructions) per cell update of a workload's step
+    (ncu op counts, profiles/fp64_flops.txt)."""
     path = os.path.join(ROOT, "profiles", "fp64_flops.txt")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         for line in fh:
             parts = line.split()
-            if len(parts) >= 2 and not line.startswith("#") and parts[0] == workload:
-                return float(parts[1])
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == workload:
+                return float(parts[1]), float(parts[2])
     return None
 
 
@@ -576,7 +583,7 @@ def run_ours(args):
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cb_case = wl.pr_droplet(384, storage="f64")
-            cv, n, dt, cores, what = _oracle_mlups(cb_case, 15.0)
+            cv, n, dt, cores, what = _oracle_mlups(cb_case, 20.0)
             cv1, n1, dt1, _, _ = _oracle_mlups(cb_case, 8.0, threads=1, half=24)
             _oracle_threads(cores)
             cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle",
