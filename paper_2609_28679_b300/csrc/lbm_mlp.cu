@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32)
         if (valid_me)
             si = n < 0 ? (long long)k  // samples in order
                        : (long long)(splitmix64(seed ^ (unsigned long long)(step * (long long)B + k)) % (unsigned long long)n);
-        const float x0 = valid_me ? (__logf((float)rho[si]) - m.norm[0]) / m.norm[1] : 0.f;
+        const float x0 = valid_me ? (logf((float)rho[si]) - m.norm[0]) / m.norm[1] : 0.f;
         const float x1 = valid_me ? ((float)e[si] - m.norm[2]) / m.norm[3] : 0.f;
         const float tt = valid_me ? ((float)T[si] - m.norm[4]) / m.norm[5] : 0.f;
         const float xa0 = __shfl_sync(0xffffffffu, x0, g8), xa1 = __shfl_sync(0xffffffffu, x1, g8);
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32)
 
         // forward; keep h1^T for the weight gradient of the second layer
         float acc[8][4];
-        mlp_layer2(m, xa0, xa1, xb0, xb1, acc);
+        mlp_layer2<true>(m, xa0, xa1, xb0, xb1, acc);
         __nv_bfloat16* H1 = h1t[warp];
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
@@ -141,8 +141,8 @@ __global__ void __launch_bounds__(kTrainWarps * 32)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int kk = k0 + (q & 1) + (q >> 1) * 8;
-                H1[kk * kStageLd + g8] = __float2bfloat16_rn(mlp_h1(m, xa0, xa1, kk));
-                H1[kk * kStageLd + g8 + 8] = __float2bfloat16_rn(mlp_h1(m, xb0, xb1, kk));
+                H1[kk * kStageLd + g8] = __float2bfloat16_rn(mlp_h1<true>(m, xa0, xa1, kk));
+                H1[kk * kStageLd + g8 + 8] = __float2bfloat16_rn(mlp_h1<true>(m, xb0, xb1, kk));
             }
         }
         float h2[8][4];
@@ -150,10 +150,10 @@ __global__ void __launch_bounds__(kTrainWarps * 32)
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
             const int n0 = 8 * nt + 2 * c;
-            h2[nt][0] = tanh_fast(acc[nt][0] + m.b2[n0]);
-            h2[nt][1] = tanh_fast(acc[nt][1] + m.b2[n0 + 1]);
-            h2[nt][2] = tanh_fast(acc[nt][2] + m.b2[n0]);
-            h2[nt][3] = tanh_fast(acc[nt][3] + m.b2[n0 + 1]);
+            h2[nt][0] = mlp_tanh<true>(acc[nt][0] + m.b2[n0]);
+            h2[nt][1] = mlp_tanh<true>(acc[nt][1] + m.b2[n0 + 1]);
+            h2[nt][2] = mlp_tanh<true>(acc[nt][2] + m.b2[n0]);
+            h2[nt][3] = mlp_tanh<true>(acc[nt][3] + m.b2[n0 + 1]);
             ya = fmaf(m.w3[n0], h2[nt][0], fmaf(m.w3[n0 + 1], h2[nt][1], ya));
             yb = fmaf(m.w3[n0], h2[nt][2], fmaf(m.w3[n0 + 1], h2[nt][3], yb));
         }
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32)
             const int n0 = 8 * nt + 2 * c;
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                const float ha = mlp_h1(m, xa0, xa1, n0 + q), hb = mlp_h1(m, xb0, xb1, n0 + q);
+                const float ha = mlp_h1<true>(m, xa0, xa1, n0 + q), hb = mlp_h1<true>(m, xb0, xb1, n0 + q);
                 const float d1a = a1[nt][q] * (1.f - ha * ha), d1b = a1[nt][2 + q] * (1.f - hb * hb);
                 gb1[2 * nt + q] = d1a + d1b;
                 gw1[2 * nt + q][0] = d1a * xa0 + d1b * xb0;

@@ -62,15 +62,26 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// tanh for the network: the one-instruction approximation (in-step
+// inference) or the correctly rounded-to-a-few-ulp library tanhf (training,
+// whose gradients are checked against a float64 reference).
+template <bool EXACT> __device__ __forceinline__ float mlp_tanh(float x)
+{
+    if constexpr (EXACT) return tanhf(x);
+    else return tanh_fast(x);
+}
+
 // First layer at (row, k): tanh(W1[k] . x_row + b1[k])
+template <bool EXACT = false>
 __device__ __forceinline__ float mlp_h1(const MlpSmem& m, float x0, float x1, int k)
 {
-    return tanh_fast(fmaf(m.w1[2 * k], x0, fmaf(m.w1[2 * k + 1], x1, m.b1[k])));
+    return mlp_tanh<EXACT>(fmaf(m.w1[2 * k], x0, fmaf(m.w1[2 * k + 1], x1, m.b1[k])));
 }
 
 // Second layer for one 16-row tile whose rows g and g+8 (g = lane/4) have
 // inputs (xa0, xa1), (xb0, xb1): acc[nt][0..1] -> row g, cols 8nt + 2c + {0,1};
 // acc[nt][2..3] -> row g + 8 (pre-activation, before b2).
+template <bool EXACT = false>
 __device__ __forceinline__ void mlp_layer2(const MlpSmem& m, float xa0, float xa1, float xb0, float xb1,
                                            float acc[8][4])
 {
@@ -81,10 +92,10 @@ __device__ __forceinline__ void mlp_layer2(const MlpSmem& m, float xa0, float xa
     for (int ks = 0; ks < 4; ++ks) {
         const int k0 = 16 * ks + 2 * c;
         uint32_t a[4];
-        a[0] = pack_bf16(mlp_h1(m, xa0, xa1, k0), mlp_h1(m, xa0, xa1, k0 + 1));
-        a[1] = pack_bf16(mlp_h1(m, xb0, xb1, k0), mlp_h1(m, xb0, xb1, k0 + 1));
-        a[2] = pack_bf16(mlp_h1(m, xa0, xa1, k0 + 8), mlp_h1(m, xa0, xa1, k0 + 9));
-        a[3] = pack_bf16(mlp_h1(m, xb0, xb1, k0 + 8), mlp_h1(m, xb0, xb1, k0 + 9));
+        a[0] = pack_bf16(mlp_h1<EXACT>(m, xa0, xa1, k0), mlp_h1<EXACT>(m, xa0, xa1, k0 + 1));
+        a[1] = pack_bf16(mlp_h1<EXACT>(m, xb0, xb1, k0), mlp_h1<EXACT>(m, xb0, xb1, k0 + 1));
+        a[2] = pack_bf16(mlp_h1<EXACT>(m, xa0, xa1, k0 + 8), mlp_h1<EXACT>(m, xa0, xa1, k0 + 9));
+        a[3] = pack_bf16(mlp_h1<EXACT>(m, xb0, xb1, k0 + 8), mlp_h1<EXACT>(m, xb0, xb1, k0 + 9));
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
             const uint32_t* w = reinterpret_cast<const uint32_t*>(m.w2 + (8 * nt + g) * kW2Ld + k0);

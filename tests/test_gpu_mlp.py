@@ -1,11 +1,15 @@
 """Learned temperature inversion: the tensor-core training kernel's
 gradients and the in-step inference routine against the FP64 oracle of the
-same network, and GPU training of the Peng-Robinson inversion.
+same network, GPU training of the Peng-Robinson inversion, and what the
+trained network gains over the method's own Newton starts.
 
-Tolerances: bfloat16 operands (8-bit mantissa, relative rounding 2^-9) in
-the 64-wide layer with float32 accumulation; gradients are compared per
-parameter block in the 2-norm relative to the oracle's, at 2e-2; the
-network output y (unit scale) to 2e-2 absolute."""
+Gradients (training kernel: accurate tanh, bfloat16 operands in the three
+products through W2, float32 accumulation) are compared per parameter block
+in the 2-norm against the oracle evaluated at the same precision points
+(mlp.loss_and_grad with bf16_products): 1e-3 relative.  In-step inference
+(one-instruction tanh) is compared per sample against a bound propagated
+from that instruction's relative error through the bfloat16 rounding of h1
+and the two layers."""
 import numpy as np
 import pytest
 
@@ -42,22 +46,56 @@ def test_gradients_match_oracle():
     rho, e, T, c = _samples(200, 11)
     p32 = _params(e, c.Tc, 3)
     loss_g, g = lbm.lbm_mlp_grad(p32, rho, e, T)
-    loss_r, gr = mlp.loss_and_grad(p32.astype(np.float64), rho, e, T)
-    assert loss_g == pytest.approx(loss_r, rel=2e-2)
+    loss_r, gr = mlp.loss_and_grad(p32.astype(np.float64), rho, e, T, bf16_products=True)
+    assert loss_g == pytest.approx(loss_r, rel=1e-3)
     d = mlp.unpack(gr)
     dg = mlp.unpack(g.astype(np.float64))
     for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
         err = np.linalg.norm(dg[name] - d[name]) / np.linalg.norm(d[name])
-        assert err <= 2e-2, (name, err)
+        assert err <= 1e-3, (name, err)
+
+
+# tanh.approx.f32: documented maximum relative error about 2^-11; taken as 2^-10
+EPS_TANH = 2.0 ** -10
+EPS32 = 2.0 ** -24
+
+
+def _inference_bound(p, rho, e):
+    """Per-sample bound on |T_hat(GPU) - T_hat(oracle, bfloat16 products)|:
+    the approximate tanh's error and float32 rounding carried through the
+    bfloat16 rounding of h1 (monotone: the rounded GPU value lies between the
+    roundings of the interval's ends), the 64 x 64 product, the second tanh
+    and the output layer."""
+    d = mlp.unpack(p)
+    x = mlp.features(p, rho, e)
+    z1 = x @ d["W1"].T + d["b1"]
+    h1 = np.tanh(z1)
+    dz1 = 8 * EPS32 * (np.abs(x) @ np.abs(d["W1"]).T + np.abs(d["b1"])) + 2.0 ** -19 * np.abs(d["W1"][:, 0])
+    dh1 = EPS_TANH * np.abs(h1) * 1.01 + dz1
+    hb = mlp.bf16(h1)
+    dhb = np.maximum(np.abs(mlp.bf16(h1 + dh1) - hb), np.abs(mlp.bf16(h1 - dh1) - hb))
+    W2b = mlp.bf16(d["W2"])
+    z2 = hb @ W2b.T + d["b2"]
+    dz2 = dhb @ np.abs(W2b).T + 64 * EPS32 * (np.abs(hb) @ np.abs(W2b).T + np.abs(d["b2"]))
+    h2 = np.tanh(z2)
+    dh2 = EPS_TANH * (np.abs(h2) + dz2) + dz2
+    dy = dh2 @ np.abs(d["W3"]) + 64 * EPS32 * (np.abs(h2) @ np.abs(d["W3"]) + abs(d["b3"][0]))
+    Tr = d["norm"][4] + d["norm"][5] * (h2 @ d["W3"] + d["b3"][0])
+    return Tr, abs(d["norm"][5]) * dy + 4 * EPS32 * np.abs(Tr)
 
 
 def test_inference_matches_oracle_forward():
     rho, e, T, c = _samples(1000, 12)
     p32 = _params(e, c.Tc, 5)
     Tg = lbm.lbm_mlp_predict(p32, rho, e)
-    Tr, _ = mlp.forward(p32.astype(np.float64), rho, e)
+    Tr, bound = _inference_bound(p32.astype(np.float64), rho, e)
     s_T = float(p32[5])
-    assert np.max(np.abs(Tg - Tr)) / s_T <= 2e-2
+    err = np.abs(Tg - Tr)
+    assert np.all(err <= bound), (float(np.max(err / bound)), float(np.max(err)) / s_T)
+    # The bound (a few % of s_T: it admits a flip of every h1 entry whose bfloat16
+    # rounding the tanh error can reach) stays well below what a dropped bias or a
+    # misplaced fragment of the product does to T_hat (~0.1 s_T for these weights).
+    assert np.median(bound) / s_T < 5e-2, float(np.median(bound) / s_T)
 
 
 def test_training_learns_the_inversion():
@@ -126,13 +164,31 @@ def test_learned_start_f32_matches_newton_run(variant):
     assert 0 <= d[3] <= 10 * c.ncell
 
 
-def test_learned_start_saves_newton_iterations_over_a_cold_start():
-    # What the trained network gains: float64 Newton iterations (oracle solver) to
-    # converge from T_hat versus from Tc, the start without a previous T.
+def test_learned_start_against_the_warm_start_on_a_running_droplet():
+    # What the trained network gains, measured on the states a time step meets:
+    # float64 Newton iterations (the oracle's solver, 1e-14) to T(rho, e) of
+    # step n+1 from the method's own start (T of step n), from the network's
+    # T_hat, and from Tc (the start with no carried temperature: the first
+    # step after initialisation).  Measured here: the carried T needs fewer
+    # iterations than T_hat (the network is accurate to ~1e-3, the step
+    # changes T by far less), T_hat fewer than Tc.  The network pays only
+    # where no temperature is carried.
     c, eos = _pr()
-    rho, e, T, _ = _samples(400, 21)
-    That = lbm.lbm_mlp_predict(_trained_params(), rho, e)
-    it_cold = np.array([eos.T(r, ee, 0.0)[1] for r, ee in zip(rho, e)])
-    it_mlp = np.array([eos.T(r, ee, t0)[1] for r, ee, t0 in zip(rho, e, That)])
-    assert np.mean(it_mlp) < np.mean(it_cold)
-    assert np.max(it_mlp) <= np.max(it_cold)
+    case = wl.pr_droplet(n=24, radius=6.0, storage="f64")
+    sim = lbm.Simulation(case)
+    sim.init()
+    sim.step(20)
+    _, _, T0 = sim.moments()
+    sim.step(1)
+    rho, u, T1 = sim.moments()
+    sim.close()
+    u = u.reshape(3, -1)
+    sel = np.arange(0, rho.size, 7)  # a sample of the cells: liquid, interface, vapour
+    e1 = np.array([eos.e(r, t) for r, t in zip(rho[sel], T1[sel])])
+    That = lbm.lbm_mlp_predict(_trained_params(), rho[sel], e1)
+    it_warm = np.array([eos.T(r, ee, t0)[1] for r, ee, t0 in zip(rho[sel], e1, T0[sel])])
+    it_mlp = np.array([eos.T(r, ee, t)[1] for r, ee, t in zip(rho[sel], e1, That)])
+    it_cold = np.array([eos.T(r, ee, 0.0)[1] for r, ee in zip(rho[sel], e1)])
+    msg = f"mean Newton iterations: warm {it_warm.mean():.2f}, learned {it_mlp.mean():.2f}, cold {it_cold.mean():.2f}"
+    assert it_warm.mean() < it_mlp.mean() < it_cold.mean(), msg
+    assert np.max(it_mlp) <= np.max(it_cold), msg

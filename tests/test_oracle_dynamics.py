@@ -12,7 +12,7 @@ from scipy import optimize
 
 from oracle import oracle as orc
 from paper_2609_28679_b300 import workloads as wl
-from tests.util import oracle_params, run_oracle
+from tests.util import oracle_params, run_oracle, maxwell
 
 
 def _uniform_case(eos="ideal", dim=2, n=4, **kw):
@@ -310,16 +310,7 @@ def test_isothermal_sound_speed():
 
 
 def _maxwell(eos, T):
-    # equal-area construction on the oracle's own pressure: P(rv) = P(rl) = Ps, int_{vl}^{vv} P dv = Ps (vv - vl)
-    from scipy import integrate
-
-    def resid(x):
-        rv, rl = x
-        Ps = eos.P(rl, T)
-        area = integrate.quad(lambda r: eos.P(r, T) / (r * r), rv, rl, epsabs=1e-13)[0]
-        return [eos.P(rv, T) - Ps, area - Ps * (1 / rv - 1 / rl)]
-
-    return optimize.fsolve(resid, [1.5, 5.8], xtol=1e-12)
+    return maxwell(eos, T)
 
 
 def test_maxwell_construction_reproduces_textbook_vdw():

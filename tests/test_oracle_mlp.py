@@ -52,3 +52,42 @@ def test_adam_fit_learns_the_inversion():
     That, _ = mlp.forward(p, rho, e)
     assert l1 < 0.02 * l0
     assert np.max(np.abs(That - T)) / Tc < 0.05
+
+
+def test_bf16_rounding_is_nearest_ties_to_even():
+    # 7 fraction bits: the spacing at 1 is 2^-7; halfway cases go to the even neighbour
+    cases = [(1.0, 1.0), (1 + 2 ** -9, 1.0), (1 + 2 ** -8, 1.0), (1 + 3 * 2 ** -9, 1 + 2 ** -7),
+             (1 + 2 ** -7 + 2 ** -8, 1 + 2 ** -6), (-2.5, -2.5), (3 + 2 ** -7, 3.0), (65280.0, 65280.0),
+             (-(1 + 3 * 2 ** -9), -(1 + 2 ** -7))]
+    for x, r in cases:
+        assert mlp.bf16(x) == r, (x, mlp.bf16(x), r)
+    # every rounded value is a float32 whose lower 16 bits are zero, within half a spacing of the input
+    x = np.random.default_rng(6).normal(0, 3, 1000)
+    r = mlp.bf16(x)
+    assert np.all((r.astype(np.float32).view(np.uint32) & 0xFFFF) == 0)
+    assert np.all(np.abs(r - x.astype(np.float32)) <= 2.0 ** -8 * np.abs(x) * (1 + 1e-6))
+
+
+def test_bf16_product_gradient():
+    # The rounded computation is smooth in b2, W3 and b3 (they act after the
+    # rounded product): its gradient there must match central differences of
+    # its own loss.  Through the rounded operands it stays within the rounding
+    # (a few 2^-9 relative) of the exact gradient.
+    rho, e, T, Tc = _samples(40, 7)
+    p = mlp.init_params((0.1, 2.6), (e.min(), e.max()), (0.85 * Tc, 1.05 * Tc), seed=8)
+    p[mlp.N_NORM:] += np.random.default_rng(9).normal(0, 0.1, mlp.N_PARAMS - mlp.N_NORM)
+    _, gb = mlp.loss_and_grad(p, rho, e, T, bf16_products=True)
+    _, gx = mlp.loss_and_grad(p, rho, e, T)
+    o = mlp.N_NORM + 2 * mlp.H + mlp.H + mlp.H * mlp.H  # first b2 entry
+    h = 1e-5
+    for k in list(range(o, o + 2 * mlp.H + 1, 7)) + [mlp.N_PARAMS - 1]:
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (mlp.loss_and_grad(pp, rho, e, T, bf16_products=True)[0] -
+              mlp.loss_and_grad(pm, rho, e, T, bf16_products=True)[0]) / (2 * h)
+        assert gb[k] == pytest.approx(fd, rel=1e-6, abs=1e-12)
+    db, dx = mlp.unpack(gb), mlp.unpack(gx)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        err = np.linalg.norm(db[name] - dx[name]) / np.linalg.norm(dx[name])
+        assert 0 < err <= 2e-2, (name, err)
