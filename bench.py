@@ -349,6 +349,22 @@ def _fp64_flops_per_cell(workload: str):
     return None
 
 
+def _first_step(lbm, newton_case, mlp_case, params):
+    """Pass times of the first step after lbm_init, whose Newton guess is the
+    initial temperature field, against the learned start (same kernel: the
+    autotuned one)."""
+    out = {}
+    for name, case, p in (("newton_from_initial_T", newton_case, None), ("learned_start", mlp_case, params)):
+        sim = lbm.Simulation(case)
+        if p is not None:
+            lbm.lbm_mlp_load(sim.h, p)
+        sim.init()
+        sim.autotune(2)  # restores the initial state
+        out[name] = _pass_times(lbm, sim, 1)
+        sim.close()
+    return out
+
+
 def _measure_forms(lbm, wl, torch, steps, headline=None):
     """Every form on its full-size workload (few steps each), next to the
     plain float64 GPU path of the same workload: MLUPS, HBM fraction, speed-up
@@ -385,6 +401,11 @@ def _measure_forms(lbm, wl, torch, steps, headline=None):
         r["rel_dev_vs_f32_newton"] = {"rho": _rel_dev(fr[0], fdn[0]), "T": _rel_dev(fr[1], fdn[1])}
         # cells whose learned temperature met the Newton tolerance in its first correction
         r["learned_start_accept_frac"] = 1.0 - r["diagnostics"][3] / float(r["cells"] * r["steps_since_init"])
+        # the first step after lbm_init: Newton from the initial temperature field against T_hat
+        r["first_step_after_init"] = _first_step(lbm, drop, drop_m, params)
+        r["first_step_after_init"]["speedup_of_macroscopic_pass"] = (
+            r["first_step_after_init"]["newton_from_initial_T"]["pass1_ms"] /
+            r["first_step_after_init"]["learned_start"]["pass1_ms"])
         res["f32_pr_droplet_384_mlp"] = r
         del fd64
         torch.cuda.empty_cache()

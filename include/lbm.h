@@ -278,8 +278,8 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz);
  *                     extrapolated faces), collide-stream pass;
  *   fused:            0, 0, the one-pass step;
  *   split:            moments, macroscopic pass (and boundary cells), collide-stream.
- * A step that prepares the carried moments first (after lbm_init or a
- * kernel change) runs before the recorded ones.  Errors as lbm_step. */
+ * The carried moments (after lbm_init or a kernel change) are prepared
+ * before the first recorded step, outside its passes.  Errors as lbm_step. */
 int lbm_step_timed(lbm_handle h, int n, double ms_per_pass[4]);
 
 /* The float64 fused multiply-add rate of the current device (TFLOP/s, 2

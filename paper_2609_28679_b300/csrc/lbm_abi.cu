@@ -32,6 +32,7 @@ struct Ops {
     int (*export_pops)(lbm_ctx*, double*, double*);
     int (*invariants)(lbm_ctx*, double*);
     int (*fused_ok)(lbm_ctx*, int, int, int);
+    int (*prepare)(lbm_ctx*);  // carried moments of the current state (fused and z-march variants)
 };
 
 }  // namespace
@@ -377,7 +378,7 @@ template <int D, typename R, typename S> struct Impl {
         return fused_shape(h->storage, D, tx, ty, tz) ? 1 : 0;
     }
 
-    static Ops ops() { return Ops{init, step, macro, export_moments, export_pops, invariants, fused_ok}; }
+    static Ops ops() { return Ops{init, step, macro, export_moments, export_pops, invariants, fused_ok, fused_prepare}; }
 };
 
 cudaError_t fused_dispatch(int storage, int dim, int eos, int mlp, int pc, int tx, int ty, int tz, const SimDev* sims,
@@ -992,10 +993,10 @@ int lbm_step_timed(lbm_handle h, int n, double ms_per_pass[4])
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
     if (n < 1 || !ms_per_pass) return fail(h, LBM_E_INVALID, "n must be >= 1 and ms_per_pass non-NULL");
     if (!h->initialized) return fail(h, LBM_E_STATE, "lbm_init has not been called");
-    // the first step prepares the carried moments outside the recorded passes
+    // the carried moments are prepared outside the recorded passes
     if ((h->variant == LBM_KERNEL_FUSED || h->variant == LBM_KERNEL_ZMARCH || h->variant == LBM_KERNEL_ZGATHER) &&
         !h->moments_valid) {
-        int rc = h->ops.step(h, 1);
+        int rc = h->ops.prepare(h);
         if (rc) return rc;
     }
     const size_t need = 4 * (size_t)n;
