@@ -70,7 +70,7 @@ extern "C" {
 #define LBM_T_MLP 1    /* learned T(rho, e) (lbm_mlp_load) with Newton fallback      */
 
 /* derivative in the Galilean correction Phi (Eq. correction) */
-#define LBM_PHI_UPWIND 0  /* 2nd-order one-sided, chosen by the sign of u_alpha */
+#define LBM_PHI_UPWIND 0  /* 3rd-order upwind-biased: (2 X+1 + 3 X0 - 6 X-1 + X-2)/6 for u >= 0, mirrored */
 #define LBM_PHI_CENTRAL 1 /* 2-point central                                     */
 
 /* kernel variants (lbm_set_kernel) */

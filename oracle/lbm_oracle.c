@@ -37,13 +37,17 @@
  *  - alpha*theta is evaluated as ((D+2)/D - eta/mu) theta - c_s^2, which equals
  *    alpha*theta of Eq. corr_bulk with theta = P/rho but has no removable
  *    singularity where P = 0 (spinodal region of van der Waals / Peng-Robinson).
- *  - The upwind-biased first derivative in Eq. correction is the second-order
- *    one-sided difference chosen by the sign of the local u_alpha (u >= 0:
- *    backward).  With phi_central = 1 the 2-point central difference is used
- *    instead: the one-sided switch injects grid-scale noise where u changes
- *    sign, which makes fluids with theta < 1/3 near rest (the liquid-vapour
- *    cases) diverge.  Laplacian and gradients are the standard (2D+1)-point
- *    and 2-point central differences (Sec. II.E).
+ *  - The upwind-biased first derivative in Eq. correction (Sec. II.E, chosen
+ *    there to make higher Mach numbers stable) is the third-order
+ *    upwind-biased difference, two points on the side the local u_alpha comes
+ *    from and one on the other: (2 X_{+1} + 3 X_0 - 6 X_{-1} + X_{-2}) / 6 for
+ *    u >= 0, mirrored for u < 0.  The linear stability of uniform flow under
+ *    this step (oracle/stability.py) singles it out: it keeps uniform flow
+ *    stable to Ma 1.2 at theta = 0.1 where the central difference fails above
+ *    Ma 0.9, while the fully one-sided second-order difference is unstable at
+ *    every Mach number.  With phi_central = 1 the 2-point central difference
+ *    is used (the liquid-vapour cases).  Laplacian and gradients are the
+ *    standard (2D+1)-point and 2-point central differences (Sec. II.E).
  *  - Half-way bounce-back walls at the z faces (Sec. III.A, Poiseuille) act on
  *    both f and g.  For the macroscopic stencils, cells beyond a wall mirror
  *    the interior: scalars (rho, lap rho, T, h) even, velocity odd, so X_z is
@@ -142,7 +146,8 @@ typedef struct {
     double accel[3];    /* body acceleration: F_B = rho * accel */
     double q;           /* volumetric heat source Q */
     int zlo, zhi;       /* Q acts where zlo <= z < zhi; zhi <= 0 means everywhere */
-    int phi_central;    /* 0: upwind-biased derivative in Phi; 1: central difference */
+    int phi_central;    /* 0: upwind-biased derivative in Phi; 1: central difference;
+                           2-5: other stencils, for the stability analysis only */
     double mu;          /* > 0: the paper's tau = mu / P per cell (Sec. II.C), one tau for f and g;
                            0: constant tau_f, tau_g */
     int isothermal;     /* 1: the g equation is not solved (Sec. III.A, isothermal tests); every cell
@@ -847,17 +852,25 @@ static void one_step(orc_state *s)
                     gT[a] = 0.5 * (nb_scalar(s, s->T, x, y, z, e[0], e[1], e[2]) -
                                    nb_scalar(s, s->T, x, y, z, -e[0], -e[1], -e[2]));
                     double X0 = s->X[(long)a * N + k], dX;
-                    if (p->phi_central) {
+                    if (p->phi_central == 1) {
                         dX = 0.5 * (nb_vector(s, s->X, a, x, y, z, e[0], e[1], e[2]) -
                                     nb_vector(s, s->X, a, x, y, z, -e[0], -e[1], -e[2]));
-                    } else if (uu[a] >= 0.0) {
-                        double Xm1 = nb_vector(s, s->X, a, x, y, z, -e[0], -e[1], -e[2]);
-                        double Xm2 = nb_vector(s, s->X, a, x, y, z, -2 * e[0], -2 * e[1], -2 * e[2]);
-                        dX = 0.5 * (3.0 * X0 - 4.0 * Xm1 + Xm2);
                     } else {
-                        double Xp1 = nb_vector(s, s->X, a, x, y, z, e[0], e[1], e[2]);
-                        double Xp2 = nb_vector(s, s->X, a, x, y, z, 2 * e[0], 2 * e[1], 2 * e[2]);
-                        dX = -0.5 * (3.0 * X0 - 4.0 * Xp1 + Xp2);
+                        /* Upwind-biased (phi_central = 0): the third-order stencil with two
+                         * points on the side the local u_alpha comes from and one on the other,
+                         * (2 X_{+1} + 3 X_0 - 6 X_{-1} + X_{-2}) / 6 for u_alpha >= 0 and its mirror
+                         * image otherwise.  Other values are stencils kept for the stability
+                         * analysis only: 2 second-order one-sided, 3 the same reversed, 4 the
+                         * third-order stencil reversed, 5 first-order upwind. */
+                        const int sch = p->phi_central;
+                        const int up = (uu[a] >= 0.0) != (sch == 3 || sch == 4);
+                        const int sg = up ? 1 : -1;  /* +1: the upwind side is the backward one */
+                        double Xb1 = nb_vector(s, s->X, a, x, y, z, -sg * e[0], -sg * e[1], -sg * e[2]);
+                        double Xb2 = nb_vector(s, s->X, a, x, y, z, -2 * sg * e[0], -2 * sg * e[1], -2 * sg * e[2]);
+                        double Xf1 = nb_vector(s, s->X, a, x, y, z, sg * e[0], sg * e[1], sg * e[2]);
+                        if (sch == 5) dX = sg * (X0 - Xb1);
+                        else if (sch == 2 || sch == 3) dX = sg * 0.5 * (3.0 * X0 - 4.0 * Xb1 + Xb2);
+                        else dX = sg * (2.0 * Xf1 + 3.0 * X0 - 6.0 * Xb1 + Xb2) / 6.0;
                     }
                     Phi[a] = -dX / r; /* Eq. correction */
                 }

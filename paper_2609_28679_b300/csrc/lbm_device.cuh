@@ -355,6 +355,17 @@ template <typename R> __device__ __forceinline__ R xflux(R rho, R u, R th)
     return rho * u * (u * u + R(3) * th - R(1));
 }
 
+// The upwind-biased first derivative of X in Eq. correction (Sec. II.E): the
+// third-order difference with two points on the side u comes from and one on
+// the other, (2 X_{+1} + 3 X_0 - 6 X_{-1} + X_{-2}) / 6 for u >= 0 and its
+// mirror image for u < 0.
+template <typename R> __host__ __device__ __forceinline__ R upwind_biased(R u, R x2, R xm1, R x0, R xp1)
+{
+    // x2: X_{-2} when u >= 0, X_{+2} otherwise
+    return u >= R(0) ? (R(2) * xp1 + R(3) * x0 - R(6) * xm1 + x2) * R(1.0 / 6.0)
+                     : -(R(2) * xm1 + R(3) * x0 - R(6) * xp1 + x2) * R(1.0 / 6.0);
+}
+
 // beta of a cell (Eq. beta, dt = 1) under the paper's tau = mu / P (Sec. II.C)
 template <typename R, typename C> __device__ __forceinline__ R relax_beta(const C& s, R P)
 {

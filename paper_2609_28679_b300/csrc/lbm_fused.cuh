@@ -433,10 +433,9 @@ __global__ void __launch_bounds__((fused_threads<D, TX, TY, TZ>()), (fused_min_b
                 R dX;
                 if (PC || s.phi_central) {
                     dX = R(0.5) * (Xa[c3 + sa] - Xa[c3 - sa]);
-                } else if (m.u[a] >= R(0)) {
-                    dX = R(0.5) * (R(3) * Xa[c3] - R(4) * Xa[c3 - sa] + Xa[c3 - 2 * sa]);
                 } else {
-                    dX = -R(0.5) * (R(3) * Xa[c3] - R(4) * Xa[c3 + sa] + Xa[c3 + 2 * sa]);
+                    dX = upwind_biased<R>(m.u[a], Xa[c3 + (m.u[a] >= R(0) ? -2 : 2) * sa], Xa[c3 - sa], Xa[c3],
+                                          Xa[c3 + sa]);
                 }
                 Phi[a] = -dX * m.ir;
             }

@@ -434,13 +434,10 @@ __device__ __forceinline__ void stencils(const SimDev& s, const R* __restrict__ 
         if (s.phi_central) {
             dX = R(0.5) * (wget(s, X, x + e0, y + e1, z + e2, true) - wget(s, X, x - e0, y - e1, z - e2, true));
         } else {
-            R X0 = wget(s, X, x, y, z, true);
-            if (u[a] >= R(0))
-                dX = R(0.5) * (R(3) * X0 - R(4) * wget(s, X, x - e0, y - e1, z - e2, true) +
-                               wget(s, X, x - 2 * e0, y - 2 * e1, z - 2 * e2, true));
-            else
-                dX = -R(0.5) * (R(3) * X0 - R(4) * wget(s, X, x + e0, y + e1, z + e2, true) +
-                                wget(s, X, x + 2 * e0, y + 2 * e1, z + 2 * e2, true));
+            const R X0 = wget(s, X, x, y, z, true);
+            const R Xm1 = wget(s, X, x - e0, y - e1, z - e2, true), Xp1 = wget(s, X, x + e0, y + e1, z + e2, true);
+            const int sg = u[a] >= R(0) ? -2 : 2;  // the second neighbour on the upwind side
+            dX = upwind_biased<R>(u[a], wget(s, X, x + sg * e0, y + sg * e1, z + sg * e2, true), Xm1, X0, Xp1);
         }
         Phi[a] = -dX / rho;
     }

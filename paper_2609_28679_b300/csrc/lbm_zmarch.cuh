@@ -167,22 +167,13 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
                             dX[2] = R(0.5) * (Wz(W_X + 2, 1) - Wz(W_X + 2, -1));
                         } else {
                             const R X0x = Wf(W_X, gk), X0y = Wf(W_X + 1, gk), X0z = Wf(W_X + 2, gk);
-                            if (m.u[0] >= R(0))
-                                dX[0] = R(0.5) * (R(3) * X0x - R(4) * Wf(W_X, cxm) +
-                                                  Wf(W_X, cell(wrapc(x - 2, nx), y, z)));
-                            else
-                                dX[0] = -R(0.5) * (R(3) * X0x - R(4) * Wf(W_X, cxp) +
-                                                   Wf(W_X, cell(wrapc(x + 2, nx), y, z)));
-                            if (m.u[1] >= R(0))
-                                dX[1] = R(0.5) * (R(3) * X0y - R(4) * Wf(W_X + 1, cym) +
-                                                  Wf(W_X + 1, cell(x, wrapc(y - 2, ny), z)));
-                            else
-                                dX[1] = -R(0.5) * (R(3) * X0y - R(4) * Wf(W_X + 1, cyp) +
-                                                   Wf(W_X + 1, cell(x, wrapc(y + 2, ny), z)));
-                            if (m.u[2] >= R(0))
-                                dX[2] = R(0.5) * (R(3) * X0z - R(4) * Wz(W_X + 2, -1) + Wz(W_X + 2, -2));
-                            else
-                                dX[2] = -R(0.5) * (R(3) * X0z - R(4) * Wz(W_X + 2, 1) + Wz(W_X + 2, 2));
+                            const bool px = m.u[0] >= R(0), py = m.u[1] >= R(0), pz = m.u[2] >= R(0);
+                            dX[0] = upwind_biased<R>(m.u[0], Wf(W_X, cell(wrapc(x + (px ? -2 : 2), nx), y, z)),
+                                                     Wf(W_X, cxm), X0x, Wf(W_X, cxp));
+                            dX[1] = upwind_biased<R>(m.u[1], Wf(W_X + 1, cell(x, wrapc(y + (py ? -2 : 2), ny), z)),
+                                                     Wf(W_X + 1, cym), X0y, Wf(W_X + 1, cyp));
+                            dX[2] = upwind_biased<R>(m.u[2], Wz(W_X + 2, pz ? -2 : 2), Wz(W_X + 2, -1), X0z,
+                                                     Wz(W_X + 2, 1));
                         }
 #pragma unroll
                         for (int a = 0; a < 3; ++a) Phi[a] = -dX[a] * m.ir;
@@ -205,29 +196,17 @@ __global__ void __launch_bounds__(kZThreads, sizeof(R) == 4 ? 2 : 1)
                             dX[1] = R(0.5) * (Wf(W_X + 1, cyp) - Wf(W_X + 1, cym));
                             dX[2] = R(0.5) * (szp * Wf(W_X + 2, czp) - szm * Wf(W_X + 2, czm));
                         } else {
-                            // second-order one-sided by the sign of u_alpha (u >= 0: backward)
+                            // upwind-biased by the sign of u_alpha (X_z odd beyond a wall)
                             const R X0x = Wf(W_X, gk), X0y = Wf(W_X + 1, gk), X0z = Wf(W_X + 2, gk);
-                            if (m.u[0] >= R(0))
-                                dX[0] = R(0.5) * (R(3) * X0x - R(4) * Wf(W_X, cxm) +
-                                                  Wf(W_X, cell(wrapc(x - 2, nx), y, z)));
-                            else
-                                dX[0] = -R(0.5) * (R(3) * X0x - R(4) * Wf(W_X, cxp) +
-                                                   Wf(W_X, cell(wrapc(x + 2, nx), y, z)));
-                            if (m.u[1] >= R(0))
-                                dX[1] = R(0.5) * (R(3) * X0y - R(4) * Wf(W_X + 1, cym) +
-                                                  Wf(W_X + 1, cell(x, wrapc(y - 2, ny), z)));
-                            else
-                                dX[1] = -R(0.5) * (R(3) * X0y - R(4) * Wf(W_X + 1, cyp) +
-                                                   Wf(W_X + 1, cell(x, wrapc(y + 2, ny), z)));
-                            if (m.u[2] >= R(0)) {
-                                const R s2 = zf[0] ? R(-1) : R(1);
-                                dX[2] = R(0.5) * (R(3) * X0z - R(4) * szm * Wf(W_X + 2, czm) +
-                                                  s2 * Wf(W_X + 2, cell(x, y, zn[0])));
-                            } else {
-                                const R s2 = zf[4] ? R(-1) : R(1);
-                                dX[2] = -R(0.5) * (R(3) * X0z - R(4) * szp * Wf(W_X + 2, czp) +
-                                                   s2 * Wf(W_X + 2, cell(x, y, zn[4])));
-                            }
+                            const bool px = m.u[0] >= R(0), py = m.u[1] >= R(0), pz = m.u[2] >= R(0);
+                            dX[0] = upwind_biased<R>(m.u[0], Wf(W_X, cell(wrapc(x + (px ? -2 : 2), nx), y, z)),
+                                                     Wf(W_X, cxm), X0x, Wf(W_X, cxp));
+                            dX[1] = upwind_biased<R>(m.u[1], Wf(W_X + 1, cell(x, wrapc(y + (py ? -2 : 2), ny), z)),
+                                                     Wf(W_X + 1, cym), X0y, Wf(W_X + 1, cyp));
+                            const int o2 = pz ? 0 : 4;
+                            const R s2 = zf[o2] ? R(-1) : R(1);
+                            dX[2] = upwind_biased<R>(m.u[2], s2 * Wf(W_X + 2, cell(x, y, zn[o2])),
+                                                     szm * Wf(W_X + 2, czm), X0z, szp * Wf(W_X + 2, czp));
                         }
 #pragma unroll
                         for (int a = 0; a < 3; ++a) Phi[a] = -dX[a] * m.ir;

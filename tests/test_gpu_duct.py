@@ -221,3 +221,55 @@ def test_throttle_joule_thomson_on_the_gpu():
     c_P = L.orc_eos_cv(o.p, r_m, T_m) + T_m * P_T ** 2 / (r_m ** 2 * P_rho)
     mu_jt = -(1.0 / r_m - T_m * P_T / (r_m ** 2 * P_rho)) / c_P
     assert (T[-2] - T[1]) / (P[-2] - P[1]) == pytest.approx(mu_jt, rel=0.02)
+
+
+# Supersonic inlet (Ma 1.5; static inlet, extrapolated outlet, the upwind-biased Phi), the
+# window in which uniform supersonic flow of this step is stable: T_in 0.02, tau 1.
+SS_T, SS_U = 0.02, 1.5 * math.sqrt(GAM * R_GAS * 0.02)
+
+
+def _ss_duct(nz=50, nx=1, ny=1, q=0.0, friction=0.0, storage="f64"):
+    return wl.Case(name="ss_duct", dim=3, nx=nx, ny=ny, nz=nz, zwalls=2, eos="ideal", R=R_GAS, cv=CV,
+                   k_over_mu=CP / 0.71, tau_f=1.0, tau_g=1.0, phi_central=0, q=q, zlo=0, zhi=0, friction=friction,
+                   face_kind=(2, 4), face_P=(SS_T, 0.0), uw_lo=(0.0, 0.0, SS_U), Tw_lo=SS_T, Tw_hi=SS_T,
+                   storage=storage, init=dict(kind="duct", rho0=1.0, u0=SS_U, T0=SS_T))
+
+
+@pytest.mark.parametrize("q,friction", [(8e-7, 0.0), (0.0, 5e-4)], ids=["rayleigh", "fanno"])
+@pytest.mark.parametrize("variant", [SPLIT, (ZMARCH, (30, 6, 32))])
+def test_supersonic_duct_parity(q, friction, variant):
+    c = _ss_duct(q=q, friction=friction)
+    fields = _noisy_fields(c, 1e-3, 41)
+    sim, o = _pair(c, 300, fields, variant)
+    _compare(sim, o, 1e-12)
+
+
+@pytest.mark.parametrize("q,friction", [(8e-7, 0.0), (0.0, 5e-4)], ids=["rayleigh", "fanno"])
+def test_supersonic_duct_parity_bundle(q, friction):
+    # a 4 x 3 bundle of ducts (transverse velocities from the noise) in float64 on the z-march
+    # with extrapolated faces
+    c = _ss_duct(nx=4, ny=3, q=q, friction=friction)
+    fields = _noisy_fields(c, 1e-3, 42)
+    sim, o = _pair(c, 300, fields, (ZMARCH, (30, 6, 32)))
+    _compare(sim, o, 1e-12)
+
+
+@pytest.mark.parametrize("q,friction", [(8e-7, 0.0), (0.0, 5e-4)], ids=["rayleigh", "fanno"])
+@pytest.mark.parametrize("variant", [SPLIT, (ZMARCH, (30, 6, 32))])
+def test_supersonic_duct_parity_f32(q, friction, variant):
+    # float32 on a single column: u_z > 0 everywhere and no transverse velocity, so the
+    # upwind-biased branch is the same as in float64 (in a bundle, noise-driven transverse
+    # velocities round across zero and take the other branch in some cells)
+    # At Ma 1.5 the uniform state has a weakly growing mode (spectral radius lam of the
+    # one-step amplification, from the oracle's own linearisation): float32 rounding
+    # (<= 2^-24 per step) grows by at most sum_k lam^k over n steps.
+    from oracle import stability as st
+
+    n = 300
+    c = _ss_duct(q=q, friction=friction, storage="f32")
+    _, r, _ = st.amplification(st.column_case(c, 16), 1.0, (0.0, 0.0, SS_U), SS_T)
+    lam = float(np.max(r))
+    tol = 1e-5 + 2.0 ** -24 * (lam ** n - 1.0) / (lam - 1.0)
+    fields = _noisy_fields(c, 1e-3, 42)
+    sim, o = _pair(c, n, fields, variant)
+    _compare(sim, o, tol, f32=True)

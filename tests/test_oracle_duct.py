@@ -183,3 +183,49 @@ def test_bench_recipes_of_the_wall_and_duct_forms_are_sound():
     m = (rho.reshape(fd.nz, -1) * uz).mean(axis=1)
     assert np.all(np.isfinite(m)) and m.min() > 0
     assert np.ptp(m[1:-1]) <= 1e-3 * m.mean()
+
+
+# Supersonic inlet (Sec. III.A: Rayleigh and Fanno flow entering at Ma 1.5): static inlet
+# (P, T, u given), extrapolated outlet, the upwind-biased Phi.  Uniform supersonic flow of
+# this step is linearly stable only at low lattice temperature and tau >= 1 (see
+# test_oracle_stability); T_in = 0.02, tau = 1.
+SS_T, SS_MA, SS_TAU = 0.02, 1.5, 1.0
+SS_U = SS_MA * math.sqrt(GAM * R_GAS * SS_T)
+
+
+def _ss_duct(nz, q=0.0, friction=0.0):
+    return wl.Case(name="ss_duct", dim=3, nx=1, ny=1, nz=nz, zwalls=2, eos="ideal", R=R_GAS, cv=CV,
+                   k_over_mu=CP / 0.71, tau_f=SS_TAU, tau_g=SS_TAU, phi_central=0, q=q, zlo=0, zhi=0,
+                   friction=friction, face_kind=(2, 4), face_P=(SS_T, 0.0), uw_lo=(0.0, 0.0, SS_U),
+                   Tw_lo=SS_T, Tw_hi=SS_T, init=dict(kind="duct", rho0=1.0, u0=SS_U, T0=SS_T))
+
+
+def test_supersonic_rayleigh_flow_relations():
+    # heat addition decelerates a supersonic flow towards Ma 1 along one Rayleigh line
+    nz, q = 50, 8e-7
+    rho, uz, T, P, Ma = _profiles(_ss_duct(nz, q=q), 20000)
+    mdot = rho * uz
+    assert np.ptp(mdot[1:-1]) <= 1e-7 * mdot.mean()
+    assert 1.0 < Ma[-2] < Ma[1] - 1e-3
+    Ts = T * (1 + GAM * Ma ** 2) ** 2 / ((1 + GAM) ** 2 * Ma ** 2)
+    Ps = P * (1 + GAM * Ma ** 2) / (1 + GAM)
+    assert np.ptp(Ts[1:-1]) <= 1e-4 * Ts.mean()
+    assert np.ptp(Ps[1:-1]) <= 1e-4 * Ps.mean()
+    H = CP * T + 0.5 * uz ** 2
+    Hana = H[1] + q * (np.arange(nz) - 1) / mdot.mean()
+    assert np.max(np.abs(H - Hana)[1:-1]) <= 0.03 * q * nz / mdot.mean()
+
+
+def test_supersonic_fanno_flow_relations():
+    # friction decelerates a supersonic flow towards Ma 1 along one Fanno line (duct well
+    # inside the choking length 4 f L*/D = 0.136 at Ma 1.5), total enthalpy constant
+    nz = 50
+    rho, uz, T, P, Ma = _profiles(_ss_duct(nz, friction=5e-4), 20000)
+    assert np.ptp((rho * uz)[1:-1]) <= 1e-7 * (rho * uz).mean()
+    assert 1.0 < Ma[-2] < Ma[1] - 0.05
+    Ts = T * (2 + (GAM - 1) * Ma ** 2) / (1 + GAM)
+    Ps = P * Ma * np.sqrt((2 + (GAM - 1) * Ma ** 2) / (1 + GAM))
+    assert np.ptp(Ts[1:-1]) <= 1e-3 * Ts.mean()
+    assert np.ptp(Ps[1:-1]) <= 2e-3 * Ps.mean()
+    H = CP * T + 0.5 * uz ** 2
+    assert np.ptp(H[1:-1]) <= 1e-3 * H.mean()
