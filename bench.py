@@ -65,9 +65,10 @@ def _peaks():
 
 # sources of each timed kernel: the ncu traffic figure counts only while they are unchanged
 _KERNEL_SOURCES = {
-    "k_zgather": ("lbm_device.cuh", "lbm_zgather.cuh"),
+    "k_zgather": ("lbm_device.cuh", "lbm_async.cuh", "lbm_zgather.cuh"),
     "k_zmacro": ("lbm_device.cuh", "lbm_split.cuh", "lbm_zmarch.cuh"),
     "k_fused": ("lbm_device.cuh", "lbm_fused.cuh"),
+    "k_ymarch": ("lbm_device.cuh", "lbm_async.cuh", "lbm_ymarch.cuh"),
 }
 
 
@@ -424,6 +425,15 @@ def _measure_forms(lbm, wl, torch, steps, headline=None):
         ri, _ = _form(lbm, torch, iso, steps, 4, warm=0, pops=1)
         ri["speedup_vs_full_model"] = r["ms_per_step"] / ri["ms_per_step"]
         res["f32_vdw_512_isothermal"] = ri
+        # a 4096^2 quench (2.4 GB of float32 populations, far above L2): the 2-D row march
+        r, fr = _form(lbm, torch, wl.vdw_spinodal(4096, storage="f32"), steps, 4, warm=0)
+        traffic, ncu_us = _ncu_traffic("k_ymarch", "vdw_spinodal_4096_f32")
+        r["ncu_dram_bytes_per_launch"] = traffic
+        res["f32_vdw_4096"] = r
+        rb, _ = _form(lbm, torch, wl.vdw_spinodal(4096, storage="bf16"), steps, 2, warm=0)
+        rb["speedup_vs_f32"] = r["ms_per_step"] / rb["ms_per_step"]
+        res["bf16_vdw_4096"] = rb
+        torch.cuda.empty_cache()
         # 64 simulations per launch under CUDA graphs
         b64, fb64 = _form(lbm, torch, wl.vdw_batch(64, storage="f64"), steps, 8, graphs=10, warm=0)
         res["f64_vdw_batch_64"] = b64

@@ -80,6 +80,8 @@ extern "C" {
 #define LBM_KERNEL_ZMARCH 3 /* D3Q27: macroscopic pass + z-marching collide-stream pass   */
 #define LBM_KERNEL_ZGATHER 4 /* D3Q27: macroscopic pass + column-march collide-stream pass with
                                 staged pulls and gathered moments (32-/16-bit storage)      */
+#define LBM_KERNEL_YMARCH 5  /* D2Q9: one pass per step, CTAs marching up x strips with row
+                                rings (32-/16-bit storage, no learned temperature)          */
 
 typedef struct lbm_ctx *lbm_handle;
 
@@ -264,11 +266,14 @@ int lbm_invariants(lbm_handle h, double *out);
 int lbm_diagnostics(lbm_handle h, long long out[4]);
 
 /* Kernel selection: variant LBM_KERNEL_AUTO / SPLIT / FUSED / ZMARCH /
- * ZGATHER; tx, ty, tz the tile of the fused variant, or for ZMARCH (3-D only)
- * the xy tile and the number of z planes each CTA marches through (0:
- * default); ZGATHER has the xy tile 30 x 14 (tx, ty 0 or 30, 14) and takes
- * tz as its number of planes.  Errors: LBM_E_INVALID for a tile the variant
- * cannot run, LBM_E_UNSUPPORTED for a lattice or boundary set it does not run. */
+ * ZGATHER / YMARCH; tx, ty, tz the tile of the fused variant, or for ZMARCH
+ * (3-D only) the xy tile and the number of z planes each CTA marches through
+ * (0: default); ZGATHER has the xy tile 30 x 14 (tx, ty 0 or 30, 14) and
+ * takes tz as its number of planes; YMARCH (2-D only) has strips of 124
+ * columns (every simulation with the central Phi) or 122, tx 0 or that width,
+ * and takes ty as the rows each CTA marches through (0: 64).  Errors:
+ * LBM_E_INVALID for a tile the variant cannot run, LBM_E_UNSUPPORTED for a
+ * lattice or boundary set it does not run. */
 int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz);
 
 /* n eager time steps (no graphs) with CUDA events recorded on h's stream

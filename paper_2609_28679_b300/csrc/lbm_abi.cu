@@ -164,6 +164,26 @@ bool zgather_ok(const lbm_ctx* h)
     return true;
 }
 
+// the row-march kernel can run h: D2Q9, 32- or 16-bit storage, one equation
+// of state, no learned temperature, per-cell fields or resistance, nx a
+// multiple of the elements per 16-byte copy
+bool ymarch_ok(const lbm_ctx* h)
+{
+    if (h->dim != 2 || h->storage == LBM_F64 || has_fields(h) || has_resistance(h)) return false;
+    const int chunk = h->storage == LBM_F32 ? 4 : 8;
+    for (const SimDev& d : h->sims)
+        if (d.eos != h->sims[0].eos || d.nx % chunk != 0 || d.t_solver == LBM_T_MLP) return false;
+    return true;
+}
+
+// owned columns of a row-march strip (narrower when some simulation takes the upwind-biased Phi)
+int ymarch_strip_width(const lbm_ctx* h)
+{
+    bool central = true;
+    for (const SimDev& d : h->sims) central = central && d.phi_central;
+    return central ? kYmStripCentral : kYmStripUpwind;
+}
+
 // every face of a simulation with zwalls == 2 has its data
 bool faces_ready(const lbm_ctx* h)
 {
@@ -188,6 +208,9 @@ cudaError_t zmacro_dispatch(int storage, int eos, int mlp, const SimDev* sims, c
 cudaError_t zgather_dispatch(int storage, int eos, int zl, const SimDev* sims, const TileEntry* tiles, int ntiles,
                              const void* src, void* dst, const void* W, void* Mout, long long Ntot,
                              cudaStream_t stream);
+cudaError_t ymarch_dispatch(int storage, int eos, int pc, int yl, const SimDev* sims, const TileEntry* tiles,
+                            int ntiles, const void* src, void* dst, const void* Min, void* Mout, long long Ntot,
+                            unsigned long long* diag, cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Typed implementation of every operation for one (D, arithmetic, storage).
@@ -259,6 +282,25 @@ template <int D, typename R, typename S> struct Impl {
         return LBM_OK;
     }
 
+    // D2Q9: the row-march one-pass step
+    static int ymarch_step(lbm_ctx* h)
+    {
+        if (!h->moments_valid) {
+            int rc = fused_prepare(h);
+            if (rc) return rc;
+        }
+        pass_mark(h, 0);
+        pass_mark(h, 1);
+        pass_mark(h, 2);
+        cudaError_t e = ymarch_dispatch(h->storage, h->sims[0].eos, all_central(h), h->ty, h->d_sims, h->d_tiles,
+                                        (int)h->tiles.size(), h->pop[h->cur], h->pop[h->cur ^ 1], mbuf(h, h->cur),
+                                        mbuf(h, h->cur ^ 1), h->Ntot, h->d_diag, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "row-march step");
+        pass_mark(h, 3);
+        h->cur ^= 1;
+        return LBM_OK;
+    }
+
     // D3Q27: macroscopic pass from the carried moments, then the z-marching collide-stream pass
     static int zmarch_step(lbm_ctx* h)
     {
@@ -303,7 +345,8 @@ template <int D, typename R, typename S> struct Impl {
     {
         if (!faces_ready(h)) return fail(h, LBM_E_STATE, "lbm_set_walls / lbm_set_face has not set every face");
         for (int it = 0; it < n; ++it) {
-            int rc = h->variant == LBM_KERNEL_FUSED ? fused_step(h)
+            int rc = h->variant == LBM_KERNEL_FUSED    ? fused_step(h)
+                     : h->variant == LBM_KERNEL_YMARCH ? ymarch_step(h)
                      : (h->variant == LBM_KERNEL_ZMARCH || h->variant == LBM_KERNEL_ZGATHER) ? zmarch_step(h)
                                                                                               : split_step(h);
             if (rc) return rc;
@@ -437,6 +480,18 @@ cudaError_t zmarch_nee_dispatch(int storage, int eos, int tx, int ty, int zl, co
     switch (storage) {
     case LBM_F64: return zmarch_nee_dispatch_f64(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
     case LBM_F32: return zmarch_nee_dispatch_f32(eos, tx, ty, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t ymarch_dispatch(int storage, int eos, int pc, int yl, const SimDev* sims, const TileEntry* tiles,
+                            int ntiles, const void* src, void* dst, const void* Min, void* Mout, long long Ntot,
+                            unsigned long long* diag, cudaStream_t stream)
+{
+    switch (storage) {
+    case LBM_F32: return ymarch_dispatch_f32(eos, pc, yl, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_BF16: return ymarch_dispatch_bf16(eos, pc, yl, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+    case LBM_F16: return ymarch_dispatch_f16(eos, pc, yl, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
     }
     return cudaErrorInvalidValue;
 }
@@ -727,6 +782,11 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
             h->variant = LBM_KERNEL_ZGATHER;
             h->tx = 30; h->ty = 14; h->tz = 32;
             rc = build_tiles(h, 30, 14, 32);
+        } else if (ymarch_ok(h) && cells >= (1LL << 22)) {
+            // large 2-D lattices: enough strips x 64-row ranges to fill the GPU several times
+            h->variant = LBM_KERNEL_YMARCH;
+            h->tx = ymarch_strip_width(h); h->ty = 64; h->tz = 1;
+            rc = build_tiles(h, h->tx, 64, 1);
         } else if (h->dim == 3 && same_eos && zmarch_ok(h, 30, 14)) {
             h->variant = LBM_KERNEL_ZMARCH;
             h->tx = 30; h->ty = 14; h->tz = 32;
@@ -977,7 +1037,8 @@ int lbm_step(lbm_handle h, int n)
     int rc = h->ops.step(h, 1);
     if (rc) return rc;
     int left = n - 1;
-    if (h->variant == LBM_KERNEL_FUSED && !h->moments_valid) return fail(h, LBM_E_STATE, "moments not prepared");
+    if ((h->variant == LBM_KERNEL_FUSED || h->variant == LBM_KERNEL_YMARCH) && !h->moments_valid)
+        return fail(h, LBM_E_STATE, "moments not prepared");
     if (!h->graph_exec[h->cur]) {
         rc = capture_graph(h);
         if (rc) return rc;
@@ -994,7 +1055,8 @@ int lbm_step_timed(lbm_handle h, int n, double ms_per_pass[4])
     if (n < 1 || !ms_per_pass) return fail(h, LBM_E_INVALID, "n must be >= 1 and ms_per_pass non-NULL");
     if (!h->initialized) return fail(h, LBM_E_STATE, "lbm_init has not been called");
     // the carried moments are prepared outside the recorded passes
-    if ((h->variant == LBM_KERNEL_FUSED || h->variant == LBM_KERNEL_ZMARCH || h->variant == LBM_KERNEL_ZGATHER) &&
+    if ((h->variant == LBM_KERNEL_FUSED || h->variant == LBM_KERNEL_YMARCH || h->variant == LBM_KERNEL_ZMARCH ||
+         h->variant == LBM_KERNEL_ZGATHER) &&
         !h->moments_valid) {
         int rc = h->ops.prepare(h);
         if (rc) return rc;
@@ -1159,6 +1221,22 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
         h->tx = 30; h->ty = 14; h->tz = tz;
         return LBM_OK;
     }
+    if (variant == LBM_KERNEL_YMARCH) {
+        if (h->dim != 2) return fail(h, LBM_E_INVALID, "the row-march kernel runs D2Q9 lattices");
+        if (!ymarch_ok(h))
+            return fail(h, LBM_E_UNSUPPORTED,
+                        "the row-march kernel needs 32- or 16-bit storage, nx a multiple of 4 (float32) or 8 "
+                        "(16-bit), one equation of state and no learned temperature or per-cell fields");
+        const int strip = ymarch_strip_width(h);
+        if (tx > 0 && tx != strip) return fail(h, LBM_E_INVALID, "the row-march kernel has a fixed strip width");
+        if (ty <= 0) ty = 64;
+        LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
+        int rc = build_tiles(h, strip, ty, 1);
+        if (rc) return rc;
+        h->variant = LBM_KERNEL_YMARCH;
+        h->tx = strip; h->ty = ty; h->tz = 1;
+        return LBM_OK;
+    }
     if (variant == LBM_KERNEL_ZMARCH) {
         if (h->dim != 3) return fail(h, LBM_E_INVALID, "the z-march kernel runs D3Q27 lattices");
         if (tx <= 0 || ty <= 0) { tx = 30; ty = 14; }
@@ -1229,6 +1307,8 @@ int lbm_autotune(lbm_handle h, int trial_steps, int* variant, int* tx, int* ty, 
     if (h->dim == 2) {
         for (auto& t : shapes2)
             if (h->ops.fused_ok(h, t[0], t[1], t[2])) cands.push_back({LBM_KERNEL_FUSED, t[0], t[1], t[2]});
+        if (ymarch_ok(h))
+            for (int yl : {32, 64, 128}) cands.push_back({LBM_KERNEL_YMARCH, 0, yl, 1});
     } else {
         for (auto& t : shapes3)
             if (h->ops.fused_ok(h, t[0], t[1], t[2])) cands.push_back({LBM_KERNEL_FUSED, t[0], t[1], t[2]});

@@ -51,4 +51,16 @@ cudaError_t zgather_dispatch_f16(int eos, int zl, const SimDev* sims, const Tile
                                  const void* src, void* dst, const void* W, void* Mout, long long Ntot,
                                  cudaStream_t stream);
 
+// row-march one-pass step for D2Q9 (32- and 16-bit storage); pc: every simulation takes the central Phi.
+// Owned columns of a strip: 128 threads less the rim and the stencils' reach (1 central, 2 upwind-biased).
+constexpr int kYmStripCentral = 124, kYmStripUpwind = 122;
+#define LBM_YMARCH_DECL(SUF)                                                                                          \
+    cudaError_t ymarch_dispatch_##SUF(int eos, int pc, int yl, const SimDev* sims, const TileEntry* tiles, int ntiles, \
+                                      const void* src, void* dst, const void* Min, void* Mout, long long Ntot,         \
+                                      unsigned long long* diag, cudaStream_t stream);
+LBM_YMARCH_DECL(f32)
+LBM_YMARCH_DECL(bf16)
+LBM_YMARCH_DECL(f16)
+#undef LBM_YMARCH_DECL
+
 }  // namespace lbm

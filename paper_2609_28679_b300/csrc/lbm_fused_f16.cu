@@ -2,6 +2,7 @@
 // for D2Q9 and D3Q27 and each equation of state.
 #include "lbm_fused.cuh"
 #include "lbm_fused_api.h"
+#include "lbm_ymarch.cuh"
 #include "lbm_zgather.cuh"
 #include "lbm_zmarch.cuh"
 
@@ -109,4 +110,11 @@ cudaError_t zgather_dispatch_f16(int eos, int zl, const SimDev* sims, const Tile
     return zgather_dispatch_t<__half>(eos, zl, sims, tiles, ntiles, src, dst, W, Mout, Ntot, stream);
 }
 
+
+cudaError_t ymarch_dispatch_f16(int eos, int pc, int yl, const SimDev* sims, const TileEntry* tiles, int ntiles,
+                              const void* src, void* dst, const void* Min, void* Mout, long long Ntot,
+                              unsigned long long* diag, cudaStream_t stream)
+{
+    return ymarch_dispatch_t<__half>(eos, pc, yl, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
+}
 }  // namespace lbm

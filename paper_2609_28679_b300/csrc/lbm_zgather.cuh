@@ -29,6 +29,7 @@
 // state per launch.
 #pragma once
 
+#include "lbm_async.cuh"
 #include "lbm_device.cuh"
 #include "lbm_fused.cuh"
 #include "lbm_split.cuh"
@@ -65,21 +66,6 @@ constexpr bool opp9_table_ok(int j = 0)
     return j == 9 || ((int)((kOpp9 >> (4 * j)) & 15u) == opp(j) && opp9_table_ok(j + 1));
 }
 static_assert(opp9_table_ok(), "kOpp9 must list opp(j) for j = 0..8");
-
-__device__ __forceinline__ void cp_async16(const void* smem, const void* gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-template <typename S> __device__ __forceinline__ float stored_to_f(S v);
-template <> __device__ __forceinline__ float stored_to_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ float stored_to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <> __device__ __forceinline__ float stored_to_f<__half>(__half v) { return __half2float(v); }
-
-__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // Macroscopic state of a cell and its stencils (div u, grad h, grad T, Phi;
 // Eq. correction) from the first pass's fields: periodic x, y; z periodic or

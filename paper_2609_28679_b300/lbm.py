@@ -22,6 +22,7 @@ LBM_IDEAL, LBM_VDW, LBM_PR = 0, 1, 2
 LBM_T_NEWTON, LBM_T_MLP = 0, 1
 LBM_PHI_UPWIND, LBM_PHI_CENTRAL = 0, 1
 LBM_KERNEL_AUTO, LBM_KERNEL_SPLIT, LBM_KERNEL_FUSED, LBM_KERNEL_ZMARCH, LBM_KERNEL_ZGATHER = 0, 1, 2, 3, 4
+LBM_KERNEL_YMARCH = 5
 LBM_FACE_INLET_TOTAL, LBM_FACE_INLET_STATIC, LBM_FACE_OUTLET_P, LBM_FACE_OUTLET_EXTRAP, LBM_FACE_INLET_PT = 1, 2, 3, 4, 5
 
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "bf16": LBM_BF16, "f16": LBM_F16}

@@ -6,7 +6,7 @@ time per step: the command line that profilers wrap.
 
 Workloads: acoustic_shear, vdw_spinodal, pr_heated_slab, pr_droplet (size =
 cells per side), thermal_couette (n x n x n/2), fanno_duct (n x n x 2n).  Kernel: auto (autotuner), split, fused[:TXxTY[xTZ]] or
-zmarch[:TXxTYxZL] or zgather[:30x14xZL].
+zmarch[:TXxTYxZL], zgather[:30x14xZL] or ymarch[:0xYL] (2-D).
 """
 from __future__ import annotations
 
@@ -26,7 +26,7 @@ _CASES = {
     "fanno_duct": lambda n, st: wl.fanno_duct(n, 2 * n, storage=st),
 }
 _VARIANTS = {"split": lbm.LBM_KERNEL_SPLIT, "fused": lbm.LBM_KERNEL_FUSED, "zmarch": lbm.LBM_KERNEL_ZMARCH,
-             "zgather": lbm.LBM_KERNEL_ZGATHER}
+             "zgather": lbm.LBM_KERNEL_ZGATHER, "ymarch": lbm.LBM_KERNEL_YMARCH}
 
 
 def main(argv=None) -> int:

@@ -35,6 +35,27 @@ def test_batched_fused_matches_oracle_per_simulation():
         off += n
 
 
+def test_row_march_graph_replay_matches_eager_steps():
+    # the 2-D row march (float32) under graph replay: the same launches, bit for bit
+    import torch
+
+    c = wl.vdw_spinodal(n=136, ny=44, storage="f32")
+    eager = lbm.Simulation(c, variant=lbm.LBM_KERNEL_YMARCH)
+    assert eager.kernel()[0] == lbm.LBM_KERNEL_YMARCH
+    eager.init()
+    eager.step(18)
+    stream = torch.cuda.Stream()
+    g = lbm.Simulation(c, variant=lbm.LBM_KERNEL_YMARCH)
+    g.use_graphs(4, stream)
+    g.init()
+    g.step(13)
+    g.step(5)
+    fe, ge = eager.populations()
+    fg, gg = g.populations()
+    assert np.array_equal(fg, fe)
+    assert np.array_equal(gg, ge)
+
+
 @pytest.mark.parametrize("variant", [lbm.LBM_KERNEL_SPLIT, lbm.LBM_KERNEL_FUSED])
 def test_graph_replay_matches_eager_steps(variant):
     import torch

@@ -20,7 +20,7 @@ from tests.util import oracle_params, rel_linf
 pytestmark = pytest.mark.gpu
 
 SPLIT, FUSED, ZMARCH = lbm.LBM_KERNEL_SPLIT, lbm.LBM_KERNEL_FUSED, lbm.LBM_KERNEL_ZMARCH
-ZGATHER = lbm.LBM_KERNEL_ZGATHER
+ZGATHER, YMARCH = lbm.LBM_KERNEL_ZGATHER, lbm.LBM_KERNEL_YMARCH
 
 
 def _variants():
@@ -363,6 +363,42 @@ def test_f32_zgather_constant_mu_walls():
     _compare(sim, o, 1e-5, f32=True)
 
 
+def _interior_tiles(nx, ny, cols):
+    """(x0, y0) of the 30 x 14 tiles whose staged boxes lie inside the lattice
+    (rows y0 - 2 ... y0 + 15; cols columns from the 16-byte chunk at or below
+    x0 - 2): tiles whose copies do not wrap around a periodic edge."""
+    c = 4 if cols == 40 else 8
+    out = []
+    for x0 in range(0, nx, 30):
+        xa = ((x0 - 2) // c) * c
+        for y0 in range(0, ny, 14):
+            if xa >= 0 and xa + cols <= nx and y0 >= 2 and y0 + 16 <= ny:
+                out.append((x0, y0))
+    return out
+
+
+@pytest.mark.parametrize("zl", [5, 16])
+def test_f32_zgather_many_tiles_walls(zl):
+    # interior tiles beside tiles whose copies wrap around x and y: walls in z (pulls
+    # across a wall), heat, gravity, several plane ranges, both population buffers as
+    # the source
+    c = wl.pr_heated_slab(n=128, nz=13, storage="f32")
+    c.ny = 60
+    c.zhi = 4
+    c.phi_central = 1
+    assert len(_interior_tiles(c.nx, c.ny, 40)) == 9
+    sim, o = _run_pair(c, 10, (ZGATHER, (30, 14, zl)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+def test_f32_zgather_many_tiles_periodic_droplet():
+    # periodic z (the source plane wraps), the droplet's interface across interior tiles
+    c = wl.pr_droplet(n=72, radius=12.0, storage="f32")
+    assert len(_interior_tiles(c.nx, c.ny, 40)) == 4
+    sim, o = _run_pair(c, 8, (ZGATHER, (30, 14, 16)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
 def test_zgather_refuses_what_it_does_not_run():
     # float64 storage, and nx not a multiple of the 16-byte copy width
     for c in (wl.pr_heated_slab(n=12, nz=6, storage="f64"), wl.pr_heated_slab(n=10, nz=6, storage="f32")):
@@ -391,6 +427,136 @@ def test_16bit_storage_error_bound(storage, tol, variant):
     rr, ur, Tr = o.moments()
     assert rel_linf(rho, rr) <= tol
     assert rel_linf(T, Tr) <= tol
+
+
+@pytest.mark.parametrize("storage,tol", [("bf16", 2e-3), ("f16", 3e-4)])
+def test_16bit_zgather_many_tiles(storage, tol):
+    # the 16-bit staged box (48 columns) on interior and wrapping tiles, walls in z
+    c = wl.pr_heated_slab(n=128, nz=10, storage=storage)
+    c.ny = 60
+    assert len(_interior_tiles(c.nx, c.ny, 48)) == 6
+    sim, o = _run_pair(c, 10, (ZGATHER, (30, 14, 4)))
+    f, g = sim.populations()
+    fr, gr = o.populations()
+    assert rel_linf(f, fr.ravel()) <= tol
+    assert rel_linf(g, gr.ravel()) <= tol
+    rho, u, T = sim.moments()
+    rr, ur, Tr = o.moments()
+    assert rel_linf(rho, rr) <= tol
+    assert rel_linf(T, Tr) <= tol
+
+
+# ---------------------------------------------------------------------------
+# The 2-D row march (strips marched in y, rings of rows): several strips with a
+# ragged last one, row ranges with a ragged last one, lattices narrower than a
+# strip (columns and rows wrap several times), both Phi readings, all three
+# equations of state, the isothermal and constant-mu modes, batches, and the
+# 16-bit storage bound.  float32 at 1e-5.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("yl", [64, 8, 5])
+def test_f32_ymarch_vdw_strips_and_row_ranges(yl):
+    c = wl.vdw_spinodal(n=264, ny=37, storage="f32")  # strips of 124: 124, 124, 16 columns
+    sim, o = _run_pair(c, 30, (YMARCH, (0, yl, 0)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+def test_f32_ymarch_ideal_upwind_phi():
+    # the upwind-biased Phi (strips of 122, stencils reaching two columns and rows), force and heat
+    c = wl.acoustic_shear(n=48, storage="f32")
+    sim, o = _run_pair(c, 50, (YMARCH, (0, 16, 0)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+@pytest.mark.parametrize("n,ny,yl", [(8, 5, 4), (4, 3, 2), (128, 12, 64)])
+def test_f32_ymarch_lattice_narrower_than_strip(n, ny, yl):
+    c = wl.vdw_spinodal(n=n, ny=ny, storage="f32", seed=7)
+    sim, o = _run_pair(c, 20, (YMARCH, (0, yl, 0)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+def test_f32_ymarch_pr_newton():
+    # Peng-Robinson (float32 Newton from the carried temperature), gravity, uniform heat
+    c = wl.Case(name="pr2", dim=2, nx=136, ny=40, eos="pr", R=1.0, cv=2.5, Tc=wl.PR_TC, Pc=wl.PR_PC,
+                omega=wl.PR_OMEGA, kappa=0.2, k_over_mu=3.5, accel=(0.0, -1e-5, 0.0), q=1e-6, phi_central=1,
+                storage="f32", init=dict(kind="noisy_temperature", rho0=0.30, amp=1e-3, T0=0.95 * wl.PR_TC, seed=3))
+    sim, o = _run_pair(c, 25, (YMARCH, (0, 16, 0)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+def test_f32_ymarch_isothermal():
+    c = wl.vdw_spinodal(n=72, ny=40, storage="f32")
+    c.isothermal = 1
+    sim, o = _run_pair(c, 25, (YMARCH, (0, 16, 0)))
+    _compare_isothermal(sim, o, 1e-5, f32=True)
+
+
+def test_f32_ymarch_constant_mu():
+    c = wl.Case(name="vdw2mu", dim=2, nx=72, ny=40, eos="vdw", R=1.0, cv=2.5, a=wl.VDW_A, b=wl.VDW_B,
+                kappa=wl.VDW_KAPPA, eta_over_mu=wl.VDW_ETA, k_over_mu=3.5, accel=(1e-4, -1e-4, 0.0),
+                phi_central=1, storage="f32",
+                init=dict(kind="noisy_density", rho0=2.0, amp=0.02, T0=1.1 * wl.VDW_TC, seed=13))
+    _with_mu(c, 2.0, 1.1 * wl.VDW_TC)
+    sim, o = _run_pair(c, 25, (YMARCH, (0, 16, 0)))
+    _compare(sim, o, 1e-5, f32=True)
+
+
+def test_f32_ymarch_batch_of_uneven_simulations():
+    cases = [wl.vdw_spinodal(n=40, ny=43, storage="f32", seed=60),
+             wl.vdw_spinodal(n=136, ny=29, storage="f32", Tr=0.85, seed=5),
+             wl.vdw_spinodal(n=8, ny=11, storage="f32", seed=28)]
+    sim = lbm.Simulation(cases)
+    lbm.lbm_set_kernel(sim.h, YMARCH, 0, 16, 0)
+    assert sim.kernel()[0] == YMARCH
+    sim.init()
+    sim.step(15)
+    rho, u, T = sim.moments()
+    off = 0
+    for c in cases:
+        o = orc.Oracle(oracle_params(c))
+        o.init(*c.fields())
+        o.step(15)
+        rr, ur, Tr = o.moments()
+        n = c.ncell
+        assert rel_linf(rho[off:off + n], rr) <= 1e-5
+        assert rel_linf(T[off:off + n], Tr) <= 1e-5
+        assert np.max(np.abs(u[2 * off:2 * off + 2 * n] - ur.ravel())) <= 1e-5
+        off += n
+
+
+@pytest.mark.parametrize("storage,tol", [("bf16", 2e-3), ("f16", 3e-4)])
+def test_16bit_ymarch_error_bound(storage, tol):
+    c = wl.vdw_spinodal(n=136, ny=30, storage=storage)
+    sim, o = _run_pair(c, 10, (YMARCH, (0, 16, 0)))
+    f, g = sim.populations()
+    fr, gr = o.populations()
+    assert rel_linf(f, fr.ravel()) <= tol
+    assert rel_linf(g, gr.ravel()) <= tol
+    rho, u, T = sim.moments()
+    rr, ur, Tr = o.moments()
+    assert rel_linf(rho, rr) <= tol
+    assert rel_linf(T, Tr) <= tol
+
+
+def test_f32_ymarch_theta_nonpositive_counted_once_per_cell():
+    c = wl.Case(name="negP", dim=2, nx=8, ny=8, eos="vdw", a=9 / 49, b=2 / 21, storage="f32",
+                init=dict(kind="uniform", rho0=5.6, T0=0.8 * 4 / 7))
+    sim = lbm.Simulation(c)
+    lbm.lbm_set_kernel(sim.h, YMARCH, 0, 3, 0)
+    sim.init()
+    sim.step(1)
+    d = sim.diagnostics()
+    assert d[1] == 64
+    assert d[0] == 0
+
+
+def test_ymarch_refuses_what_it_does_not_run():
+    # float64 storage, nx not a multiple of the 16-byte copy width, 3-D lattices
+    for c in (wl.vdw_spinodal(n=16, storage="f64"), wl.vdw_spinodal(n=10, storage="f32"),
+              wl.vdw_spinodal(n=12, storage="bf16"), wl.pr_heated_slab(n=8, nz=4, storage="f32")):
+        sim = lbm.Simulation(c)
+        with pytest.raises(lbm.LbmError, match="row-march"):
+            lbm.lbm_set_kernel(sim.h, YMARCH, 0, 16, 0)
+        sim.close()
 
 
 # ---------------------------------------------------------------------------
