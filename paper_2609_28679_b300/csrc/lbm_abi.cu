@@ -140,11 +140,24 @@ bool has_resistance(const lbm_ctx* h)
 
 bool zmarch_shape(int storage, int tx, int ty);
 
+// The tiled kernels address a population as (population index) * N + cell in
+// 32-bit arithmetic; per: how many populations' worth of cells their largest
+// offset spans (Q for the fused step, 27 for the z-marches, 18 for the row
+// march, which indexes f and g from one base).  Larger simulations run on the
+// split kernels, whose indices are 64-bit.
+bool offsets32(const lbm_ctx* h, unsigned long long per)
+{
+    for (const SimDev& d : h->sims)
+        if (per * (unsigned long long)d.N > 0xffffffffULL) return false;
+    return true;
+}
+
 // the z-march kernel can run h with this xy tile (extrapolated faces: tiles
 // 30 x 14 and 30 x 6 with 32- or 64-bit storage)
 bool zmarch_ok(const lbm_ctx* h, int tx, int ty)
 {
-    if (h->dim != 3 || has_fields(h) || (has_resistance(h) && !has_nee(h))) return false;  // resistance: extrapolated variant only
+    if (h->dim != 3 || has_fields(h) || (has_resistance(h) && !has_nee(h)) || !offsets32(h, 27))
+        return false;  // resistance: extrapolated variant only
     for (const SimDev& d : h->sims)
         if (d.eos != h->sims[0].eos) return false;
     if (has_nee(h))
@@ -157,7 +170,8 @@ bool zmarch_ok(const lbm_ctx* h, int tx, int ty)
 // resistance or per-cell fields, nx a multiple of the elements per 16-byte copy
 bool zgather_ok(const lbm_ctx* h)
 {
-    if (h->dim != 3 || h->storage == LBM_F64 || has_fields(h) || has_resistance(h) || has_nee(h)) return false;
+    if (h->dim != 3 || h->storage == LBM_F64 || has_fields(h) || has_resistance(h) || has_nee(h) || !offsets32(h, 27))
+        return false;
     const int chunk = h->storage == LBM_F32 ? 4 : 8;
     for (const SimDev& d : h->sims)
         if (d.eos != h->sims[0].eos || d.nx % chunk != 0) return false;
@@ -169,7 +183,7 @@ bool zgather_ok(const lbm_ctx* h)
 // multiple of the elements per 16-byte copy
 bool ymarch_ok(const lbm_ctx* h)
 {
-    if (h->dim != 2 || h->storage == LBM_F64 || has_fields(h) || has_resistance(h)) return false;
+    if (h->dim != 2 || h->storage == LBM_F64 || has_fields(h) || has_resistance(h) || !offsets32(h, 18)) return false;
     const int chunk = h->storage == LBM_F32 ? 4 : 8;
     for (const SimDev& d : h->sims)
         if (d.eos != h->sims[0].eos || d.nx % chunk != 0 || d.t_solver == LBM_T_MLP) return false;
@@ -414,7 +428,7 @@ template <int D, typename R, typename S> struct Impl {
 
     static int fused_ok(lbm_ctx* h, int tx, int ty, int tz)
     {
-        if (split_only(h)) return 0;  // extrapolated faces or duct friction: split kernels only
+        if (split_only(h) || !offsets32(h, Lat<D>::Q)) return 0;  // extrapolated faces, duct friction, size: split kernels
         for (const SimDev& d : h->sims)
             if (d.eos != h->sims[0].eos) return 0;  // one equation of state per fused launch
         if (uses_mlp(h) && h->storage != LBM_F32) return 0;  // learned start built for float32 storage
@@ -1210,7 +1224,8 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
         if (!zgather_ok(h))
             return fail(h, LBM_E_UNSUPPORTED,
                         "the gathering z-march needs 32- or 16-bit storage, nx a multiple of 4 (float32) or 8 (16-bit), "
-                        "one equation of state and no extrapolated faces, resistance or per-cell fields");
+                        "at most 159 M cells per simulation, one equation of state and no extrapolated faces, "
+                        "resistance or per-cell fields");
         if ((tx > 0 && tx != 30) || (ty > 0 && ty != 14))
             return fail(h, LBM_E_INVALID, "the gathering z-march has the fixed xy tile 30 x 14");
         if (tz <= 0) tz = 32;
@@ -1226,7 +1241,8 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
         if (!ymarch_ok(h))
             return fail(h, LBM_E_UNSUPPORTED,
                         "the row-march kernel needs 32- or 16-bit storage, nx a multiple of 4 (float32) or 8 "
-                        "(16-bit), one equation of state and no learned temperature or per-cell fields");
+                        "(16-bit), at most 238 M cells per simulation, one equation of state and no learned "
+                        "temperature or per-cell fields");
         const int strip = ymarch_strip_width(h);
         if (tx > 0 && tx != strip) return fail(h, LBM_E_INVALID, "the row-march kernel has a fixed strip width");
         if (ty <= 0) ty = 64;
@@ -1245,7 +1261,9 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
             if (d.eos != h->sims[0].eos) return fail(h, LBM_E_INVALID, "one equation of state per z-march launch");
         if (!zmarch_shape(h->storage, tx, ty)) return fail(h, LBM_E_INVALID, "z-march tile not built");
         if (!zmarch_ok(h, tx, ty))
-            return fail(h, LBM_E_UNSUPPORTED, "extrapolated faces on the z-march: tiles 30x14 or 30x6, 32- or 64-bit storage");
+            return fail(h, LBM_E_UNSUPPORTED,
+                        "the z-march needs at most 159 M cells per simulation; extrapolated faces on the z-march: tiles "
+                        "30x14 or 30x6, 32- or 64-bit storage");
         LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
         int rc = build_tiles(h, tx, ty, tz);
         if (rc) return rc;

@@ -562,6 +562,21 @@ def test_ymarch_refuses_what_it_does_not_run():
 # ---------------------------------------------------------------------------
 # Edge cases
 # ---------------------------------------------------------------------------
+def test_tiled_kernels_refuse_simulations_past_32bit_offsets():
+    # 560 x 560 x 512 = 160.6 M cells (bf16, about 57 GB with the work arrays): 27 N exceeds
+    # 2^32, so the tiled 3-D kernels, which address populations with 32-bit offsets, refuse
+    # it and the default is the split path (64-bit indices).  Nothing is stepped.
+    c = wl.pr_heated_slab(n=560, nz=512, storage="bf16")
+    sim = lbm.Simulation(c)
+    try:
+        assert sim.kernel()[0] == SPLIT
+        for v in (ZGATHER, ZMARCH, FUSED):
+            with pytest.raises(lbm.LbmError):
+                lbm.lbm_set_kernel(sim.h, v, 0, 0, 0)
+    finally:
+        sim.close()
+
+
 def test_zero_steps_returns_initial_equilibrium():
     c = wl.acoustic_shear(n=8, storage="f64")
     sim, o = _run_pair(c, 0, SPLIT)
