@@ -562,17 +562,16 @@ def test_ymarch_refuses_what_it_does_not_run():
 # ---------------------------------------------------------------------------
 # Edge cases
 # ---------------------------------------------------------------------------
-def test_tiled_kernels_refuse_simulations_past_32bit_offsets():
-    # 560 x 560 x 512 = 160.6 M cells (bf16, about 57 GB with the work arrays): 27 N exceeds
-    # 2^32, so the tiled 3-D kernels, which address populations with 32-bit offsets, refuse
-    # it and the default is the split path (64-bit indices).  Nothing is stepped.
-    c = wl.pr_heated_slab(n=560, nz=512, storage="bf16")
+def test_row_march_refuses_simulations_past_its_32bit_offsets():
+    # lbm_create keeps Q N below 2^32; the row march indexes f and g from one base (18 N),
+    # so a 2-D lattice of 16384 x 14600 = 239.2 M cells (bf16, about 50 GB with the work
+    # arrays) must stay on the fused kernel.  Nothing is stepped.
+    c = wl.vdw_spinodal(n=16384, ny=14600, storage="bf16")
     sim = lbm.Simulation(c)
     try:
-        assert sim.kernel()[0] == SPLIT
-        for v in (ZGATHER, ZMARCH, FUSED):
-            with pytest.raises(lbm.LbmError):
-                lbm.lbm_set_kernel(sim.h, v, 0, 0, 0)
+        assert sim.kernel()[0] == FUSED
+        with pytest.raises(lbm.LbmError, match="238 M cells"):
+            lbm.lbm_set_kernel(sim.h, YMARCH, 0, 64, 0)
     finally:
         sim.close()
 
