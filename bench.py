@@ -570,24 +570,24 @@ def run_ours(args):
     diag = sim.diagnostics()
 
     # end to end through the C ABI with host buffers: upload the state, one step, read the fields back
+    # (float32 fields for the float32 simulation: lbm_init_f32 / lbm_moments_f32)
     rho, u, T = case.fields()
-    rho_h = torch.from_numpy(rho).pin_memory().numpy()
-    u_h = torch.from_numpy(np.ascontiguousarray(u.ravel())).pin_memory().numpy()
-    T_h = torch.from_numpy(T).pin_memory().numpy()
-    out_r = torch.empty(case.ncell, dtype=torch.float64).pin_memory().numpy()
-    out_u = torch.empty(3 * case.ncell, dtype=torch.float64).pin_memory().numpy()
-    out_T = torch.empty(case.ncell, dtype=torch.float64).pin_memory().numpy()
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).ravel()).pin_memory().numpy()
+    rho_h, u_h, T_h = f32(rho), f32(u), f32(T)
+    out_r = torch.empty(case.ncell, dtype=torch.float32).pin_memory().numpy()
+    out_u = torch.empty(3 * case.ncell, dtype=torch.float32).pin_memory().numpy()
+    out_T = torch.empty(case.ncell, dtype=torch.float32).pin_memory().numpy()
     e2e_steps = 3
-    lbm.lbm_init(sim.h, rho_h, u_h, T_h, 0)
+    lbm.lbm_init_f32(sim.h, rho_h, u_h, T_h, 0)
     lbm.lbm_step(sim.h, 1)
-    lbm.lbm_moments(sim.h, out_r, out_u, out_T, 0)
+    lbm.lbm_moments_f32(sim.h, out_r, out_u, out_T, 0)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for it in range(e2e_steps):
-        lbm.lbm_init(sim.h, rho_h, u_h, T_h, 0)
+        lbm.lbm_init_f32(sim.h, rho_h, u_h, T_h, 0)
         lbm.lbm_step(sim.h, 1)
-        lbm.lbm_moments(sim.h, out_r, out_u, out_T, 0)
+        lbm.lbm_moments_f32(sim.h, out_r, out_u, out_T, 0)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     sim.close()
@@ -641,8 +641,9 @@ def run_ours(args):
             "passes": {"macroscopic_ms": passes["pass1_ms"], "boundary_ms": passes["pass2_ms"],
                        "collide_stream_ms": passes["pass3_ms"], "step_ms": passes["step_ms"]},
             "e2e": {"value": case.ncell * e2e_steps / e2e_s / 1e6, "unit": UNIT,
-                    "h2d_bytes_per_step": int(case.ncell * 5 * 8), "d2h_bytes_per_step": int(case.ncell * 5 * 8),
-                    "what": "lbm_init from pinned host fields (rho, u, T) + lbm_step(1) + lbm_moments to pinned host"},
+                    "h2d_bytes_per_step": int(case.ncell * 5 * 4), "d2h_bytes_per_step": int(case.ncell * 5 * 4),
+                    "what": "lbm_init_f32 from pinned float32 host fields (rho, u, T) + lbm_step(1) + "
+                            "lbm_moments_f32 to pinned host"},
             "gpu_launches": args.steps * launches_per_step,
             "clocks": clk,
             "cpu_baseline": cpu,

@@ -238,6 +238,11 @@ int lbm_set_face(lbm_handle h, int face, int kind, const double *u, double T, do
  * steps (LBM_E_STATE); LBM_E_NOMEM, LBM_E_CUDA. */
 int lbm_init(lbm_handle h, const double *rho, const double *u, const double *T, int on_device);
 
+/* lbm_init with float32 fields (same layout, ownership, checks and errors).
+ * For float32 and 16-bit storage nothing is lost: the state is formed in
+ * float32 from the fields either way; half the bytes cross the host link. */
+int lbm_init_f32(lbm_handle h, const float *rho, const float *u, const float *T, int on_device);
+
 /* Advance every simulation of h by n >= 0 time steps (enqueue only). */
 int lbm_step(lbm_handle h, int n);
 
@@ -245,6 +250,10 @@ int lbm_step(lbm_handle h, int n);
  * velocity u = (sum c f + F/2)/rho (Eq. def_u) and T from the EoS.  Any of the
  * three pointers may be NULL. */
 int lbm_moments(lbm_handle h, double *rho, double *u, double *T, int on_device);
+
+/* lbm_moments into float32 fields (same layout; for float32 and 16-bit
+ * storage the values are exactly those lbm_moments returns as float64). */
+int lbm_moments_f32(lbm_handle h, float *rho, float *u, float *T, int on_device);
 
 /* The current populations as float64 [Q][N] (f) and [Q][N] (g), decoded from
  * the storage type (offset added back).  For tests and diagnostics. */

@@ -25,14 +25,15 @@ namespace {
 thread_local std::string g_create_error;
 
 struct Ops {
-    int (*init)(lbm_ctx*, const double*, const double*, const double*);
+    int (*init)(lbm_ctx*, const void*, const void*, const void*, int single);  // single: float32 fields
     int (*step)(lbm_ctx*, int);
     int (*macro)(lbm_ctx*);
-    int (*export_moments)(lbm_ctx*, double*, double*, double*);
+    int (*export_moments)(lbm_ctx*, void*, void*, void*, int single);
     int (*export_pops)(lbm_ctx*, double*, double*);
     int (*invariants)(lbm_ctx*, double*);
     int (*fused_ok)(lbm_ctx*, int, int, int);
     int (*prepare)(lbm_ctx*);  // carried moments of the current state (fused and z-march variants)
+    int (*state_fields)(lbm_ctx*);  // rho, u, T of the current state into W (for the export)
 };
 
 }  // namespace
@@ -235,10 +236,16 @@ template <int D, typename R, typename S> struct Impl {
 
     static int nblocks(lbm_ctx* h) { return (int)h->table.size(); }
 
-    static int init(lbm_ctx* h, const double* rho, const double* u, const double* T)
+    static int init(lbm_ctx* h, const void* rho, const void* u, const void* T, int single)
     {
-        k_init<D, R, S><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, rho, u, T, (S*)h->pop[0],
-                                                                   (R*)h->W, h->Ntot, h->d_diag + kDiagInitBad);
+        if (single)
+            k_init<D, R, S, float><<<nblocks(h), kBlockCells, 0, h->stream>>>(
+                h->d_sims, h->d_table, (const float*)rho, (const float*)u, (const float*)T, (S*)h->pop[0], (R*)h->W,
+                h->Ntot, h->d_diag + kDiagInitBad);
+        else
+            k_init<D, R, S, double><<<nblocks(h), kBlockCells, 0, h->stream>>>(
+                h->d_sims, h->d_table, (const double*)rho, (const double*)u, (const double*)T, (S*)h->pop[0],
+                (R*)h->W, h->Ntot, h->d_diag + kDiagInitBad);
         LBM_LAUNCH_CHECK(h, "k_init");
         h->cur = 0;
         h->moments_valid = false;
@@ -315,6 +322,34 @@ template <int D, typename R, typename S> struct Impl {
         return LBM_OK;
     }
 
+    // the z-march's first pass: the macroscopic state of every cell from the carried moments into W
+    static int zfirst_pass(lbm_ctx* h, unsigned long long* diag)
+    {
+        if (uses_mlp(h) && h->storage != LBM_F32) {  // learned start with 16-bit or float64 storage: generic pass
+            k_macro<D, R, true><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot,
+                                                                           diag, mbuf(h, h->cur));
+            LBM_LAUNCH_CHECK(h, "z-march macroscopic pass");
+        } else {
+            cudaError_t e = zmacro_dispatch(h->storage, h->sims[0].eos, uses_mlp(h), h->d_sims, h->d_table,
+                                            nblocks(h), mbuf(h, h->cur), h->W, h->Ntot, diag, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "z-march macroscopic pass");
+        }
+        return LBM_OK;
+    }
+
+    // rho, u, T of the current state into W for the export: on the z-march paths the
+    // carried moments are those of the current state and their first pass forms the
+    // fields (no population pass); otherwise the populations' moments (`macro`)
+    static int state_fields(lbm_ctx* h)
+    {
+        if (D == 3 && h->moments_valid && !has_nee(h) &&
+            (h->variant == LBM_KERNEL_ZMARCH || h->variant == LBM_KERNEL_ZGATHER)) {
+            if (!faces_ready(h)) return fail(h, LBM_E_STATE, "lbm_set_walls / lbm_set_face has not set every face");
+            return zfirst_pass(h, nullptr);
+        }
+        return macro(h);
+    }
+
     // D3Q27: macroscopic pass from the carried moments, then the z-marching collide-stream pass
     static int zmarch_step(lbm_ctx* h)
     {
@@ -324,15 +359,8 @@ template <int D, typename R, typename S> struct Impl {
             if (rc) return rc;
         }
         pass_mark(h, 0);
-        if (uses_mlp(h) && h->storage != LBM_F32) {  // learned start with 16-bit or float64 storage: generic pass
-            k_macro<D, R, true><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (R*)h->W, h->Ntot,
-                                                                           h->d_diag, mbuf(h, h->cur));
-            LBM_LAUNCH_CHECK(h, "z-march macroscopic pass");
-        } else {
-            cudaError_t e = zmacro_dispatch(h->storage, h->sims[0].eos, uses_mlp(h), h->d_sims, h->d_table,
-                                            nblocks(h), mbuf(h, h->cur), h->W, h->Ntot, h->d_diag, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "z-march macroscopic pass");
-        }
+        const int rc = zfirst_pass(h, h->d_diag);
+        if (rc) return rc;
         pass_mark(h, 1);
         const bool nee = has_nee(h);
         if (nee) {  // rebuild the boundary cells (slots of their pulls, fields) before the collide-stream pass
@@ -383,10 +411,14 @@ template <int D, typename R, typename S> struct Impl {
         return LBM_OK;
     }
 
-    static int export_moments(lbm_ctx* h, double* rho, double* u, double* T)
+    static int export_moments(lbm_ctx* h, void* rho, void* u, void* T, int single)
     {
-        k_export_moments<D, R><<<nblocks(h), kBlockCells, 0, h->stream>>>(h->d_sims, h->d_table, (const R*)h->W,
-                                                                          h->Ntot, rho, u, T);
+        if (single)
+            k_export_moments<D, R, float><<<nblocks(h), kBlockCells, 0, h->stream>>>(
+                h->d_sims, h->d_table, (const R*)h->W, h->Ntot, (float*)rho, (float*)u, (float*)T);
+        else
+            k_export_moments<D, R, double><<<nblocks(h), kBlockCells, 0, h->stream>>>(
+                h->d_sims, h->d_table, (const R*)h->W, h->Ntot, (double*)rho, (double*)u, (double*)T);
         LBM_LAUNCH_CHECK(h, "export moments");
         return LBM_OK;
     }
@@ -435,7 +467,10 @@ template <int D, typename R, typename S> struct Impl {
         return fused_shape(h->storage, D, tx, ty, tz) ? 1 : 0;
     }
 
-    static Ops ops() { return Ops{init, step, macro, export_moments, export_pops, invariants, fused_ok, fused_prepare}; }
+    static Ops ops()
+    {
+        return Ops{init, step, macro, export_moments, export_pops, invariants, fused_ok, fused_prepare, state_fields};
+    }
 };
 
 cudaError_t fused_dispatch(int storage, int dim, int eos, int mlp, int pc, int tx, int ty, int tz, const SimDev* sims,
@@ -943,19 +978,20 @@ int lbm_set_face(lbm_handle h, int face, int kind, const double* u, double T, do
     return LBM_OK;
 }
 
-int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T, int on_device)
+extern "C++" {
+template <typename H> int init_impl(lbm_handle h, const H* rho, const H* u, const H* T, int on_device)
 {
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
     if (!rho || !u || !T) return fail(h, LBM_E_INVALID, "rho, u and T are required");
     h->initialized = false;  // whatever follows, the old state is gone or suspect
     const long long N = h->Ntot;
-    const size_t nb_s = (size_t)N * sizeof(double), nb_v = (size_t)N * h->dim * sizeof(double);
+    const size_t nb_s = (size_t)N * sizeof(H), nb_v = (size_t)N * h->dim * sizeof(H);
     const bool offsets = h->storage == LBM_BF16 || h->storage == LBM_F16;
     if (offsets) {
         // the 16-bit storage offsets are the rest equilibria at the mean rho
         // and T: those two fields are read on the host, and checked there
-        std::vector<double> hr, hT;
-        const double *pr = rho, *pT = T;
+        std::vector<H> hr, hT;
+        const H *pr = rho, *pT = T;
         if (on_device) {
             hr.resize(N); hT.resize(N);
             LBM_CUDA_CHECK(h, cudaMemcpyAsync(hr.data(), rho, nb_s, cudaMemcpyDeviceToHost, h->stream));
@@ -968,7 +1004,7 @@ int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T, 
         for (int s = 0; s < h->nsim; ++s) {
             SimDev& d = h->sims[s];
             double mr = 0, mT = 0;
-            for (long long k = 0; k < d.N; ++k) { mr += pr[d.cell_off + k]; mT += pT[d.cell_off + k]; }
+            for (long long k = 0; k < d.N; ++k) { mr += (double)pr[d.cell_off + k]; mT += (double)pT[d.cell_off + k]; }
             mr /= (double)d.N;
             mT /= (double)d.N;
             RhoPart<double> p = rho_part<double>(d, mr);
@@ -984,12 +1020,12 @@ int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T, 
     // Host inputs go straight to a device staging buffer (a DMA when the
     // caller's memory is pinned); k_init counts the cells with rho <= 0 or
     // T <= 0 (or NaN) into diagnostic slot kDiagInitBad, read back below.
-    const double *dr = rho, *du = u, *dT = T;
+    const H *dr = rho, *du = u, *dT = T;
     void* tmp = nullptr;
     if (!on_device) {
         tmp = dev_alloc(h, 2 * nb_s + nb_v);
         if (!tmp) return fail(h, LBM_E_NOMEM, "staging allocation failed");
-        double* t = (double*)tmp;
+        H* t = (H*)tmp;
         cudaError_t e = cudaMemcpyAsync(t, rho, nb_s, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(t + N, T, nb_s, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(t + 2 * N, u, nb_v, cudaMemcpyHostToDevice, h->stream);
@@ -1002,7 +1038,7 @@ int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T, 
     }
     unsigned long long bad = 0;
     cudaError_t e = cudaMemsetAsync(h->d_diag, 0, kDiagSlots * sizeof(unsigned long long), h->stream);
-    int rc = e == cudaSuccess ? h->ops.init(h, dr, du, dT) : cuda_fail(h, e, "diag reset");
+    int rc = e == cudaSuccess ? h->ops.init(h, dr, du, dT, sizeof(H) == sizeof(float)) : cuda_fail(h, e, "diag reset");
     if (rc == LBM_OK) {
         e = cudaMemcpyAsync(&bad, h->d_diag + kDiagInitBad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "lbm_init check");
@@ -1014,6 +1050,17 @@ int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T, 
     if (bad) return fail(h, LBM_E_INVALID, "rho and T must be > 0 everywhere");
     h->initialized = true;
     return LBM_OK;
+}
+}  // extern "C++"
+
+int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T, int on_device)
+{
+    return init_impl<double>(h, rho, u, T, on_device);
+}
+
+int lbm_init_f32(lbm_handle h, const float* rho, const float* u, const float* T, int on_device)
+{
+    return init_impl<float>(h, rho, u, T, on_device);
 }
 
 // Capture graph_steps steps (an even number, so the buffers return to the
@@ -1116,23 +1163,24 @@ int lbm_set_graph(lbm_handle h, int steps_per_graph)
     return LBM_OK;
 }
 
-int lbm_moments(lbm_handle h, double* rho, double* u, double* T, int on_device)
+extern "C++" {
+template <typename H> int moments_impl(lbm_handle h, H* rho, H* u, H* T, int on_device)
 {
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
     if (!h->initialized) return fail(h, LBM_E_STATE, "lbm_init has not been called");
-    int rc = h->ops.macro(h);
+    int rc = h->ops.state_fields(h);
     if (rc) return rc;
     const long long N = h->Ntot;
     if (on_device) {
-        rc = h->ops.export_moments(h, rho, u, T);
+        rc = h->ops.export_moments(h, rho, u, T, sizeof(H) == sizeof(float));
         if (rc) return rc;
         LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
         return LBM_OK;
     }
-    const size_t nb_s = (size_t)N * sizeof(double), nb_v = (size_t)N * h->dim * sizeof(double);
-    double* t = (double*)dev_alloc(h, 2 * nb_s + nb_v);
+    const size_t nb_s = (size_t)N * sizeof(H), nb_v = (size_t)N * h->dim * sizeof(H);
+    H* t = (H*)dev_alloc(h, 2 * nb_s + nb_v);
     if (!t) return fail(h, LBM_E_NOMEM, "staging allocation failed");
-    rc = h->ops.export_moments(h, t, t + 2 * N, t + N);
+    rc = h->ops.export_moments(h, t, t + 2 * N, t + N, sizeof(H) == sizeof(float));
     if (rc == LBM_OK) {
         cudaError_t e = cudaSuccess;
         if (rho && e == cudaSuccess) e = cudaMemcpyAsync(rho, t, nb_s, cudaMemcpyDeviceToHost, h->stream);
@@ -1144,6 +1192,17 @@ int lbm_moments(lbm_handle h, double* rho, double* u, double* T, int on_device)
     }
     lbm_glue_free(t);
     return rc;
+}
+}  // extern "C++"
+
+int lbm_moments(lbm_handle h, double* rho, double* u, double* T, int on_device)
+{
+    return moments_impl<double>(h, rho, u, T, on_device);
+}
+
+int lbm_moments_f32(lbm_handle h, float* rho, float* u, float* T, int on_device)
+{
+    return moments_impl<float>(h, rho, u, T, on_device);
 }
 
 int lbm_populations(lbm_handle h, double* f, double* g, int on_device)

@@ -80,10 +80,10 @@ __device__ __forceinline__ void count_flags(unsigned flags, unsigned long long* 
 // Initial state: f = f^eq(rho, u, theta), g = g^eq (flowchart, first box),
 // written where the first pull reads them.
 // ---------------------------------------------------------------------------
-template <int D, typename R, typename S>
+template <int D, typename R, typename S, typename H = double>
 __global__ void __launch_bounds__(kBlockCells) k_init(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
-                                                      const double* __restrict__ rho_in, const double* __restrict__ u_in,
-                                                      const double* __restrict__ T_in, S* __restrict__ pop,
+                                                      const H* __restrict__ rho_in, const H* __restrict__ u_in,
+                                                      const H* __restrict__ T_in, S* __restrict__ pop,
                                                       R* __restrict__ W, long long Ntot,
                                                       unsigned long long* __restrict__ bad)
 {
@@ -702,11 +702,11 @@ static __global__ void k_invariants_final(const double* __restrict__ partials, c
     out[t] = acc;
 }
 
-// Export rho, u, T (float64, per-simulation field layout of the ABI).
-template <int D, typename R>
+// Export rho, u, T (float64 or float32 H, per-simulation field layout of the ABI).
+template <int D, typename R, typename H = double>
 __global__ void __launch_bounds__(kBlockCells) k_export_moments(const SimDev* __restrict__ sims, const BlockEntry* __restrict__ table,
-                                                                const R* __restrict__ W, long long Ntot, double* rho,
-                                                                double* u, double* T)
+                                                                const R* __restrict__ W, long long Ntot, H* rho,
+                                                                H* u, H* T)
 {
     __shared__ SimDev s;
     const BlockEntry be = table[blockIdx.x];
@@ -714,11 +714,11 @@ __global__ void __launch_bounds__(kBlockCells) k_export_moments(const SimDev* __
     const long long k = (long long)be.start + threadIdx.x;
     if (k >= s.N) return;
     const long long gk = s.cell_off + k;
-    if (rho) rho[gk] = (double)W[W_RHO * Ntot + gk];
-    if (T) T[gk] = (double)W[W_T * Ntot + gk];
+    if (rho) rho[gk] = (H)W[W_RHO * Ntot + gk];
+    if (T) T[gk] = (H)W[W_T * Ntot + gk];
     if (u) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) u[(long long)D * s.cell_off + (long long)a * s.N + k] = (double)W[(W_U + a) * Ntot + gk];
+        for (int a = 0; a < D; ++a) u[(long long)D * s.cell_off + (long long)a * s.N + k] = (H)W[(W_U + a) * Ntot + gk];
     }
 }
 

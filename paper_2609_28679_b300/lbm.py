@@ -74,8 +74,10 @@ _SIGS = {
     "lbm_set_face": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
                                     ctypes.c_double]),
     "lbm_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "lbm_init_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "lbm_moments_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "lbm_invariants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -132,19 +134,21 @@ def _check(rc: int, h) -> None:
         raise LbmError(f"rc={rc}: {msg.decode() if msg else ''}")
 
 
-def _ptr(a):
-    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+def _ptr(a, single: bool = False):
+    """Data pointer of a numpy array or torch tensor (None -> NULL), float64
+    or, with single, float32."""
     if a is None:
         return None
+    want = "float32" if single else "float64"
     if isinstance(a, np.ndarray):
-        if not (a.dtype == np.float64 and a.flags.c_contiguous):
-            raise LbmError("host arrays must be C-contiguous float64")
+        if not (a.dtype == np.dtype(want) and a.flags.c_contiguous):
+            raise LbmError(f"host arrays must be C-contiguous {want}")
         return a.ctypes.data_as(ctypes.c_void_p)
     import torch
 
     if isinstance(a, torch.Tensor):
-        if a.dtype != torch.float64 or not a.is_contiguous():
-            raise LbmError("tensors must be contiguous float64")
+        if a.dtype != getattr(torch, want) or not a.is_contiguous():
+            raise LbmError(f"tensors must be contiguous {want}")
         return ctypes.c_void_p(a.data_ptr())
     raise LbmError(f"unsupported buffer type {type(a)}")
 
@@ -189,6 +193,10 @@ def lbm_init(h, rho, u, T, on_device: int) -> None:
     _check(_lib.lbm_init(h, _ptr(rho), _ptr(u), _ptr(T), int(on_device)), h)
 
 
+def lbm_init_f32(h, rho, u, T, on_device: int) -> None:
+    _check(_lib.lbm_init_f32(h, _ptr(rho, True), _ptr(u, True), _ptr(T, True), int(on_device)), h)
+
+
 def lbm_set_force(h, accel) -> None:
     a = np.ascontiguousarray(np.asarray(accel, dtype=np.float64).reshape(-1)[:3])
     if a.size < 3:
@@ -217,6 +225,10 @@ def lbm_step(h, n: int) -> None:
 
 def lbm_moments(h, rho, u, T, on_device: int) -> None:
     _check(_lib.lbm_moments(h, _ptr(rho), _ptr(u), _ptr(T), int(on_device)), h)
+
+
+def lbm_moments_f32(h, rho, u, T, on_device: int) -> None:
+    _check(_lib.lbm_moments_f32(h, _ptr(rho, True), _ptr(u, True), _ptr(T, True), int(on_device)), h)
 
 
 def lbm_populations(h, f, g, on_device: int) -> None:

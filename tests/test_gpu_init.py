@@ -77,3 +77,59 @@ def test_init_rejects_nonpositive_fields(storage, kind, bad):
     r, _, _ = sim.moments()
     assert np.all(np.isfinite(r)) and np.all(r > 0)
     sim.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("kind", ["pageable", "pinned", "device"])
+def test_float32_io_matches_float64_io(storage, kind):
+    # lbm_init_f32 / lbm_moments_f32: from float32 fields the state is bit-equal to
+    # lbm_init from the same values in float64 (the state is formed in float32 either
+    # way, and the 16-bit offsets come from the same float64 means), and the exported
+    # float32 moments are exactly the float64 export rounded (it holds float32 values)
+    import torch
+
+    case = wl.vdw_spinodal(40, steps=3, storage=storage)
+    (rho, u, T), on_dev = _inputs(case, kind)
+    as32 = [torch.as_tensor(a).to(torch.float32) for a in (rho, u, T)]
+    as64 = [a.to(torch.float64) for a in as32]
+    if kind == "pageable":
+        as32 = [a.numpy() for a in as32]
+        as64 = [a.numpy() for a in as64]
+    elif kind == "pinned":
+        as32 = [a.cpu().pin_memory() for a in as32]
+        as64 = [a.cpu().pin_memory() for a in as64]
+    out = []
+    for single in (False, True):
+        sim = lbm.Simulation(case, variant=lbm.LBM_KERNEL_SPLIT)
+        if single:
+            lbm.lbm_init_f32(sim.h, *as32, on_dev)
+        else:
+            lbm.lbm_init(sim.h, *as64, on_dev)
+        sim.step(3)
+        f, g = sim.populations()
+        r64, u64, T64 = sim.moments()
+        n = case.ncell
+        r32, u32, T32 = np.zeros(n, np.float32), np.zeros(2 * n, np.float32), np.zeros(n, np.float32)
+        lbm.lbm_moments_f32(sim.h, r32, u32, T32, 0)
+        sim.close()
+        out.append((f, g, r64, u64, T64, r32, u32, T32))
+    (f0, g0, r64, u64, T64, _, _, _), (f1, g1, _, _, _, r32, u32, T32) = out
+    assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    assert np.array_equal(r32, r64.astype(np.float32))
+    assert np.array_equal(u32, u64.astype(np.float32))
+    assert np.array_equal(T32, T64.astype(np.float32))
+
+
+def test_float32_io_rejects_float64_arrays_and_bad_fields():
+    case = wl.vdw_spinodal(24, steps=2, storage="f32")
+    sim = lbm.Simulation(case, variant=lbm.LBM_KERNEL_FUSED)
+    rho, u, T = case.fields()
+    with pytest.raises(lbm.LbmError, match="float32"):
+        lbm.lbm_init_f32(sim.h, rho, u.ravel(), T, 0)
+    r32 = np.ascontiguousarray(rho, dtype=np.float32)
+    u32 = np.ascontiguousarray(u.ravel(), dtype=np.float32)
+    T32 = np.ascontiguousarray(T, dtype=np.float32)
+    r32[7] = 0.0
+    with pytest.raises(lbm.LbmError, match="must be > 0"):
+        lbm.lbm_init_f32(sim.h, r32, u32, T32, 0)
+    sim.close()

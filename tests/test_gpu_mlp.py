@@ -166,13 +166,15 @@ def test_learned_start_f32_matches_newton_run(variant):
 
 def test_learned_start_against_the_warm_start_on_a_running_droplet():
     # What the trained network gains, measured on the states a time step meets:
-    # float64 Newton iterations (the oracle's solver, 1e-14) to T(rho, e) of
-    # step n+1 from the method's own start (T of step n), from the network's
-    # T_hat, and from Tc (the start with no carried temperature: the first
-    # step after initialisation).  Measured here: the carried T needs fewer
-    # iterations than T_hat (the network is accurate to ~1e-3, the step
-    # changes T by far less), T_hat fewer than Tc.  The network pays only
-    # where no temperature is carried.
+    # the relative error of each start of the temperature inversion of step n+1 --
+    # the method's own start (T of step n), the network's T_hat, Tc (the start with
+    # no carried temperature: the first step after initialisation) -- and the float64
+    # Newton iterations (the oracle's solver, 1e-14) from each.  Measured: the
+    # carried T is off by 2.8e-4 (median), T_hat by 6.7e-4 to 8.8e-4 (trainings
+    # differ: their bf16 reductions sum in varying order), Tc by 0.11; in iterations
+    # to 1e-14 the warm and learned starts are within a few cells in a thousand of
+    # each other (2.998 against 3.004-3.008), so only the learned start's gain over Tc
+    # is asserted there.  The network pays only where no temperature is carried.
     c, eos = _pr()
     case = wl.pr_droplet(n=24, radius=6.0, storage="f64")
     sim = lbm.Simulation(case)
@@ -182,13 +184,18 @@ def test_learned_start_against_the_warm_start_on_a_running_droplet():
     sim.step(1)
     rho, u, T1 = sim.moments()
     sim.close()
-    u = u.reshape(3, -1)
     sel = np.arange(0, rho.size, 7)  # a sample of the cells: liquid, interface, vapour
     e1 = np.array([eos.e(r, t) for r, t in zip(rho[sel], T1[sel])])
     That = lbm.lbm_mlp_predict(_trained_params(), rho[sel], e1)
+    Tc = c.Tc  # the start with no carried temperature
+    err_warm = np.median(np.abs(T0[sel] - T1[sel]) / T1[sel])
+    err_mlp = np.median(np.abs(That - T1[sel]) / T1[sel])
+    err_cold = np.median(np.abs(Tc - T1[sel]) / T1[sel])
     it_warm = np.array([eos.T(r, ee, t0)[1] for r, ee, t0 in zip(rho[sel], e1, T0[sel])])
     it_mlp = np.array([eos.T(r, ee, t)[1] for r, ee, t in zip(rho[sel], e1, That)])
     it_cold = np.array([eos.T(r, ee, 0.0)[1] for r, ee in zip(rho[sel], e1)])
-    msg = f"mean Newton iterations: warm {it_warm.mean():.2f}, learned {it_mlp.mean():.2f}, cold {it_cold.mean():.2f}"
-    assert it_warm.mean() < it_mlp.mean() < it_cold.mean(), msg
-    assert np.max(it_mlp) <= np.max(it_cold), msg
+    msg = (f"median start error: warm {err_warm:.2e}, learned {err_mlp:.2e}, cold {err_cold:.2e}; "
+           f"mean Newton iterations: warm {it_warm.mean():.3f}, learned {it_mlp.mean():.3f}, cold {it_cold.mean():.3f}")
+    assert 1.5 * err_warm < err_mlp < err_cold / 50, msg
+    assert it_mlp.mean() < it_cold.mean() and np.max(it_mlp) <= np.max(it_cold), msg
+    assert it_warm.mean() < it_cold.mean(), msg
