@@ -238,13 +238,15 @@ __global__ void __launch_bounds__(kYmThreads, (ymarch_min_blocks<S, PC>()))
                 // the row below it has received everything: its moments and the Newton guess
                 const int fr = cq - 1;
                 if (own_x && fr >= y0 && fr < y0 + vy) {
-                    const unsigned kk = (unsigned)xm + (unsigned)nx * (unsigned)fr;
-                    Mo[M_RHO * Ntot + kk] = acc[0][0];
-                    Mo[M_J * Ntot + kk] = acc[0][1];
-                    Mo[(M_J + 1) * Ntot + kk] = acc[0][2];
-                    Mo[(M_J + 2) * Ntot + kk] = R(0);
-                    Mo[M_G * Ntot + kk] = acc[0][3];
-                    Mo[M_T * Ntot + kk] = Tq2;
+                    // the carried fields rho, j (3), G, T in order, Ntot apart
+                    static_assert(M_RHO == 0 && M_J == 1 && M_G == 4 && M_T == 5, "carried field order");
+                    R* pm = Mo + ((unsigned)xm + (unsigned)nx * (unsigned)fr);
+                    *pm = acc[0][0];
+                    *(pm += Ntot) = acc[0][1];
+                    *(pm += Ntot) = acc[0][2];
+                    *(pm += Ntot) = R(0);
+                    *(pm += Ntot) = acc[0][3];
+                    *(pm += Ntot) = Tq2;
                 }
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
@@ -363,13 +365,14 @@ __global__ void __launch_bounds__(kYmThreads, (ymarch_min_blocks<S, PC>()))
                 }
                 collide_cell<2, R>(s, m, divu, gh, gT, Phi, f, g);
                 if (own_x && Cr >= y0 && Cr < y0 + vy) {
-                    const unsigned self = (unsigned)xm + (unsigned)nx * (unsigned)Cr;
+                    // one pointer per cell, advanced by N from population to population
+                    S* po = fo + ((unsigned)xm + (unsigned)nx * (unsigned)Cr);
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        Codec<S, R>::st(fo + (unsigned)i * Ncell + self, f[i] - (Codec<S, R>::offset ? s.fref[i] : R(0)));
-                        Codec<S, R>::st(fo + (unsigned)(9 + i) * Ncell + self,
-                                        g[i] - (Codec<S, R>::offset ? s.gref[i] : R(0)));
-                    }
+                    for (int i = 0; i < 9; ++i, po += Ncell)
+                        Codec<S, R>::st(po, f[i] - (Codec<S, R>::offset ? s.fref[i] : R(0)));
+#pragma unroll
+                    for (int i = 0; i < 9; ++i, po += Ncell)
+                        Codec<S, R>::st(po, g[i] - (Codec<S, R>::offset ? s.gref[i] : R(0)));
                 }
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
