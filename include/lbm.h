@@ -280,7 +280,10 @@ int lbm_diagnostics(lbm_handle h, long long out[4]);
  * (0: default); ZGATHER has the xy tile 30 x 14 (tx, ty 0 or 30, 14) and
  * takes tz as its number of planes; YMARCH (2-D only) has strips of 124
  * columns (every simulation with the central Phi) or 122, tx 0 or that width,
- * and takes ty as the rows each CTA marches through (0: 64).  Errors:
+ * and takes ty as the rows each CTA marches through (0: the row count that
+ * lets the device's resident CTAs take the strips' ranges in the fewest
+ * rounds of (rows + pipeline fill), at least 32; also the automatic choice
+ * for 2-D lattices of 4 M cells and more).  Errors:
  * LBM_E_INVALID for a tile the variant cannot run, LBM_E_UNSUPPORTED for a
  * lattice or boundary set it does not run. */
 int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz);

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/lbm.h: argument checking,
 // device buffers (through PyTorch's caching allocator), simulation tables and
 // kernel launches on the handle's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -226,6 +227,7 @@ cudaError_t zgather_dispatch(int storage, int eos, int zl, const SimDev* sims, c
 cudaError_t ymarch_dispatch(int storage, int eos, int pc, int yl, const SimDev* sims, const TileEntry* tiles,
                             int ntiles, const void* src, void* dst, const void* Min, void* Mout, long long Ntot,
                             unsigned long long* diag, cudaStream_t stream);
+int ymarch_rows(const lbm_ctx* h);
 
 // ---------------------------------------------------------------------------
 // Typed implementation of every operation for one (D, arithmetic, storage).
@@ -545,6 +547,57 @@ cudaError_t ymarch_dispatch(int storage, int eos, int pc, int yl, const SimDev* 
     return cudaErrorInvalidValue;
 }
 
+cudaError_t ymarch_slots(int storage, int eos, int pc, int* slots)
+{
+    switch (storage) {
+    case LBM_F32: return ymarch_slots_f32(eos, pc, slots);
+    case LBM_BF16: return ymarch_slots_bf16(eos, pc, slots);
+    case LBM_F16: return ymarch_slots_f16(eos, pc, slots);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Rows per range of the row march.  A range of YL rows takes YL + 2 RM + 8
+// steps (the pipeline fills and drains over the rim and stencil rows; RM = 1
+// for the central Phi, 2 upwind-biased).  The tile table lists the ranges
+// longest first and the resident CTAs take them round-robin, one per CTA per
+// round, so the first CTA carries the longest range of every round and the
+// step lasts the sum of those.  The row count YL = ceil(ny / n) that
+// minimises this sum is taken, no shorter than 32 rows and with at most 16
+// rounds (shorter ranges re-read their halo rows for a growing share of the
+// bytes and add fill steps); ties go to the longer ranges.
+int ymarch_rows(const lbm_ctx* h)
+{
+    const int strip = ymarch_strip_width(h);
+    const int pc = strip == kYmStripCentral;
+    int slots = 0;
+    if (ymarch_slots(h->storage, h->sims[0].eos, pc, &slots) != cudaSuccess || slots < 1) return 64;
+    const int ovh = pc ? 10 : 12;
+    int ny_max = 1;
+    for (const SimDev& d : h->sims) ny_max = d.ny > ny_max ? d.ny : ny_max;
+    long long best = -1;
+    int pick = 64, prev = 0;
+    std::vector<int> cost;
+    for (int n = 1; n <= ny_max; ++n) {
+        const int yl = (ny_max + n - 1) / n;
+        if (n > 1 && yl < 32) break;
+        if (yl == prev) continue;  // the same row count as fewer ranges
+        prev = yl;
+        cost.clear();
+        for (const SimDev& d : h->sims) {
+            const int nstrip = (d.nx + strip - 1) / strip;
+            for (int y0 = 0; y0 < d.ny; y0 += yl) cost.insert(cost.end(), nstrip, std::min(yl, d.ny - y0) + ovh);
+        }
+        if (n > 1 && cost.size() > (size_t)16 * slots) break;
+        std::sort(cost.begin(), cost.end(), [](int a, int b) { return a > b; });
+        const size_t G = std::min(cost.size(), (size_t)slots);
+        long long t = 0;
+        for (size_t k = 0; k < cost.size(); k += G) t += cost[k];
+        if (best < 0 || t < best) { best = t; pick = yl; }
+    }
+    return pick;
+}
+
 cudaError_t zgather_dispatch(int storage, int eos, int zl, const SimDev* sims, const TileEntry* tiles, int ntiles,
                              const void* src, void* dst, const void* W, void* Mout, long long Ntot,
                              cudaStream_t stream)
@@ -709,7 +762,9 @@ int upload_sims(lbm_ctx* h)
     return LBM_OK;
 }
 
-int build_tiles(lbm_ctx* h, int tx, int ty, int tz)
+// rows_first: the row march's order, ranges with the most rows first (its
+// tiles are independent within a step, so only the schedule changes)
+int build_tiles(lbm_ctx* h, int tx, int ty, int tz, bool rows_first = false)
 {
     h->tiles.clear();
     for (int s = 0; s < h->nsim; ++s) {
@@ -718,6 +773,11 @@ int build_tiles(lbm_ctx* h, int tx, int ty, int tz)
         for (int z0 = 0; z0 < d.nz; z0 += zt)
             for (int y0 = 0; y0 < d.ny; y0 += ty)
                 for (int x0 = 0; x0 < d.nx; x0 += tx) h->tiles.push_back(TileEntry{s, x0, y0, z0});
+    }
+    if (rows_first) {
+        auto rows = [&](const TileEntry& t) { return std::min(ty, h->sims[t.sim].ny - t.y0); };
+        std::stable_sort(h->tiles.begin(), h->tiles.end(),
+                         [&](const TileEntry& a, const TileEntry& b) { return rows(a) > rows(b); });
     }
     lbm_glue_free(h->d_tiles);
     h->d_tiles = (TileEntry*)dev_alloc(h, h->tiles.size() * sizeof(TileEntry));
@@ -832,10 +892,10 @@ int create_impl(int nsim, const lbm_lattice* L, const lbm_eos* E, const double* 
             h->tx = 30; h->ty = 14; h->tz = 32;
             rc = build_tiles(h, 30, 14, 32);
         } else if (ymarch_ok(h) && cells >= (1LL << 22)) {
-            // large 2-D lattices: enough strips x 64-row ranges to fill the GPU several times
+            // large 2-D lattices: the row march, ranges sized to the resident CTAs
             h->variant = LBM_KERNEL_YMARCH;
-            h->tx = ymarch_strip_width(h); h->ty = 64; h->tz = 1;
-            rc = build_tiles(h, h->tx, 64, 1);
+            h->tx = ymarch_strip_width(h); h->ty = ymarch_rows(h); h->tz = 1;
+            rc = build_tiles(h, h->tx, h->ty, 1, true);
         } else if (h->dim == 3 && same_eos && zmarch_ok(h, 30, 14)) {
             h->variant = LBM_KERNEL_ZMARCH;
             h->tx = 30; h->ty = 14; h->tz = 32;
@@ -1304,9 +1364,9 @@ int lbm_set_kernel(lbm_handle h, int variant, int tx, int ty, int tz)
                         "temperature or per-cell fields");
         const int strip = ymarch_strip_width(h);
         if (tx > 0 && tx != strip) return fail(h, LBM_E_INVALID, "the row-march kernel has a fixed strip width");
-        if (ty <= 0) ty = 64;
+        if (ty <= 0) ty = ymarch_rows(h);
         LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
-        int rc = build_tiles(h, strip, ty, 1);
+        int rc = build_tiles(h, strip, ty, 1, true);
         if (rc) return rc;
         h->variant = LBM_KERNEL_YMARCH;
         h->tx = strip; h->ty = ty; h->tz = 1;
@@ -1384,8 +1444,11 @@ int lbm_autotune(lbm_handle h, int trial_steps, int* variant, int* tx, int* ty, 
     if (h->dim == 2) {
         for (auto& t : shapes2)
             if (h->ops.fused_ok(h, t[0], t[1], t[2])) cands.push_back({LBM_KERNEL_FUSED, t[0], t[1], t[2]});
-        if (ymarch_ok(h))
+        if (ymarch_ok(h)) {
+            const int ym = ymarch_rows(h);
             for (int yl : {32, 64, 128}) cands.push_back({LBM_KERNEL_YMARCH, 0, yl, 1});
+            if (ym != 32 && ym != 64 && ym != 128) cands.push_back({LBM_KERNEL_YMARCH, 0, ym, 1});
+        }
     } else {
         for (auto& t : shapes3)
             if (h->ops.fused_ok(h, t[0], t[1], t[2])) cands.push_back({LBM_KERNEL_FUSED, t[0], t[1], t[2]});

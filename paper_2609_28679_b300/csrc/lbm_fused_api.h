@@ -57,7 +57,8 @@ constexpr int kYmStripCentral = 124, kYmStripUpwind = 122;
 #define LBM_YMARCH_DECL(SUF)                                                                                          \
     cudaError_t ymarch_dispatch_##SUF(int eos, int pc, int yl, const SimDev* sims, const TileEntry* tiles, int ntiles, \
                                       const void* src, void* dst, const void* Min, void* Mout, long long Ntot,         \
-                                      unsigned long long* diag, cudaStream_t stream);
+                                      unsigned long long* diag, cudaStream_t stream);                         \
+    cudaError_t ymarch_slots_##SUF(int eos, int pc, int* slots);
 LBM_YMARCH_DECL(f32)
 LBM_YMARCH_DECL(bf16)
 LBM_YMARCH_DECL(f16)

@@ -117,4 +117,8 @@ cudaError_t ymarch_dispatch_bf16(int eos, int pc, int yl, const SimDev* sims, co
 {
     return ymarch_dispatch_t<__nv_bfloat16>(eos, pc, yl, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
 }
+cudaError_t ymarch_slots_bf16(int eos, int pc, int* slots)
+{
+    return ymarch_slots_t<__nv_bfloat16>(eos, pc, slots);
+}
 }  // namespace lbm

@@ -146,4 +146,8 @@ cudaError_t ymarch_dispatch_f32(int eos, int pc, int yl, const SimDev* sims, con
 {
     return ymarch_dispatch_t<float>(eos, pc, yl, sims, tiles, ntiles, src, dst, Min, Mout, Ntot, diag, stream);
 }
+cudaError_t ymarch_slots_f32(int eos, int pc, int* slots)
+{
+    return ymarch_slots_t<float>(eos, pc, slots);
+}
 }  // namespace lbm

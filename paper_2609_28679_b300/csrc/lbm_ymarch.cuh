@@ -389,9 +389,9 @@ __global__ void __launch_bounds__(kYmThreads, (ymarch_min_blocks<S, PC>()))
     }
 }
 
+// CTAs of the row march resident on the whole device: the persistent grid
 template <typename S, int EK, bool PC>
-cudaError_t ymarch_launch(const SimDev* sims, const TileEntry* tiles, int ntiles, int YL, const void* src, void* dst,
-                          const void* Min, void* Mout, long long Ntot, unsigned long long* diag, cudaStream_t stream)
+cudaError_t ymarch_grid_cap(int& cap)
 {
     constexpr size_t smem = YmShape<S, PC>::smem_bytes;
     static_assert(smem <= 227u * 1024u, "row-march rings do not fit in shared memory");
@@ -407,6 +407,18 @@ cudaError_t ymarch_launch(const SimDev* sims, const TileEntry* tiles, int ntiles
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         grid_cap = per_sm * nsm;
     }
+    cap = grid_cap;
+    return cudaSuccess;
+}
+
+template <typename S, int EK, bool PC>
+cudaError_t ymarch_launch(const SimDev* sims, const TileEntry* tiles, int ntiles, int YL, const void* src, void* dst,
+                          const void* Min, void* Mout, long long Ntot, unsigned long long* diag, cudaStream_t stream)
+{
+    constexpr size_t smem = YmShape<S, PC>::smem_bytes;
+    int grid_cap = 0;
+    cudaError_t e = ymarch_grid_cap<S, EK, PC>(grid_cap);
+    if (e != cudaSuccess) return e;
     const int grid = ntiles < grid_cap ? ntiles : grid_cap;
     k_ymarch<S, EK, PC><<<grid, kYmThreads, smem, stream>>>(sims, tiles, ntiles, YL, (const S*)src, (S*)dst,
                                                            (const float*)Min, (float*)Mout, Ntot, diag);
@@ -429,6 +441,23 @@ cudaError_t ymarch_dispatch_t(int eos, int pc, int yl, const SimDev* sims, const
         if (eos == EOS_PR) LBM_YM(EOS_PR, false);
     }
 #undef LBM_YM
+    return cudaErrorInvalidValue;
+}
+
+template <typename S>
+cudaError_t ymarch_slots_t(int eos, int pc, int* slots)
+{
+#define LBM_YS(EK, P) return ymarch_grid_cap<S, EK, P>(*slots)
+    if (pc) {
+        if (eos == EOS_IDEAL) LBM_YS(EOS_IDEAL, true);
+        if (eos == EOS_VDW) LBM_YS(EOS_VDW, true);
+        if (eos == EOS_PR) LBM_YS(EOS_PR, true);
+    } else {
+        if (eos == EOS_IDEAL) LBM_YS(EOS_IDEAL, false);
+        if (eos == EOS_VDW) LBM_YS(EOS_VDW, false);
+        if (eos == EOS_PR) LBM_YS(EOS_PR, false);
+    }
+#undef LBM_YS
     return cudaErrorInvalidValue;
 }
 

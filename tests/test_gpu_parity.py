@@ -559,6 +559,34 @@ def test_ymarch_refuses_what_it_does_not_run():
         sim.close()
 
 
+def test_ymarch_range_length_and_order_leave_the_step_bit_identical():
+    # every owned cell's arithmetic is the same whichever range covers it: the
+    # default ranges (sized to the resident CTAs, longest first) and fixed ones
+    # give the same bits on a batch of ragged sizes
+    cases = [wl.vdw_spinodal(n=264, ny=37, storage="f32", seed=3), wl.vdw_spinodal(n=128, ny=96, storage="f32", seed=4),
+             wl.vdw_spinodal(n=16, ny=8, storage="f32", seed=5), wl.vdw_spinodal(n=500, ny=70, storage="f32", seed=6)]
+    out = {}
+    for yl in (0, 16, 64):
+        sim = lbm.Simulation(cases)
+        lbm.lbm_set_kernel(sim.h, YMARCH, 0, yl, 0)
+        k = sim.kernel()
+        assert k[0] == YMARCH
+        if yl == 0:
+            assert k[2] >= 32  # at least 32 rows (the tallest lattice has 96)
+        else:
+            assert k[2] == yl
+        sim.init()
+        sim.step(12)
+        out[yl] = (sim.populations(), sim.moments())
+        sim.close()
+    for yl in (16, 64):
+        (f0, g0), m0 = out[0]
+        (f1, g1), m1 = out[yl]
+        assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+        for a, b in zip(m0, m1):
+            assert np.array_equal(a, b)
+
+
 # ---------------------------------------------------------------------------
 # Edge cases
 # ---------------------------------------------------------------------------
