@@ -452,13 +452,38 @@ __device__ __forceinline__ void collide_cell(const C& s, const Macro<R>& m, R di
             gb[d] = s2 * (es * B0[0][d] + Hs[0][d]);
             gk[d] = s2 * B0[0][d];
         }
+        if constexpr (std::is_same<R, float>::value) {
+            // f_i and g_i side by side in two-wide float32 multiply-adds (the
+            // same products, sums and rounding as the scalar lines below)
+            const float2 c0 = make_float2(cf0, cg0);
+            float2 P1[3], P2[3], Q1[3], Q2[3];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int d0 = dig(i, 0), d1 = dig(i, 1);
-            f[i] = cf0 * f[i] + fa[d0] * A0[1][d1] + fs[d0] * As[1][d1];
-            R gi = cg0 * g[i] + ga[d0] * A0[1][d1] + gh0[d0] * H0[1][d1] + gb[d0] * B0[1][d1] + gk[d0] * Hs[1][d1];
-            if (cnorm2(i) == 1) gi += cc(i, 0) != 0 ? R(cc(i, 0)) * hq[0] : R(cc(i, 1)) * hq[1];
-            g[i] = gi;
+            for (int d = 0; d < 3; ++d) {
+                P1[d] = make_float2(fa[d], ga[d]);
+                P2[d] = make_float2(fs[d], gh0[d]);
+                Q1[d] = make_float2(A0[1][d], A0[1][d]);
+                Q2[d] = make_float2(As[1][d], H0[1][d]);
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int d0 = dig(i, 0), d1 = dig(i, 1);
+                float2 w = __fmul2_rn(c0, make_float2(f[i], g[i]));
+                w = __ffma2_rn(P1[d0], Q1[d1], w);
+                w = __ffma2_rn(P2[d0], Q2[d1], w);
+                f[i] = w.x;
+                R gi = w.y + gb[d0] * B0[1][d1] + gk[d0] * Hs[1][d1];
+                if (cnorm2(i) == 1) gi += cc(i, 0) != 0 ? R(cc(i, 0)) * hq[0] : R(cc(i, 1)) * hq[1];
+                g[i] = gi;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int d0 = dig(i, 0), d1 = dig(i, 1);
+                f[i] = cf0 * f[i] + fa[d0] * A0[1][d1] + fs[d0] * As[1][d1];
+                R gi = cg0 * g[i] + ga[d0] * A0[1][d1] + gh0[d0] * H0[1][d1] + gb[d0] * B0[1][d1] + gk[d0] * Hs[1][d1];
+                if (cnorm2(i) == 1) gi += cc(i, 0) != 0 ? R(cc(i, 0)) * hq[0] : R(cc(i, 1)) * hq[1];
+                g[i] = gi;
+            }
         }
     } else {
         // 3-D: per population (folding the xy products costs registers that the

@@ -68,6 +68,7 @@ __device__ __forceinline__ R heat_q(const C& s, int z)
 // 2: Newton cap, 3: learned temperature not accepted by the residual test).
 __device__ __forceinline__ void count_flags(unsigned flags, unsigned long long* diag)
 {
+    if (!__any_sync(0xffffffffu, flags != 0u)) return;  // the usual case: nothing to count in this warp
     const unsigned lane = threadIdx.x & 31u;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
