@@ -397,6 +397,26 @@ template <typename R> __host__ __device__ __forceinline__ void hpsi3(R u, R th, 
     o[2] = R(0.5) * (o2 - o1);
 }
 
+// psi3 and hpsi3 for two axes at once (two-wide float32 operations)
+__device__ __forceinline__ void psi3_x2(float2 xi, float2 zeta, float2* o)
+{
+    const float2 one = make_float2(1.f, 1.f), half = make_float2(0.5f, 0.5f), mone = make_float2(-1.f, -1.f);
+    o[0] = __ffma2_rn(mone, zeta, one);
+    o[1] = __fmul2_rn(half, __fadd2_rn(zeta, xi));
+    o[2] = __fmul2_rn(half, __ffma2_rn(mone, xi, zeta));
+}
+__device__ __forceinline__ void hpsi3_x2(float2 u, float2 th, float2* o)
+{
+    const float2 half = make_float2(0.5f, 0.5f), f25 = make_float2(2.5f, 2.5f), mone = make_float2(-1.f, -1.f);
+    const float2 u2 = __fmul2_rn(u, u);
+    const float2 hu2 = __fmul2_rn(half, u2);
+    const float2 o1 = __ffma2_rn(th, u, __fmul2_rn(hu2, u));
+    const float2 o2 = __ffma2_rn(th, th, __ffma2_rn(__fmul2_rn(f25, th), u2, __fmul2_rn(hu2, u2)));
+    o[0] = __ffma2_rn(mone, o2, hu2);
+    o[1] = __fmul2_rn(half, __fadd2_rn(o2, o1));
+    o[2] = __fmul2_rn(half, __ffma2_rn(mone, o1, o2));
+}
+
 // In the isothermal mode g is relaxed here all the same and never read: f's
 // collision takes nothing from g, and skipping it under a runtime test cost
 // the fused kernel more than the work it saved.
@@ -421,13 +441,35 @@ __device__ __forceinline__ void collide_cell(const C& s, const Macro<R>& m, R di
 
     // per-axis factors
     R A0[3][3], As[3][3], B0[3][3], H0[3][3], Hs[3][3];
+    if constexpr (D == 2 && std::is_same<R, float>::value) {
+        // the x and y factors side by side in two-wide float32 operations
+        const float2 u2v = make_float2(m.u[0], m.u[1]), usv = make_float2(us[0], us[1]);
+        const float2 thv = make_float2(m.theta, m.theta), tsv = make_float2(ths, ths);
+        const float2 phv = make_float2(Phi[0], Phi[1]);
+        float2 a0[3], as[3], b0[3], h0[3], hs[3];
+        const float2 zs = __ffma2_rn(usv, usv, tsv);
+        psi3_x2(u2v, __ffma2_rn(u2v, u2v, thv), a0);
+        psi3_x2(usv, __fadd2_rn(zs, phv), as);
+        psi3_x2(usv, zs, b0);
+        hpsi3_x2(u2v, thv, h0);
+        hpsi3_x2(usv, tsv, hs);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-        psi3<R>(m.u[a], m.theta + m.u[a] * m.u[a], A0[a]);              // f^eq, g^eq
-        psi3<R>(us[a], ths + us[a] * us[a] + Phi[a], As[a]);            // f*
-        psi3<R>(us[a], ths + us[a] * us[a], B0[a]);                     // g* (no Phi)
-        hpsi3<R>(m.u[a], m.theta, H0[a]);
-        hpsi3<R>(us[a], ths, Hs[a]);
+        for (int d = 0; d < 3; ++d) {
+            A0[0][d] = a0[d].x; A0[1][d] = a0[d].y;
+            As[0][d] = as[d].x; As[1][d] = as[d].y;
+            B0[0][d] = b0[d].x; B0[1][d] = b0[d].y;
+            H0[0][d] = h0[d].x; H0[1][d] = h0[d].y;
+            Hs[0][d] = hs[d].x; Hs[1][d] = hs[d].y;
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            psi3<R>(m.u[a], m.theta + m.u[a] * m.u[a], A0[a]);              // f^eq, g^eq
+            psi3<R>(us[a], ths + us[a] * us[a] + Phi[a], As[a]);            // f*
+            psi3<R>(us[a], ths + us[a] * us[a], B0[a]);                     // g* (no Phi)
+            hpsi3<R>(m.u[a], m.theta, H0[a]);
+            hpsi3<R>(us[a], ths, Hs[a]);
+        }
     }
     R bf = (R)s.beta_f, bg = (R)s.beta_g;
     if (s.mu > 0) bf = bg = relax_beta<R>(s, m.P);

@@ -323,6 +323,31 @@ template <typename R>
 __device__ __forceinline__ void grad_lap_zm(const R* __restrict__ rho, int x, int y, int z, int nx, int ny, int nz,
                                             bool mirror, R* gl)
 {
+    if (nx >= 4 && y >= 2 && y < ny - 2 && z >= 2 && z < nz - 2) {
+        // two or more cells from the y and z ends: the 25 densities at fixed offsets from
+        // the cell (x wrapped through its four offsets), summed as in the general case below
+        const int NX = nx, NP = nx * ny;
+        const R* c0 = rho + ((unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z));
+        const int xp = x + 1 < nx ? 1 : 1 - nx, xm = x > 0 ? -1 : nx - 1;
+        const int xpp = x + 2 < nx ? 2 : 2 - nx, xmm = x > 1 ? -2 : nx - 2;
+        auto lap7 = [&](int o, int oxp, int oxm, int oyp, int oym, int ozp, int ozm) {
+            const R c = c0[o];
+            R L = c0[oxp] - R(2) * c + c0[oxm];
+            L += c0[oyp] - R(2) * c + c0[oym];
+            L += c0[ozp] - R(2) * c + c0[ozm];
+            return L;
+        };
+        const R Lxp = lap7(xp, xpp, 0, xp + NX, xp - NX, xp + NP, xp - NP);
+        const R Lxm = lap7(xm, 0, xmm, xm + NX, xm - NX, xm + NP, xm - NP);
+        const R Lyp = lap7(NX, NX + xp, NX + xm, 2 * NX, 0, NX + NP, NX - NP);
+        const R Lym = lap7(-NX, -NX + xp, -NX + xm, 0, -2 * NX, -NX + NP, -NX - NP);
+        const R Lzp = lap7(NP, NP + xp, NP + xm, NP + NX, NP - NX, 2 * NP, 0);
+        const R Lzm = lap7(-NP, -NP + xp, -NP + xm, -NP + NX, -NP - NX, 0, -2 * NP);
+        gl[0] = R(0.5) * (Lxp - Lxm);
+        gl[1] = R(0.5) * (Lyp - Lym);
+        gl[2] = R(0.5) * (Lzp - Lzm);
+        return;
+    }
     auto at = [&](int xx, int yy, int zz) {
         return rho[(unsigned)xx + (unsigned)nx * ((unsigned)yy + (unsigned)ny * (unsigned)zz)];
     };
