@@ -378,9 +378,17 @@ __device__ __forceinline__ void grad_lap_zm(const R* __restrict__ rho, int x, in
 // Eq. correction) from the carried moments rho, j, G, with last step's T as
 // the Newton start (or the learned start, ML), written to the field buffer W.
 // One thread per cell, constants of the simulation typed and with the EoS
-// fixed at compile time.
+// fixed at compile time.  The pass waits mostly on its global loads: the
+// float32 Peng-Robinson pass is bounded to six blocks of 256 threads per SM
+// (40 registers, a small spill), which ran 1 % faster per 384^3 step than
+// four blocks at 64 registers; five lost half of that, seven and eight lost it all.
+// The other forms keep the blocks per SM their register use gives them.
+template <typename R, int EK, bool ML> constexpr int zmacro_min_blocks()
+{
+    return sizeof(R) == 4 && !ML && EK == EOS_PR ? 6 : (ML || (sizeof(R) == 8 && EK == EOS_PR) ? 3 : 4);
+}
 template <typename R, int EK, bool ML>
-__global__ void __launch_bounds__(kBlockCells) k_zmacro(const SimDev* __restrict__ sims,
+__global__ void __launch_bounds__(kBlockCells, zmacro_min_blocks<R, EK, ML>()) k_zmacro(const SimDev* __restrict__ sims,
                                                         const BlockEntry* __restrict__ table, const R* __restrict__ M,
                                                         R* __restrict__ W, long long Ntot, unsigned long long* diag)
 {
