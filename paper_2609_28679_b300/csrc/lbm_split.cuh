@@ -45,10 +45,12 @@ __device__ __forceinline__ void load_sim(SimDev& dst, const SimDev* sims, int si
 template <typename C>
 __device__ __forceinline__ void cell_xyz(const C& s, long long k, int& x, int& y, int& z)
 {
-    x = (int)(k % s.nx);
-    long long r = k / s.nx;
-    y = (int)(r % s.ny);
-    z = (int)(r / s.ny);
+    // k < N, and lbm_create keeps Q N below 2^32 per simulation: 32-bit division
+    const unsigned ku = (unsigned)k, nx = (unsigned)s.nx, ny = (unsigned)s.ny;
+    const unsigned r = ku / nx;
+    x = (int)(ku - r * nx);
+    z = (int)(r / ny);
+    y = (int)(r - (unsigned)z * ny);
 }
 
 template <typename C>
@@ -137,6 +139,23 @@ __device__ __forceinline__ void pull_cell(const SimDev& s, const S* __restrict__
     constexpr int Q = Lat<D>::Q;
     const S* fb = pop + s.pop_off;
     const S* gb = fb + (long long)Q * s.N;
+    if (x >= 1 && x < s.nx - 1 && y >= 1 && y < s.ny - 1 && (D == 2 || (z >= 1 && z < s.nz - 1))) {
+        // every source cell x - c_i lies inside the lattice: the same elements at
+        // fixed offsets c_x + c_y nx + c_z nx ny from the cell
+        const long long k = (long long)x + (long long)s.nx * ((long long)y + (long long)s.ny * (long long)z);
+        const long long NX = s.nx, NP = (long long)s.nx * s.ny;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const long long idx = (long long)i * s.N + k - (cc(i, 0) + cc(i, 1) * NX + (D == 3 ? cc(i, 2) * NP : 0));
+            f[i] = Codec<S, R>::ld(fb + idx);
+            g[i] = Codec<S, R>::ld(gb + idx);
+            if (Codec<S, R>::offset) {
+                f[i] += (R)s.fref[i];
+                g[i] += (R)s.gref[i];
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         int j;
