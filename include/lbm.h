@@ -229,8 +229,10 @@ int lbm_set_face(lbm_handle h, int face, int kind, const double *u, double T, do
  * float64, N the total cells of the handle (simulations concatenated, u per
  * simulation as dim planes of its cells); on_device 0: host memory (pinned
  * memory is copied by DMA, pageable memory through the driver's staging),
- * 1: device memory.  The caller keeps ownership; the call synchronises, so
- * the buffers may be reused on return.  For 16-bit storage the per-direction
+ * 1: device memory.  From host memory, handles of 2 M cells or more copy in
+ * up to eight runs of cells on a copy stream of their own, each run set up
+ * on h's stream while the next one crosses the link.  The caller keeps
+ * ownership; the call synchronises, so the buffers may be reused on return.  For 16-bit storage the per-direction
  * offsets f^ref, g^ref are the rest equilibria at the mean rho and mean T of
  * each simulation.  Errors: LBM_E_INVALID for a NULL field or for rho <= 0,
  * T <= 0 or NaN in any cell (checked on the device for 32- and 64-bit
@@ -248,7 +250,9 @@ int lbm_step(lbm_handle h, int n);
 
 /* Macroscopic fields of the current state: rho (Eq. def_h), the physical
  * velocity u = (sum c f + F/2)/rho (Eq. def_u) and T from the EoS.  Any of the
- * three pointers may be NULL. */
+ * three pointers may be NULL.  Layout and on_device as lbm_init; to host
+ * memory, handles of 2 M cells or more copy run by run as the runs are
+ * evaluated.  Synchronises. */
 int lbm_moments(lbm_handle h, double *rho, double *u, double *T, int on_device);
 
 /* lbm_moments into float32 fields (same layout; for float32 and 16-bit

@@ -26,15 +26,19 @@ namespace {
 thread_local std::string g_create_error;
 
 struct Ops {
-    int (*init)(lbm_ctx*, const void*, const void*, const void*, int single);  // single: float32 fields
+    // blocks [b0, b0 + nb) of the block table; nb < 0: all of them
+    int (*init)(lbm_ctx*, const void*, const void*, const void*, int single, int b0, int nb);  // single: float32 fields
     int (*step)(lbm_ctx*, int);
     int (*macro)(lbm_ctx*);
-    int (*export_moments)(lbm_ctx*, void*, void*, void*, int single);
+    int (*export_moments)(lbm_ctx*, void*, void*, void*, int single, int b0, int nb);
     int (*export_pops)(lbm_ctx*, double*, double*);
     int (*invariants)(lbm_ctx*, double*);
     int (*fused_ok)(lbm_ctx*, int, int, int);
     int (*prepare)(lbm_ctx*);  // carried moments of the current state (fused and z-march variants)
     int (*state_fields)(lbm_ctx*);  // rho, u, T of the current state into W (for the export)
+    // the same for blocks [b0, b0 + nb) alone where the variant allows it (the z-march's first
+    // pass); returns LBM_E_UNSUPPORTED, having done nothing, where it does not
+    int (*state_part)(lbm_ctx*, int b0, int nb);
 };
 
 }  // namespace
@@ -69,6 +73,8 @@ struct lbm_ctx {
     float* d_mlp = nullptr;            // learned temperature parameters (lbm_mlp_load)
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};  // per starting buffer parity
     std::vector<cudaEvent_t> pass_ev;  // lbm_step_timed: 4 events per step (start, after passes 1, 2, 3)
+    cudaStream_t xfer = nullptr;       // host-link copies of lbm_init / lbm_moments, beside the kernels
+    std::vector<cudaEvent_t> xfer_ev;
     int pass_step = -1;                // step of lbm_step_timed being recorded (-1: none)
     std::string err;
     Ops ops{};
@@ -238,15 +244,17 @@ template <int D, typename R, typename S> struct Impl {
 
     static int nblocks(lbm_ctx* h) { return (int)h->table.size(); }
 
-    static int init(lbm_ctx* h, const void* rho, const void* u, const void* T, int single)
+    static int init(lbm_ctx* h, const void* rho, const void* u, const void* T, int single, int b0, int nb)
     {
+        if (nb < 0) { b0 = 0; nb = nblocks(h); }
+        if (nb == 0) return LBM_OK;
         if (single)
-            k_init<D, R, S, float><<<nblocks(h), kBlockCells, 0, h->stream>>>(
-                h->d_sims, h->d_table, (const float*)rho, (const float*)u, (const float*)T, (S*)h->pop[0], (R*)h->W,
-                h->Ntot, h->d_diag + kDiagInitBad);
+            k_init<D, R, S, float><<<nb, kBlockCells, 0, h->stream>>>(
+                h->d_sims, h->d_table + b0, (const float*)rho, (const float*)u, (const float*)T, (S*)h->pop[0],
+                (R*)h->W, h->Ntot, h->d_diag + kDiagInitBad);
         else
-            k_init<D, R, S, double><<<nblocks(h), kBlockCells, 0, h->stream>>>(
-                h->d_sims, h->d_table, (const double*)rho, (const double*)u, (const double*)T, (S*)h->pop[0],
+            k_init<D, R, S, double><<<nb, kBlockCells, 0, h->stream>>>(
+                h->d_sims, h->d_table + b0, (const double*)rho, (const double*)u, (const double*)T, (S*)h->pop[0],
                 (R*)h->W, h->Ntot, h->d_diag + kDiagInitBad);
         LBM_LAUNCH_CHECK(h, "k_init");
         h->cur = 0;
@@ -352,6 +360,20 @@ template <int D, typename R, typename S> struct Impl {
         return macro(h);
     }
 
+    static int state_part(lbm_ctx* h, int b0, int nb)
+    {
+        if (!(D == 3 && h->moments_valid && !has_nee(h) &&
+              (h->variant == LBM_KERNEL_ZMARCH || h->variant == LBM_KERNEL_ZGATHER)) ||
+            (uses_mlp(h) && h->storage != LBM_F32))
+            return LBM_E_UNSUPPORTED;
+        if (!faces_ready(h)) return fail(h, LBM_E_STATE, "lbm_set_walls / lbm_set_face has not set every face");
+        if (nb == 0) return LBM_OK;
+        cudaError_t e = zmacro_dispatch(h->storage, h->sims[0].eos, uses_mlp(h), h->d_sims, h->d_table + b0, nb,
+                                        mbuf(h, h->cur), h->W, h->Ntot, nullptr, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "z-march macroscopic pass");
+        return LBM_OK;
+    }
+
     // D3Q27: macroscopic pass from the carried moments, then the z-marching collide-stream pass
     static int zmarch_step(lbm_ctx* h)
     {
@@ -413,14 +435,16 @@ template <int D, typename R, typename S> struct Impl {
         return LBM_OK;
     }
 
-    static int export_moments(lbm_ctx* h, void* rho, void* u, void* T, int single)
+    static int export_moments(lbm_ctx* h, void* rho, void* u, void* T, int single, int b0, int nb)
     {
+        if (nb < 0) { b0 = 0; nb = nblocks(h); }
+        if (nb == 0) return LBM_OK;
         if (single)
-            k_export_moments<D, R, float><<<nblocks(h), kBlockCells, 0, h->stream>>>(
-                h->d_sims, h->d_table, (const R*)h->W, h->Ntot, (float*)rho, (float*)u, (float*)T);
+            k_export_moments<D, R, float><<<nb, kBlockCells, 0, h->stream>>>(
+                h->d_sims, h->d_table + b0, (const R*)h->W, h->Ntot, (float*)rho, (float*)u, (float*)T);
         else
-            k_export_moments<D, R, double><<<nblocks(h), kBlockCells, 0, h->stream>>>(
-                h->d_sims, h->d_table, (const R*)h->W, h->Ntot, (double*)rho, (double*)u, (double*)T);
+            k_export_moments<D, R, double><<<nb, kBlockCells, 0, h->stream>>>(
+                h->d_sims, h->d_table + b0, (const R*)h->W, h->Ntot, (double*)rho, (double*)u, (double*)T);
         LBM_LAUNCH_CHECK(h, "export moments");
         return LBM_OK;
     }
@@ -471,7 +495,8 @@ template <int D, typename R, typename S> struct Impl {
 
     static Ops ops()
     {
-        return Ops{init, step, macro, export_moments, export_pops, invariants, fused_ok, fused_prepare, state_fields};
+        return Ops{init,     step,     macro,         export_moments, export_pops,
+                   invariants, fused_ok, fused_prepare, state_fields,   state_part};
     }
 };
 
@@ -745,6 +770,10 @@ void free_all(lbm_ctx* h)
     drop_graph(h);
     for (cudaEvent_t ev : h->pass_ev) cudaEventDestroy(ev);
     h->pass_ev.clear();
+    for (cudaEvent_t ev : h->xfer_ev) cudaEventDestroy(ev);
+    h->xfer_ev.clear();
+    if (h->xfer) cudaStreamDestroy(h->xfer);
+    h->xfer = nullptr;
     void* ptrs[] = {h->d_sims, h->d_table, h->d_sim_block_start, h->d_tiles, h->pop[0], h->pop[1],
                     h->W, h->M, h->d_diag, h->d_partials, h->d_mlp, h->d_face_table};
     for (void* p : ptrs) lbm_glue_free(p);
@@ -1039,6 +1068,69 @@ int lbm_set_face(lbm_handle h, int face, int kind, const double* u, double T, do
 }
 
 extern "C++" {
+// Host-field transfers in parts: the block table is cut into up to kXferParts
+// runs of blocks, part c's cells cross the host link on h->xfer while the
+// kernels work on part c - 1 (or part c's copy waits for its kernels, on the
+// way out).  Lattices under 2 M cells go in one part.
+constexpr int kXferParts = 8;
+
+int xfer_parts(const lbm_ctx* h)
+{
+    const long long p = h->Ntot >> 20;
+    const int nb = (int)h->table.size();
+    int n = p < 2 ? 1 : (p > kXferParts ? kXferParts : (int)p);
+    return n > nb ? (nb > 0 ? nb : 1) : n;
+}
+
+// the copy stream and n + 1 events (created once per handle)
+int xfer_setup(lbm_ctx* h, int n)
+{
+    if (!h->xfer) LBM_CUDA_CHECK(h, cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking));
+    while ((int)h->xfer_ev.size() < n + 1) {
+        cudaEvent_t ev = nullptr;
+        LBM_CUDA_CHECK(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        h->xfer_ev.push_back(ev);
+    }
+    return LBM_OK;
+}
+
+// blocks and cells of part c of n: blocks [b0, b1), global cells [lo, hi)
+void xfer_part(const lbm_ctx* h, int c, int n, int& b0, int& b1, long long& lo, long long& hi)
+{
+    const long long nb = (long long)h->table.size();
+    b0 = (int)(nb * c / n);
+    b1 = (int)(nb * (c + 1) / n);
+    lo = hi = 0;
+    if (b1 <= b0) return;
+    const BlockEntry& f = h->table[b0];
+    const BlockEntry& l = h->table[b1 - 1];
+    const SimDev& sl = h->sims[l.sim];
+    lo = h->sims[f.sim].cell_off + f.start;
+    hi = sl.cell_off + std::min<long long>((long long)l.start + kBlockCells, sl.N);
+}
+
+// rho and T of the global cells [lo, hi) (offset lo in both arrays) and u (per
+// simulation, component-major: D cell_off + a N + k), any of them null to skip
+template <typename H>
+cudaError_t xfer_cells(const lbm_ctx* h, H* dr, H* du, H* dT, const H* sr, const H* su, const H* sT, long long lo,
+                       long long hi, cudaMemcpyKind kind, cudaStream_t st)
+{
+    const size_t n = (size_t)(hi - lo) * sizeof(H);
+    cudaError_t e = cudaSuccess;
+    if (n == 0) return e;
+    if (dr && sr) e = cudaMemcpyAsync(dr + lo, sr + lo, n, kind, st);
+    if (e == cudaSuccess && dT && sT) e = cudaMemcpyAsync(dT + lo, sT + lo, n, kind, st);
+    if (e != cudaSuccess || !du || !su) return e;
+    for (const SimDev& d : h->sims) {
+        const long long a0 = std::max<long long>(lo, d.cell_off), a1 = std::min<long long>(hi, d.cell_off + d.N);
+        for (int a = 0; a < h->dim && a0 < a1 && e == cudaSuccess; ++a) {
+            const long long o = (long long)h->dim * d.cell_off + (long long)a * d.N + (a0 - d.cell_off);
+            e = cudaMemcpyAsync(du + o, su + o, (size_t)(a1 - a0) * sizeof(H), kind, st);
+        }
+    }
+    return e;
+}
+
 template <typename H> int init_impl(lbm_handle h, const H* rho, const H* u, const H* T, int on_device)
 {
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
@@ -1078,31 +1170,47 @@ template <typename H> int init_impl(lbm_handle h, const H* rho, const H* u, cons
         if (rc) return rc;
     }
     // Host inputs go straight to a device staging buffer (a DMA when the
-    // caller's memory is pinned); k_init counts the cells with rho <= 0 or
-    // T <= 0 (or NaN) into diagnostic slot kDiagInitBad, read back below.
+    // caller's memory is pinned), in parts: k_init of part c runs while part
+    // c + 1 crosses the link.  k_init counts the cells with rho <= 0 or T <= 0
+    // (or NaN) into diagnostic slot kDiagInitBad, read back below.
+    const int single = sizeof(H) == sizeof(float);
     const H *dr = rho, *du = u, *dT = T;
     void* tmp = nullptr;
+    int parts = 1;
     if (!on_device) {
+        parts = xfer_parts(h);
+        int rc = xfer_setup(h, parts);
+        if (rc) return rc;
         tmp = dev_alloc(h, 2 * nb_s + nb_v);
         if (!tmp) return fail(h, LBM_E_NOMEM, "staging allocation failed");
         H* t = (H*)tmp;
-        cudaError_t e = cudaMemcpyAsync(t, rho, nb_s, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(t + N, T, nb_s, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(t + 2 * N, u, nb_v, cudaMemcpyHostToDevice, h->stream);
-        if (e != cudaSuccess) {
-            cudaStreamSynchronize(h->stream);
-            lbm_glue_free(tmp);
-            return cuda_fail(h, e, "lbm_init upload");
-        }
         dr = t; dT = t + N; du = t + 2 * N;
     }
     unsigned long long bad = 0;
     cudaError_t e = cudaMemsetAsync(h->d_diag, 0, kDiagSlots * sizeof(unsigned long long), h->stream);
-    int rc = e == cudaSuccess ? h->ops.init(h, dr, du, dT, sizeof(H) == sizeof(float)) : cuda_fail(h, e, "diag reset");
+    int rc = e == cudaSuccess ? LBM_OK : cuda_fail(h, e, "diag reset");
+    if (rc == LBM_OK && on_device) {
+        rc = h->ops.init(h, dr, du, dT, single, 0, -1);
+    } else if (rc == LBM_OK) {
+        // the copies start after the work queued so far (the staging buffer may reuse its memory)
+        e = cudaEventRecord(h->xfer_ev[parts], h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->xfer, h->xfer_ev[parts], 0);
+        for (int c = 0; c < parts && e == cudaSuccess && rc == LBM_OK; ++c) {
+            int b0, b1;
+            long long lo, hi;
+            xfer_part(h, c, parts, b0, b1, lo, hi);
+            e = xfer_cells<H>(h, (H*)dr, (H*)du, (H*)dT, rho, u, T, lo, hi, cudaMemcpyHostToDevice, h->xfer);
+            if (e == cudaSuccess) e = cudaEventRecord(h->xfer_ev[c], h->xfer);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->xfer_ev[c], 0);
+            if (e == cudaSuccess) rc = h->ops.init(h, dr, du, dT, single, b0, b1 - b0);
+        }
+        if (e != cudaSuccess && rc == LBM_OK) rc = cuda_fail(h, e, "lbm_init upload");
+    }
     if (rc == LBM_OK) {
         e = cudaMemcpyAsync(&bad, h->d_diag + kDiagInitBad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "lbm_init check");
     }
+    if (h->xfer) cudaStreamSynchronize(h->xfer);  // after an error copies may still be in flight
     cudaError_t se = cudaStreamSynchronize(h->stream);
     lbm_glue_free(tmp);
     if (rc) return rc;
@@ -1228,28 +1336,44 @@ template <typename H> int moments_impl(lbm_handle h, H* rho, H* u, H* T, int on_
 {
     if (!h) return fail(nullptr, LBM_E_INVALID, "handle is NULL");
     if (!h->initialized) return fail(h, LBM_E_STATE, "lbm_init has not been called");
-    int rc = h->ops.state_fields(h);
-    if (rc) return rc;
     const long long N = h->Ntot;
+    const int single = sizeof(H) == sizeof(float);
     if (on_device) {
-        rc = h->ops.export_moments(h, rho, u, T, sizeof(H) == sizeof(float));
+        int rc = h->ops.state_fields(h);
+        if (rc == LBM_OK) rc = h->ops.export_moments(h, rho, u, T, single, 0, -1);
         if (rc) return rc;
         LBM_CUDA_CHECK(h, cudaStreamSynchronize(h->stream));
         return LBM_OK;
     }
+    // to the host in parts: part c's fields cross the link while the kernels
+    // work on part c + 1 (the z-march's first pass too, where it runs by parts)
+    const int parts = xfer_parts(h);
+    int rc = xfer_setup(h, parts);
+    if (rc) return rc;
+    const bool by_parts = parts > 1 && h->ops.state_part(h, 0, 0) == LBM_OK;
+    if (!by_parts) {
+        rc = h->ops.state_fields(h);
+        if (rc) return rc;
+    }
     const size_t nb_s = (size_t)N * sizeof(H), nb_v = (size_t)N * h->dim * sizeof(H);
     H* t = (H*)dev_alloc(h, 2 * nb_s + nb_v);
     if (!t) return fail(h, LBM_E_NOMEM, "staging allocation failed");
-    rc = h->ops.export_moments(h, t, t + 2 * N, t + N, sizeof(H) == sizeof(float));
-    if (rc == LBM_OK) {
-        cudaError_t e = cudaSuccess;
-        if (rho && e == cudaSuccess) e = cudaMemcpyAsync(rho, t, nb_s, cudaMemcpyDeviceToHost, h->stream);
-        if (T && e == cudaSuccess) e = cudaMemcpyAsync(T, t + N, nb_s, cudaMemcpyDeviceToHost, h->stream);
-        if (u && e == cudaSuccess) e = cudaMemcpyAsync(u, t + 2 * N, nb_v, cudaMemcpyDeviceToHost, h->stream);
-        cudaError_t se = cudaStreamSynchronize(h->stream);
-        if (e == cudaSuccess) e = se;
-        if (e != cudaSuccess) rc = cuda_fail(h, e, "lbm_moments copy");
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < parts && rc == LBM_OK && e == cudaSuccess; ++c) {
+        int b0, b1;
+        long long lo, hi;
+        xfer_part(h, c, parts, b0, b1, lo, hi);
+        if (by_parts) rc = h->ops.state_part(h, b0, b1 - b0);
+        if (rc == LBM_OK) rc = h->ops.export_moments(h, t, t + 2 * N, t + N, single, b0, b1 - b0);
+        if (rc == LBM_OK) e = cudaEventRecord(h->xfer_ev[c], h->stream);
+        if (rc == LBM_OK && e == cudaSuccess) e = cudaStreamWaitEvent(h->xfer, h->xfer_ev[c], 0);
+        if (rc == LBM_OK && e == cudaSuccess)
+            e = xfer_cells<H>(h, rho, u, T, t, t + 2 * N, t + N, lo, hi, cudaMemcpyDeviceToHost, h->xfer);
     }
+    const cudaError_t sx = cudaStreamSynchronize(h->xfer);
+    const cudaError_t ss = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = sx != cudaSuccess ? sx : ss;
+    if (rc == LBM_OK && e != cudaSuccess) rc = cuda_fail(h, e, "lbm_moments copy");
     lbm_glue_free(t);
     return rc;
 }

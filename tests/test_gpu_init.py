@@ -133,3 +133,70 @@ def test_float32_io_rejects_float64_arrays_and_bad_fields():
     with pytest.raises(lbm.LbmError, match="must be > 0"):
         lbm.lbm_init_f32(sim.h, r32, u32, T32, 0)
     sim.close()
+
+
+def test_host_transfers_in_parts_match_device_transfers_3d():
+    # 160^3 (4.1 M cells): lbm_init_f32 from pinned host memory and lbm_moments_f32 to it
+    # go in three parts (copies beside k_init, and beside the gathering z-march's first
+    # pass and the export); the state and the moments equal those from and to the device
+    import torch
+
+    case = wl.pr_droplet(160, storage="f32", radius=20.0)
+    rho, u, T = case.fields()
+    host = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).ravel()).pin_memory() for a in (rho, u, T)]
+    dev = [a.cuda() for a in host]
+    n = case.ncell
+    out = []
+    for on_dev in (0, 1):
+        sim = lbm.Simulation(case)
+        assert sim.kernel()[0] == lbm.LBM_KERNEL_ZGATHER
+        lbm.lbm_init_f32(sim.h, *(dev if on_dev else host), on_dev)
+        sim.step(2)
+        if on_dev:
+            res = [torch.zeros(m, dtype=torch.float32, device="cuda") for m in (n, 3 * n, n)]
+            lbm.lbm_moments_f32(sim.h, *res, 1)
+            res = [r.cpu().numpy() for r in res]
+        else:
+            res = [torch.zeros(m, dtype=torch.float32).pin_memory() for m in (n, 3 * n, n)]
+            lbm.lbm_moments_f32(sim.h, *res, 0)
+            res = [r.numpy().copy() for r in res]
+        sim.close()
+        out.append(res)
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    assert np.all(out[0][0] > 0) and np.all(out[0][2] > 0)
+
+
+def test_host_transfers_in_parts_match_device_transfers_batch():
+    # a 2-D batch of uneven simulations, 2.3 M cells: two parts, the boundary inside
+    # the first simulation; float64 pageable host fields against device fields (split
+    # kernels: they sum in a fixed order, so equal inputs give equal bits)
+    import torch
+
+    cases = [wl.vdw_spinodal(n=1500, ny=900, storage="f32", seed=11), wl.vdw_spinodal(n=700, ny=500, storage="f32", seed=12),
+             wl.vdw_spinodal(n=1000, ny=600, storage="f32", seed=13)]
+    fs = [c.fields() for c in cases]
+    rho = np.concatenate([f[0] for f in fs]).astype(np.float64)
+    u = np.concatenate([f[1].ravel() for f in fs]).astype(np.float64)
+    T = np.concatenate([f[2] for f in fs]).astype(np.float64)
+    out = []
+    for on_dev in (0, 1):
+        sim = lbm.Simulation(cases, variant=lbm.LBM_KERNEL_SPLIT)
+        if on_dev:
+            lbm.lbm_init(sim.h, *[torch.from_numpy(a).cuda() for a in (rho, u, T)], 1)
+        else:
+            lbm.lbm_init(sim.h, rho, u, T, 0)
+        sim.step(2)
+        f, g = sim.populations()
+        if on_dev:
+            res = [torch.zeros(m, dtype=torch.float64, device="cuda") for m in (rho.size, u.size, T.size)]
+            lbm.lbm_moments(sim.h, *res, 1)
+            res = [r.cpu().numpy() for r in res]
+        else:
+            res = list(sim.moments())
+        sim.close()
+        out.append((f, g, res))
+    (f0, g0, m0), (f1, g1, m1) = out
+    assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    for a, b in zip(m0, m1):
+        assert np.array_equal(a, b)
