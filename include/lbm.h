@@ -231,7 +231,8 @@ int lbm_set_face(lbm_handle h, int face, int kind, const double *u, double T, do
  * memory is copied by DMA, pageable memory through the driver's staging),
  * 1: device memory.  From host memory, handles of 2 M cells or more copy in
  * up to eight runs of cells on a copy stream of their own, each run set up
- * on h's stream while the next one crosses the link.  The caller keeps
+ * on h's stream while the next one crosses the link (with, on the kernels
+ * that carry moments between steps, those of the new state).  The caller keeps
  * ownership; the call synchronises, so the buffers may be reused on return.  For 16-bit storage the per-direction
  * offsets f^ref, g^ref are the rest equilibria at the mean rho and mean T of
  * each simulation.  Errors: LBM_E_INVALID for a NULL field or for rho <= 0,

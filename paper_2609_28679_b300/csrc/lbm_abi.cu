@@ -35,6 +35,7 @@ struct Ops {
     int (*invariants)(lbm_ctx*, double*);
     int (*fused_ok)(lbm_ctx*, int, int, int);
     int (*prepare)(lbm_ctx*);  // carried moments of the current state (fused and z-march variants)
+    int (*prepare_part)(lbm_ctx*, int b0, int nb);  // the same for blocks [b0, b0 + nb), M left marked as it was
     int (*state_fields)(lbm_ctx*);  // rho, u, T of the current state into W (for the export)
     // the same for blocks [b0, b0 + nb) alone where the variant allows it (the z-march's first
     // pass); returns LBM_E_UNSUPPORTED, having done nothing, where it does not
@@ -293,6 +294,15 @@ template <int D, typename R, typename S> struct Impl {
         return LBM_OK;
     }
 
+    static int prepare_part(lbm_ctx* h, int b0, int nb)
+    {
+        if (nb <= 0) return LBM_OK;
+        fused_moments_launch<D, R, S>(h->d_sims, h->d_table + b0, nb, (const S*)h->pop[h->cur], (const R*)h->W,
+                                      mbuf(h, h->cur), h->Ntot, h->stream);
+        LBM_LAUNCH_CHECK(h, "fused moments");
+        return LBM_OK;
+    }
+
     static int fused_step(lbm_ctx* h)
     {
         if (!h->moments_valid) {
@@ -495,8 +505,8 @@ template <int D, typename R, typename S> struct Impl {
 
     static Ops ops()
     {
-        return Ops{init,     step,     macro,         export_moments, export_pops,
-                   invariants, fused_ok, fused_prepare, state_fields,   state_part};
+        return Ops{init,     step,     macro,         export_moments, export_pops, invariants,
+                   fused_ok, fused_prepare, prepare_part, state_fields,   state_part};
     }
 };
 
@@ -1109,6 +1119,25 @@ void xfer_part(const lbm_ctx* h, int c, int n, int& b0, int& b1, long long& lo, 
     hi = sl.cell_off + std::min<long long>((long long)l.start + kBlockCells, sl.N);
 }
 
+// The pulls of run c (k_fused_prep) read only cells initialised once k_init
+// has run on runs 0 .. c + 1: the run lies in one simulation, holds none of
+// its first wrap layer (plane in 3-D, row in 2-D: those pull from the last
+// one), and run c + 1 covers the pulls' forward reach (a layer, a row and a
+// cell); everything before run c is initialised first.
+bool run_pulls_ready(const lbm_ctx* h, int c, int n)
+{
+    if (c + 1 >= n) return false;
+    int b0, b1, n0, n1;
+    long long lo, hi, nlo, nhi;
+    xfer_part(h, c, n, b0, b1, lo, hi);
+    xfer_part(h, c + 1, n, n0, n1, nlo, nhi);
+    if (b1 <= b0 || h->table[b0].sim != h->table[b1 - 1].sim) return false;
+    const SimDev& d = h->sims[h->table[b0].sim];
+    const long long layer = h->dim == 3 ? (long long)d.nx * d.ny : (long long)d.nx;
+    const long long reach = layer + d.nx + 1;
+    return lo - d.cell_off >= layer && hi + reach <= nhi;
+}
+
 // rho and T of the global cells [lo, hi) (offset lo in both arrays) and u (per
 // simulation, component-major: D cell_off + a N + k), any of them null to skip
 template <typename H>
@@ -1195,6 +1224,18 @@ template <typename H> int init_impl(lbm_handle h, const H* rho, const H* u, cons
         // the copies start after the work queued so far (the staging buffer may reuse its memory)
         e = cudaEventRecord(h->xfer_ev[parts], h->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->xfer, h->xfer_ev[parts], 0);
+        // the variants that carry moments between steps get them here, run by run
+        // where the pulls allow (beside the upload), the rest after the last run
+        const bool carried = parts > 1 && (h->variant == LBM_KERNEL_FUSED || h->variant == LBM_KERNEL_YMARCH ||
+                                           h->variant == LBM_KERNEL_ZMARCH || h->variant == LBM_KERNEL_ZGATHER);
+        std::vector<char> prepared(parts, 0);
+        auto prepare_run = [&](int c) {
+            int b0, b1;
+            long long lo, hi;
+            xfer_part(h, c, parts, b0, b1, lo, hi);
+            prepared[c] = 1;
+            return h->ops.prepare_part(h, b0, b1 - b0);
+        };
         for (int c = 0; c < parts && e == cudaSuccess && rc == LBM_OK; ++c) {
             int b0, b1;
             long long lo, hi;
@@ -1203,8 +1244,13 @@ template <typename H> int init_impl(lbm_handle h, const H* rho, const H* u, cons
             if (e == cudaSuccess) e = cudaEventRecord(h->xfer_ev[c], h->xfer);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->xfer_ev[c], 0);
             if (e == cudaSuccess) rc = h->ops.init(h, dr, du, dT, single, b0, b1 - b0);
+            if (e == cudaSuccess && rc == LBM_OK && carried && c >= 1 && run_pulls_ready(h, c - 1, parts))
+                rc = prepare_run(c - 1);
         }
         if (e != cudaSuccess && rc == LBM_OK) rc = cuda_fail(h, e, "lbm_init upload");
+        for (int c = 0; c < parts && carried && rc == LBM_OK; ++c)
+            if (!prepared[c]) rc = prepare_run(c);
+        if (carried && rc == LBM_OK) h->moments_valid = true;
     }
     if (rc == LBM_OK) {
         e = cudaMemcpyAsync(&bad, h->d_diag + kDiagInitBad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream);

@@ -167,10 +167,12 @@ def test_host_transfers_in_parts_match_device_transfers_3d():
     assert np.all(out[0][0] > 0) and np.all(out[0][2] > 0)
 
 
-def test_host_transfers_in_parts_match_device_transfers_batch():
+@pytest.mark.parametrize("variant", [lbm.LBM_KERNEL_SPLIT, lbm.LBM_KERNEL_YMARCH])
+def test_host_transfers_in_parts_match_device_transfers_batch(variant):
     # a 2-D batch of uneven simulations, 2.3 M cells: two parts, the boundary inside
-    # the first simulation; float64 pageable host fields against device fields (split
-    # kernels: they sum in a fixed order, so equal inputs give equal bits)
+    # the first simulation; float64 pageable host fields against device fields (kernels
+    # that sum in a fixed order, so equal inputs give equal bits; the row march carries
+    # moments, which the host upload prepares run by run and the device one at the first step)
     import torch
 
     cases = [wl.vdw_spinodal(n=1500, ny=900, storage="f32", seed=11), wl.vdw_spinodal(n=700, ny=500, storage="f32", seed=12),
@@ -181,7 +183,7 @@ def test_host_transfers_in_parts_match_device_transfers_batch():
     T = np.concatenate([f[2] for f in fs]).astype(np.float64)
     out = []
     for on_dev in (0, 1):
-        sim = lbm.Simulation(cases, variant=lbm.LBM_KERNEL_SPLIT)
+        sim = lbm.Simulation(cases, variant=variant)
         if on_dev:
             lbm.lbm_init(sim.h, *[torch.from_numpy(a).cuda() for a in (rho, u, T)], 1)
         else:
