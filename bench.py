@@ -63,7 +63,8 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback (6.4 TB/s, no MEASURED_PEAKS.json)"
 
 
-# sources of each timed kernel: the ncu traffic figure counts only while they are unchanged
+# sources of each timed kernel: the ncu traffic figure counts only while they and the
+# compile flags (build.py) are unchanged
 _KERNEL_SOURCES = {
     "k_zgather": ("lbm_device.cuh", "lbm_async.cuh", "lbm_zgather.cuh"),
     "k_zmacro": ("lbm_device.cuh", "lbm_split.cuh", "lbm_zmarch.cuh"),
@@ -74,7 +75,7 @@ _KERNEL_SOURCES = {
 
 def _kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for name in _KERNEL_SOURCES.get(kernel, ("lbm_device.cuh",)):
+    for name in _KERNEL_SOURCES.get(kernel, ("lbm_device.cuh",)) + ("../build.py",):
         with open(os.path.join(ROOT, "paper_2609_28679_b300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

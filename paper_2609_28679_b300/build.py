@@ -50,7 +50,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     for cu in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         obj = os.path.join(BUILD, os.path.basename(cu) + ".o")
         if force or _newer(obj, [cu] + headers):
-            cmd = ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-cudart", "shared",
+            cmd = ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-prec-div=false", "-prec-sqrt=false",
+                   "-Xcompiler", "-fPIC", "-cudart", "shared",
                    "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-c", cu, "-o", obj]
             if ptxas_verbose:
                 cmd.insert(1, "-Xptxas=-v")
